@@ -1,0 +1,596 @@
+"""FP64 CPU oracle of the per-time-step PISO update and its discrete adjoint.
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, plain reference that the
+CUDA path is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import it; the product path never does.
+
+It restates, in the paper's order and notation, the collocated first-order
+finite-volume PISO scheme of arXiv:2505.16992:
+
+* Sec. 2.1 and App. A.1 (Eqs. advection, advectionMat, pressureRHS, pressure,
+  correction): one implicit-Euler predictor solve C u* = u^n/dt - grad p + S,
+  then two correctors h = A^-1(u^n/dt + S - H u), div(A^-1 grad p) = div h,
+  u = h - A^-1 grad p.
+* App. A.2 "Grid Transformations": metrics T_ji = d xi^j / d x_i and
+  J = det(dx/dxi) at cell centres; contravariant flux U^j = J T_j . u.
+* App. A.2 Eq. advMatDiscrete (central advection entries 0.5 N_f U_f),
+  Eq. difMatDiscrete (orthogonal diffusion, alpha_jj = J T_j . T_j),
+  Eq. velRHSdiscrete (Dirichlet boundary fluxes on the right-hand side),
+  Eq. pMatDiscrete (pressure matrix from alpha_jj / A),
+  Eqs. pressureRHSdiscrete / pressureRHSdivDiscrete (divergence of h),
+  Eq. velCorrDiscrete (cell-centred central pressure gradient).
+* App. A.3 (boundaries): block connections only change the neighbour lookup;
+  Dirichlet velocity faces carry their own values and imply 0-Neumann pressure;
+  the advective outflow Eq. advOut updates its face values before each step and
+  is rescaled to balance the in- and outflow.
+* Sec. 2.3 and App. A.4 (gradients): linear solves are differentiated by the
+  transposed solve  A^T db = dx,  dA = -db (x) x  on the sparsity pattern; every
+  other operation by its exact transpose.
+
+Readings of points the paper leaves open (the same readings the CUDA path
+implements; each is listed in the design notes):
+
+* R1 every momentum row is taken per unit volume: C_P = 1/dt + (1/J_P)(...),
+  C_F = (1/J_P)(0.5 N_f U_f - nu mean(alpha_jj)), matching the 1/J_P of the
+  velocity right-hand side.
+* R2 face interpolation is the arithmetic mean of the two cells.
+* R3 boundary faces use the adjacent cell's metrics.
+* R4 the predictor right-hand side contains -grad p^n; h does not.
+* R5 at a Dirichlet face the missing pressure neighbour is p_P.
+* R6 the divergence b includes the prescribed boundary flux N_b J_P T_j . u_b.
+* R7 the pressure system is singular (constants); b is projected to zero mean
+  and each solution is returned with zero mean.
+* R10 the outflow update uses the stable factor c/(1+c), c = 2 dt |T_j . u_m|.
+* Non-orthogonal cross terms (alpha_jk, j != k) are not part of this scheme;
+  meshes where they are non-zero are rejected.
+* Block connections join a side to the opposite side of the same axis with the
+  same tangential ordering (no axis permutation).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import krylov
+
+
+# ----------------------------------------------------------------------------
+# mesh: metrics, neighbours, boundary faces
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Options:
+    pred_grad_p: bool = True     # R4
+    n_correctors: int = 2        # App. A.1: two corrector rounds
+    adv_rtol: float = 1e-14
+    p_rtol: float = 1e-14
+    atol: float = 0.0
+    maxit: int = 100000
+    solver: str = "krylov"       # "krylov" | "direct"
+    update_outflow: bool = True  # App. A.3 advective outflow update before the step
+
+
+class Mesh:
+    """Multi-block structured mesh (Sec. 2.2; App. A.5 Domain/Block/Boundary).
+
+    blocks: sequence of (res, vertices); connections: (blk_a, side_a, blk_b, side_b);
+    dirichlet: (blk, side, values (nfaces, ndim)); outflow: (blk, side, u_m, values).
+    """
+
+    def __init__(self, ndim: int, blocks: Sequence, connections: Sequence = (),
+                 dirichlet: Sequence = (), outflow: Sequence = ()):
+        self.ndim = d = ndim
+        self.nsides = 2 * d
+        self.res = [tuple(int(v) for v in (b[0] if isinstance(b, tuple) else b.res)) for b in blocks]
+        verts = [np.asarray(b[1] if isinstance(b, tuple) else b.vertices, dtype=np.float64) for b in blocks]
+        self.offsets = np.cumsum([0] + [r[0] * r[1] * r[2] for r in self.res])
+        self.N = N = int(self.offsets[-1])
+
+        # --- metrics at cell centres (App. A.2): M_ik = d x_i / d xi^k from
+        # differences of opposite face centres, T = M^-1, J = det M.
+        M = np.zeros((N, d, d))
+        for bi, (r, V) in enumerate(zip(self.res, verts)):
+            o = self.offsets[bi]
+            M[o:o + r[0] * r[1] * r[2]] = _block_jacobian(V, d)
+        self.J = np.linalg.det(M)
+        if np.any(self.J <= 0):
+            raise ValueError("mesh has cells with non-positive volume")
+        self.T = np.linalg.inv(M)                     # T[i, j, k] = d xi^j / d x_k at cell i
+        G = np.einsum("njk,nlk->njl", self.T, self.T) * self.J[:, None, None]
+        self.alpha = np.stack([G[:, j, j] for j in range(d)])   # (d, N): alpha_jj
+        off = np.abs(G - np.einsum("nj,jk->njk", self.alpha.T, np.eye(d)))
+        if off.max() > 1e-9 * np.abs(G).max():
+            raise ValueError("non-orthogonal mesh: cross-diffusion terms are not supported")
+
+        # --- neighbours and boundary faces
+        self.nb = -np.ones((self.nsides, N), dtype=np.int64)
+        self.bval = np.zeros((self.nsides, d, N))
+        self.is_bface = np.zeros((self.nsides, N), dtype=bool)
+        self.is_outflow = np.zeros((self.nsides, N), dtype=bool)
+        self.u_m = np.zeros((self.nsides, d, N))
+        assigned = {}
+        for (a, sa, b, sb) in connections:
+            if sb // 2 != sa // 2 or sb % 2 == sa % 2:
+                raise ValueError("connections must join opposite sides of the same axis")
+            for key in ((a, sa), (b, sb)):
+                if key in assigned:
+                    raise ValueError(f"side {key} has two boundaries")
+                assigned[key] = "conn"
+            self._connect(a, sa, b, sb)
+            if (a, sa) != (b, sb):
+                self._connect(b, sb, a, sa)
+        for (blk, s, vals) in dirichlet:
+            if (blk, s) in assigned:
+                raise ValueError(f"side {(blk, s)} has two boundaries")
+            assigned[(blk, s)] = "dir"
+            self._set_faces(blk, s, np.asarray(vals, dtype=np.float64), None)
+        for (blk, s, um, vals) in outflow:
+            if (blk, s) in assigned:
+                raise ValueError(f"side {(blk, s)} has two boundaries")
+            assigned[(blk, s)] = "out"
+            self._set_faces(blk, s, np.asarray(vals, dtype=np.float64), np.asarray(um, dtype=np.float64))
+        # interior neighbours inside each block
+        for bi, r in enumerate(self.res):
+            o = self.offsets[bi]
+            idx, coords = _block_index(r)
+            strides = (1, r[0], r[0] * r[1])
+            for s in range(self.nsides):
+                ax, hi = s // 2, s % 2
+                c = coords[ax]
+                inner = (c < r[ax] - 1) if hi else (c > 0)
+                step = strides[ax] if hi else -strides[ax]
+                self.nb[s, o + idx[inner]] = o + idx[inner] + step
+                if not np.all(inner) and (bi, s) not in assigned:
+                    raise ValueError(f"block {bi} side {s} has no boundary")
+        self.safe_nb = np.where(self.nb >= 0, self.nb, np.arange(N)[None, :])
+        self.inner = self.nb >= 0
+        self.has_outflow = bool(self.is_outflow.any())
+
+    # -- boundary helpers ------------------------------------------------------
+    def side_cells(self, blk: int, s: int) -> np.ndarray:
+        """Global indices of the cells on a block side, in boundary-face order."""
+        r = self.res[blk]
+        o = self.offsets[blk]
+        ax, hi = s // 2, s % 2
+        idx, coords = _block_index(r)
+        m = coords[ax] == (r[ax] - 1 if hi else 0)
+        cells = idx[m]
+        t = [a for a in range(3) if a != ax][: 2 if self.ndim == 3 else 1]
+        # face order: lower tangential axis fastest
+        keys = [coords[a][m] for a in t]
+        if len(keys) == 2:
+            order = np.lexsort((keys[0], keys[1]))
+        else:
+            order = np.argsort(keys[0], kind="stable")
+        return o + cells[order]
+
+    def _connect(self, a, sa, b, sb):
+        ca, cb = self.side_cells(a, sa), self.side_cells(b, sb)
+        if len(ca) != len(cb):
+            raise ValueError("connected sides must have matching resolution")
+        self.nb[sa, ca] = cb
+
+    def _set_faces(self, blk, s, vals, um):
+        cells = self.side_cells(blk, s)
+        if vals.shape != (len(cells), self.ndim):
+            raise ValueError(f"boundary values for block {blk} side {s} must be ({len(cells)}, {self.ndim})")
+        self.is_bface[s, cells] = True
+        self.bval[s, :, cells] = vals
+        if um is not None:
+            self.is_outflow[s, cells] = True
+            self.u_m[s, :, cells] = um[None, :]
+
+    def side_values(self, bval, blk, s):
+        return bval[s, :, self.side_cells(blk, s)]
+
+    # -- elementary per-cell quantities ---------------------------------------
+    def contravariant(self, v: np.ndarray) -> np.ndarray:
+        """U^j = J T_j . v at each cell (App. A.2), shape (d, N)."""
+        return np.einsum("n,njk,kn->jn", self.J, self.T, v)
+
+    def face_flux_b(self, s: int, vb: np.ndarray) -> np.ndarray:
+        """J_P T_j,P . v_b for the boundary face on side s of every cell (R3)."""
+        j = s // 2
+        return self.J * np.einsum("nk,kn->n", self.T[:, j, :], vb)
+
+
+def _block_index(r):
+    nx, ny, nz = r
+    idx = np.arange(nx * ny * nz)
+    x = idx % nx
+    y = (idx // nx) % ny
+    z = idx // (nx * ny)
+    return idx, (x, y, z)
+
+
+def _block_jacobian(V: np.ndarray, d: int) -> np.ndarray:
+    """d x / d xi at cell centres from opposite face-centre differences."""
+    if d == 2:                                    # V[y, x, 2]
+        fxm = 0.5 * (V[:-1, :-1] + V[1:, :-1])
+        fxp = 0.5 * (V[:-1, 1:] + V[1:, 1:])
+        fym = 0.5 * (V[:-1, :-1] + V[:-1, 1:])
+        fyp = 0.5 * (V[1:, :-1] + V[1:, 1:])
+        cols = [fxp - fxm, fyp - fym]             # each (ny, nx, 2)
+        M = np.stack(cols, axis=-1)               # (ny, nx, 2[i], 2[k])
+        return M.reshape(-1, 2, 2)
+    def face(a, b, c, e):
+        return 0.25 * (a + b + c + e)
+    v = V                                         # V[z, y, x, 3]
+    fxm = face(v[:-1, :-1, :-1], v[:-1, 1:, :-1], v[1:, :-1, :-1], v[1:, 1:, :-1])
+    fxp = face(v[:-1, :-1, 1:], v[:-1, 1:, 1:], v[1:, :-1, 1:], v[1:, 1:, 1:])
+    fym = face(v[:-1, :-1, :-1], v[:-1, :-1, 1:], v[1:, :-1, :-1], v[1:, :-1, 1:])
+    fyp = face(v[:-1, 1:, :-1], v[:-1, 1:, 1:], v[1:, 1:, :-1], v[1:, 1:, 1:])
+    fzm = face(v[:-1, :-1, :-1], v[:-1, :-1, 1:], v[:-1, 1:, :-1], v[:-1, 1:, 1:])
+    fzp = face(v[1:, :-1, :-1], v[1:, :-1, 1:], v[1:, 1:, :-1], v[1:, 1:, 1:])
+    M = np.stack([fxp - fxm, fyp - fym, fzp - fzm], axis=-1)
+    return M.reshape(-1, 3, 3)
+
+
+def sign(s: int) -> float:
+    """Face sign N_f: +1 on the + side of an axis, -1 on the - side."""
+    return 1.0 if s % 2 else -1.0
+
+
+def opp(s: int) -> int:
+    return s ^ 1
+
+
+# ----------------------------------------------------------------------------
+# forward operators (App. A.2)
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Matrix:
+    """Stencil matrix: row P = diag[P] x_P + sum_s off[s, P] x_{nb(P,s)}."""
+    diag: np.ndarray
+    off: np.ndarray
+
+
+def assemble_C(mesh: Mesh, u, nu, dt, S, bval):
+    """Advection-diffusion matrix C = C^t + C^adv + C^nu and the velocity
+    right-hand side without the pressure gradient (Eqs. advMatDiscrete,
+    difMatDiscrete, velRHSdiscrete; per-unit-volume rows, R1)."""
+    d, N = mesh.ndim, mesh.N
+    U = mesh.contravariant(u)
+    diag = np.full(N, 1.0 / dt)
+    off = np.zeros((mesh.nsides, N))
+    rhs0 = u / dt
+    if S is not None:
+        rhs0 = rhs0 + S
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        P = np.nonzero(mesh.inner[s])[0]
+        F = mesh.nb[s, P]
+        Uf = 0.5 * (U[j, P] + U[j, F])
+        Df = nu * 0.5 * (mesh.alpha[j, P] + mesh.alpha[j, F])
+        off[s, P] = (0.5 * n * Uf - Df) / mesh.J[P]
+        diag[P] += (0.5 * n * Uf + Df) / mesh.J[P]
+        B = np.nonzero(mesh.is_bface[s])[0]
+        ub = bval[s][:, B]
+        Ub = mesh.face_flux_b(s, bval[s])[B]
+        diag[B] += 2.0 * mesh.alpha[j, B] * nu / mesh.J[B]
+        rhs0[:, B] += ub * ((2.0 * mesh.alpha[j, B] * nu - n * Ub) / mesh.J[B])[None, :]
+    return Matrix(diag, off), rhs0
+
+
+def matvec(mesh: Mesh, M: Matrix, x: np.ndarray) -> np.ndarray:
+    """y = M x for a scalar field (N,) or each component of (d, N)."""
+    y = M.diag * x
+    for s in range(mesh.nsides):
+        y = y + M.off[s] * x[..., mesh.safe_nb[s]]
+    return y
+
+
+def matvec_T(mesh: Mesh, M: Matrix, y: np.ndarray) -> np.ndarray:
+    """x = M^T y, gathered: the entry of row F = nb(P,s) that points back at P
+    is F's coefficient on the opposite side."""
+    x = M.diag * y
+    for s in range(mesh.nsides):
+        F = mesh.safe_nb[s]
+        coef = np.where(mesh.inner[s], M.off[opp(s)][F], 0.0)
+        x = x + coef * y[..., F]
+    return x
+
+
+def offdiag_matvec(mesh: Mesh, M: Matrix, x):
+    return matvec(mesh, Matrix(np.zeros(mesh.N), M.off), x)
+
+
+def to_sparse(mesh: Mesh, M: Matrix) -> sp.csr_matrix:
+    rows = [np.arange(mesh.N)]
+    cols = [np.arange(mesh.N)]
+    vals = [M.diag]
+    for s in range(mesh.nsides):
+        P = np.nonzero(mesh.inner[s])[0]
+        rows.append(P)
+        cols.append(mesh.nb[s, P])
+        vals.append(M.off[s, P])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(mesh.N, mesh.N))
+
+
+def grad_p(mesh: Mesh, p: np.ndarray) -> np.ndarray:
+    """(grad p)_i = sum_j T_ji (p_{j+1} - p_{j-1}) / 2 (Eq. velCorrDiscrete), with
+    p_P standing in for a missing neighbour at Dirichlet faces (R5)."""
+    d = mesh.ndim
+    g = np.zeros((d, mesh.N))
+    for j in range(d):
+        dp = 0.5 * (p[mesh.safe_nb[2 * j + 1]] - p[mesh.safe_nb[2 * j]])
+        g += mesh.T[:, j, :].T * dp[None, :]
+    return g
+
+
+def grad_p_T(mesh: Mesh, g: np.ndarray) -> np.ndarray:
+    """Transpose of grad_p: p_bar = sum over the stencil of T_ji g_i (+-0.5)."""
+    d = mesh.ndim
+    out = np.zeros(mesh.N)
+    for j in range(d):
+        w = 0.5 * np.einsum("nk,kn->n", mesh.T[:, j, :], g)   # per-cell 0.5 T_j . g
+        np.add.at(out, mesh.safe_nb[2 * j + 1], w)
+        np.add.at(out, mesh.safe_nb[2 * j], -w)
+    return out
+
+
+def assemble_P(mesh: Mesh, A: np.ndarray) -> Matrix:
+    """Pressure matrix: P_F = mean(alpha_jj / A) over the face, P_P = -sum P_F
+    (Eq. pMatDiscrete); Dirichlet faces contribute nothing (0-Neumann)."""
+    w = mesh.alpha / A[None, :]
+    off = np.zeros((mesh.nsides, mesh.N))
+    for s in range(mesh.nsides):
+        j = s // 2
+        P = np.nonzero(mesh.inner[s])[0]
+        off[s, P] = 0.5 * (w[j, P] + w[j, mesh.nb[s, P]])
+    return Matrix(-off.sum(axis=0), off)
+
+
+def pressure_rhs_vec(mesh: Mesh, C: Matrix, rhs0: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """h = A^-1 (u^n/dt + boundary terms + S - H u)  (Eq. pressureRHSdiscrete)."""
+    return (rhs0 - offdiag_matvec(mesh, C, u)) / C.diag[None, :]
+
+
+def divergence(mesh: Mesh, h: np.ndarray, bval) -> np.ndarray:
+    """b_P = sum_f N_f mean(J T_j . h) over inner faces (Eq. pressureRHSdivDiscrete)
+    plus the prescribed flux N_b J_P T_j . u_b over Dirichlet faces (R6)."""
+    F = mesh.contravariant(h)
+    b = np.zeros(mesh.N)
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        P = np.nonzero(mesh.inner[s])[0]
+        b[P] += n * 0.5 * (F[j, P] + F[j, mesh.nb[s, P]])
+        B = np.nonzero(mesh.is_bface[s])[0]
+        b[B] += n * mesh.face_flux_b(s, bval[s])[B]
+    return b
+
+
+def divergence_T(mesh: Mesh, gb: np.ndarray) -> np.ndarray:
+    """Transpose of the inner-face part of ``divergence``:
+    h_bar_P = sum_f 0.5 N_f J_P T_j,P (b_bar_P - b_bar_F)  (the neighbour's row
+    sees the same face with the opposite sign)."""
+    d = mesh.ndim
+    gF = np.zeros((d, mesh.N))
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        P = np.nonzero(mesh.inner[s])[0]
+        gF[j, P] += n * 0.5 * (gb[P] - gb[mesh.nb[s, P]])
+    # F^j = J T_j . h  ->  h_bar_k = J sum_j T_jk F_bar^j
+    return np.einsum("n,njk,jn->kn", mesh.J, mesh.T, gF)
+
+
+def correct(mesh: Mesh, h, A, p):
+    """u = h - A^-1 grad p (Eq. velCorrDiscrete)."""
+    return h - grad_p(mesh, p) / A[None, :]
+
+
+def outflow_update(mesh: Mesh, u, bval, dt):
+    """Advective outflow (App. A.3, Eq. advOut, reading R10): each outflow face
+    moves towards its cell value with factor c/(1+c), c = 2 dt |T_j . u_m|; then
+    all outflow faces are scaled so the outflow balances the inflow through the
+    other Dirichlet faces."""
+    if not mesh.has_outflow:
+        return bval
+    bval = bval.copy()
+    q_in = 0.0
+    q_out = 0.0
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        O = np.nonzero(mesh.is_outflow[s])[0]
+        if len(O):
+            c = 2.0 * dt * np.abs(np.einsum("nk,kn->n", mesh.T[O, j, :], mesh.u_m[s][:, O]))
+            f = c / (1.0 + c)
+            bval[s][:, O] = bval[s][:, O] - f[None, :] * (bval[s][:, O] - u[:, O])
+            q_out += float(np.sum(n * mesh.face_flux_b(s, bval[s])[O]))
+        D = np.nonzero(mesh.is_bface[s] & ~mesh.is_outflow[s])[0]
+        q_in -= float(np.sum(n * mesh.face_flux_b(s, bval[s])[D]))
+    if q_out != 0.0:
+        scale = q_in / q_out
+        for s in range(mesh.nsides):
+            O = np.nonzero(mesh.is_outflow[s])[0]
+            bval[s][:, O] *= scale
+    return bval
+
+
+# ----------------------------------------------------------------------------
+# linear solves
+# ----------------------------------------------------------------------------
+
+def solve_C(mesh, C, rhs, x0, opts: Options):
+    out = np.empty_like(rhs)
+    infos = []
+    if opts.solver == "direct":
+        Cs = to_sparse(mesh, C)
+        for c in range(rhs.shape[0]):
+            out[c] = krylov.direct_solve(Cs, rhs[c])
+        return out, infos
+    for c in range(rhs.shape[0]):
+        out[c], info = krylov.bicgstab(lambda v: matvec(mesh, C, v), rhs[c], x0[c],
+                                       opts.adv_rtol, opts.atol, opts.maxit)
+        infos.append(info)
+    return out, infos
+
+
+def solve_C_T(mesh, C, rhs, opts: Options):
+    out = np.empty_like(rhs)
+    if opts.solver == "direct":
+        CsT = to_sparse(mesh, C).T
+        for c in range(rhs.shape[0]):
+            out[c] = krylov.direct_solve(CsT, rhs[c])
+        return out
+    for c in range(rhs.shape[0]):
+        out[c], _ = krylov.bicgstab(lambda v: matvec_T(mesh, C, v), rhs[c], np.zeros(mesh.N),
+                                    opts.adv_rtol, opts.atol, opts.maxit)
+    return out
+
+
+def solve_P(mesh, Pm: Matrix, b, x0, opts: Options):
+    """Solve P x = b for mean-free b; returns mean-free x (R7).  CG runs on the
+    positive semi-definite -P."""
+    if opts.solver == "direct":
+        return krylov.direct_solve_singular(to_sparse(mesh, Pm), b), None
+    neg = Matrix(-Pm.diag, -Pm.off)
+    x, info = krylov.pcg(lambda v: matvec(mesh, neg, v), neg.diag, -b, x0, opts.p_rtol,
+                         opts.atol, opts.maxit)
+    return x - x.mean(), info
+
+
+# ----------------------------------------------------------------------------
+# the PISO step (App. A.1) and its adjoint (Sec. 2.3, App. A.4)
+# ----------------------------------------------------------------------------
+
+def piso_step(mesh: Mesh, u, p, dt, nu, S=None, bval=None, opts: Optional[Options] = None):
+    """One PISO step.  Returns (u_new, p_new, tape); tape['bval'] holds the
+    boundary values after the outflow update (they carry over to the next step)."""
+    opts = opts or Options()
+    bval = mesh.bval if bval is None else bval
+    if opts.update_outflow:
+        bval = outflow_update(mesh, u, bval, dt)
+    C, rhs0 = assemble_C(mesh, u, nu, dt, S, bval)
+    rhs = rhs0 - grad_p(mesh, p) if opts.pred_grad_p else rhs0
+    ustar, adv_info = solve_C(mesh, C, rhs, u, opts)
+    A = C.diag
+    Pm = assemble_P(mesh, A)
+    uk, pk = ustar, p
+    corr = []
+    p_infos = []
+    for _ in range(opts.n_correctors):
+        h = pressure_rhs_vec(mesh, C, rhs0, uk)
+        b = divergence(mesh, h, bval)
+        b = b - b.mean()
+        x, info = solve_P(mesh, Pm, b, pk, opts)
+        p_infos.append(info)
+        unew = correct(mesh, h, A, x)
+        corr.append(dict(u_in=uk, h=h, b=b, x=x))
+        uk, pk = unew, x
+    tape = dict(u=u, p=p, S=S, nu=nu, dt=dt, bval=bval, C=C, rhs0=rhs0, rhs=rhs, ustar=ustar,
+                Pm=Pm, corr=corr, u_out=uk, p_out=pk, adv_info=adv_info, p_infos=p_infos)
+    return uk, pk, tape
+
+
+def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Options] = None):
+    """Reverse of ``piso_step``: given dL/du^{n+1} and dL/dp^{n+1}, return
+    dL/du^n, dL/dp^n, dL/dS and dL/dnu (the outflow update and the boundary
+    values are held fixed)."""
+    opts = opts or Options()
+    d, N = mesh.ndim, mesh.N
+    C, Pm = tape["C"], tape["Pm"]
+    A = C.diag
+    nu, dt, bval = tape["nu"], tape["dt"], tape["bval"]
+    gA = np.zeros(N)                  # dL/dA (A = diag C)
+    gCoff = np.zeros((mesh.nsides, N))
+    grhs0 = np.zeros((d, N))
+    gw = np.zeros((d, N))             # dL/d(alpha_jj / A)
+    gu = np.array(du_out, dtype=np.float64, copy=True)
+    gp_last = np.array(dp_out, dtype=np.float64, copy=True)
+    ncorr = len(tape["corr"])
+    for k in reversed(range(ncorr)):
+        cr = tape["corr"][k]
+        x, h, uin = cr["x"], cr["h"], cr["u_in"]
+        # u_{k+1} = h - grad(x) / A
+        gh = gu.copy()
+        gx = -grad_p_T(mesh, gu / A[None, :])
+        gA += np.sum(gu * grad_p(mesh, x), axis=0) / A ** 2
+        if k == ncorr - 1:
+            gx = gx + gp_last
+        # x = Pi(P^+ Pi b): transposed (symmetric) solve
+        gx = gx - gx.mean()
+        y, _ = solve_P(mesh, Pm, gx, np.zeros(N), opts)
+        gb = y - y.mean()
+        # dP = -y (x) x on the pattern -> d(alpha/A): 0.5 (y_P - y_F)(x_P - x_F) per inner face
+        for s in range(mesh.nsides):
+            j = s // 2
+            P = np.nonzero(mesh.inner[s])[0]
+            F = mesh.nb[s, P]
+            gw[j, P] += 0.5 * (y[P] - y[F]) * (x[P] - x[F])
+        # b = div(h) + boundary flux
+        gh += divergence_T(mesh, gb)
+        # h = (rhs0 - H u_in) / A
+        gg = gh / A[None, :]
+        gA -= np.sum(gh * h, axis=0) / A
+        grhs0 += gg
+        gu = -offdiag_matvec_T(mesh, C, gg)
+        for s in range(mesh.nsides):
+            gCoff[s] -= np.sum(gg * uin[:, mesh.safe_nb[s]], axis=0) * mesh.inner[s]
+    # pressure matrix built from w = alpha / A
+    gA -= np.sum(gw * mesh.alpha, axis=0) / A ** 2
+    # predictor: u* = C^-1 rhs
+    ustar = tape["ustar"]
+    z = solve_C_T(mesh, C, gu, opts)
+    grhs = z
+    gA -= np.sum(z * ustar, axis=0)
+    for s in range(mesh.nsides):
+        gCoff[s] -= np.sum(z * ustar[:, mesh.safe_nb[s]], axis=0) * mesh.inner[s]
+    grhs0 += grhs
+    gp_in = -grad_p_T(mesh, grhs) if opts.pred_grad_p else np.zeros(N)
+    # assembly
+    gu_in = grhs0 / dt
+    gS = grhs0.copy()
+    gnu = 0.0
+    gU = np.zeros((d, N))
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        P = np.nonzero(mesh.inner[s])[0]
+        F = mesh.nb[s, P]
+        # off[s,P] = (0.5 n Uf - nu Df)/J_P,  diag[P] += (0.5 n Uf + nu Df)/J_P
+        gUf = 0.5 * n * (gCoff[s, P] + gA[P]) / mesh.J[P]
+        np.add.at(gU[j], P, 0.5 * gUf)
+        np.add.at(gU[j], F, 0.5 * gUf)
+        Df = 0.5 * (mesh.alpha[j, P] + mesh.alpha[j, F])
+        gnu += float(np.sum((gA[P] - gCoff[s, P]) * Df / mesh.J[P]))
+        B = np.nonzero(mesh.is_bface[s])[0]
+        gnu += float(np.sum(gA[B] * 2.0 * mesh.alpha[j, B] / mesh.J[B]))
+        ub = bval[s][:, B]
+        gnu += float(np.sum(grhs0[:, B] * ub * (2.0 * mesh.alpha[j, B] / mesh.J[B])[None, :]))
+    gu_in += np.einsum("n,njk,jn->kn", mesh.J, mesh.T, gU)
+    return gu_in, gp_in, gS, gnu
+
+
+def offdiag_matvec_T(mesh: Mesh, M: Matrix, y):
+    return matvec_T(mesh, Matrix(np.zeros(mesh.N), M.off), y)
+
+
+# ----------------------------------------------------------------------------
+# convenience
+# ----------------------------------------------------------------------------
+
+def mesh_from_case(case) -> Mesh:
+    """Build a Mesh from any object with ndim/blocks/connections/dirichlet/outflow
+    attributes (the seeded input generators produce such objects)."""
+    return Mesh(case.ndim, [(b.res, b.vertices) for b in case.blocks], case.connections,
+                case.dirichlet, case.outflow)
+
+
+def rollout(mesh: Mesh, u, p, dt, nu, S, steps, opts=None, bval=None):
+    bval = mesh.bval if bval is None else bval
+    for _ in range(steps):
+        u, p, tape = piso_step(mesh, u, p, dt, nu, S, bval, opts)
+        bval = tape["bval"]
+    return u, p, bval
+
+
+def rhie_chow_residual(mesh: Mesh, tape: Dict, k: int = -1) -> np.ndarray:
+    """Face-flux divergence of corrector k in the compact (Rhie-Chow) form:
+    sum_f N_f [mean(J T_j . h) - P_F (p_F - p_P)] + boundary flux = b - P x."""
+    cr = tape["corr"][k]
+    return cr["b"] - matvec(mesh, tape["Pm"], cr["x"])
