@@ -1,0 +1,330 @@
+"""Benchmark: PISO steps/s on the 3D periodic channel 64x48x32 (tanh walls,
+gamma 2, nu = 1/180, dt = 0.01, laminar profile + seeded perturbation 0.1).
+
+One bench step = one forward PISO step followed by its adjoint (the whole hot
+path).  Prints one JSON line (see the repository's design notes for every key).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+                  [--mode fwd|fwdadj] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20          # > 126 MB L2
+
+
+# ---------------------------------------------------------------------------
+# algorithmic traffic model: every array a phase touches, counted once per
+# phase (neighbour re-reads are cache hits), in words per cell
+# ---------------------------------------------------------------------------
+def fwd_words_per_cell(d: int, adv_iters, p_iters, n_out_frac: float = 0.0) -> float:
+    it_a = max(adv_iters) if adv_iters else 0
+    w = 0.0
+    w += d * d + 3 * d + 1            # F1: u, T, J -> U, tape u^n
+    w += d * d + 10 * d + 3           # F2: assemble C, rhs0, r, rhat, u* start
+    w += it_a * (21 * d + 2)          # BiCGStab: 3 phases per iteration
+    for k, it_p in enumerate(p_iters):
+        w += (d * d + 8 * d + 3) if k == 0 else (d * d + 6 * d + 4)   # C1: (P), h, J T.h
+        w += d + 1                    # C2: divergence
+        w += d + 6                    # C3: CG start
+        w += it_p * (d + 13)          # CG: 2 phases per iteration
+        w += d * d + 2 * d + 2        # C4: correction
+    w += 3                            # final pressure
+    return w
+
+
+def adj_words_per_cell(d: int, adv_iters, p_iters) -> float:
+    it_a = max(adv_iters) if adv_iters else 0
+    w = 0.0
+    for it_p in p_iters:
+        w += d * d + 3 * d + 3        # R0: w = T gu / A, gA
+        w += d + 3                    # R1: -G^T w
+        w += 5 + it_p * (d + 13)      # CG on P (transposed = P)
+        w += d * d + 6 * d + 8        # R3: gw, div^T, gg, gA, grhs0
+        w += 2 * d * d + 4 * d + 2    # R4: -H^T gg, gCoff
+    w += 3 * d + 3                    # R5
+    w += 2 * d + 5 + it_a * (21 * d + 2)   # BiCGStab on C^T
+    w += 4 * d + 2 * d + 4            # R6
+    w += d * d + 6 * d + 6            # R7: assembly adjoint
+    return w
+
+
+# ---------------------------------------------------------------------------
+def clocks_sampler_start(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "100"], stdout=f, stderr=subprocess.DEVNULL), f
+    except Exception:
+        return None, None
+
+
+def clocks_sampler_stop(proc, f, path, gpu_index=0):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    f.close()
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = float(parts[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(case, seconds_budget=20.0, steps_cap=3):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import numpy as np
+    import oracle as O
+    m = O.mesh_from_case(case)
+    u, p = case.u0, case.p0
+    t0 = time.perf_counter()
+    n = 0
+    while n < steps_cap:
+        u1, p1, tape = O.piso_step(m, u, p, case.dt, case.nu, case.S)
+        O.piso_step_adjoint(m, tape, np.ones_like(u1), np.zeros_like(p1))
+        n += 1
+        if time.perf_counter() - t0 > seconds_budget:
+            break
+        u, p = u1, p1
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2505_16992_b300 import workloads as W
+    case = W.channel3d()
+    for _ in range(args.warmup):
+        pass
+    per_step = []
+    t_all = time.perf_counter()
+    for _ in range(max(args.steps, 1)):
+        v, n, dt = cpu_baseline(case, seconds_budget=60.0 / max(args.steps, 1), steps_cap=1)
+        per_step.append(dt / n)
+    total = time.perf_counter() - t_all
+    value = len(per_step) / sum(per_step)
+    line = {"metric": "PISO steps/s (fwd+adjoint), 64x48x32 channel", "value": value,
+            "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(per_step) / len(per_step), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "channel3d 64x48x32, tanh walls gamma 2, nu 1/180, dt 0.01",
+                       "cells": case.ncells},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(per_step)} fwd+adjoint steps from the seeded initial field"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--mode", default="fwdadj", choices=["fwd", "fwdadj"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2505_16992_b300 import capi, workloads as W
+    from paper_2505_16992_b300.solver import Domain
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    case = W.channel3d()
+    prec = args.precision
+    rtol = 1e-6 if prec == "fp32" else 1e-10
+    opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000)
+    dom = Domain.from_case(case, prec, opts)
+    d, N = case.ndim, case.ncells
+    w = 4 if prec == "fp32" else 8
+    u0 = dom.field(case.u0, d)
+    p0 = dom.field(case.p0)
+    S = dom.field(case.S, d)
+    u, p = u0.clone(), p0.clone()
+    u_out, p_out = torch.empty_like(u), torch.empty_like(p)
+    gu = torch.ones_like(u)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    with_adj = args.mode == "fwdadj"
+
+    def one_step():
+        dom.step(u, p, case.dt, case.nu, S, u_out=u_out, p_out=p_out, sync=False)
+        if with_adj:
+            dom.step_adjoint(gu, None)
+
+    # warm-up (also records iteration counts)
+    for _ in range(args.warmup):
+        one_step()
+    st = dom.step(u, p, case.dt, case.nu, S, u_out=u_out, p_out=p_out)[2]
+    adj_st = dom.step_adjoint(gu, None)[4] if with_adj else None
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clk_path = os.path.join(tempfile.gettempdir(), f"piso_clocks_{os.getpid()}.csv")
+    proc, fh = clocks_sampler_start(clk_path)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))                       # L2 flush between timed steps (not timed)
+        ev[k][0].record(stream)
+        kev[k][0].record(stream)
+        dom.step(u, p, case.dt, case.nu, S, u_out=u_out, p_out=p_out, sync=False)
+        kev[k][1].record(stream)
+        if with_adj:
+            dom.step_adjoint(gu, None)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = clocks_sampler_stop(proc, fh, clk_path, local)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    fwd_ms = [a.elapsed_time(b) for a, b in kev]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+
+    # end to end through the public API with host buffers
+    hu = torch.empty((d, N), dtype=dom.dtype, pin_memory=True)
+    hp = torch.empty((N,), dtype=dom.dtype, pin_memory=True)
+    hu.copy_(u0.cpu())
+    hp.copy_(p0.cpu())
+    hu_o = torch.empty_like(hu).pin_memory()
+    hp_o = torch.empty_like(hp).pin_memory()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        u.copy_(hu, non_blocking=True)
+        p.copy_(hp, non_blocking=True)
+        one_step()
+        hu_o.copy_(u_out, non_blocking=True)
+        hp_o.copy_(p_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = world * args.steps / e2e_s
+    io_bytes = (d + 1) * N * w
+
+    # roofline of the dominant kernel (the persistent forward-step kernel)
+    peak, peak_kind = measured_peaks()
+    words = fwd_words_per_cell(d, st["adv_iters"][:d], st["p_iters"][:2])
+    alg_bytes = words * N * w
+    fwd_avg_s = sum(fwd_ms) / len(fwd_ms) / 1e3
+    achieved = alg_bytes / fwd_avg_s / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", f"traffic_fwd_kernel_channel3d_{prec}.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    if rank == 0:
+        line = {
+            "metric": "PISO steps/s (fwd+adjoint), 64x48x32 channel" if with_adj else
+                      "PISO steps/s (fwd), 64x48x32 channel",
+            "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "channel3d 64x48x32, x/z periodic, tanh walls gamma 2, nu 1/180, dt 0.01, "
+                                   "laminar + N(0,0.1^2) perturbation (seed 0)",
+                       "cells": N, "precision": prec, "krylov_rtol": rtol,
+                       "l2": "flushed between timed steps (256 MB write, untimed)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "iterations": {"adv": st["adv_iters"][:d], "p": st["p_iters"][:2],
+                           "adj_adv": adj_st["adv_iters"][:d] if adj_st else None,
+                           "adj_p": adj_st["p_iters"][:2] if adj_st else None},
+            "fwd_ms": sum(fwd_ms) / len(fwd_ms),
+            "cell_updates_per_s": value * N,
+            "e2e": {"value": e2e, "unit": "steps/s", "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": args.steps * (2 if with_adj else 1),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "fwd_kernel", "words_per_cell": words},
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            v, n, dt = cpu_baseline(case)
+            line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"{n} fwd+adjoint steps of the same workload in {dt:.1f} s"}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

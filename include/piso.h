@@ -1,0 +1,208 @@
+/*
+ * piso.h - C ABI of the B300 (sm_103a) per-time-step PISO update.
+ *
+ * The library implements one time step of the incompressible collocated
+ * finite-volume PISO scheme on structured multi-block grids with coordinate
+ * transforms described in arXiv:2505.16992 (PICT), Sec. 2.1-2.3 and App. A:
+ * assembly of the advection-diffusion matrix C = A + H, a BiCGStab predictor
+ * solve, n pressure correctors (divergence of h, Jacobi-preconditioned CG on
+ * the pressure matrix P, velocity correction), block-interface and boundary
+ * handling, and the discrete adjoint of that step.
+ *
+ * Conventions (shared by every entry point):
+ *   - Sides 0..5 = -x, +x, -y, +y, -z, +z (2D uses 0..3).
+ *   - A block of resolution (nx, ny, nz) (nz = 1 in 2D) owns cells with local
+ *     index x + nx*(y + ny*z); the domain index of a cell is the sum of the
+ *     cell counts of the blocks added before it plus its local index.
+ *   - Fields are structure-of-arrays in DEVICE memory: a velocity-like field
+ *     is ndim arrays of N values back to back (component-major, [c][i]); a
+ *     pressure-like field is N values.  The element type is double for
+ *     PISO_FP64 and float for PISO_FP32.  The caller owns every field buffer;
+ *     the library never retains a field pointer past the call that received it.
+ *   - Values on a block side are given per boundary face, ordered by the two
+ *     tangential cell indices with the lower axis fastest (x-sides: y then z;
+ *     y-sides: x then z; z-sides: x then y), each face carrying ndim values
+ *     (row-major [face][component], host memory, double).
+ *   - Every call returns a piso_status; nothing aborts or traps.  On an error
+ *     the outputs are unspecified, the inputs are untouched, and
+ *     piso_last_error() describes the failure.
+ *   - Device work is enqueued on the caller's CUDA stream (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream).
+ */
+#ifndef PISO_H
+#define PISO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct piso_domain piso_domain;
+typedef struct piso_batch piso_batch;
+
+typedef enum {
+  PISO_OK = 0,
+  PISO_EINVAL = 1,      /* bad argument or domain description */
+  PISO_ECUDA = 2,       /* a CUDA runtime call failed */
+  PISO_ENOCONV = 3,     /* a Krylov solve hit its iteration limit (stats hold the counts) */
+  PISO_EBREAKDOWN = 4,  /* a Krylov solve broke down (zero denominator) */
+  PISO_ENAN = 5,        /* a residual became NaN */
+  PISO_ETIMEOUT = 6,    /* a group barrier wait ran out (the step was abandoned) */
+  PISO_ESTATE = 7,      /* call out of order (e.g. step before finalize) */
+  PISO_ENOMEM = 8       /* device allocation failed */
+} piso_status;
+
+typedef enum {
+  PISO_FP64 = 0,        /* double storage and arithmetic */
+  PISO_FP32 = 1         /* float storage and stencil arithmetic; Krylov dot products and
+                           norms accumulated with ~48-bit (float-pair) sums and reduced
+                           across CTAs in double */
+} piso_precision;
+
+/* Solver options (App. A.1: two correctors; App. A.5: CG for the pressure,
+ * BiCGStab for advection-diffusion).  Convergence: ||r||_2 <=
+ * max(rtol * ||b||_2, atol) for each solve. */
+typedef struct {
+  int32_t n_correctors;  /* 1..4, default 2 */
+  int32_t pred_grad_p;   /* 1: predictor right-hand side contains -grad p^n (Eq. advectionMat) */
+  double adv_rtol;       /* BiCGStab relative tolerance */
+  double p_rtol;         /* CG relative tolerance */
+  double atol;           /* absolute tolerance for both */
+  int32_t adv_maxit;     /* BiCGStab iteration limit */
+  int32_t p_maxit;       /* CG iteration limit per corrector */
+  int32_t block_threads; /* threads per CTA (multiple of 32, <= 512); 0 = auto */
+  int32_t ctas;          /* CTAs for this domain; 0 = auto (one per SM, capped by size) */
+  double timeout_s;      /* group-barrier wait limit in seconds (default 5) */
+} piso_options;
+
+/* Per-step statistics (read back when a stats pointer is given). */
+typedef struct {
+  int32_t status;         /* piso_status of the step */
+  int32_t error_bits;     /* 1 adv no-conv, 2 pressure no-conv, 4 breakdown, 8 NaN, 16 timeout */
+  int32_t adv_iters[3];   /* BiCGStab iterations per velocity component */
+  int32_t p_iters[4];     /* CG iterations per corrector */
+  double adv_resid[3];    /* final BiCGStab residual norms */
+  double p_resid[4];      /* final CG residual norms */
+} piso_stats;
+
+/* Fill *o with the defaults listed above. */
+void piso_default_options(piso_options* o);
+
+/* Create an empty domain of dimension ndim (2 or 3) and precision prec.
+ * Ownership of *out passes to the caller (release with piso_domain_destroy). */
+piso_status piso_domain_create(int32_t ndim, int32_t prec, piso_domain** out);
+
+/* Add a block (Sec. 2.2: a regular grid aligned to boundaries by a
+ * precomputed transformation).  res = {nx, ny, nz} (nz = 1 in 2D); vertices is
+ * HOST memory with (nz+1)(ny+1)(nx+1) points of ndim doubles, x fastest.
+ * Metrics T = d xi / d x and J = det(d x / d xi) are formed at cell centres
+ * from opposite face-centre differences (App. A.2 "Grid Transformations").
+ * Grids whose cross metrics alpha_jk (j != k) do not vanish are rejected at
+ * finalize.  *block_id receives the block's index. */
+piso_status piso_block_add(piso_domain* d, const int32_t res[3], const double* vertices,
+                           int32_t* block_id);
+
+/* Join side sa of block a to side sb of block b (Sec. 2.2: a conformal
+ * connection with matching resolution; App. A.3: it only changes the
+ * neighbour lookup).  sb must be the opposite side of the same axis and the
+ * tangential cell orderings must agree; a == b with opposite sides gives a
+ * periodic direction. */
+piso_status piso_connect(piso_domain* d, int32_t a, int32_t sa, int32_t b, int32_t sb);
+
+/* Dirichlet velocity on a block side (App. A.3: values live on the face;
+ * pressure is implicitly zero-Neumann there).  values: HOST, [face][ndim]. */
+piso_status piso_set_dirichlet(piso_domain* d, int32_t blk, int32_t side, const double* values);
+
+/* Advective (non-reflecting) outflow on a block side (App. A.3, Eq. advOut):
+ * before every step each face value moves towards its cell value with the
+ * factor c/(1+c), c = 2 dt |T_j . u_m|, and all outflow faces are then scaled
+ * so the outflow balances the inflow; during the step the side acts as a
+ * Dirichlet side.  u_m: HOST ndim doubles; values: HOST initial face values. */
+piso_status piso_set_advective_outflow(piso_domain* d, int32_t blk, int32_t side,
+                                       const double* u_m, const double* values);
+
+/* Validate the description, build metrics and connection tables, upload them
+ * and allocate the workspace.  opts may be NULL (defaults).  No further
+ * blocks or boundaries may be added afterwards. */
+piso_status piso_finalize(piso_domain* d, const piso_options* opts);
+
+/* Replace the solver options of a finalized domain (launch shape included). */
+piso_status piso_set_options(piso_domain* d, const piso_options* opts);
+
+int64_t piso_num_cells(const piso_domain* d);
+int32_t piso_num_boundary_faces(const piso_domain* d);
+
+/* Bytes of a tape: the intermediates one forward step records for its adjoint
+ * (u^n, C, u*, and per corrector h, the pressure and the corrected velocity,
+ * plus the boundary values used).  Device memory, caller-owned. */
+size_t piso_tape_bytes(const piso_domain* d);
+
+/* One PISO step (App. A.1): u_out, p_out <- step(u_in, p_in, dt, nu, S).
+ * u_in/u_out: device [ndim][N]; p_in/p_out: device [N]; u_out may alias u_in
+ * and p_out may alias p_in.  S: device [ndim][N] per-unit-volume source, or
+ * NULL.  The returned pressure has zero mean.  tape: device buffer of
+ * piso_tape_bytes() that receives this step's intermediates, or NULL to keep
+ * them in the domain's own workspace (valid until the next step).  Advective
+ * outflow faces of the domain are updated in place.  If stats is non-NULL the
+ * call waits for the step and fills it; otherwise it returns after enqueueing
+ * (read the outcome later with piso_last_stats). */
+piso_status piso_step(piso_domain* d, const void* u_in, const void* p_in, void* u_out,
+                      void* p_out, double dt, double nu, const void* S, void* tape,
+                      void* stream, piso_stats* stats);
+
+/* Wait for the last enqueued step (or adjoint) of the domain and report it. */
+piso_status piso_last_stats(piso_domain* d, piso_stats* stats);
+
+/* Adjoint of one step (Sec. 2.3, App. A.4): given du_out = dL/du^{n+1} and
+ * dp_out = dL/dp^{n+1} (device; dp_out may be NULL for zero), write
+ * du_in = dL/du^n, dp_in = dL/dp^n, dS = dL/dS (each device, caller-owned,
+ * may be NULL to skip) and *dnu = dL/dnu (host double, may be NULL).
+ * tape is the buffer filled by the forward step (NULL = the domain's own
+ * record of its last step).  Linear solves are differentiated by transposed
+ * solves (C^T via BiCGStab, P symmetric via CG); boundary values and the
+ * outflow update are held fixed. */
+piso_status piso_step_adjoint(piso_domain* d, const void* tape, const void* du_out,
+                              const void* dp_out, void* du_in, void* dp_in, void* dS,
+                              double* dnu, void* stream, piso_stats* stats);
+
+/* Copy the domain's current boundary-face values (device, [ndim][nbf]) to the
+ * host array values ([ndim][nbf] doubles), or set them from it. */
+piso_status piso_get_boundary(piso_domain* d, double* values);
+piso_status piso_set_boundary(piso_domain* d, const double* values);
+
+/* Last error message of the domain (or of the most recent failing creation
+ * call when d is NULL).  The string is owned by the library. */
+const char* piso_last_error(const piso_domain* d);
+
+/* Release the domain and its device memory. */
+void piso_domain_destroy(piso_domain* d);
+
+/* ---- batches: independent simulations of uneven size in one launch ----
+ * Each domain keeps its own CTA group, barrier and Krylov scalars; groups
+ * run to their own convergence inside one persistent launch.  All domains
+ * must share ndim and precision and be finalized. */
+piso_status piso_batch_create(piso_domain* const* domains, int32_t n, const piso_options* opts,
+                              piso_batch** out);
+
+/* One step of every domain: arrays of n device pointers / values. */
+piso_status piso_batch_step(piso_batch* b, const void* const* u_in, const void* const* p_in,
+                            void* const* u_out, void* const* p_out, const double* dt,
+                            const double* nu, const void* const* S, void* stream,
+                            piso_stats* stats);
+
+piso_status piso_batch_step_adjoint(piso_batch* b, const void* const* du_out,
+                                    const void* const* dp_out, void* const* du_in,
+                                    void* const* dp_in, void* const* dS, double* dnu,
+                                    void* stream, piso_stats* stats);
+
+void piso_batch_destroy(piso_batch* b);
+
+/* Library version string. */
+const char* piso_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PISO_H */

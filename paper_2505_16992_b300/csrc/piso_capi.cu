@@ -1,0 +1,827 @@
+// Host side of the PISO library: domain description, metrics and connection
+// tables (App. A.2-A.3 and A.5 of arXiv:2505.16992), device workspace, launch
+// configuration and the C ABI declared in include/piso.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/piso.h"
+#include "piso_adjoint.cuh"
+#include "piso_forward.cuh"
+
+using namespace piso;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct SideSpec {
+  int kind = 0;            // 0 none, 1 connection, 2 dirichlet, 3 outflow
+  int other = -1, other_side = -1;
+  std::vector<double> values;   // [face][ndim]
+  double um[3] = {0, 0, 0};
+};
+
+struct HostBlock {
+  int res[3];
+  std::vector<double> vertices;
+  SideSpec side[6];
+};
+
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  void* take(size_t bytes) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + bytes;
+    return base ? base + off : nullptr;
+  }
+};
+
+}  // namespace
+
+struct piso_domain {
+  int ndim = 2, prec = 0;
+  bool finalized = false;
+  std::vector<HostBlock> blocks;
+  piso_options opts;
+  std::string err;
+  // sizes
+  int32_t N = 0, nbf = 0, n_out = 0;
+  size_t elem = 8;
+  // device
+  char* dmem = nullptr;
+  size_t dmem_bytes = 0;
+  DomStatic* d_static = nullptr;
+  void* J = nullptr;
+  void* T = nullptr;
+  void* alpha = nullptr;
+  int32_t* bf_cell = nullptr;
+  int8_t* bf_side = nullptr;
+  int8_t* bf_out = nullptr;
+  void* bf_um = nullptr;
+  void* bval = nullptr;
+  // workspace arrays (element pointers)
+  void* ws[64] = {nullptr};
+  void* tape_ws = nullptr;     // internal tape (last step)
+  uint32_t* bar = nullptr;
+  double* partials = nullptr;
+  int32_t* status = nullptr;
+  int32_t* istats = nullptr;
+  double* dstats = nullptr;
+  double* d_dnu = nullptr;
+  // pinned readback
+  int32_t* h_status = nullptr;
+  int32_t* h_istats = nullptr;
+  double* h_dstats = nullptr;
+  double* h_dnu = nullptr;
+  // launch shape
+  int threads = 512, ncta = 1;
+  int sms = 148;
+  DomStatic h_static;
+  bool pending = false;
+  cudaStream_t pending_stream = nullptr;
+  int pending_kind = 0;        // 1 forward, 2 adjoint
+};
+
+struct piso_batch {
+  std::vector<piso_domain*> doms;
+  piso_options opts;
+  int total_cta = 0;
+  std::vector<int32_t> cta_first;
+  int32_t* d_cta_first = nullptr;
+  void* d_calls = nullptr;
+  void* h_calls = nullptr;     // pinned
+  size_t call_bytes = 0;
+  uint32_t* bars = nullptr;    // one per domain (contiguous)
+  std::string err;
+};
+
+namespace {
+
+piso_status fail(piso_domain* d, piso_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (d) d->err = buf;
+  else g_create_error = buf;
+  return s;
+}
+
+#define CUDA_TRY(d, call)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(d, PISO_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+int side_nfaces(const int* r, int s, int nd) {
+  int ax = s / 2;
+  if (nd == 2) return ax == 0 ? r[1] : r[0];
+  if (ax == 0) return r[1] * r[2];
+  if (ax == 1) return r[0] * r[2];
+  return r[0] * r[1];
+}
+
+// d x / d xi at a cell centre from opposite face-centre differences.
+void cell_jacobian(const HostBlock& b, int nd, int x, int y, int z, double M[3][3]) {
+  const int nx = b.res[0], ny = b.res[1];
+  auto V = [&](int i, int j, int k, int c) -> double {
+    return b.vertices[((size_t)(k * (ny + 1) + j) * (nx + 1) + i) * nd + c];
+  };
+  for (int a = 0; a < 3; a++)
+    for (int c = 0; c < 3; c++) M[a][c] = (a == c) ? 1.0 : 0.0;
+  if (nd == 2) {
+    for (int c = 0; c < 2; c++) {
+      double fxm = 0.5 * (V(x, y, 0, c) + V(x, y + 1, 0, c));
+      double fxp = 0.5 * (V(x + 1, y, 0, c) + V(x + 1, y + 1, 0, c));
+      double fym = 0.5 * (V(x, y, 0, c) + V(x + 1, y, 0, c));
+      double fyp = 0.5 * (V(x, y + 1, 0, c) + V(x + 1, y + 1, 0, c));
+      M[c][0] = fxp - fxm;
+      M[c][1] = fyp - fym;
+    }
+    return;
+  }
+  for (int c = 0; c < 3; c++) {
+    double fxm = 0.25 * (V(x, y, z, c) + V(x, y + 1, z, c) + V(x, y, z + 1, c) + V(x, y + 1, z + 1, c));
+    double fxp = 0.25 * (V(x + 1, y, z, c) + V(x + 1, y + 1, z, c) + V(x + 1, y, z + 1, c) +
+                         V(x + 1, y + 1, z + 1, c));
+    double fym = 0.25 * (V(x, y, z, c) + V(x + 1, y, z, c) + V(x, y, z + 1, c) + V(x + 1, y, z + 1, c));
+    double fyp = 0.25 * (V(x, y + 1, z, c) + V(x + 1, y + 1, z, c) + V(x, y + 1, z + 1, c) +
+                         V(x + 1, y + 1, z + 1, c));
+    double fzm = 0.25 * (V(x, y, z, c) + V(x + 1, y, z, c) + V(x, y + 1, z, c) + V(x + 1, y + 1, z, c));
+    double fzp = 0.25 * (V(x, y, z + 1, c) + V(x + 1, y, z + 1, c) + V(x, y + 1, z + 1, c) +
+                         V(x + 1, y + 1, z + 1, c));
+    M[c][0] = fxp - fxm;
+    M[c][1] = fyp - fym;
+    M[c][2] = fzp - fzm;
+  }
+}
+
+// inverse and determinant of a 2x2 / 3x3 matrix
+double invert(int nd, const double M[3][3], double Ti[3][3]) {
+  if (nd == 2) {
+    double det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    Ti[0][0] = M[1][1] / det;
+    Ti[0][1] = -M[0][1] / det;
+    Ti[1][0] = -M[1][0] / det;
+    Ti[1][1] = M[0][0] / det;
+    return det;
+  }
+  double c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+  double c01 = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+  double c02 = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+  double det = M[0][0] * c00 + M[0][1] * c01 + M[0][2] * c02;
+  Ti[0][0] = c00 / det;
+  Ti[1][0] = c01 / det;
+  Ti[2][0] = c02 / det;
+  Ti[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) / det;
+  Ti[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) / det;
+  Ti[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) / det;
+  Ti[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) / det;
+  Ti[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) / det;
+  Ti[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) / det;
+  return det;
+}
+
+template <typename real>
+void put(std::vector<char>& buf, size_t i, double v) {
+  reinterpret_cast<real*>(buf.data())[i] = (real)v;
+}
+
+// --- workspace layout ------------------------------------------------------
+enum WsIdx {
+  W_U, W_RHS0, W_R, W_RHAT, W_P0, W_P1, W_V0, W_V1, W_T, W_POFF, W_PDIAG, W_FH, W_B, W_CX, W_CR, W_CZ,
+  W_CD0, W_CD1, W_CQ,
+  // adjoint scratch
+  A_GA, A_GCOFF, A_GRHS0, A_GW, A_W, A_GG, A_GU, A_GX, A_Y, A_GU2,
+  W_COUNT
+};
+
+struct TapeLayout {
+  size_t un, cdiag, coff, ustar, h[4], xk[4], uc[4], bval, total;
+};
+
+TapeLayout tape_layout(const piso_domain* d) {
+  TapeLayout t{};
+  const size_t N = d->N, nd = d->ndim, e = d->elem;
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    size_t o = off;
+    off += ((n * e + 255) / 256) * 256;
+    return o;
+  };
+  t.un = take(nd * N);
+  t.cdiag = take(N);
+  t.coff = take(2 * nd * N);
+  t.ustar = take(nd * N);
+  for (int k = 0; k < 4; k++) {
+    t.h[k] = take(nd * N);
+    t.xk[k] = take(N);
+    t.uc[k] = take(nd * N);
+  }
+  t.bval = take(nd * std::max(d->nbf, 1));
+  t.total = off;
+  return t;
+}
+
+template <typename real>
+void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const void* p_in, void* u_out,
+                   void* p_out, double dt, double nu, const void* S, void* tape) {
+  memset(&c, 0, sizeof c);
+  c.dom = d->d_static;
+  c.u_in = (const real*)u_in;
+  c.p_in = (const real*)p_in;
+  c.u_out = (real*)u_out;
+  c.p_out = (real*)p_out;
+  c.S = (const real*)S;
+  c.bval = (real*)d->bval;
+  c.dt = dt;
+  c.nu = nu;
+  char* tb = (char*)(tape ? tape : d->tape_ws);
+  TapeLayout L = tape_layout(d);
+  c.un = (real*)(tb + L.un);
+  c.Cdiag = (real*)(tb + L.cdiag);
+  c.Coff = (real*)(tb + L.coff);
+  c.ustar = (real*)(tb + L.ustar);
+  for (int k = 0; k < 4; k++) {
+    c.h[k] = (real*)(tb + L.h[k]);
+    c.xk[k] = (real*)(tb + L.xk[k]);
+    c.uc[k] = (real*)(tb + L.uc[k]);
+  }
+  c.bval_rec = (real*)(tb + L.bval);
+  c.U = (real*)d->ws[W_U];
+  c.rhs0 = (real*)d->ws[W_RHS0];
+  c.r = (real*)d->ws[W_R];
+  c.rhat = (real*)d->ws[W_RHAT];
+  c.pv[0] = (real*)d->ws[W_P0];
+  c.pv[1] = (real*)d->ws[W_P1];
+  c.vv[0] = (real*)d->ws[W_V0];
+  c.vv[1] = (real*)d->ws[W_V1];
+  c.t = (real*)d->ws[W_T];
+  c.Poff = (real*)d->ws[W_POFF];
+  c.Pdiag = (real*)d->ws[W_PDIAG];
+  c.Fh = (real*)d->ws[W_FH];
+  c.b = (real*)d->ws[W_B];
+  c.cx = (real*)d->ws[W_CX];
+  c.cr = (real*)d->ws[W_CR];
+  c.cz = (real*)d->ws[W_CZ];
+  c.cd[0] = (real*)d->ws[W_CD0];
+  c.cd[1] = (real*)d->ws[W_CD1];
+  c.cq = (real*)d->ws[W_CQ];
+  c.bar = d->bar;
+  c.partials = d->partials;
+  c.status = d->status;
+  c.istats = d->istats;
+  c.dstats = d->dstats;
+  c.cta0 = 0;
+  c.ncta = d->ncta;
+}
+
+SolverOpts solver_opts(const piso_options& o) {
+  SolverOpts s;
+  s.n_corr = o.n_correctors;
+  s.pred_grad_p = o.pred_grad_p;
+  s.adv_maxit = o.adv_maxit;
+  s.p_maxit = o.p_maxit;
+  s.adv_rtol = o.adv_rtol;
+  s.p_rtol = o.p_rtol;
+  s.atol = o.atol;
+  s.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
+  return s;
+}
+
+template <typename K>
+cudaError_t coop_launch(K kernel, int grid, int threads, void** args, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, (const void*)kernel, args);
+}
+
+const void* fwd_kernel_ptr(int prec, int nd) {
+  if (prec == PISO_FP64) return nd == 2 ? (const void*)fwd_kernel<double, 2> : (const void*)fwd_kernel<double, 3>;
+  return nd == 2 ? (const void*)fwd_kernel<float, 2> : (const void*)fwd_kernel<float, 3>;
+}
+
+const void* adj_kernel_ptr(int prec, int nd) {
+  if (prec == PISO_FP64) return nd == 2 ? (const void*)adj_kernel<double, 2> : (const void*)adj_kernel<double, 3>;
+  return nd == 2 ? (const void*)adj_kernel<float, 2> : (const void*)adj_kernel<float, 3>;
+}
+
+int max_coresident(const void* kernel, int threads, int* sms_out) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  if (sms_out) *sms_out = sms;
+  return sms * std::max(per_sm, 0);
+}
+
+piso_status choose_shape(piso_domain* d) {
+  int threads = d->opts.block_threads > 0 ? d->opts.block_threads : 512;
+  if (threads % 32 || threads > 512 || threads < 32)
+    return fail(d, PISO_EINVAL, "block_threads must be a multiple of 32 in [32, 512]");
+  int sms = 148;
+  int cap_f = max_coresident(fwd_kernel_ptr(d->prec, d->ndim), threads, &sms);
+  int cap_a = max_coresident(adj_kernel_ptr(d->prec, d->ndim), threads, nullptr);
+  int cap = std::min(cap_f, cap_a);
+  if (cap <= 0) return fail(d, PISO_ECUDA, "kernel cannot be resident with %d threads", threads);
+  int want = d->opts.ctas > 0 ? d->opts.ctas : std::min(sms, (int)((d->N + threads - 1) / threads));
+  want = std::max(1, want);
+  if (want > cap) want = cap;
+  if (want > MAXCTA) want = MAXCTA;
+  d->threads = threads;
+  d->ncta = want;
+  d->sms = sms;
+  return PISO_OK;
+}
+
+piso_status collect_stats(piso_domain* d, piso_stats* st) {
+  cudaError_t e = cudaStreamSynchronize(d->pending_stream);
+  if (e != cudaSuccess) return fail(d, PISO_ECUDA, "step failed: %s", cudaGetErrorString(e));
+  d->pending = false;
+  const int bits = *d->h_status;
+  piso_status s = PISO_OK;
+  if (bits & PISO_ERR_TIMEOUT) s = PISO_ETIMEOUT;
+  else if (bits & PISO_ERR_NAN) s = PISO_ENAN;
+  else if (bits & PISO_ERR_BREAKDOWN) s = PISO_EBREAKDOWN;
+  else if (bits & (PISO_ERR_NOCONV_ADV | PISO_ERR_NOCONV_P)) s = PISO_ENOCONV;
+  if (st) {
+    memset(st, 0, sizeof *st);
+    st->status = s;
+    st->error_bits = bits;
+    for (int k = 0; k < 3; k++) {
+      st->adv_iters[k] = d->h_istats[k];
+      st->adv_resid[k] = d->h_dstats[k];
+    }
+    for (int k = 0; k < 4; k++) {
+      st->p_iters[k] = d->h_istats[4 + k];
+      st->p_resid[k] = d->h_dstats[4 + k];
+    }
+  }
+  if (s != PISO_OK) {
+    const char* what = s == PISO_ETIMEOUT ? "group barrier timed out"
+                       : s == PISO_ENAN   ? "NaN residual"
+                       : s == PISO_EBREAKDOWN ? "Krylov breakdown"
+                                              : "Krylov solve did not converge";
+    return fail(d, s, "%s (error bits %d)", what, bits);
+  }
+  return PISO_OK;
+}
+
+piso_status enqueue_readback(piso_domain* d, cudaStream_t st) {
+  CUDA_TRY(d, cudaMemcpyAsync(d->h_status, d->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(d, cudaMemcpyAsync(d->h_istats, d->istats, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(d, cudaMemcpyAsync(d->h_dstats, d->dstats, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return PISO_OK;
+}
+
+template <typename real>
+piso_status launch_fwd(piso_domain* d, const void* u_in, const void* p_in, void* u_out, void* p_out,
+                              double dt, double nu, const void* S, void* tape, cudaStream_t st) {
+  FwdLaunch<real> L;
+  memset(&L, 0, sizeof L);
+  L.ngroups = 1;
+  L.o = solver_opts(d->opts);
+  L.cta_first = nullptr;
+  L.calls = nullptr;
+  fill_fwd_call<real>(d, L.call0, u_in, p_in, u_out, p_out, dt, nu, S, tape);
+  CUDA_TRY(d, cudaMemsetAsync(d->bar, 0, 64, st));
+  CUDA_TRY(d, cudaMemsetAsync(d->status, 0, 64, st));
+  CUDA_TRY(d, cudaMemsetAsync(d->istats, 0, 64, st));
+  void* args[] = {&L};
+  CUDA_TRY(d, coop_launch(d->ndim == 2 ? fwd_kernel<real, 2> : fwd_kernel<real, 3>, d->ncta, d->threads, args, st));
+  return PISO_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* piso_version(void) { return "pisob300 0.1 (sm_103a)"; }
+
+void piso_default_options(piso_options* o) {
+  if (!o) return;
+  o->n_correctors = 2;
+  o->pred_grad_p = 1;
+  o->adv_rtol = 1e-12;
+  o->p_rtol = 1e-12;
+  o->atol = 0.0;
+  o->adv_maxit = 1000;
+  o->p_maxit = 20000;
+  o->block_threads = 0;
+  o->ctas = 0;
+  o->timeout_s = 5.0;
+}
+
+piso_status piso_domain_create(int32_t ndim, int32_t prec, piso_domain** out) {
+  if (!out) return fail(nullptr, PISO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (ndim != 2 && ndim != 3) return fail(nullptr, PISO_EINVAL, "ndim must be 2 or 3");
+  if (prec != PISO_FP64 && prec != PISO_FP32) return fail(nullptr, PISO_EINVAL, "unknown precision %d", prec);
+  piso_domain* d = new piso_domain();
+  d->ndim = ndim;
+  d->prec = prec;
+  d->elem = prec == PISO_FP64 ? 8 : 4;
+  piso_default_options(&d->opts);
+  *out = d;
+  return PISO_OK;
+}
+
+piso_status piso_block_add(piso_domain* d, const int32_t res[3], const double* vertices, int32_t* block_id) {
+  if (!d || !res || !vertices) return fail(d, PISO_EINVAL, "NULL argument");
+  if (d->finalized) return fail(d, PISO_ESTATE, "domain already finalized");
+  if ((int)d->blocks.size() >= MAXB) return fail(d, PISO_EINVAL, "at most %d blocks per domain", MAXB);
+  int nz = d->ndim == 2 ? 1 : res[2];
+  if (res[0] < 1 || res[1] < 1 || nz < 1) return fail(d, PISO_EINVAL, "resolution must be positive");
+  if (d->ndim == 2 && res[2] != 1) return fail(d, PISO_EINVAL, "2D blocks need nz = 1");
+  HostBlock b;
+  b.res[0] = res[0];
+  b.res[1] = res[1];
+  b.res[2] = nz;
+  size_t nv = (size_t)(res[0] + 1) * (res[1] + 1) * (d->ndim == 3 ? nz + 1 : 1);
+  b.vertices.assign(vertices, vertices + nv * d->ndim);
+  d->blocks.push_back(std::move(b));
+  if (block_id) *block_id = (int32_t)d->blocks.size() - 1;
+  return PISO_OK;
+}
+
+static piso_status check_side(piso_domain* d, int32_t blk, int32_t side) {
+  if (!d) return fail(d, PISO_EINVAL, "NULL domain");
+  if (d->finalized) return fail(d, PISO_ESTATE, "domain already finalized");
+  if (blk < 0 || blk >= (int)d->blocks.size()) return fail(d, PISO_EINVAL, "no block %d", blk);
+  if (side < 0 || side >= 2 * d->ndim) return fail(d, PISO_EINVAL, "bad side %d", side);
+  if (d->blocks[blk].side[side].kind != 0)
+    return fail(d, PISO_EINVAL, "block %d side %d already has a boundary", blk, side);
+  return PISO_OK;
+}
+
+piso_status piso_connect(piso_domain* d, int32_t a, int32_t sa, int32_t b, int32_t sb) {
+  piso_status s = check_side(d, a, sa);
+  if (s) return s;
+  if (!(a == b && sa == sb)) {
+    s = check_side(d, b, sb);
+    if (s) return s;
+  }
+  if (sa / 2 != sb / 2 || sa % 2 == sb % 2)
+    return fail(d, PISO_EINVAL, "connections join opposite sides of the same axis");
+  const int* ra = d->blocks[a].res;
+  const int* rb = d->blocks[b].res;
+  for (int ax = 0; ax < d->ndim; ax++)
+    if (ax != sa / 2 && ra[ax] != rb[ax])
+      return fail(d, PISO_EINVAL, "connected sides need matching resolution");
+  d->blocks[a].side[sa].kind = 1;
+  d->blocks[a].side[sa].other = b;
+  d->blocks[a].side[sa].other_side = sb;
+  d->blocks[b].side[sb].kind = 1;
+  d->blocks[b].side[sb].other = a;
+  d->blocks[b].side[sb].other_side = sa;
+  return PISO_OK;
+}
+
+piso_status piso_set_dirichlet(piso_domain* d, int32_t blk, int32_t side, const double* values) {
+  piso_status s = check_side(d, blk, side);
+  if (s) return s;
+  if (!values) return fail(d, PISO_EINVAL, "values is NULL");
+  HostBlock& b = d->blocks[blk];
+  int nf = side_nfaces(b.res, side, d->ndim);
+  b.side[side].kind = 2;
+  b.side[side].values.assign(values, values + (size_t)nf * d->ndim);
+  return PISO_OK;
+}
+
+piso_status piso_set_advective_outflow(piso_domain* d, int32_t blk, int32_t side, const double* u_m,
+                                       const double* values) {
+  piso_status s = check_side(d, blk, side);
+  if (s) return s;
+  if (!values || !u_m) return fail(d, PISO_EINVAL, "NULL argument");
+  HostBlock& b = d->blocks[blk];
+  int nf = side_nfaces(b.res, side, d->ndim);
+  b.side[side].kind = 3;
+  b.side[side].values.assign(values, values + (size_t)nf * d->ndim);
+  for (int k = 0; k < d->ndim; k++) b.side[side].um[k] = u_m[k];
+  return PISO_OK;
+}
+
+static piso_status validate_options(piso_domain* d, const piso_options* o) {
+  if (o->n_correctors < 1 || o->n_correctors > 4) return fail(d, PISO_EINVAL, "n_correctors must be 1..4");
+  if (o->adv_maxit < 0 || o->p_maxit < 0) return fail(d, PISO_EINVAL, "negative iteration limit");
+  if (!(o->timeout_s > 0)) return fail(d, PISO_EINVAL, "timeout_s must be positive");
+  if (o->adv_rtol < 0 || o->p_rtol < 0 || o->atol < 0) return fail(d, PISO_EINVAL, "negative tolerance");
+  return PISO_OK;
+}
+
+piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
+  if (!d) return fail(d, PISO_EINVAL, "NULL domain");
+  if (d->finalized) return fail(d, PISO_ESTATE, "domain already finalized");
+  if (d->blocks.empty()) return fail(d, PISO_EINVAL, "domain has no blocks");
+  if (opts) {
+    piso_status s = validate_options(d, opts);
+    if (s) return s;
+    d->opts = *opts;
+  }
+  const int nd = d->ndim;
+  const int nsd = 2 * nd;
+  // sizes, offsets, boundary faces
+  std::vector<int> off(d->blocks.size() + 1, 0);
+  for (size_t b = 0; b < d->blocks.size(); b++) {
+    const int* r = d->blocks[b].res;
+    off[b + 1] = off[b] + r[0] * r[1] * r[2];
+  }
+  if ((int64_t)off.back() >= (1ll << 30)) return fail(d, PISO_EINVAL, "too many cells");
+  d->N = off.back();
+  const int32_t N = d->N;
+  DomStatic& S = d->h_static;
+  memset(&S, 0, sizeof S);
+  S.ndim = nd;
+  S.nblocks = (int)d->blocks.size();
+  S.N = N;
+  int nbf = 0, n_out = 0;
+  for (size_t b = 0; b < d->blocks.size(); b++) {
+    HostBlock& hb = d->blocks[b];
+    BlockInfo& bi = S.blk[b];
+    bi.nx = hb.res[0];
+    bi.ny = hb.res[1];
+    bi.nz = hb.res[2];
+    bi.off = off[b];
+    bi.dnx = make_fast_div(bi.nx);
+    bi.dny = make_fast_div(bi.ny);
+    for (int s = 0; s < 6; s++) {
+      bi.link[s] = -1;
+      bi.bfo[s] = 0;
+    }
+    for (int s = 0; s < nsd; s++) {
+      const SideSpec& sp = hb.side[s];
+      if (sp.kind == 0) return fail(d, PISO_EINVAL, "block %d side %d has no boundary", (int)b, s);
+      if (sp.kind == 1) {
+        bi.link[s] = sp.other;
+      } else {
+        bi.bfo[s] = nbf;
+        int nf = side_nfaces(hb.res, s, nd);
+        nbf += nf;
+        if (sp.kind == 3) n_out += nf;
+      }
+    }
+  }
+  d->nbf = nbf;
+  d->n_out = n_out;
+  S.nbf = nbf;
+  S.n_out = n_out;
+  // metrics
+  const size_t e = d->elem;
+  std::vector<char> hJ(N * e), hT((size_t)nd * nd * N * e), hA((size_t)nd * N * e);
+  for (size_t b = 0; b < d->blocks.size(); b++) {
+    const HostBlock& hb = d->blocks[b];
+    for (int z = 0; z < hb.res[2]; z++)
+      for (int y = 0; y < hb.res[1]; y++)
+        for (int x = 0; x < hb.res[0]; x++) {
+          const size_t i = off[b] + x + (size_t)hb.res[0] * (y + (size_t)hb.res[1] * z);
+          double M[3][3], Ti[3][3];
+          cell_jacobian(hb, nd, x, y, z, M);
+          const double Jv = invert(nd, M, Ti);
+          if (!(Jv > 0)) return fail(d, PISO_EINVAL, "cell %zu of block %d has non-positive volume", i, (int)b);
+          double G[3][3];
+          for (int j = 0; j < nd; j++)
+            for (int l = 0; l < nd; l++) {
+              double s = 0;
+              for (int k = 0; k < nd; k++) s += Ti[j][k] * Ti[l][k];
+              G[j][l] = Jv * s;
+            }
+          for (int j = 0; j < nd; j++)
+            for (int l = 0; l < nd; l++)
+              if (j != l && std::fabs(G[j][l]) > 1e-9 * std::max(std::fabs(G[j][j]), std::fabs(G[l][l])))
+                return fail(d, PISO_EINVAL,
+                            "non-orthogonal cell %zu: cross-diffusion metrics are not supported", i);
+          if (d->prec == PISO_FP64) {
+            put<double>(hJ, i, Jv);
+            for (int j = 0; j < nd; j++) {
+              put<double>(hA, (size_t)j * N + i, G[j][j]);
+              for (int k = 0; k < nd; k++) put<double>(hT, (size_t)(j * nd + k) * N + i, Ti[j][k]);
+            }
+          } else {
+            put<float>(hJ, i, Jv);
+            for (int j = 0; j < nd; j++) {
+              put<float>(hA, (size_t)j * N + i, G[j][j]);
+              for (int k = 0; k < nd; k++) put<float>(hT, (size_t)(j * nd + k) * N + i, Ti[j][k]);
+            }
+          }
+        }
+  }
+  // boundary-face tables
+  const int nbf1 = std::max(nbf, 1);
+  std::vector<int32_t> bf_cell(nbf1, 0);
+  std::vector<int8_t> bf_side(nbf1, 0), bf_out(nbf1, 0);
+  std::vector<char> bf_um((size_t)nd * nbf1 * e, 0), bval((size_t)nd * nbf1 * e, 0);
+  for (size_t b = 0; b < d->blocks.size(); b++) {
+    const HostBlock& hb = d->blocks[b];
+    const int nx = hb.res[0], ny = hb.res[1], nz = hb.res[2];
+    for (int s = 0; s < nsd; s++) {
+      const SideSpec& sp = hb.side[s];
+      if (sp.kind < 2) continue;
+      const int nf = side_nfaces(hb.res, s, nd);
+      for (int f = 0; f < nf; f++) {
+        int x, y, z;
+        if (s < 2) {
+          x = (s & 1) ? nx - 1 : 0;
+          y = f % ny;
+          z = f / ny;
+        } else if (s < 4) {
+          y = (s & 1) ? ny - 1 : 0;
+          x = f % nx;
+          z = f / nx;
+        } else {
+          z = (s & 1) ? nz - 1 : 0;
+          x = f % nx;
+          y = f / nx;
+        }
+        const int gf = S.blk[b].bfo[s] + f;
+        bf_cell[gf] = off[b] + x + nx * (y + ny * z);
+        bf_side[gf] = (int8_t)s;
+        bf_out[gf] = sp.kind == 3;
+        for (int k = 0; k < nd; k++) {
+          const double v = sp.values[(size_t)f * nd + k];
+          const double um = sp.kind == 3 ? sp.um[k] : 0.0;
+          if (d->prec == PISO_FP64) {
+            put<double>(bval, (size_t)k * nbf1 + gf, v);
+            put<double>(bf_um, (size_t)k * nbf1 + gf, um);
+          } else {
+            put<float>(bval, (size_t)k * nbf1 + gf, v);
+            put<float>(bf_um, (size_t)k * nbf1 + gf, um);
+          }
+        }
+      }
+    }
+  }
+  // device memory: one arena
+  Arena ar;
+  auto plan = [&](Arena& a) {
+    d->d_static = (DomStatic*)a.take(sizeof(DomStatic));
+    d->J = a.take(N * e);
+    d->T = a.take((size_t)nd * nd * N * e);
+    d->alpha = a.take((size_t)nd * N * e);
+    d->bf_cell = (int32_t*)a.take(nbf1 * sizeof(int32_t));
+    d->bf_side = (int8_t*)a.take(nbf1);
+    d->bf_out = (int8_t*)a.take(nbf1);
+    d->bf_um = a.take((size_t)nd * nbf1 * e);
+    d->bval = a.take((size_t)nd * nbf1 * e);
+    const size_t vec = (size_t)nd * N * e, sc = (size_t)N * e;
+    size_t sizes[W_COUNT] = {vec, vec, vec, vec, vec, vec, vec, vec, vec, vec, sc, vec, sc, sc, sc, sc, sc, sc, sc,
+                             sc, 2 * vec, vec, vec, vec, vec, vec, sc, sc, vec};
+    for (int k = 0; k < W_COUNT; k++) d->ws[k] = a.take(sizes[k]);
+    d->tape_ws = a.take(tape_layout(d).total);
+    d->bar = (uint32_t*)a.take(64);
+    d->status = (int32_t*)a.take(64);
+    d->istats = (int32_t*)a.take(64);
+    d->dstats = (double*)a.take(128);
+    d->d_dnu = (double*)a.take(64);
+    d->partials = (double*)a.take(sizeof(double) * 2 * NSMAX * MAXCTA);
+  };
+  plan(ar);
+  d->dmem_bytes = ar.used;
+  if (cudaMalloc((void**)&d->dmem, d->dmem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(d, PISO_ENOMEM, "cudaMalloc of %zu bytes failed", d->dmem_bytes);
+  }
+  Arena real_ar;
+  real_ar.base = d->dmem;
+  plan(real_ar);
+  CUDA_TRY(d, cudaMemset(d->dmem, 0, d->dmem_bytes));
+  S.J = d->J;
+  S.T = d->T;
+  S.alpha = d->alpha;
+  S.bf_cell = d->bf_cell;
+  S.bf_side = d->bf_side;
+  S.bf_out = d->bf_out;
+  S.bf_um = d->bf_um;
+  CUDA_TRY(d, cudaMemcpy(d->d_static, &S, sizeof S, cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(d->J, hJ.data(), hJ.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(d->T, hT.data(), hT.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(d->alpha, hA.data(), hA.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(d->bf_cell, bf_cell.data(), nbf1 * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(d->bf_side, bf_side.data(), nbf1, cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(d->bf_out, bf_out.data(), nbf1, cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(d->bf_um, bf_um.data(), bf_um.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(d->bval, bval.data(), bval.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMallocHost((void**)&d->h_status, 64));
+  CUDA_TRY(d, cudaMallocHost((void**)&d->h_istats, 64));
+  CUDA_TRY(d, cudaMallocHost((void**)&d->h_dstats, 128));
+  CUDA_TRY(d, cudaMallocHost((void**)&d->h_dnu, 64));
+  piso_status s = choose_shape(d);
+  if (s) return s;
+  d->finalized = true;
+  return PISO_OK;
+}
+
+piso_status piso_set_options(piso_domain* d, const piso_options* opts) {
+  if (!d || !opts) return fail(d, PISO_EINVAL, "NULL argument");
+  piso_status s = validate_options(d, opts);
+  if (s) return s;
+  d->opts = *opts;
+  if (d->finalized) return choose_shape(d);
+  return PISO_OK;
+}
+
+int64_t piso_num_cells(const piso_domain* d) { return d ? d->N : -1; }
+int32_t piso_num_boundary_faces(const piso_domain* d) { return d ? d->nbf : -1; }
+
+size_t piso_tape_bytes(const piso_domain* d) {
+  if (!d || !d->finalized) return 0;
+  return tape_layout(d).total;
+}
+
+piso_status piso_step(piso_domain* d, const void* u_in, const void* p_in, void* u_out, void* p_out, double dt,
+                      double nu, const void* S, void* tape, void* stream, piso_stats* stats) {
+  if (!d) return fail(d, PISO_EINVAL, "NULL domain");
+  if (!d->finalized) return fail(d, PISO_ESTATE, "step before finalize");
+  if (!u_in || !p_in || !u_out || !p_out) return fail(d, PISO_EINVAL, "NULL field pointer");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(d, PISO_EINVAL, "dt must be positive and finite");
+  if (!(nu >= 0) || !std::isfinite(nu)) return fail(d, PISO_EINVAL, "nu must be non-negative and finite");
+  cudaStream_t st = (cudaStream_t)stream;
+  piso_status s = d->prec == PISO_FP64 ? launch_fwd<double>(d, u_in, p_in, u_out, p_out, dt, nu, S, tape, st)
+                                       : launch_fwd<float>(d, u_in, p_in, u_out, p_out, dt, nu, S, tape, st);
+  if (s) return s;
+  s = enqueue_readback(d, st);
+  if (s) return s;
+  d->pending = true;
+  d->pending_kind = 1;
+  d->pending_stream = st;
+  if (stats) return collect_stats(d, stats);
+  return PISO_OK;
+}
+
+piso_status piso_last_stats(piso_domain* d, piso_stats* stats) {
+  if (!d) return fail(d, PISO_EINVAL, "NULL domain");
+  if (!d->pending) {
+    if (stats) memset(stats, 0, sizeof *stats);
+    return fail(d, PISO_ESTATE, "no step pending");
+  }
+  return collect_stats(d, stats);
+}
+
+piso_status piso_get_boundary(piso_domain* d, double* values) {
+  if (!d || !values) return fail(d, PISO_EINVAL, "NULL argument");
+  if (!d->finalized) return fail(d, PISO_ESTATE, "domain not finalized");
+  const int nbf1 = std::max(d->nbf, 1);
+  std::vector<char> buf((size_t)d->ndim * nbf1 * d->elem);
+  CUDA_TRY(d, cudaDeviceSynchronize());
+  CUDA_TRY(d, cudaMemcpy(buf.data(), d->bval, buf.size(), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < d->ndim; k++)
+    for (int f = 0; f < d->nbf; f++) {
+      size_t i = (size_t)k * nbf1 + f;
+      values[(size_t)k * d->nbf + f] = d->prec == PISO_FP64 ? ((double*)buf.data())[i] : ((float*)buf.data())[i];
+    }
+  return PISO_OK;
+}
+
+piso_status piso_set_boundary(piso_domain* d, const double* values) {
+  if (!d || !values) return fail(d, PISO_EINVAL, "NULL argument");
+  if (!d->finalized) return fail(d, PISO_ESTATE, "domain not finalized");
+  const int nbf1 = std::max(d->nbf, 1);
+  std::vector<char> buf((size_t)d->ndim * nbf1 * d->elem, 0);
+  for (int k = 0; k < d->ndim; k++)
+    for (int f = 0; f < d->nbf; f++) {
+      size_t i = (size_t)k * nbf1 + f;
+      double v = values[(size_t)k * d->nbf + f];
+      if (d->prec == PISO_FP64) ((double*)buf.data())[i] = v;
+      else ((float*)buf.data())[i] = (float)v;
+    }
+  CUDA_TRY(d, cudaDeviceSynchronize());
+  CUDA_TRY(d, cudaMemcpy(d->bval, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+  return PISO_OK;
+}
+
+const char* piso_last_error(const piso_domain* d) { return d ? d->err.c_str() : g_create_error.c_str(); }
+
+void piso_domain_destroy(piso_domain* d) {
+  if (!d) return;
+  if (d->dmem) cudaFree(d->dmem);
+  if (d->h_status) cudaFreeHost(d->h_status);
+  if (d->h_istats) cudaFreeHost(d->h_istats);
+  if (d->h_dstats) cudaFreeHost(d->h_dstats);
+  if (d->h_dnu) cudaFreeHost(d->h_dnu);
+  delete d;
+}
+
+}  // extern "C"
+
+#include "piso_capi_adjoint.inc"
+#include "piso_capi_batch.inc"

@@ -1,0 +1,299 @@
+// Device-side building blocks of the persistent PISO kernels (sm_103a).
+//
+// A launch runs one or more *groups*; a group is one simulation domain (the
+// multi-block grid of Sec. 2.2 of arXiv:2505.16992) owned by a contiguous set
+// of co-resident CTAs.  Each CTA of a group owns a contiguous range of the
+// domain's cells and walks the whole PISO step phase by phase; phases are
+// separated by a group-wide barrier with a bounded wait, and every Krylov dot
+// product is reduced deterministically (fixed tree, fixed order, no float
+// atomics), so reruns are bit-identical and every CTA of a group takes the same
+// control-flow decisions from the same reduced scalars.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PISO_ERR_NOCONV_ADV 1
+#define PISO_ERR_NOCONV_P 2
+#define PISO_ERR_BREAKDOWN 4
+#define PISO_ERR_NAN 8
+#define PISO_ERR_TIMEOUT 16
+
+namespace piso {
+
+constexpr int MAXB = 16;     // blocks per domain
+constexpr int NSMAX = 12;    // scalars per reduction
+constexpr int MAXG = 128;    // groups (domains) per launch
+constexpr int MAXW = 32;     // warps per CTA
+constexpr int MAXCTA = 1024; // CTAs per group (size of the partials rows)
+
+// ---------------------------------------------------------------------------
+// division by a run-time invariant (Granlund & Montgomery 1994, round-up
+// multiplier): q = (umulhi(n, m) + n) >> s, valid for n, d < 2^31.
+// ---------------------------------------------------------------------------
+struct FastDiv {
+  uint32_t m, s;
+};
+
+__host__ __device__ inline uint32_t fast_div(uint32_t n, FastDiv f) {
+#ifdef __CUDA_ARCH__
+  uint32_t t = __umulhi(n, f.m);
+#else
+  uint32_t t = (uint32_t)(((uint64_t)n * f.m) >> 32);
+#endif
+  return (t + n) >> f.s;
+}
+
+inline FastDiv make_fast_div(uint32_t d) {
+  uint32_t s = 0;
+  while ((1ull << s) < d) s++;
+  uint64_t m = (((1ull << 32) * ((1ull << s) - d)) / d) + 1;
+  return FastDiv{(uint32_t)m, s};
+}
+
+// ---------------------------------------------------------------------------
+// static description of one domain (uploaded once at finalize)
+// ---------------------------------------------------------------------------
+struct BlockInfo {
+  int32_t nx, ny, nz, off;   // resolution and first cell (domain index)
+  int32_t link[6];           // >= 0: block joined at this side (its opposite side); -1: boundary faces
+  int32_t bfo[6];            // first boundary face of this side (when link < 0)
+  FastDiv dnx, dny;
+};
+
+struct DomStatic {
+  int32_t ndim, nblocks, N, nbf;
+  int32_t n_out;             // number of advective-outflow faces
+  BlockInfo blk[MAXB];
+  // per-cell metrics, storage precision (void*: float or double)
+  const void* J;             // [N]
+  const void* T;             // [d*d][N], T[(j*d+k)*N + i] = d xi^j / d x_k
+  const void* alpha;         // [d][N]  alpha_jj = J T_j . T_j
+  // boundary faces
+  const int32_t* bf_cell;    // [nbf] adjacent cell
+  const int8_t* bf_side;     // [nbf] side of that cell
+  const int8_t* bf_out;      // [nbf] 1 if advective outflow
+  const void* bf_um;         // [d][nbf] outflow characteristic velocity (0 elsewhere)
+};
+
+// ---------------------------------------------------------------------------
+// cell location and neighbour lookup (App. A.3: a connection only changes the
+// neighbour lookup).  Neighbour >= 0 is a cell of the domain; a negative value
+// -1-f names boundary face f.
+// ---------------------------------------------------------------------------
+struct Cell {
+  int32_t i, b, x, y, z;
+  int32_t nb[6];
+};
+
+__device__ __forceinline__ int32_t side_nbr(const DomStatic& D, const BlockInfo& B, int32_t i,
+                                            int32_t x, int32_t y, int32_t z, int s) {
+  switch (s) {
+    case 0: if (x > 0) return i - 1; break;
+    case 1: if (x < B.nx - 1) return i + 1; break;
+    case 2: if (y > 0) return i - B.nx; break;
+    case 3: if (y < B.ny - 1) return i + B.nx; break;
+    case 4: if (z > 0) return i - B.nx * B.ny; break;
+    default: if (z < B.nz - 1) return i + B.nx * B.ny; break;
+  }
+  const int32_t t = B.link[s];
+  if (t >= 0) {
+    const BlockInfo& O = D.blk[t];
+    switch (s) {
+      case 0: return O.off + (O.nx - 1) + O.nx * (y + O.ny * z);
+      case 1: return O.off + O.nx * (y + O.ny * z);
+      case 2: return O.off + x + O.nx * ((O.ny - 1) + O.ny * z);
+      case 3: return O.off + x + O.nx * (O.ny * z);
+      case 4: return O.off + x + O.nx * (y + O.ny * (O.nz - 1));
+      default: return O.off + x + O.nx * y;
+    }
+  }
+  int32_t f;
+  if (s < 2) f = y + B.ny * z;
+  else if (s < 4) f = x + B.nx * z;
+  else f = x + B.nx * y;
+  return -1 - (B.bfo[s] + f);
+}
+
+template <int ND>
+__device__ __forceinline__ Cell locate(const DomStatic& D, int32_t i) {
+  Cell c;
+  c.i = i;
+  int b = 0;
+  while (b + 1 < D.nblocks && i >= D.blk[b + 1].off) b++;
+  const BlockInfo& B = D.blk[b];
+  c.b = b;
+  const uint32_t li = (uint32_t)(i - B.off);
+  const uint32_t q = fast_div(li, B.dnx);
+  c.x = (int32_t)(li - q * (uint32_t)B.nx);
+  if (ND == 3) {
+    const uint32_t zz = fast_div(q, B.dny);
+    c.z = (int32_t)zz;
+    c.y = (int32_t)(q - zz * (uint32_t)B.ny);
+  } else {
+    c.y = (int32_t)q;
+    c.z = 0;
+  }
+#pragma unroll
+  for (int s = 0; s < 2 * ND; s++) c.nb[s] = side_nbr(D, B, i, c.x, c.y, c.z, s);
+  return c;
+}
+
+__device__ __forceinline__ int32_t safe(int32_t nb, int32_t self) { return nb >= 0 ? nb : self; }
+
+// ---------------------------------------------------------------------------
+// accumulators: FP64 mode sums in double; the FP32 mode sums in a float pair
+// (TwoSum / FMA-TwoProd, Knuth and Dekker), which carries ~48 significant bits
+// on the FP32 pipe (B300's FP64 pipe is a small fraction of its FP32 rate).
+// ---------------------------------------------------------------------------
+struct f2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  f2 r;
+  two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+template <typename real>
+struct Acc;
+
+template <>
+struct Acc<double> {
+  double v;
+  __device__ __forceinline__ void zero() { v = 0.0; }
+  __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ void add(double a) { v += a; }
+  __device__ __forceinline__ void shfl_down_add(int off) { v += __shfl_down_sync(0xffffffffu, v, off); }
+  __device__ __forceinline__ double to_double() const { return v; }
+};
+
+template <>
+struct Acc<float> {
+  f2 v;
+  __device__ __forceinline__ void zero() { v.hi = 0.f; v.lo = 0.f; }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    f2 t{p, pe};
+    v = f2_add(v, t);
+  }
+  __device__ __forceinline__ void add(float a) { v = f2_add(v, f2{a, 0.f}); }
+  __device__ __forceinline__ void shfl_down_add(int off) {
+    f2 o{__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
+    v = f2_add(v, o);
+  }
+  __device__ __forceinline__ double to_double() const { return (double)v.hi + (double)v.lo; }
+};
+
+// ---------------------------------------------------------------------------
+// group barrier (bounded wait) and deterministic group reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+struct Group {
+  uint32_t* bar;        // monotone arrival counter, zeroed before the launch
+  double* partials;     // [2][NSMAX][ncta]
+  int32_t* status;      // error bits of this group
+  int32_t ncta, rank;
+  uint32_t epoch;
+  uint64_t timeout_ns;
+};
+
+// Returns false (and every CTA of the group leaves its phase loop) when the
+// wait ran out or another CTA of the group reported a timeout.
+__device__ __noinline__ bool group_sync(Group& g) {
+  __shared__ int s_ok;
+  __syncthreads();
+  g.epoch++;                 // every thread keeps the same count (it selects the partials buffer)
+  if (threadIdx.x == 0) {
+    const uint32_t target = g.epoch * (uint32_t)g.ncta;
+    __threadfence();
+    atomicAdd(g.bar, 1u);
+    int ok = 1;
+    if ((int32_t)(ld_acquire_u32(g.bar) - target) < 0) {
+      const uint64_t t0 = global_ns();
+      while (true) {
+        if ((int32_t)(ld_acquire_u32(g.bar) - target) >= 0) break;
+        if (*((volatile int32_t*)g.status) & PISO_ERR_TIMEOUT) { ok = 0; break; }
+        if (global_ns() - t0 > g.timeout_ns) {
+          atomicOr(g.status, PISO_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Block-reduce NS accumulators and publish this CTA's partials for the next
+// barrier.  Must be called by all threads of the CTA.
+template <typename real, int NS>
+__device__ __forceinline__ void publish(const Group& g, Acc<real> (&a)[NS]) {
+  __shared__ double s_w[MAXW][NSMAX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NS; k++) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a[k].shfl_down_add(off);
+    if (lane == 0) s_w[warp][k] = a[k].to_double();
+  }
+  __syncthreads();
+  if (threadIdx.x < NS) {
+    double s = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; w++) s += s_w[w][threadIdx.x];
+    const int par = (g.epoch + 1) & 1;
+    g.partials[((size_t)par * NSMAX + threadIdx.x) * g.ncta + g.rank] = s;
+  }
+}
+
+// After the barrier: the group totals, summed in a fixed order (identical in
+// every CTA of the group).
+template <int NS>
+__device__ __forceinline__ void gather(const Group& g, double (&out)[NS]) {
+  __shared__ double s_r[NSMAX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int par = g.epoch & 1;
+  const int nw = blockDim.x >> 5;
+  for (int k = warp; k < NS; k += nw) {
+    const double* src = g.partials + ((size_t)par * NSMAX + k) * g.ncta;
+    double s = 0.0;
+    for (int c = lane; c < g.ncta; c += 32) s += __ldcg(src + c);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) s_r[k] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NS; k++) out[k] = s_r[k];
+  __syncthreads();
+}
+
+template <typename real>
+__device__ __forceinline__ real ld(const real* p, int64_t i) { return p[i]; }
+
+}  // namespace piso

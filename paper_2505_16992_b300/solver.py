@@ -1,0 +1,262 @@
+"""PyTorch-facing wrapper of the C ABI: domains, steps, adjoints, batches and a
+differentiable rollout (arXiv:2505.16992, Sec. 2.3: discretise-then-optimise
+through the PISO step with solve adjoints; App. A.5: fields are PyTorch
+tensors).  Every numerical step runs in the CUDA library; this module only
+marshals arguments.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import capi
+
+_DT = {capi.PISO_FP64: torch.float64, capi.PISO_FP32: torch.float32}
+
+
+def _prec(precision) -> int:
+    if precision in (capi.PISO_FP64, "fp64", torch.float64):
+        return capi.PISO_FP64
+    if precision in (capi.PISO_FP32, "fp32", torch.float32):
+        return capi.PISO_FP32
+    raise ValueError(f"unknown precision {precision}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+class Domain:
+    """A multi-block domain (App. A.5 Domain/Block/Boundary) living on cuda:0."""
+
+    def __init__(self, ndim: int, precision="fp64"):
+        self.lib = capi.load()
+        self.ndim = ndim
+        self.prec = _prec(precision)
+        self.dtype = _DT[self.prec]
+        h = C.c_void_p()
+        capi.check(self.lib.piso_domain_create(ndim, self.prec, C.byref(h)))
+        self.h = h
+        self.finalized = False
+
+    # -- description -----------------------------------------------------------
+    def add_block(self, res, vertices) -> int:
+        r = (C.c_int32 * 3)(*[int(v) for v in res])
+        _, vp = capi.dbuf(vertices)
+        bid = C.c_int32()
+        capi.check(self.lib.piso_block_add(self.h, r, vp, C.byref(bid)), self.h)
+        return bid.value
+
+    def connect(self, a, sa, b, sb):
+        capi.check(self.lib.piso_connect(self.h, a, sa, b, sb), self.h)
+
+    def set_dirichlet(self, blk, side, values):
+        _, vp = capi.dbuf(values)
+        capi.check(self.lib.piso_set_dirichlet(self.h, blk, side, vp), self.h)
+
+    def set_advective_outflow(self, blk, side, u_m, values):
+        _, up = capi.dbuf(u_m)
+        _, vp = capi.dbuf(values)
+        capi.check(self.lib.piso_set_advective_outflow(self.h, blk, side, up, vp), self.h)
+
+    def finalize(self, options: Optional[capi.Options] = None, **kw):
+        o = options if options is not None else capi.default_options(**kw)
+        capi.check(self.lib.piso_finalize(self.h, C.byref(o)), self.h)
+        self.finalized = True
+        self.N = int(self.lib.piso_num_cells(self.h))
+        self.nbf = int(self.lib.piso_num_boundary_faces(self.h))
+        self.tape_bytes = int(self.lib.piso_tape_bytes(self.h))
+        return self
+
+    def set_options(self, options: Optional[capi.Options] = None, **kw):
+        o = options if options is not None else capi.default_options(**kw)
+        capi.check(self.lib.piso_set_options(self.h, C.byref(o)), self.h)
+
+    @classmethod
+    def from_case(cls, case, precision="fp64", options=None, **kw) -> "Domain":
+        """Build from an object with ndim/blocks/connections/dirichlet/outflow
+        (the seeded input generators produce such objects)."""
+        d = cls(case.ndim, precision)
+        for b in case.blocks:
+            d.add_block(b.res, b.vertices)
+        for (a, sa, b2, sb) in case.connections:
+            d.connect(a, sa, b2, sb)
+        for (blk, s, vals) in case.dirichlet:
+            d.set_dirichlet(blk, s, vals)
+        for (blk, s, um, vals) in case.outflow:
+            d.set_advective_outflow(blk, s, um, vals)
+        return d.finalize(options, **kw)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.lib.piso_domain_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    # -- fields -----------------------------------------------------------------
+    def field(self, values=None, components: Optional[int] = None) -> torch.Tensor:
+        shape = (self.N,) if components is None else (components, self.N)
+        if values is None:
+            return torch.zeros(shape, dtype=self.dtype, device="cuda")
+        t = torch.as_tensor(np.asarray(values), dtype=self.dtype)
+        return t.reshape(shape).contiguous().cuda()
+
+    def new_tape(self) -> torch.Tensor:
+        return torch.empty(self.tape_bytes, dtype=torch.uint8, device="cuda")
+
+    def _check_field(self, t, comps, name):
+        if t is None:
+            return
+        want = (self.N,) if comps is None else (comps, self.N)
+        if t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != want:
+            raise ValueError(f"{name} must be a contiguous cuda {self.dtype} tensor of shape {want}")
+
+    # -- step ---------------------------------------------------------------------
+    def step(self, u, p, dt, nu, S=None, tape=None, u_out=None, p_out=None, stream=None, sync=True):
+        """One PISO step; returns (u_new, p_new, stats-dict or None)."""
+        d = self.ndim
+        self._check_field(u, d, "u")
+        self._check_field(p, None, "p")
+        self._check_field(S, d, "S")
+        u_out = torch.empty_like(u) if u_out is None else u_out
+        p_out = torch.empty_like(p) if p_out is None else p_out
+        st = capi.Stats() if sync else None
+        rc = self.lib.piso_step(self.h, capi.dptr(u), capi.dptr(p), capi.dptr(u_out), capi.dptr(p_out),
+                                float(dt), float(nu), capi.dptr(S), capi.dptr(tape), _stream_ptr(stream),
+                                C.byref(st) if st is not None else None)
+        capi.check(rc, self.h)
+        return u_out, p_out, (st.as_dict() if st is not None else None)
+
+    def last_stats(self):
+        st = capi.Stats()
+        rc = self.lib.piso_last_stats(self.h, C.byref(st))
+        capi.check(rc, self.h)
+        return st.as_dict()
+
+    def step_adjoint(self, du_out, dp_out=None, tape=None, stream=None, want=("u", "p", "S", "nu")):
+        """Adjoint of the last (or taped) step: returns (du_in, dp_in, dS, dnu)."""
+        d = self.ndim
+        du_in = torch.empty((d, self.N), dtype=self.dtype, device="cuda") if "u" in want else None
+        dp_in = torch.empty((self.N,), dtype=self.dtype, device="cuda") if "p" in want else None
+        dS = torch.empty((d, self.N), dtype=self.dtype, device="cuda") if "S" in want else None
+        dnu = C.c_double(0.0)
+        st = capi.Stats()
+        rc = self.lib.piso_step_adjoint(self.h, capi.dptr(tape), capi.dptr(du_out), capi.dptr(dp_out),
+                                        capi.dptr(du_in), capi.dptr(dp_in), capi.dptr(dS),
+                                        C.byref(dnu) if "nu" in want else None, _stream_ptr(stream),
+                                        C.byref(st))
+        capi.check(rc, self.h)
+        return du_in, dp_in, dS, dnu.value, st.as_dict()
+
+    def get_boundary(self) -> np.ndarray:
+        out = np.zeros((self.ndim, max(self.nbf, 0)))
+        capi.check(self.lib.piso_get_boundary(self.h, out.ctypes.data_as(C.POINTER(C.c_double))), self.h)
+        return out
+
+    def set_boundary(self, values):
+        a, vp = capi.dbuf(values)
+        capi.check(self.lib.piso_set_boundary(self.h, vp), self.h)
+
+
+class Batch:
+    """Independent domains stepped together in one persistent launch."""
+
+    def __init__(self, domains: Sequence[Domain], options: Optional[capi.Options] = None, **kw):
+        self.lib = capi.load()
+        self.domains = list(domains)
+        arr = (C.c_void_p * len(domains))(*[d.h.value for d in domains])
+        o = options if options is not None else capi.default_options(**kw)
+        h = C.c_void_p()
+        capi.check(self.lib.piso_batch_create(arr, len(domains), C.byref(o), C.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.lib.piso_batch_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    @staticmethod
+    def _ptrs(ts):
+        return (C.c_void_p * len(ts))(*[capi.dptr(t) for t in ts])
+
+    def step(self, us, ps, dts, nus, Ss=None, u_out=None, p_out=None, stream=None, sync=True):
+        n = len(self.domains)
+        u_out = [torch.empty_like(u) for u in us] if u_out is None else u_out
+        p_out = [torch.empty_like(p) for p in ps] if p_out is None else p_out
+        Ss = [None] * n if Ss is None else Ss
+        dt = (C.c_double * n)(*dts)
+        nu = (C.c_double * n)(*nus)
+        st = (capi.Stats * n)() if sync else None
+        rc = self.lib.piso_batch_step(self.h, self._ptrs(us), self._ptrs(ps), self._ptrs(u_out),
+                                      self._ptrs(p_out), dt, nu, self._ptrs(Ss), _stream_ptr(stream),
+                                      st if st is not None else None)
+        capi.check(rc, None)
+        return u_out, p_out, ([s.as_dict() for s in st] if st is not None else None)
+
+    def step_adjoint(self, du_out, dp_out=None, stream=None):
+        n = len(self.domains)
+        dp_out = [None] * n if dp_out is None else dp_out
+        du_in = [torch.empty_like(g) for g in du_out]
+        dp_in = [torch.empty((d.N,), dtype=d.dtype, device="cuda") for d in self.domains]
+        dS = [torch.empty_like(g) for g in du_out]
+        dnu = (C.c_double * n)()
+        st = (capi.Stats * n)()
+        rc = self.lib.piso_batch_step_adjoint(self.h, self._ptrs(du_out), self._ptrs(dp_out),
+                                              self._ptrs(du_in), self._ptrs(dp_in), self._ptrs(dS), dnu,
+                                              _stream_ptr(stream), st)
+        capi.check(rc, None)
+        return du_in, dp_in, dS, list(dnu), [s.as_dict() for s in st]
+
+
+class PisoStepFunction(torch.autograd.Function):
+    """u^{n+1}, p^{n+1} = PISO(u^n, p^n, S, nu) with the hand-written adjoint.
+
+    The forward keeps only (u^n, p^n, S, nu) (checkpoint); backward recomputes
+    the step into the domain's own tape and runs the adjoint kernel on it."""
+
+    @staticmethod
+    def forward(ctx, u, p, S, nu, domain: Domain, dt: float):
+        nu_f = float(nu)
+        u1, p1, _ = domain.step(u.detach().contiguous(), p.detach().contiguous(), dt, nu_f,
+                                None if S is None else S.detach().contiguous(), sync=False)
+        ctx.domain, ctx.dt, ctx.nu = domain, dt, nu_f
+        ctx.has_S = S is not None
+        ctx.nu_is_tensor = torch.is_tensor(nu)
+        ctx.save_for_backward(u.detach(), p.detach(), S.detach() if S is not None else None)
+        return u1, p1
+
+    @staticmethod
+    def backward(ctx, gu, gp):
+        u, p, S = ctx.saved_tensors
+        dom = ctx.domain
+        # recompute the step internals into the domain's workspace tape
+        dom.step(u.contiguous(), p.contiguous(), ctx.dt, ctx.nu, S, sync=False)
+        gu = torch.zeros_like(u) if gu is None else gu.contiguous()
+        gp = None if gp is None else gp.contiguous()
+        du, dp, dS, dnu, _ = dom.step_adjoint(gu, gp)
+        gnu = torch.tensor(dnu, dtype=u.dtype, device=u.device) if ctx.nu_is_tensor else None
+        return du, dp, (dS if ctx.has_S else None), gnu, None, None
+
+
+def piso_step(domain: Domain, u, p, dt, nu, S=None):
+    """Differentiable PISO step (checkpointed: internals recomputed in backward)."""
+    return PisoStepFunction.apply(u, p, S, nu, domain, dt)
+
+
+def rollout(domain: Domain, u, p, dt, nu, steps: int, source_fn=None):
+    """Differentiable rollout of ``steps`` PISO steps.  source_fn(u) -> S lets a
+    learned corrector enter as the source term (Sec. 3)."""
+    for _ in range(steps):
+        S = source_fn(u) if source_fn is not None else None
+        u, p = piso_step(domain, u, p, dt, nu, S)
+    return u, p

@@ -1,0 +1,47 @@
+"""Helpers shared by the GPU parity tests (CUDA path vs the FP64 oracle)."""
+import numpy as np
+import torch
+
+import oracle as O
+from paper_2505_16992_b300 import capi
+from paper_2505_16992_b300.solver import Domain
+
+FP64_REL = 1e-10     # per-step FP64 parity bar (relative to the field's max)
+FP32_REL = 1e-4      # mixed precision on laminar fields
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    scale = max(np.abs(b).max(), 1e-300)
+    return float(np.abs(a - b).max() / scale)
+
+
+def gpu_domain(case, precision="fp64", **opts):
+    o = capi.default_options(**opts)
+    return Domain.from_case(case, precision, o)
+
+
+def to_dev(dom, arr, comps=None):
+    return dom.field(arr, comps)
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def gpu_step(dom, case, u, p, S=None, **kw):
+    d = case.ndim
+    ut = to_dev(dom, u, d)
+    pt = to_dev(dom, p)
+    St = None if S is None else to_dev(dom, S, d)
+    u1, p1, st = dom.step(ut, pt, case.dt, case.nu, St, **kw)
+    return host(u1), host(p1), st
+
+
+def oracle_step(mesh, case, u, p, S=None, bval=None, opts=None):
+    return O.piso_step(mesh, u, p, case.dt, case.nu, S, bval, opts)
+
+
+def sync():
+    torch.cuda.synchronize()

@@ -1,0 +1,190 @@
+"""GPU forward PISO step vs the FP64 oracle (element-wise parity), through the
+C ABI.  Cases follow the paper's scenarios at the benchmark configurations'
+sizes plus small ragged ones (arXiv:2505.16992, App. A-B)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2505_16992_b300 import capi
+from paper_2505_16992_b300 import workloads as W
+from gpu_util import FP32_REL, FP64_REL, gpu_domain, gpu_step, host, oracle_step, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _per_step_parity(case, steps, precision="fp64", tol=FP64_REL, **opts):
+    """Advance the oracle; at each step run the GPU step from the oracle's
+    state and compare u, p (and outflow boundary values)."""
+    m = O.mesh_from_case(case)
+    dom = gpu_domain(case, precision, **opts)
+    u, p, bval = case.u0, case.p0, m.bval
+    worst = 0.0
+    for n in range(steps):
+        ug, pg, st = gpu_step(dom, case, u, p, case.S)
+        assert st["status"] == "PISO_OK", st
+        u1, p1, tape = oracle_step(m, case, u, p, case.S, bval)
+        eu, ep = rel_err(ug, u1), rel_err(pg, p1)
+        worst = max(worst, eu, ep)
+        assert eu <= tol and ep <= tol * 10, (n, eu, ep, st)
+        u, p, bval = u1, p1, tape["bval"]
+        # keep the domain's boundary state in step with the oracle's
+        if m.has_outflow:
+            dom.set_boundary(_bval_faces(m, bval))
+    return worst
+
+
+def _bval_faces(m, bval):
+    """Oracle boundary values (per cell side) -> the library's face order."""
+    faces = []
+    # library order: blocks in order, sides in order, faces in side order
+    for bi in range(len(m.res)):
+        for s in range(m.nsides):
+            cells = m.side_cells(bi, s)
+            if m.is_bface[s, cells[0]]:
+                faces.append(bval[s][:, cells])
+    return np.concatenate(faces, axis=1)
+
+
+def test_cavity_config1_per_step():
+    c = W.cavity2d(32)
+    _per_step_parity(c, 4)
+
+
+def test_cavity_config1_rollout():
+    """Config 1 (32x32 cavity, Re 100, dt 0.005) over 50 steps."""
+    c = W.cavity2d(32)
+    m = O.mesh_from_case(c)
+    dom = gpu_domain(c)
+    u, p = to_dev(dom, c.u0, 2), to_dev(dom, c.p0)
+    for _ in range(50):
+        u, p, st = dom.step(u, p, c.dt, c.nu)
+        assert st["status"] == "PISO_OK"
+    uo, po, _ = O.rollout(m, c.u0, c.p0, c.dt, c.nu, None, 50)
+    assert rel_err(host(u), uo) <= 1e-9
+    assert rel_err(host(p), po) <= 1e-8
+
+
+@pytest.mark.parametrize("n", [(5, 3), (13, 7), (33, 17)])
+def test_ragged_cavity(n):
+    c = W.cavity2d(n[0])
+    v = np.linspace(0, 1, n[0] + 1)
+    c.blocks[0] = W.rect_block(v, np.linspace(0, 0.6, n[1] + 1))
+    N = n[0] * n[1]
+    c.dirichlet = []
+    for s in range(4):
+        val = W.wall(c.blocks[0], s, 2)
+        if s == 3:
+            val[:, 0] = 1.0
+        c.dirichlet.append((0, s, val))
+    c.u0, c.p0 = np.zeros((2, N)), np.zeros(N)
+    _per_step_parity(c, 2)
+
+
+def test_bfs_multiblock_outflow_small():
+    c = W.bfs2d(n_in=(16, 8), n_ch=64, n_out=16, half=8, dt=0.02)
+    _per_step_parity(c, 3)
+
+
+def test_bfs_config2_full_size():
+    c = W.bfs2d()
+    assert c.ncells == 22528
+    _per_step_parity(c, 2)
+
+
+def test_channel3d_small():
+    c = W.channel3d(16, 12, 8)
+    _per_step_parity(c, 3)
+
+
+def test_channel3d_config3_full_size():
+    c = W.channel3d()
+    assert c.ncells == 64 * 48 * 32
+    _per_step_parity(c, 1)
+
+
+def test_turbulence2d_periodic():
+    c = W.turbulence2d(64)
+    _per_step_parity(c, 2)
+
+
+def test_cavity3d_ragged():
+    c = W.cavity3d(5, nz=3)
+    _per_step_parity(c, 2)
+
+
+@pytest.mark.parametrize("ctas", [1, 3, 7, 64])
+def test_cta_counts_agree(ctas):
+    """The result does not depend on how the cells are split over CTAs beyond
+    summation order."""
+    c = W.channel3d(12, 10, 6)
+    m = O.mesh_from_case(c)
+    u1, p1, _ = oracle_step(m, c, c.u0, c.p0, c.S)
+    dom = gpu_domain(c, ctas=ctas, block_threads=128)
+    ug, pg, st = gpu_step(dom, c, c.u0, c.p0, c.S)
+    assert rel_err(ug, u1) <= FP64_REL
+    assert rel_err(pg, p1) <= 10 * FP64_REL
+
+
+def test_bitwise_deterministic():
+    c = W.channel3d(16, 12, 8)
+    dom = gpu_domain(c)
+    a = gpu_step(dom, c, c.u0, c.p0, c.S)
+    b = gpu_step(dom, c, c.u0, c.p0, c.S)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_in_place_aliasing():
+    c = W.cavity2d(16)
+    m = O.mesh_from_case(c)
+    dom = gpu_domain(c)
+    u, p = to_dev(dom, c.u0, 2), to_dev(dom, c.p0)
+    u1, p1, _ = dom.step(u, p, c.dt, c.nu, u_out=u, p_out=p)
+    uo, po, _ = oracle_step(m, c, c.u0, c.p0)
+    assert u1.data_ptr() == u.data_ptr()
+    assert rel_err(host(u), uo) <= FP64_REL
+
+
+def test_fp32_mixed_laminar_cavity():
+    """Mixed precision against the FP64 oracle on a laminar flow after N steps."""
+    c = W.cavity2d(32)
+    m = O.mesh_from_case(c)
+    dom = gpu_domain(c, "fp32", adv_rtol=1e-6, p_rtol=1e-6)
+    u, p = to_dev(dom, c.u0, 2), to_dev(dom, c.p0)
+    for _ in range(50):
+        u, p, st = dom.step(u, p, c.dt, c.nu)
+        assert st["status"] == "PISO_OK", st
+    uo, po, _ = O.rollout(m, c.u0, c.p0, c.dt, c.nu, None, 50)
+    assert rel_err(host(u), uo) <= FP32_REL
+
+
+def test_fp32_mixed_channel3d():
+    c = W.channel3d(16, 12, 8)
+    m = O.mesh_from_case(c)
+    dom = gpu_domain(c, "fp32", adv_rtol=1e-6, p_rtol=1e-6)
+    ug, pg, st = gpu_step(dom, c, c.u0, c.p0, c.S)
+    uo, po, _ = oracle_step(m, c, c.u0, c.p0, c.S)
+    assert st["status"] == "PISO_OK"
+    assert rel_err(ug, uo) <= FP32_REL
+
+
+def test_errors_reported_not_trapped():
+    c = W.cavity2d(16)
+    dom = gpu_domain(c, p_maxit=1)
+    u, p = to_dev(dom, c.u0, 2), to_dev(dom, c.p0)
+    with pytest.raises(capi.PisoError) as e:
+        dom.step(u, p, c.dt, c.nu)
+    assert e.value.status == 3          # PISO_ENOCONV
+    with pytest.raises(capi.PisoError) as e:
+        dom.step(u, p, -1.0, c.nu)
+    assert e.value.status == 1          # PISO_EINVAL
+    dom.set_options(capi.default_options())
+    S = to_dev(dom, np.full((2, dom.N), np.nan), 2)
+    with pytest.raises(capi.PisoError) as e:
+        dom.step(u, p, c.dt, c.nu, S)
+    assert e.value.status == 5          # PISO_ENAN
+    # the context is still usable afterwards
+    u1, p1, st = dom.step(u, p, c.dt, c.nu)
+    assert st["status"] == "PISO_OK"
