@@ -66,7 +66,8 @@ typedef enum {
  * max(rtol * ||b||_2, atol) for each solve. */
 typedef struct {
   int32_t n_correctors;  /* 1..4, default 2 */
-  int32_t pred_grad_p;   /* 1: predictor right-hand side contains -grad p^n (Eq. advectionMat) */
+  int32_t pred_grad_p;   /* 0 (default): predictor right-hand side of Eq. velRHSdiscrete;
+                            1: add -grad p^n (Eq. advectionMat; unstable on anisotropic cells) */
   double adv_rtol;       /* BiCGStab relative tolerance */
   double p_rtol;         /* CG relative tolerance */
   double atol;           /* absolute tolerance for both */

@@ -422,7 +422,7 @@ const char* piso_version(void) { return "pisob300 0.1 (sm_103a)"; }
 void piso_default_options(piso_options* o) {
   if (!o) return;
   o->n_correctors = 2;
-  o->pred_grad_p = 1;
+  o->pred_grad_p = 0;
   o->adv_rtol = 1e-12;
   o->p_rtol = 1e-12;
   o->atol = 0.0;

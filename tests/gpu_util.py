@@ -18,6 +18,9 @@ def rel_err(a, b):
 
 
 def gpu_domain(case, precision="fp64", **opts):
+    if precision == "fp64":
+        opts.setdefault("adv_rtol", 1e-13)
+        opts.setdefault("p_rtol", 1e-13)
     o = capi.default_options(**opts)
     return Domain.from_case(case, precision, o)
 

@@ -10,7 +10,12 @@ import oracle as O
 from paper_2505_16992_b300 import workloads as W
 
 
-def _fd_check(case, seed, eps=1e-6, rtol=1e-6):
+def fd4(L, eps):
+    """Fourth-order central difference of a scalar function at 0."""
+    return (8.0 * (L(eps) - L(-eps)) - (L(2 * eps) - L(-2 * eps))) / (12.0 * eps)
+
+
+def _fd_check(case, seed, eps=1e-4, rtol=1e-6):
     m = O.mesh_from_case(case)
     d, N = m.ndim, m.N
     rng = np.random.default_rng(seed)
@@ -34,7 +39,7 @@ def _fd_check(case, seed, eps=1e-6, rtol=1e-6):
     _, _, tape = O.piso_step(m, u0, p0, case.dt, nu0, S0, bval, opts)
     gu, gp, gS, gnu = O.piso_step_adjoint(m, tape, ubar, pbar)
     adj = float(np.sum(gu * du) + np.sum(gp * dp) + np.sum(gS * dS) + gnu * dnu)
-    fd = (L(eps) - L(-eps)) / (2 * eps)
+    fd = fd4(L, eps)
     assert abs(adj - fd) <= rtol * max(abs(fd), 1e-12), (adj, fd)
     return adj, fd
 
@@ -52,9 +57,12 @@ def test_adjoint_matches_central_fd(name):
     _fd_check(c, seed=11)
 
 
-def test_adjoint_each_input_separately():
-    """Per-input directional derivatives (u^n, p^n, S, nu) each match FD."""
+@pytest.mark.parametrize("pred_grad_p", [False, True])
+def test_adjoint_each_input_separately(pred_grad_p):
+    """Per-input directional derivatives (u^n, p^n, S, nu) each match FD, with
+    and without the predictor pressure gradient (reading R4)."""
     c = W.cavity2d(5, nu=0.05, dt=0.05)
+    opts = O.Options(pred_grad_p=pred_grad_p)
     m = O.mesh_from_case(c)
     d, N = 2, m.N
     rng = np.random.default_rng(5)
@@ -62,17 +70,19 @@ def test_adjoint_each_input_separately():
     p0 = rng.standard_normal(N)
     S0 = rng.standard_normal((d, N))
     ubar, pbar = rng.standard_normal((d, N)), rng.standard_normal(N)
-    _, _, tape = O.piso_step(m, u0, p0, c.dt, c.nu, S0)
-    g = O.piso_step_adjoint(m, tape, ubar, pbar)
-    eps = 1e-6
+    _, _, tape = O.piso_step(m, u0, p0, c.dt, c.nu, S0, None, opts)
+    g = O.piso_step_adjoint(m, tape, ubar, pbar, opts)
+    if not pred_grad_p:
+        assert np.all(g[1] == 0.0)
+    eps = 1e-4
     dirs = [rng.standard_normal((d, N)), rng.standard_normal(N), rng.standard_normal((d, N)), 0.01]
     for k in range(4):
         def L(t):
             args = [u0, p0, S0, c.nu]
             args[k] = args[k] + t * dirs[k]
-            u1, p1, _ = O.piso_step(m, args[0], args[1], c.dt, args[3], args[2])
+            u1, p1, _ = O.piso_step(m, args[0], args[1], c.dt, args[3], args[2], None, opts)
             return float(np.sum(ubar * u1) + np.sum(pbar * p1))
-        fd = (L(eps) - L(-eps)) / (2 * eps)
+        fd = fd4(L, eps)
         adj = float(np.sum(g[k] * dirs[k])) if k < 3 else g[3] * dirs[3]
         assert abs(adj - fd) <= 1e-6 * max(abs(fd), 1e-12), (k, adj, fd)
 
