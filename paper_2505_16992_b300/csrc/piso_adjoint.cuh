@@ -1,6 +1,389 @@
+// Adjoint of one PISO step as one persistent cooperative launch
+// (arXiv:2505.16992, Sec. 2.3 and App. A.4).  The linear solves are
+// differentiated by transposed solves (A^T db = dx, dA = -db (x) x on the
+// sparsity pattern; App. A.5: the forward solvers with the transposed matrix),
+// every other operation by its exact transpose, read off the implemented
+// forward operator (reading R9).  Boundary values and the outflow update are
+// held fixed.
 #pragma once
 #include "piso_forward.cuh"
+
 namespace piso {
+
+template <typename real>
+struct AdjCall {
+  const DomStatic* dom;
+  // tape (recorded by the forward step)
+  const double* hdr;         // [dt, nu]
+  const real* Cdiag;
+  const real* Coff;
+  const real* ustar;
+  const real* h[4];
+  const real* xk[4];
+  const real* uc[4];
+  const real* bval;          // [d][nbf]
+  // seeds and results
+  const real* du_out;        // [d][N]
+  const real* dp_out;        // [N] or nullptr
+  real* du_in;               // [d][N]
+  real* dp_in;               // [N] or nullptr
+  real* dS;                  // [d][N] or nullptr
+  double* dnu;               // device scalar
+  // scratch
+  real* Poff;                // [d][N] pressure matrix rebuilt from A
+  real* Pdiag;               // [N]
+  real* gA;                  // [N]       dL/dA, A = diag C
+  real* gCoff;               // [2d][N]   dL/d(off-diagonal C)
+  real* grhs0;               // [d][N]    dL/d(rhs0)
+  real* gw;                  // [d][N]    dL/d(alpha_jj / A)
+  real* W;                   // [d][N]    T . (gu / A), later T . z
+  real* gg;                  // [d][N]
+  real* gu;                  // [d][N]
+  real* gx;                  // [N]
+  real* z;                   // [d][N]    transposed predictor solve
+  real* r;
+  real* rhat;
+  real* pv[2];
+  real* vv[2];
+  real* t;
+  real* cx;
+  real* crb[2];
+  real* cwb[2];
+  real* csb[2];
+  real* cp;
+  uint32_t* bar;
+  double* partials;
+  int32_t* status;
+  int32_t* istats;
+  double* dstats;
+  int32_t cta0, ncta;
+};
+
 template <typename real, int ND>
-__global__ void __launch_bounds__(512, 1) adj_kernel(int dummy) {}
+__device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g) {
+  __shared__ DomStatic D;
+  __shared__ BiState bs;
+  __shared__ CgState cs;
+  __shared__ double s_mean;
+  copy_to_smem(&D, A.dom);
+  __syncthreads();
+  const int32_t N = D.N;
+  const Ctx<real, ND> X{D, g, (int32_t)(((int64_t)N * g.rank) / g.ncta),
+                        (int32_t)(((int64_t)N * (g.rank + 1)) / g.ncta), N};
+  const real* J = reinterpret_cast<const real*>(D.J);
+  const real* T = reinterpret_cast<const real*>(D.T);
+  const real* AL = reinterpret_cast<const real*>(D.alpha);
+  const int NSD = 2 * ND;
+  const int32_t nbf = D.nbf;
+  auto Tm = [&](int j, int k, int32_t i) -> real { return T[(size_t)(j * ND + k) * N + i]; };
+  const real inv_dt = (real)(1.0 / A.hdr[0]);
+  const int K = o.n_corr;
+
+  // (G^T W)_P for the cell-centred central gradient with the R5 boundary rule:
+  // G(p)_Q = sum_j T_Q,j . 0.5 (p_{nb(Q,+j)} - p_{nb(Q,-j)}), p_Q standing in
+  // for a missing neighbour.  W_j(Q) = T_Q,j . g_Q is precomputed.
+  auto gradT = [&](const Cell& c, const real* Wv) -> real {
+    real acc = 0;
+#pragma unroll
+    for (int j = 0; j < ND; j++) {
+      const real* w = Wv + (size_t)j * N;
+      const int32_t Fm = c.nb[2 * j], Fp = c.nb[2 * j + 1];
+      const real wP = w[c.i];
+      acc += real(0.5) * ((Fm >= 0 ? w[Fm] : real(0)) + (Fp < 0 ? wP : real(0)) - (Fp >= 0 ? w[Fp] : real(0)) -
+                          (Fm < 0 ? wP : real(0)));
+    }
+    return acc;
+  };
+
+  for (int k = K - 1; k >= 0; k--) {
+    const real* xk = A.xk[k];
+    const real* hk = A.h[k];
+    const real* uin = (k == 0) ? A.ustar : A.uc[k - 1];
+    const real* gsrc = (k == K - 1) ? A.du_out : A.gu;
+    // R0: W = T . (gu / A); dL/dA from u = h - A^-1 grad x.  On the first
+    // pass also rebuild P from A (Eq. pMatDiscrete) and clear the accumulators.
+    X.cells([&](const Cell& c) {
+      const int32_t P = c.i;
+      const real aP = A.Cdiag[P];
+      if (k == K - 1) {
+        real pd = 0;
+#pragma unroll
+        for (int s = 0; s < NSD; s++) {
+          const int j = s >> 1;
+          const int32_t F = c.nb[s];
+          real pf = 0;
+          if (F >= 0) pf = real(0.5) * (AL[(size_t)j * N + P] / aP + AL[(size_t)j * N + F] / A.Cdiag[F]);
+          pd -= pf;
+          if (s & 1) A.Poff[(size_t)j * N + P] = pf;
+          A.gCoff[(size_t)s * N + P] = 0;
+        }
+        A.Pdiag[P] = pd;
+#pragma unroll
+        for (int i = 0; i < ND; i++) {
+          A.grhs0[(size_t)i * N + P] = 0;
+          A.gw[(size_t)i * N + P] = 0;
+        }
+      }
+      real gu[ND], gp[ND];
+#pragma unroll
+      for (int i = 0; i < ND; i++) {
+        gu[i] = gsrc[(size_t)i * N + P];
+        gp[i] = 0;
+      }
+      const real xP = xk[P];
+#pragma unroll
+      for (int j = 0; j < ND; j++) {
+        const real xp = c.nb[2 * j + 1] >= 0 ? xk[c.nb[2 * j + 1]] : xP;
+        const real xm = c.nb[2 * j] >= 0 ? xk[c.nb[2 * j]] : xP;
+        const real dd = real(0.5) * (xp - xm);
+        real w = 0;
+#pragma unroll
+        for (int i = 0; i < ND; i++) {
+          gp[i] += Tm(j, i, P) * dd;
+          w += Tm(j, i, P) * gu[i];
+        }
+        A.W[(size_t)j * N + P] = w / aP;
+      }
+      real ga = 0;
+#pragma unroll
+      for (int i = 0; i < ND; i++) ga += gu[i] * gp[i];
+      ga /= aP * aP;
+      A.gA[P] = (k == K - 1) ? ga : A.gA[P] + ga;
+    });
+    if (!plain_sync(g)) return;
+    // R1: gx = -G^T W (+ dL/dp^{n+1} after the last corrector); its mean
+    {
+      Acc<real> a[1];
+      a[0].zero();
+      X.cells([&](const Cell& c) {
+        real v = -gradT(c, A.W);
+        if (k == K - 1 && A.dp_out) v += A.dp_out[c.i];
+        A.gx[c.i] = v;
+        A.cx[c.i] = real(0);
+        a[0].add(v);
+      });
+      if (!reduce_sync<real, 1>(g, a, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
+    }
+    // transposed pressure solve: P y = gx - mean (P is symmetric)
+    if (!cg_pressure<real, ND>(X, cs, o.p_rtol, o.atol, o.p_maxit, A.Pdiag, A.Poff, A.gx, s_mean, A.cx, A.crb,
+                               A.cwb, A.csb, A.cp))
+      return;
+    if (threadIdx.x == 0 && g.rank == 0) {
+      A.istats[4 + k] = cs.it;
+      A.dstats[4 + k] = sqrt(cs.res2);
+      if (!cs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
+    }
+    // R3: dP = -y (x) x on the pattern -> d(alpha/A); h_bar = gu + div^T y;
+    //     gg = h_bar / A; dL/dA and dL/drhs0 from h = A^-1 (rhs0 - H u)
+    X.cells([&](const Cell& c) {
+      const int32_t P = c.i;
+      const real yP = A.cx[P], xP = xk[P];
+      const real aP = A.Cdiag[P];
+      real Fb[ND];
+#pragma unroll
+      for (int j = 0; j < ND; j++) {
+        real gwj = 0, fb = 0;
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+          const int s = 2 * j + e;
+          const int32_t F = c.nb[s];
+          if (F < 0) continue;
+          const real n = e ? real(1) : real(-1);
+          const real dy = yP - A.cx[F];
+          gwj += real(0.5) * dy * (xP - xk[F]);
+          fb += real(0.5) * n * dy;
+        }
+        A.gw[(size_t)j * N + P] += gwj;
+        Fb[j] = fb * J[P];
+      }
+      real ga = 0;
+#pragma unroll
+      for (int i = 0; i < ND; i++) {
+        real hb = gsrc[(size_t)i * N + P];
+#pragma unroll
+        for (int j = 0; j < ND; j++) hb += Tm(j, i, P) * Fb[j];
+        const real ggi = hb / aP;
+        A.gg[(size_t)i * N + P] = ggi;
+        ga += hb * hk[(size_t)i * N + P];
+        A.grhs0[(size_t)i * N + P] += ggi;
+      }
+      A.gA[P] -= ga / aP;
+    });
+    if (!plain_sync(g)) return;
+    // R4: gu_in = -H^T gg; dL/dH = -gg (x) u_in on the pattern
+    X.cells([&](const Cell& c) {
+      const int32_t P = c.i;
+      real ggP[ND];
+#pragma unroll
+      for (int i = 0; i < ND; i++) ggP[i] = A.gg[(size_t)i * N + P];
+#pragma unroll
+      for (int s = 0; s < NSD; s++) {
+        const int32_t F = c.nb[s];
+        if (F < 0) continue;
+        real acc = 0;
+#pragma unroll
+        for (int i = 0; i < ND; i++) acc += ggP[i] * uin[(size_t)i * N + F];
+        A.gCoff[(size_t)s * N + P] -= acc;
+      }
+#pragma unroll
+      for (int i = 0; i < ND; i++) {
+        real v = 0;
+#pragma unroll
+        for (int s = 0; s < NSD; s++) {
+          const int32_t F = c.nb[s];
+          if (F >= 0) v += A.Coff[(size_t)(s ^ 1) * N + F] * A.gg[(size_t)i * N + F];
+        }
+        A.gu[(size_t)i * N + P] = -v;
+      }
+    });
+    if (!plain_sync(g)) return;
+  }
+
+  // R5: dL/dA from the pressure matrix (w = alpha / A); start the transposed
+  // predictor solve C^T z = gu with z0 = 0.
+  {
+    Acc<real> a[2 * ND];
+#pragma unroll
+    for (int k = 0; k < 2 * ND; k++) a[k].zero();
+    X.own([&](int32_t P) {
+      const real aP = A.Cdiag[P];
+      real s = 0;
+#pragma unroll
+      for (int j = 0; j < ND; j++) s += A.gw[(size_t)j * N + P] * AL[(size_t)j * N + P];
+      A.gA[P] -= s / (aP * aP);
+#pragma unroll
+      for (int i = 0; i < ND; i++) {
+        const real b = A.gu[(size_t)i * N + P];
+        A.z[(size_t)i * N + P] = 0;
+        A.r[(size_t)i * N + P] = b;
+        A.rhat[(size_t)i * N + P] = b;
+        a[i].add_prod(b, b);
+        a[ND + i].add_prod(b, b);
+      }
+    });
+    if (!reduce_sync<real, 2 * ND>(g, a, [&](const double* q) { bicg_start<ND>(bs, q, o.adv_rtol, o.atol, g.status); }))
+      return;
+  }
+  if (!bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t)) return;
+  if (threadIdx.x == 0 && g.rank == 0) {
+    int nc = 0;
+    for (int k = 0; k < ND; k++) {
+      A.istats[k] = bs.iters[k];
+      A.dstats[k] = sqrt(bs.res2[k]);
+      if (!bs.conv[k]) nc = 1;
+    }
+    if (nc) atomicOr(g.status, PISO_ERR_NOCONV_ADV);
+  }
+  // R6: dC = -z (x) u* on the pattern; dL/drhs0 += z; outputs dS and the
+  //     1/dt part of du_in; W = T . z for the predictor pressure gradient
+  Acc<real> anu[1];
+  anu[0].zero();
+  X.cells([&](const Cell& c) {
+    const int32_t P = c.i;
+    real zP[ND];
+    real ga = 0;
+#pragma unroll
+    for (int i = 0; i < ND; i++) {
+      zP[i] = A.z[(size_t)i * N + P];
+      ga += zP[i] * A.ustar[(size_t)i * N + P];
+    }
+    A.gA[P] -= ga;
+#pragma unroll
+    for (int s = 0; s < NSD; s++) {
+      const int32_t F = c.nb[s];
+      if (F < 0) continue;
+      real acc = 0;
+#pragma unroll
+      for (int i = 0; i < ND; i++) acc += zP[i] * A.ustar[(size_t)i * N + F];
+      A.gCoff[(size_t)s * N + P] -= acc;
+    }
+    real gr[ND];
+#pragma unroll
+    for (int i = 0; i < ND; i++) {
+      gr[i] = A.grhs0[(size_t)i * N + P] + zP[i];
+      A.du_in[(size_t)i * N + P] = gr[i] * inv_dt;
+      if (A.dS) A.dS[(size_t)i * N + P] = gr[i];
+    }
+    if (o.pred_grad_p) {
+#pragma unroll
+      for (int j = 0; j < ND; j++) {
+        real w = 0;
+#pragma unroll
+        for (int i = 0; i < ND; i++) w += Tm(j, i, P) * zP[i];
+        A.W[(size_t)j * N + P] = w;
+      }
+    }
+    // nu from the Dirichlet terms of the right-hand side (Eq. velRHSdiscrete)
+    const real invJ = real(1) / J[P];
+#pragma unroll
+    for (int s = 0; s < NSD; s++) {
+      const int32_t F = c.nb[s];
+      if (F >= 0) continue;
+      const int32_t f = -1 - F;
+      const real two_a = real(2) * AL[(size_t)(s >> 1) * N + P] * invJ;
+      real acc = 0;
+#pragma unroll
+      for (int i = 0; i < ND; i++) acc += gr[i] * A.bval[(size_t)i * nbf + f];
+      anu[0].add(acc * two_a);
+    }
+  });
+  if (!plain_sync(g)) return;
+  // R7: dp_in = -G^T (T . z) (reading R4 option); assembly adjoint: the face
+  //     fluxes U_f = (U_P + U_F)/2, U = J T . u^n, and the nu terms of C
+  X.cells([&](const Cell& c) {
+    const int32_t P = c.i;
+    if (A.dp_in) A.dp_in[P] = o.pred_grad_p ? -gradT(c, A.W) : real(0);
+    const real invJ = real(1) / J[P];
+    const real gAP = A.gA[P];
+    real Ub[ND];
+#pragma unroll
+    for (int j = 0; j < ND; j++) Ub[j] = 0;
+#pragma unroll
+    for (int s = 0; s < NSD; s++) {
+      const int j = s >> 1;
+      const real n = (s & 1) ? real(1) : real(-1);
+      const int32_t F = c.nb[s];
+      const real aP = AL[(size_t)j * N + P];
+      if (F >= 0) {
+        const real gcP = A.gCoff[(size_t)s * N + P];
+        const real gcF = A.gCoff[(size_t)(s ^ 1) * N + F];
+        const real own = real(0.5) * n * (gcP + gAP) * invJ;
+        const real nbr = -real(0.5) * n * (gcF + A.gA[F]) / J[F];
+        Ub[j] += real(0.5) * (own + nbr);
+        const real Df = real(0.5) * (aP + AL[(size_t)j * N + F]);
+        anu[0].add((gAP - gcP) * Df * invJ);
+      } else {
+        anu[0].add(gAP * real(2) * aP * invJ);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < ND; i++) {
+      real v = 0;
+#pragma unroll
+      for (int j = 0; j < ND; j++) v += Tm(j, i, P) * Ub[j];
+      A.du_in[(size_t)i * N + P] += J[P] * v;
+    }
+  });
+  reduce_sync<real, 1>(g, anu, [&](const double* q) {
+    if (g.rank == 0) *A.dnu = q[0];
+  });
 }
+
+template <typename real, int ND>
+__global__ void __launch_bounds__(512, 1) adj_kernel(const __grid_constant__ Launch<AdjCall<real>> L) {
+  __shared__ AdjCall<real> A;
+  const int gi = find_group(L.ngroups, L.cta_first);
+  copy_to_smem(&A, L.calls ? L.calls + gi : &L.call0);
+  __syncthreads();
+  Group g;
+  g.bar = A.bar;
+  g.partials = A.partials;
+  g.status = A.status;
+  g.ncta = A.ncta;
+  g.rank = blockIdx.x - A.cta0;
+  g.epoch = 0;
+  g.timeout_ns = L.o.timeout_ns;
+  adj_group<real, ND>(A, L.o, g);
+}
+
+}  // namespace piso

@@ -199,15 +199,28 @@ void put(std::vector<char>& buf, size_t i, double v) {
 
 // --- workspace layout ------------------------------------------------------
 enum WsIdx {
-  W_U, W_RHS0, W_R, W_RHAT, W_P0, W_P1, W_V0, W_V1, W_T, W_POFF, W_PDIAG, W_FH, W_B, W_CX, W_CR, W_CZ,
-  W_CD0, W_CD1, W_CQ,
+  W_U, W_RHS0, W_R, W_RHAT, W_P0, W_P1, W_V0, W_V1, W_T, W_POFF, W_PDIAG, W_FH, W_B, W_CX,
+  W_CRB0, W_CRB1, W_CWB0, W_CWB1, W_CSB0, W_CSB1, W_CP,
   // adjoint scratch
-  A_GA, A_GCOFF, A_GRHS0, A_GW, A_W, A_GG, A_GU, A_GX, A_Y, A_GU2,
+  A_GA, A_GCOFF, A_GRHS0, A_GW, A_W, A_GG, A_GU, A_GX, A_Z, A_DU,
   W_COUNT
 };
 
+// size of workspace array k in units of N elements
+int ws_units(int k, int nd) {
+  switch (k) {
+    case W_PDIAG: case W_B: case W_CX: case W_CRB0: case W_CRB1: case W_CWB0: case W_CWB1: case W_CSB0:
+    case W_CSB1: case W_CP: case A_GA: case A_GX:
+      return 1;
+    case A_GCOFF:
+      return 2 * nd;
+    default:
+      return nd;
+  }
+}
+
 struct TapeLayout {
-  size_t un, cdiag, coff, ustar, h[4], xk[4], uc[4], bval, total;
+  size_t hdr, un, cdiag, coff, ustar, h[4], xk[4], uc[4], bval, total;
 };
 
 TapeLayout tape_layout(const piso_domain* d) {
@@ -219,6 +232,8 @@ TapeLayout tape_layout(const piso_domain* d) {
     off += ((n * e + 255) / 256) * 256;
     return o;
   };
+  t.hdr = off;
+  off += 256;
   t.un = take(nd * N);
   t.cdiag = take(N);
   t.coff = take(2 * nd * N);
@@ -258,6 +273,7 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
     c.uc[k] = (real*)(tb + L.uc[k]);
   }
   c.bval_rec = (real*)(tb + L.bval);
+  c.hdr = (double*)(tb + L.hdr);
   c.U = (real*)d->ws[W_U];
   c.rhs0 = (real*)d->ws[W_RHS0];
   c.r = (real*)d->ws[W_R];
@@ -272,11 +288,13 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
   c.Fh = (real*)d->ws[W_FH];
   c.b = (real*)d->ws[W_B];
   c.cx = (real*)d->ws[W_CX];
-  c.cr = (real*)d->ws[W_CR];
-  c.cz = (real*)d->ws[W_CZ];
-  c.cd[0] = (real*)d->ws[W_CD0];
-  c.cd[1] = (real*)d->ws[W_CD1];
-  c.cq = (real*)d->ws[W_CQ];
+  c.crb[0] = (real*)d->ws[W_CRB0];
+  c.crb[1] = (real*)d->ws[W_CRB1];
+  c.cwb[0] = (real*)d->ws[W_CWB0];
+  c.cwb[1] = (real*)d->ws[W_CWB1];
+  c.csb[0] = (real*)d->ws[W_CSB0];
+  c.csb[1] = (real*)d->ws[W_CSB1];
+  c.cp = (real*)d->ws[W_CP];
   c.bar = d->bar;
   c.partials = d->partials;
   c.status = d->status;
@@ -395,7 +413,7 @@ piso_status enqueue_readback(piso_domain* d, cudaStream_t st) {
 template <typename real>
 piso_status launch_fwd(piso_domain* d, const void* u_in, const void* p_in, void* u_out, void* p_out,
                               double dt, double nu, const void* S, void* tape, cudaStream_t st) {
-  FwdLaunch<real> L;
+  Launch<FwdCall<real>> L;
   memset(&L, 0, sizeof L);
   L.ngroups = 1;
   L.o = solver_opts(d->opts);
@@ -683,10 +701,7 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
     d->bf_out = (int8_t*)a.take(nbf1);
     d->bf_um = a.take((size_t)nd * nbf1 * e);
     d->bval = a.take((size_t)nd * nbf1 * e);
-    const size_t vec = (size_t)nd * N * e, sc = (size_t)N * e;
-    size_t sizes[W_COUNT] = {vec, vec, vec, vec, vec, vec, vec, vec, vec, vec, sc, vec, sc, sc, sc, sc, sc, sc, sc,
-                             sc, 2 * vec, vec, vec, vec, vec, vec, sc, sc, vec};
-    for (int k = 0; k < W_COUNT; k++) d->ws[k] = a.take(sizes[k]);
+    for (int k = 0; k < W_COUNT; k++) d->ws[k] = a.take((size_t)ws_units(k, nd) * N * e);
     d->tape_ws = a.take(tape_layout(d).total);
     d->bar = (uint32_t*)a.take(64);
     d->status = (int32_t*)a.take(64);

@@ -175,6 +175,8 @@ struct Acc<double> {
   __device__ __forceinline__ void add(double a) { v += a; }
   __device__ __forceinline__ void shfl_down_add(int off) { v += __shfl_down_sync(0xffffffffu, v, off); }
   __device__ __forceinline__ double to_double() const { return v; }
+  __device__ __forceinline__ double pack() const { return v; }
+  __device__ __forceinline__ void unpack_add(double w) { v += w; }
 };
 
 template <>
@@ -193,6 +195,14 @@ struct Acc<float> {
     v = f2_add(v, o);
   }
   __device__ __forceinline__ double to_double() const { return (double)v.hi + (double)v.lo; }
+  // 8-byte transport of the float pair (no FP64 arithmetic on the way)
+  __device__ __forceinline__ double pack() const {
+    return __hiloint2double(__float_as_int(v.hi), __float_as_int(v.lo));
+  }
+  __device__ __forceinline__ void unpack_add(double w) {
+    f2 o{__int_as_float(__double2hiint(w)), __int_as_float(__double2loint(w))};
+    v = f2_add(v, o);
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -293,7 +303,94 @@ __device__ __forceinline__ void gather(const Group& g, double (&out)[NS]) {
   __syncthreads();
 }
 
-template <typename real>
-__device__ __forceinline__ real ld(const real* p, int64_t i) { return p[i]; }
+// Arrival and bounded wait of one CTA at barrier g.epoch (called by one thread
+// after the CTA's writes were ordered by __syncthreads).
+__device__ __noinline__ int barrier_arrive_wait(const Group& g) {
+  const uint32_t target = g.epoch * (uint32_t)g.ncta;
+  __threadfence();
+  atomicAdd(g.bar, 1u);
+  int ok = 1;
+  if ((int32_t)(ld_acquire_u32(g.bar) - target) < 0) {
+    const uint64_t t0 = global_ns();
+    while (true) {
+      if ((int32_t)(ld_acquire_u32(g.bar) - target) >= 0) break;
+      if (*((volatile int32_t*)g.status) & PISO_ERR_TIMEOUT) { ok = 0; break; }
+      if (global_ns() - t0 > g.timeout_ns) {
+        atomicOr(g.status, PISO_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  __threadfence();
+  return ok;
+}
+
+// One phase boundary with a reduction: block-reduce the NS accumulators,
+// publish this CTA's partials, wait at the group barrier, sum the group's
+// partials in a fixed order (warp 0; identical in every CTA) and let thread 0
+// run update(totals) on the shared solver state before the closing
+// __syncthreads.  Returns false when the barrier wait ran out.
+template <typename real, int NS, typename F>
+__device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& update) {
+  __shared__ double s_w[MAXW * NSMAX];
+  __shared__ double s_tot[NSMAX];
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NS; k++) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a[k].shfl_down_add(off);
+    if (lane == 0) s_w[warp * NSMAX + k] = a[k].pack();
+  }
+  __syncthreads();
+  g.epoch++;
+  if (warp == 0) {
+    double* P = g.partials + (size_t)(g.epoch & 1) * NSMAX * g.ncta;
+#pragma unroll
+    for (int k = 0; k < NS; k++) {
+      Acc<real> v;
+      v.zero();
+      if (lane < nw) v.unpack_add(s_w[lane * NSMAX + k]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v.shfl_down_add(off);
+      if (lane == 0) __stcg(P + (size_t)k * g.ncta + g.rank, v.pack());
+    }
+    int ok = 1;
+    if (lane == 0) ok = barrier_arrive_wait(g);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) {
+      Acc<real> v[NS];
+#pragma unroll
+      for (int k = 0; k < NS; k++) {
+        v[k].zero();
+        for (int c = lane; c < g.ncta; c += 32) v[k].unpack_add(__ldcg(P + (size_t)k * g.ncta + c));
+      }
+#pragma unroll
+      for (int k = 0; k < NS; k++) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k].shfl_down_add(off);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NS; k++) s_tot[k] = v[k].to_double();
+        update(s_tot);
+      }
+    }
+    if (lane == 0) s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// A phase boundary without a reduction.
+__device__ __forceinline__ bool plain_sync(Group& g) {
+  __shared__ int s_ok2;
+  __syncthreads();
+  g.epoch++;
+  if (threadIdx.x == 0) s_ok2 = barrier_arrive_wait(g);
+  __syncthreads();
+  return s_ok2 != 0;
+}
 
 }  // namespace piso

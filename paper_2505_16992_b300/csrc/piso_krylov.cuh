@@ -1,0 +1,427 @@
+// Krylov solvers used by the forward and adjoint PISO kernels (arXiv:2505.16992,
+// App. A.5: BiCGStab for advection-diffusion, CG for the pressure; Sec. 2.3:
+// the adjoint re-uses them with the transposed matrix).  They run inside the
+// persistent kernel: every iteration phase walks the CTA's cells and ends in a
+// deterministic group reduction.
+#pragma once
+#include "piso_device.cuh"
+
+namespace piso {
+
+struct SolverOpts {
+  int32_t n_corr, pred_grad_p, adv_maxit, p_maxit;
+  double adv_rtol, p_rtol, atol;
+  uint64_t timeout_ns;
+};
+
+// Execution context of one CTA inside its group.
+template <typename real, int ND>
+struct Ctx {
+  const DomStatic& D;   // shared-memory copy
+  Group& g;
+  int32_t lo, hi, N;
+  template <typename F>
+  __device__ __forceinline__ void cells(F&& f) const {
+    for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += blockDim.x) {
+      const Cell c = locate<ND>(D, i);
+      f(c);
+    }
+  }
+  template <typename F>
+  __device__ __forceinline__ void own(F&& f) const {
+    for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += blockDim.x) f(i);
+  }
+};
+
+// Row coefficients of C (TR = false) or C^T (TR = true) for cell c:
+// (M y)_P = diag * y_P + sum_s cf[s] * y_{nb(P,s)} over inner faces.  The
+// entry of C^T on the face to F = nb(P,s) is F's own coefficient on the
+// opposite side (gather form, no atomics).
+template <typename real, int ND, bool TR>
+__device__ __forceinline__ void c_row(const Cell& c, int32_t N, const real* Cdiag, const real* Coff, real& diag,
+                                      real (&cf)[2 * ND]) {
+  diag = Cdiag[c.i];
+#pragma unroll
+  for (int s = 0; s < 2 * ND; s++) {
+    const int32_t Q = c.nb[s];
+    if (Q >= 0) cf[s] = TR ? Coff[(size_t)(s ^ 1) * N + Q] : Coff[(size_t)s * N + c.i];
+    else cf[s] = real(0);
+  }
+}
+
+// Face coefficients of the pressure matrix P for cell c (symmetric: the - face
+// of P is the + face of its - neighbour).
+template <typename real, int ND>
+__device__ __forceinline__ void p_row(const Cell& c, int32_t N, const real* Poff, real (&pf)[2 * ND]) {
+#pragma unroll
+  for (int s = 0; s < 2 * ND; s++) {
+    const int j = s >> 1;
+    const int32_t Q = c.nb[s];
+    pf[s] = Q >= 0 ? ((s & 1) ? Poff[(size_t)j * N + c.i] : Poff[(size_t)j * N + Q]) : real(0);
+  }
+}
+
+// Krylov scalar state, owned by thread 0 and broadcast through shared memory.
+struct BiState {
+  double rho[3], rho_old[3], alpha[3], omega[3], tol2[3], res2[3];
+  int active[3], sconv[3], iters[3], conv[3];
+  int any, it, first;
+};
+
+struct CgState {
+  double gam, gam_old, delta, alpha, alpha_old, beta, tol2, res2;
+  int active, it, first, conv;
+};
+
+// Thread 0: BiCGStab start from the reduced ||b||^2 and ||r0||^2 per component.
+template <int ND>
+__device__ __forceinline__ void bicg_start(BiState& bs, const double* q, double rtol, double atol, int32_t* status) {
+  bs.any = 0;
+  bs.it = 0;
+  bs.first = 1;
+  for (int k = 0; k < ND; k++) {
+    bs.tol2[k] = fmax(rtol * rtol * q[k], atol * atol);
+    bs.res2[k] = q[ND + k];
+    bs.rho[k] = q[ND + k];
+    bs.rho_old[k] = bs.alpha[k] = bs.omega[k] = 1.0;
+    bs.iters[k] = 0;
+    bs.sconv[k] = 0;
+    bs.conv[k] = !(bs.res2[k] > bs.tol2[k]);
+    bs.active[k] = !bs.conv[k];
+    if (bs.res2[k] != bs.res2[k]) {
+      bs.active[k] = 0;
+      bs.conv[k] = 0;
+      atomicOr(status, PISO_ERR_NAN);
+    }
+    bs.any |= bs.active[k];
+  }
+}
+
+// BiCGStab (van der Vorst 1992) on M x = b, M = C or C^T, for the ND velocity
+// components sharing M, each with its own scalars; converged components
+// freeze.  On entry x = x0, r = b - M x0, rhat = r and bs came from bicg_start.
+// Three reductions per iteration; p and s are formed on the fly at the stencil.
+template <typename real, int ND, bool TR>
+__device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const real* Cdiag, const real* Coff,
+                         real* x, real* r, const real* rhat, real* const (&pv)[2], real* const (&vv)[2], real* t) {
+  const int32_t N = X.N;
+  int cur = 0;
+  while (bs.any && bs.it < maxit) {
+    // BA: p = r + beta (p - omega v), v = M p
+    {
+      Acc<real> a[ND];
+      real beta[ND], om[ND];
+      int act[ND];
+#pragma unroll
+      for (int k = 0; k < ND; k++) {
+        a[k].zero();
+        act[k] = bs.active[k];
+        beta[k] = bs.first ? real(0) : (real)((bs.rho[k] / bs.rho_old[k]) * (bs.alpha[k] / bs.omega[k]));
+        om[k] = (real)bs.omega[k];
+      }
+      const int first = bs.first;
+      const real* pold = pv[cur ^ 1];
+      const real* vold = vv[cur ^ 1];
+      real* pnew = pv[cur];
+      real* vnew = vv[cur];
+      X.cells([&](const Cell& c) {
+        real diag, cf[2 * ND];
+        c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+          if (!act[k]) continue;
+          const size_t o_ = (size_t)k * N;
+          auto pn = [&](int32_t Q) -> real {
+            const real rq = r[o_ + Q];
+            return first ? rq : rq + beta[k] * (pold[o_ + Q] - om[k] * vold[o_ + Q]);
+          };
+          const real pP = pn(c.i);
+          real v = diag * pP;
+#pragma unroll
+          for (int s = 0; s < 2 * ND; s++)
+            if (c.nb[s] >= 0) v += cf[s] * pn(c.nb[s]);
+          pnew[o_ + c.i] = pP;
+          vnew[o_ + c.i] = v;
+          a[k].add_prod(rhat[o_ + c.i], v);
+        }
+      });
+      const bool ok = reduce_sync<real, ND>(X.g, a, [&](const double* q) {
+        bs.it++;
+        for (int k = 0; k < ND; k++) {
+          if (!bs.active[k]) continue;
+          bs.iters[k]++;
+          if (q[k] == 0.0 || q[k] != q[k]) {
+            bs.active[k] = 0;
+            atomicOr(X.g.status, q[k] == 0.0 ? PISO_ERR_BREAKDOWN : PISO_ERR_NAN);
+            continue;
+          }
+          bs.alpha[k] = bs.rho[k] / q[k];
+        }
+      });
+      if (!ok) return false;
+    }
+    // BB: s = r - alpha v, t = M s
+    {
+      Acc<real> a[3 * ND];
+      real al[ND];
+      int act[ND];
+#pragma unroll
+      for (int k = 0; k < ND; k++) {
+        act[k] = bs.active[k];
+        al[k] = (real)bs.alpha[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 3 * ND; k++) a[k].zero();
+      const real* vnew = vv[cur];
+      X.cells([&](const Cell& c) {
+        real diag, cf[2 * ND];
+        c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+          if (!act[k]) continue;
+          const size_t o_ = (size_t)k * N;
+          auto sv = [&](int32_t Q) -> real { return r[o_ + Q] - al[k] * vnew[o_ + Q]; };
+          const real sP = sv(c.i);
+          real tt = diag * sP;
+#pragma unroll
+          for (int s = 0; s < 2 * ND; s++)
+            if (c.nb[s] >= 0) tt += cf[s] * sv(c.nb[s]);
+          t[o_ + c.i] = tt;
+          a[k].add_prod(tt, sP);
+          a[ND + k].add_prod(tt, tt);
+          a[2 * ND + k].add_prod(sP, sP);
+        }
+      });
+      const bool ok = reduce_sync<real, 3 * ND>(X.g, a, [&](const double* q) {
+        for (int k = 0; k < ND; k++) {
+          if (!bs.active[k]) continue;
+          if (!(q[2 * ND + k] > bs.tol2[k])) {
+            bs.sconv[k] = 1;
+            bs.res2[k] = q[2 * ND + k];
+          } else if (q[ND + k] == 0.0 || q[ND + k] != q[ND + k]) {
+            bs.active[k] = 0;
+            atomicOr(X.g.status, q[ND + k] == 0.0 ? PISO_ERR_BREAKDOWN : PISO_ERR_NAN);
+          } else {
+            bs.omega[k] = q[k] / q[ND + k];
+          }
+        }
+      });
+      if (!ok) return false;
+    }
+    // BC: x += alpha p + omega s, r = s - omega t
+    {
+      Acc<real> a[2 * ND];
+      real al[ND], om[ND];
+      int act[ND], sc[ND];
+#pragma unroll
+      for (int k = 0; k < ND; k++) {
+        act[k] = bs.active[k];
+        sc[k] = bs.sconv[k];
+        al[k] = (real)bs.alpha[k];
+        om[k] = (real)bs.omega[k];
+        a[k].zero();
+        a[ND + k].zero();
+      }
+      const real* pnew = pv[cur];
+      const real* vnew = vv[cur];
+      X.own([&](int32_t P) {
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+          if (!act[k]) continue;
+          const size_t o_ = (size_t)k * N;
+          const real sP = r[o_ + P] - al[k] * vnew[o_ + P];
+          if (sc[k]) {
+            x[o_ + P] += al[k] * pnew[o_ + P];
+            continue;
+          }
+          x[o_ + P] += al[k] * pnew[o_ + P] + om[k] * sP;
+          const real rr = sP - om[k] * t[o_ + P];
+          r[o_ + P] = rr;
+          a[k].add_prod(rhat[o_ + P], rr);
+          a[ND + k].add_prod(rr, rr);
+        }
+      });
+      const bool ok = reduce_sync<real, 2 * ND>(X.g, a, [&](const double* q) {
+        bs.any = 0;
+        for (int k = 0; k < ND; k++) {
+          if (!bs.active[k]) continue;
+          if (bs.sconv[k]) {
+            bs.active[k] = 0;
+            bs.conv[k] = 1;
+            continue;
+          }
+          bs.res2[k] = q[ND + k];
+          if (bs.res2[k] != bs.res2[k]) {
+            bs.active[k] = 0;
+            atomicOr(X.g.status, PISO_ERR_NAN);
+          } else if (!(bs.res2[k] > bs.tol2[k])) {
+            bs.active[k] = 0;
+            bs.conv[k] = 1;
+          } else if (q[k] == 0.0) {
+            bs.active[k] = 0;
+            atomicOr(X.g.status, PISO_ERR_BREAKDOWN);
+          } else {
+            bs.rho_old[k] = bs.rho[k];
+            bs.rho[k] = q[k];
+          }
+          bs.any |= bs.active[k];
+        }
+        bs.first = 0;
+      });
+      if (!ok) return false;
+    }
+    cur ^= 1;
+  }
+  return true;
+}
+
+// Jacobi-preconditioned CG in the single-reduction form of Chronopoulos and
+// Gear (1989) for  (-P) x = -(b - bmean)  (R7: the pressure system is singular
+// and b is projected to zero mean).  D = -diag(P) is the preconditioner.  On
+// entry x holds x0; on return x holds the solution (not mean-corrected).
+// rb, wb, sb are ping-pong buffers for r, w = A u and s = A p; pdir holds p.
+template <typename real, int ND>
+__device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, double atol, int maxit,
+                            const real* Pdiag, const real* Poff, const real* b, double bmean, real* x,
+                            real* const (&rb)[2], real* const (&wb)[2], real* const (&sb)[2], real* pdir) {
+  const int32_t N = X.N;
+  // I1: r0 = b' - A' x0 with b' = -(b - mean), A' = -P
+  {
+    Acc<real> a[2];
+    a[0].zero();
+    a[1].zero();
+    const real mb = (real)bmean;
+    X.cells([&](const Cell& c) {
+      real pf[2 * ND];
+      p_row<real, ND>(c, N, Poff, pf);
+      const real bp = -(b[c.i] - mb);
+      real px = Pdiag[c.i] * x[c.i];
+#pragma unroll
+      for (int s = 0; s < 2 * ND; s++)
+        if (c.nb[s] >= 0) px += pf[s] * x[c.nb[s]];
+      const real r = bp + px;
+      rb[0][c.i] = r;
+      a[0].add_prod(bp, bp);
+      a[1].add_prod(r, r);
+    });
+    const bool ok = reduce_sync<real, 2>(X.g, a, [&](const double* q) {
+      cs.tol2 = fmax(rtol * rtol * q[0], atol * atol);
+      cs.res2 = q[1];
+      cs.it = 0;
+      cs.first = 1;
+      cs.conv = !(cs.res2 > cs.tol2);
+      cs.active = !cs.conv;
+      if (cs.res2 != cs.res2) {
+        cs.active = 0;
+        cs.conv = 0;
+        atomicOr(X.g.status, PISO_ERR_NAN);
+      }
+    });
+    if (!ok) return false;
+  }
+  if (!cs.active) return true;
+  // I2: w0 = A' u0, u0 = D^-1 r0
+  {
+    Acc<real> a[2];
+    a[0].zero();
+    a[1].zero();
+    const real* r0 = rb[0];
+    X.cells([&](const Cell& c) {
+      real pf[2 * ND];
+      p_row<real, ND>(c, N, Poff, pf);
+      const real rP = r0[c.i];
+      const real uP = rP / (-Pdiag[c.i]);
+      real w = rP;
+#pragma unroll
+      for (int s = 0; s < 2 * ND; s++) {
+        const int32_t Q = c.nb[s];
+        if (Q >= 0) w -= pf[s] * (r0[Q] / (-Pdiag[Q]));
+      }
+      wb[0][c.i] = w;
+      a[0].add_prod(rP, uP);
+      a[1].add_prod(w, uP);
+    });
+    const bool ok = reduce_sync<real, 2>(X.g, a, [&](const double* q) {
+      cs.gam = q[0];
+      cs.delta = q[1];
+      if (cs.delta == 0.0 || cs.delta != cs.delta) {
+        cs.active = 0;
+        atomicOr(X.g.status, cs.delta == 0.0 ? PISO_ERR_BREAKDOWN : PISO_ERR_NAN);
+      } else {
+        cs.alpha = cs.gam / cs.delta;
+        cs.beta = 0.0;
+      }
+    });
+    if (!ok) return false;
+  }
+  int cur = 0;
+  while (cs.active && cs.it < maxit) {
+    Acc<real> a[3];
+    a[0].zero();
+    a[1].zero();
+    a[2].zero();
+    const real al = (real)cs.alpha, be = (real)cs.beta;
+    const int first = cs.first;
+    const real* r_i = rb[cur];
+    const real* w_i = wb[cur];
+    const real* s_o = sb[cur ^ 1];
+    real* s_n = sb[cur];
+    real* r_n = rb[cur ^ 1];
+    real* w_n = wb[cur ^ 1];
+    X.cells([&](const Cell& c) {
+      real pf[2 * ND];
+      p_row<real, ND>(c, N, Poff, pf);
+      auto sQ = [&](int32_t Q) -> real { return first ? w_i[Q] : w_i[Q] + be * s_o[Q]; };
+      auto u1 = [&](int32_t Q) -> real { return (r_i[Q] - al * sQ(Q)) / (-Pdiag[Q]); };
+      const int32_t P = c.i;
+      const real dP = -Pdiag[P];
+      const real uP = r_i[P] / dP;
+      const real p = first ? uP : uP + be * pdir[P];
+      pdir[P] = p;
+      x[P] += al * p;
+      const real sP = sQ(P);
+      s_n[P] = sP;
+      const real r1 = r_i[P] - al * sP;
+      r_n[P] = r1;
+      const real u1P = r1 / dP;
+      real w1 = r1;
+#pragma unroll
+      for (int s = 0; s < 2 * ND; s++)
+        if (c.nb[s] >= 0) w1 -= pf[s] * u1(c.nb[s]);
+      w_n[P] = w1;
+      a[0].add_prod(r1, u1P);
+      a[1].add_prod(w1, u1P);
+      a[2].add_prod(r1, r1);
+    });
+    const bool ok = reduce_sync<real, 3>(X.g, a, [&](const double* q) {
+      cs.it++;
+      cs.res2 = q[2];
+      cs.first = 0;
+      if (cs.res2 != cs.res2) {
+        cs.active = 0;
+        atomicOr(X.g.status, PISO_ERR_NAN);
+      } else if (!(cs.res2 > cs.tol2)) {
+        cs.active = 0;
+        cs.conv = 1;
+      } else {
+        cs.gam_old = cs.gam;
+        cs.alpha_old = cs.alpha;
+        cs.gam = q[0];
+        cs.delta = q[1];
+        cs.beta = cs.gam / cs.gam_old;
+        const double den = cs.delta - cs.beta * cs.gam / cs.alpha_old;
+        if (den == 0.0 || cs.gam_old == 0.0) {
+          cs.active = 0;
+          atomicOr(X.g.status, PISO_ERR_BREAKDOWN);
+        } else {
+          cs.alpha = cs.gam / den;
+        }
+      }
+    });
+    if (!ok) return false;
+    cur ^= 1;
+  }
+  return true;
+}
+
+}  // namespace piso

@@ -1,0 +1,136 @@
+"""GPU adjoint PISO step vs the oracle's adjoint (arXiv:2505.16992, Sec. 2.3,
+App. A.4), through the C ABI; the autograd wrapper and a checkpointed rollout."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2505_16992_b300 import capi
+from paper_2505_16992_b300 import workloads as W
+from paper_2505_16992_b300.solver import piso_step, rollout
+from gpu_util import gpu_domain, host, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+ADJ_REL = 1e-8
+
+
+def _adjoint_parity(case, seed=0, tol=ADJ_REL, precision="fp64", pred_grad_p=0, **opts):
+    m = O.mesh_from_case(case)
+    dom = gpu_domain(case, precision, pred_grad_p=pred_grad_p, **opts)
+    d, N = case.ndim, case.ncells
+    rng = np.random.default_rng(seed)
+    u0 = case.u0 + 0.2 * rng.standard_normal((d, N))
+    p0 = rng.standard_normal(N)
+    S0 = (case.S if case.S is not None else 0.0) + 0.1 * rng.standard_normal((d, N))
+    ubar = rng.standard_normal((d, N))
+    pbar = rng.standard_normal(N)
+    # forward on both sides from the same state
+    u1, p1, st = dom.step(to_dev(dom, u0, d), to_dev(dom, p0), case.dt, case.nu, to_dev(dom, S0, d))
+    assert st["status"] == "PISO_OK"
+    oo = O.Options(pred_grad_p=bool(pred_grad_p))
+    uo, po, tape = O.piso_step(m, u0, p0, case.dt, case.nu, S0, None, oo)
+    du, dp, dS, dnu, ast = dom.step_adjoint(to_dev(dom, ubar, d), to_dev(dom, pbar))
+    assert ast["status"] == "PISO_OK", ast
+    gu, gp, gS, gnu = O.piso_step_adjoint(m, tape, ubar, pbar, oo)
+    errs = dict(u=rel_err(host(du), gu), S=rel_err(host(dS), gS), nu=abs(dnu - gnu) / max(abs(gnu), 1e-300))
+    if pred_grad_p:
+        errs["p"] = rel_err(host(dp), gp)
+    else:
+        assert np.all(host(dp) == 0.0)
+    for k, v in errs.items():
+        assert v <= tol, (k, errs, ast)
+    return errs
+
+
+def test_adjoint_cavity():
+    _adjoint_parity(W.cavity2d(32, nu=0.01, dt=0.01))
+
+
+def test_adjoint_cavity_pred_grad_p():
+    _adjoint_parity(W.cavity2d(16, nu=0.05, dt=0.05), pred_grad_p=1)
+
+
+def test_adjoint_turbulence2d_config4_size():
+    _adjoint_parity(W.turbulence2d(128))
+
+
+def test_adjoint_channel3d_small():
+    _adjoint_parity(W.channel3d(16, 12, 8))
+
+
+def test_adjoint_channel3d_full_size():
+    _adjoint_parity(W.channel3d(), tol=1e-7)
+
+
+def test_adjoint_bfs_multiblock():
+    _adjoint_parity(W.bfs2d(n_in=(16, 8), n_ch=64, n_out=16, half=8, dt=0.02), p_rtol=1e-12)
+
+
+@pytest.mark.parametrize("ctas", [1, 5])
+def test_adjoint_ragged_ctas(ctas):
+    c = W.cavity3d(5, nz=3)
+    _adjoint_parity(c, ctas=ctas, block_threads=64)
+
+
+def test_adjoint_fp32_mixed():
+    _adjoint_parity(W.cavity2d(32, nu=0.01, dt=0.01), tol=2e-3, precision="fp32", adv_rtol=1e-6, p_rtol=1e-6)
+
+
+def test_adjoint_matches_gpu_finite_difference():
+    """Self-consistency on the GPU alone: <ubar, du1> along a direction equals
+    the adjoint's directional derivative (4th-order central differences)."""
+    c = W.channel3d(12, 10, 6)
+    dom = gpu_domain(c)
+    d, N = c.ndim, c.ncells
+    rng = np.random.default_rng(3)
+    u0 = to_dev(dom, c.u0, d)
+    p0 = to_dev(dom, c.p0)
+    S0 = to_dev(dom, c.S, d)
+    ubar = to_dev(dom, rng.standard_normal((d, N)), d)
+    du = to_dev(dom, rng.standard_normal((d, N)), d)
+
+    def L(t):
+        u1, p1, _ = dom.step(u0 + t * du, p0, c.dt, c.nu, S0)
+        return float((ubar * u1).sum())
+
+    dom.step(u0, p0, c.dt, c.nu, S0)
+    gu, _, _, _, _ = dom.step_adjoint(ubar, None)
+    adj = float((gu * du).sum())
+    e = 1e-4
+    fd = (8 * (L(e) - L(-e)) - (L(2 * e) - L(-2 * e))) / (12 * e)
+    assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
+
+
+def test_autograd_rollout_checkpointed():
+    """Gradient of a loss after 4 steps w.r.t. u^0, S and nu through the
+    autograd wrapper (checkpointed recompute) vs the oracle chained adjoint."""
+    c = W.turbulence2d(32, nu=0.01, dt=0.02)
+    m = O.mesh_from_case(c)
+    dom = gpu_domain(c)
+    d, N = c.ndim, c.ncells
+    rng = np.random.default_rng(7)
+    target = rng.standard_normal((d, N))
+    u0 = to_dev(dom, c.u0, d).requires_grad_(True)
+    S = to_dev(dom, c.S, d).requires_grad_(True)
+    nu = torch.tensor(c.nu, dtype=torch.float64, device="cuda", requires_grad=True)
+    p0 = to_dev(dom, c.p0)
+    u, p = u0, p0
+    for _ in range(4):
+        u, p = piso_step(dom, u, p, c.dt, nu, S)
+    loss = ((u - to_dev(dom, target, d)) ** 2).sum()
+    loss.backward()
+    # oracle
+    uo, po, tapes = c.u0, c.p0, []
+    for _ in range(4):
+        uo, po, t = O.piso_step(m, uo, po, c.dt, c.nu, c.S)
+        tapes.append(t)
+    gu, gp = 2 * (uo - target), np.zeros(N)
+    gS, gnu = np.zeros((d, N)), 0.0
+    for t in reversed(tapes):
+        gu, gp, gs, gn = O.piso_step_adjoint(m, t, gu, gp)
+        gS += gs
+        gnu += gn
+    assert rel_err(host(u0.grad), gu) <= 1e-7
+    assert rel_err(host(S.grad), gS) <= 1e-7
+    assert abs(float(nu.grad) - gnu) <= 1e-7 * abs(gnu)

@@ -85,13 +85,13 @@ def test_ragged_cavity(n):
 
 def test_bfs_multiblock_outflow_small():
     c = W.bfs2d(n_in=(16, 8), n_ch=64, n_out=16, half=8, dt=0.02)
-    _per_step_parity(c, 3)
+    _per_step_parity(c, 3, p_rtol=1e-12)
 
 
 def test_bfs_config2_full_size():
     c = W.bfs2d()
     assert c.ncells == 22528
-    _per_step_parity(c, 2)
+    _per_step_parity(c, 2, p_rtol=1e-12)
 
 
 def test_channel3d_small():
