@@ -28,17 +28,19 @@ L2_FLUSH_BYTES = 256 << 20          # > 126 MB L2
 # algorithmic traffic model: every array a phase touches, counted once per
 # phase (neighbour re-reads are cache hits), in words per cell
 # ---------------------------------------------------------------------------
-def fwd_words_per_cell(d: int, adv_iters, p_iters, n_out_frac: float = 0.0) -> float:
+def fwd_words_per_cell(d: int, adv_iters, p_iters) -> float:
+    """Stored-array words per cell one forward launch touches (each array once
+    per phase; neighbour re-reads are cache hits).  One line per kernel phase."""
     it_a = max(adv_iters) if adv_iters else 0
     w = 0.0
-    w += d * d + 3 * d + 1            # F1: u, T, J -> U, tape u^n
-    w += d * d + 10 * d + 3           # F2: assemble C, rhs0, r, rhat, u* start
-    w += it_a * (21 * d + 2)          # BiCGStab: 3 phases per iteration
+    w += d * d + 3 * d + 1            # F1: u, T, J -> u^n copy, U
+    w += 11 * d + 3                   # F2: u, S, U, alpha, J -> C (2d+1), 1/A, alpha/A, rhs0, r, rhat, u*
+    w += it_a * (21 * d + 2)          # BiCGStab: BA 8d+1, BB 5d+1, BC 8d per iteration
     for k, it_p in enumerate(p_iters):
-        w += (d * d + 8 * d + 3) if k == 0 else (d * d + 6 * d + 4)   # C1: (P), h, J T.h
-        w += d + 1                    # C2: divergence
-        w += d + 6                    # C3: CG start
-        w += it_p * (d + 13)          # CG: 2 phases per iteration
+        w += (d * d + 8 * d + 4) if k == 0 else (d * d + 6 * d + 4)   # C1: (P), h, J T.h
+        w += d + 3                    # C2: divergence, x0
+        w += (d + 4) + (d + 3)        # CG start: r0, w0
+        w += it_p * (d + 11)          # CG (one phase per iteration)
         w += d * d + 2 * d + 2        # C4: correction
     w += 3                            # final pressure
     return w
@@ -46,17 +48,17 @@ def fwd_words_per_cell(d: int, adv_iters, p_iters, n_out_frac: float = 0.0) -> f
 
 def adj_words_per_cell(d: int, adv_iters, p_iters) -> float:
     it_a = max(adv_iters) if adv_iters else 0
-    w = 0.0
+    w = 6 * d + 3                     # R0 extra on the first pass: rebuild P, clear accumulators
     for it_p in p_iters:
-        w += d * d + 3 * d + 3        # R0: w = T gu / A, gA
-        w += d + 3                    # R1: -G^T w
-        w += 5 + it_p * (d + 13)      # CG on P (transposed = P)
-        w += d * d + 6 * d + 8        # R3: gw, div^T, gg, gA, grhs0
-        w += 2 * d * d + 4 * d + 2    # R4: -H^T gg, gCoff
-    w += 3 * d + 3                    # R5
-    w += 2 * d + 5 + it_a * (21 * d + 2)   # BiCGStab on C^T
-    w += 4 * d + 2 * d + 4            # R6
-    w += d * d + 6 * d + 6            # R7: assembly adjoint
+        w += d * d + 2 * d + 4        # R0: W = T gu / A, dL/dA
+        w += d + 3                    # R1: -G^T W
+        w += (d + 4) + (d + 3) + it_p * (d + 11)   # CG on P
+        w += d * d + 7 * d + 6        # R3: d(alpha/A), div^T y, gg, dL/dA, dL/drhs0
+        w += 9 * d                    # R4: -H^T gg, dL/dH
+    w += 6 * d + 3                    # R5: start of the C^T solve
+    w += it_a * (21 * d + 2)          # BiCGStab on C^T
+    w += 9 * d + 3                    # R6: dL/dC from the predictor, dS, du (1/dt part)
+    w += d * d + 5 * d + 3            # R7: assembly adjoint
     return w
 
 
@@ -100,6 +102,17 @@ def clocks_sampler_stop(proc, f, path, gpu_index=0):
         return None
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
             "samples": len(sm)}
+
+
+def whole_job_value(total_s: float, steps: int, world: int, dist=None, device="cuda") -> float:
+    """Replicas: every rank times its own K steps; the job's throughput is the
+    units all ranks processed over the slowest rank's time."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return world * steps / total_s
 
 
 def measured_peaks():
@@ -244,11 +257,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     fwd_ms = [a.elapsed_time(b) for a, b in kev]
     total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
+    value = whole_job_value(total_s, args.steps, world, dist)
+    total_s = world * args.steps / value
 
     # end to end through the public API with host buffers
     hu = torch.empty((d, N), dtype=dom.dtype, pin_memory=True)
@@ -270,11 +280,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = world * args.steps / e2e_s
+    e2e = whole_job_value(e2e_s, args.steps, world, dist)
     io_bytes = (d + 1) * N * w
 
     # roofline of the dominant kernel (the persistent forward-step kernel)

@@ -76,6 +76,9 @@ typedef struct {
   int32_t block_threads; /* threads per CTA (multiple of 32, <= 512); 0 = auto */
   int32_t ctas;          /* CTAs for this domain; 0 = auto (one per SM, capped by size) */
   double timeout_s;      /* group-barrier wait limit in seconds (default 5) */
+  int32_t fault_withhold_cta; /* fault injection for tests: this CTA of the domain skips its
+                                 first barrier arrival, so every wait of the step runs out and
+                                 the call returns PISO_ETIMEOUT; -1 (default) = off */
 } piso_options;
 
 /* Per-step statistics (read back when a stats pointer is given). */

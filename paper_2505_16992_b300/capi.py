@@ -19,7 +19,7 @@ class Options(C.Structure):
     _fields_ = [("n_correctors", C.c_int32), ("pred_grad_p", C.c_int32), ("adv_rtol", C.c_double),
                 ("p_rtol", C.c_double), ("atol", C.c_double), ("adv_maxit", C.c_int32),
                 ("p_maxit", C.c_int32), ("block_threads", C.c_int32), ("ctas", C.c_int32),
-                ("timeout_s", C.c_double)]
+                ("timeout_s", C.c_double), ("fault_withhold_cta", C.c_int32)]
 
 
 class Stats(C.Structure):

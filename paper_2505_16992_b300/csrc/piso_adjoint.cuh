@@ -32,6 +32,7 @@ struct AdjCall {
   // scratch
   real* Poff;                // [d][N] pressure matrix rebuilt from A
   real* Pdiag;               // [N]
+  real* Pinv;                // [N]
   real* gA;                  // [N]       dL/dA, A = diag C
   real* gCoff;               // [2d][N]   dL/d(off-diagonal C)
   real* grhs0;               // [d][N]    dL/d(rhs0)
@@ -68,8 +69,9 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   copy_to_smem(&D, A.dom);
   __syncthreads();
   const int32_t N = D.N;
-  const Ctx<real, ND> X{D, g, (int32_t)(((int64_t)N * g.rank) / g.ncta),
-                        (int32_t)(((int64_t)N * (g.rank + 1)) / g.ncta), N};
+  const int32_t lo = (int32_t)(((int64_t)N * g.rank) / g.ncta);
+  const int32_t hi = (int32_t)(((int64_t)N * (g.rank + 1)) / g.ncta);
+  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap)};
   const real* J = reinterpret_cast<const real*>(D.J);
   const real* T = reinterpret_cast<const real*>(D.T);
   const real* AL = reinterpret_cast<const real*>(D.alpha);
@@ -118,6 +120,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
           A.gCoff[(size_t)s * N + P] = 0;
         }
         A.Pdiag[P] = pd;
+        A.Pinv[P] = real(1) / (-pd);
 #pragma unroll
         for (int i = 0; i < ND; i++) {
           A.grhs0[(size_t)i * N + P] = 0;
@@ -165,8 +168,8 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       if (!reduce_sync<real, 1>(g, a, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
     }
     // transposed pressure solve: P y = gx - mean (P is symmetric)
-    if (!cg_pressure<real, ND>(X, cs, o.p_rtol, o.atol, o.p_maxit, A.Pdiag, A.Poff, A.gx, s_mean, A.cx, A.crb,
-                               A.cwb, A.csb, A.cp))
+    if (!cg_pressure<real, ND>(X, cs, o.p_rtol, o.atol, o.p_maxit, A.Pdiag, A.Pinv, A.Poff, A.gx, s_mean, A.cx,
+                               A.crb, A.cwb, A.csb, A.cp))
       return;
     if (threadIdx.x == 0 && g.rank == 0) {
       A.istats[4 + k] = cs.it;
@@ -383,6 +386,7 @@ __global__ void __launch_bounds__(512, 1) adj_kernel(const __grid_constant__ Lau
   g.rank = blockIdx.x - A.cta0;
   g.epoch = 0;
   g.timeout_ns = L.o.timeout_ns;
+  g.withhold = (L.o.withhold_cta == g.rank) ? 1 : 0;
   adj_group<real, ND>(A, L.o, g);
 }
 

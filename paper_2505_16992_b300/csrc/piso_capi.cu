@@ -99,7 +99,7 @@ struct piso_batch {
   void* d_calls = nullptr;
   void* h_calls = nullptr;     // pinned
   size_t call_bytes = 0;
-  uint32_t* bars = nullptr;    // one per domain (contiguous)
+  void* h_calls_aux = nullptr; // device/pinned control block of the batch launch
   std::string err;
 };
 
@@ -200,7 +200,7 @@ void put(std::vector<char>& buf, size_t i, double v) {
 // --- workspace layout ------------------------------------------------------
 enum WsIdx {
   W_U, W_RHS0, W_R, W_RHAT, W_P0, W_P1, W_V0, W_V1, W_T, W_POFF, W_PDIAG, W_FH, W_B, W_CX,
-  W_CRB0, W_CRB1, W_CWB0, W_CWB1, W_CSB0, W_CSB1, W_CP,
+  W_CRB0, W_CRB1, W_CWB0, W_CWB1, W_CSB0, W_CSB1, W_CP, W_PINV, W_INVA, W_AW,
   // adjoint scratch
   A_GA, A_GCOFF, A_GRHS0, A_GW, A_W, A_GG, A_GU, A_GX, A_Z, A_DU,
   W_COUNT
@@ -210,7 +210,7 @@ enum WsIdx {
 int ws_units(int k, int nd) {
   switch (k) {
     case W_PDIAG: case W_B: case W_CX: case W_CRB0: case W_CRB1: case W_CWB0: case W_CWB1: case W_CSB0:
-    case W_CSB1: case W_CP: case A_GA: case A_GX:
+    case W_CSB1: case W_CP: case A_GA: case A_GX: case W_PINV: case W_INVA:
       return 1;
     case A_GCOFF:
       return 2 * nd;
@@ -285,6 +285,9 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
   c.t = (real*)d->ws[W_T];
   c.Poff = (real*)d->ws[W_POFF];
   c.Pdiag = (real*)d->ws[W_PDIAG];
+  c.Pinv = (real*)d->ws[W_PINV];
+  c.invA = (real*)d->ws[W_INVA];
+  c.Aw = (real*)d->ws[W_AW];
   c.Fh = (real*)d->ws[W_FH];
   c.b = (real*)d->ws[W_B];
   c.cx = (real*)d->ws[W_CX];
@@ -314,15 +317,32 @@ SolverOpts solver_opts(const piso_options& o) {
   s.p_rtol = o.p_rtol;
   s.atol = o.atol;
   s.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
+  s.nbt_cap = 0;
+  s.withhold_cta = o.fault_withhold_cta;
   return s;
 }
 
+// Dynamic shared memory for the per-CTA neighbour table: 2*ndim int32 per cell
+// of the largest CTA range, when that fits beside the static shared memory.
+constexpr size_t NBT_MAX_BYTES = 160 * 1024;
+
+size_t nbt_bytes(int ndim, int64_t N, int ncta, int32_t* cap) {
+  const int64_t per = (N + ncta - 1) / ncta;
+  const size_t b = (size_t)per * 2 * ndim * sizeof(int32_t);
+  if (b > NBT_MAX_BYTES) {
+    *cap = 0;
+    return 0;
+  }
+  *cap = (int32_t)per;
+  return b;
+}
+
 template <typename K>
-cudaError_t coop_launch(K kernel, int grid, int threads, void** args, cudaStream_t st) {
+cudaError_t coop_launch(K kernel, int grid, int threads, void** args, cudaStream_t st, size_t smem = 0) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -346,7 +366,8 @@ int max_coresident(const void* kernel, int threads, int* sms_out) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NBT_MAX_BYTES);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, NBT_MAX_BYTES);
   if (sms_out) *sms_out = sms;
   return sms * std::max(per_sm, 0);
 }
@@ -419,12 +440,14 @@ piso_status launch_fwd(piso_domain* d, const void* u_in, const void* p_in, void*
   L.o = solver_opts(d->opts);
   L.cta_first = nullptr;
   L.calls = nullptr;
+  const size_t smem = nbt_bytes(d->ndim, d->N, d->ncta, &L.o.nbt_cap);
   fill_fwd_call<real>(d, L.call0, u_in, p_in, u_out, p_out, dt, nu, S, tape);
   CUDA_TRY(d, cudaMemsetAsync(d->bar, 0, 64, st));
   CUDA_TRY(d, cudaMemsetAsync(d->status, 0, 64, st));
   CUDA_TRY(d, cudaMemsetAsync(d->istats, 0, 64, st));
   void* args[] = {&L};
-  CUDA_TRY(d, coop_launch(d->ndim == 2 ? fwd_kernel<real, 2> : fwd_kernel<real, 3>, d->ncta, d->threads, args, st));
+  CUDA_TRY(d, coop_launch(d->ndim == 2 ? fwd_kernel<real, 2> : fwd_kernel<real, 3>, d->ncta, d->threads, args, st,
+                          smem));
   return PISO_OK;
 }
 
@@ -449,6 +472,7 @@ void piso_default_options(piso_options* o) {
   o->block_threads = 0;
   o->ctas = 0;
   o->timeout_s = 5.0;
+  o->fault_withhold_cta = -1;
 }
 
 piso_status piso_domain_create(int32_t ndim, int32_t prec, piso_domain** out) {

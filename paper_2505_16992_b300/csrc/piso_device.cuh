@@ -227,88 +227,26 @@ struct Group {
   int32_t ncta, rank;
   uint32_t epoch;
   uint64_t timeout_ns;
+  int32_t withhold;     // fault injection: this CTA skips its first arrival (1) or not (0)
 };
 
-// Returns false (and every CTA of the group leaves its phase loop) when the
-// wait ran out or another CTA of the group reported a timeout.
-__device__ __noinline__ bool group_sync(Group& g) {
-  __shared__ int s_ok;
-  __syncthreads();
-  g.epoch++;                 // every thread keeps the same count (it selects the partials buffer)
-  if (threadIdx.x == 0) {
-    const uint32_t target = g.epoch * (uint32_t)g.ncta;
-    __threadfence();
-    atomicAdd(g.bar, 1u);
-    int ok = 1;
-    if ((int32_t)(ld_acquire_u32(g.bar) - target) < 0) {
-      const uint64_t t0 = global_ns();
-      while (true) {
-        if ((int32_t)(ld_acquire_u32(g.bar) - target) >= 0) break;
-        if (*((volatile int32_t*)g.status) & PISO_ERR_TIMEOUT) { ok = 0; break; }
-        if (global_ns() - t0 > g.timeout_ns) {
-          atomicOr(g.status, PISO_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// Block-reduce NS accumulators and publish this CTA's partials for the next
-// barrier.  Must be called by all threads of the CTA.
-template <typename real, int NS>
-__device__ __forceinline__ void publish(const Group& g, Acc<real> (&a)[NS]) {
-  __shared__ double s_w[MAXW][NSMAX];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NS; k++) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) a[k].shfl_down_add(off);
-    if (lane == 0) s_w[warp][k] = a[k].to_double();
-  }
-  __syncthreads();
-  if (threadIdx.x < NS) {
-    double s = 0.0;
-    const int nw = blockDim.x >> 5;
-    for (int w = 0; w < nw; w++) s += s_w[w][threadIdx.x];
-    const int par = (g.epoch + 1) & 1;
-    g.partials[((size_t)par * NSMAX + threadIdx.x) * g.ncta + g.rank] = s;
-  }
-}
-
-// After the barrier: the group totals, summed in a fixed order (identical in
-// every CTA of the group).
-template <int NS>
-__device__ __forceinline__ void gather(const Group& g, double (&out)[NS]) {
-  __shared__ double s_r[NSMAX];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int par = g.epoch & 1;
-  const int nw = blockDim.x >> 5;
-  for (int k = warp; k < NS; k += nw) {
-    const double* src = g.partials + ((size_t)par * NSMAX + k) * g.ncta;
-    double s = 0.0;
-    for (int c = lane; c < g.ncta; c += 32) s += __ldcg(src + c);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) s_r[k] = s;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NS; k++) out[k] = s_r[k];
-  __syncthreads();
+__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Arrival and bounded wait of one CTA at barrier g.epoch (called by one thread
-// after the CTA's writes were ordered by __syncthreads).
+// after __syncthreads ordered the CTA's writes).  The release increment makes
+// those writes visible to every CTA whose acquire load sees the count.
 __device__ __noinline__ int barrier_arrive_wait(const Group& g) {
   const uint32_t target = g.epoch * (uint32_t)g.ncta;
-  __threadfence();
-  atomicAdd(g.bar, 1u);
+  if (!(g.withhold && g.epoch == 1)) {
+#ifdef PISO_FULL_FENCES
+    __threadfence();
+    atomicAdd(g.bar, 1u);
+#else
+    red_release_add(g.bar, 1u);
+#endif
+  }
   int ok = 1;
   if ((int32_t)(ld_acquire_u32(g.bar) - target) < 0) {
     const uint64_t t0 = global_ns();
@@ -322,15 +260,21 @@ __device__ __noinline__ int barrier_arrive_wait(const Group& g) {
       }
     }
   }
+#ifdef PISO_FULL_FENCES
   __threadfence();
+#endif
   return ok;
 }
 
 // One phase boundary with a reduction: block-reduce the NS accumulators,
 // publish this CTA's partials, wait at the group barrier, sum the group's
-// partials in a fixed order (warp 0; identical in every CTA) and let thread 0
-// run update(totals) on the shared solver state before the closing
-// __syncthreads.  Returns false when the barrier wait ran out.
+// partials in a fixed order (identical in every CTA) and let thread 0 run
+// update(totals) on the shared solver state.  Warp k reduces scalar k, so the
+// block- and group-level sums of different scalars proceed in parallel and
+// each lane issues all its partial loads before adding.  Returns false when
+// the barrier wait ran out.
+constexpr int GATHER_UNROLL = 8;
+
 template <typename real, int NS, typename F>
 __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& update) {
   __shared__ double s_w[MAXW * NSMAX];
@@ -345,42 +289,44 @@ __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& up
   }
   __syncthreads();
   g.epoch++;
-  if (warp == 0) {
-    double* P = g.partials + (size_t)(g.epoch & 1) * NSMAX * g.ncta;
+  double* P = g.partials + (size_t)(g.epoch & 1) * NSMAX * g.ncta;
+  for (int k = warp; k < NS; k += nw) {
+    Acc<real> v;
+    v.zero();
+    if (lane < nw) v.unpack_add(s_w[lane * NSMAX + k]);
 #pragma unroll
-    for (int k = 0; k < NS; k++) {
-      Acc<real> v;
-      v.zero();
-      if (lane < nw) v.unpack_add(s_w[lane * NSMAX + k]);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v.shfl_down_add(off);
-      if (lane == 0) __stcg(P + (size_t)k * g.ncta + g.rank, v.pack());
-    }
-    int ok = 1;
-    if (lane == 0) ok = barrier_arrive_wait(g);
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (ok) {
-      Acc<real> v[NS];
-#pragma unroll
-      for (int k = 0; k < NS; k++) {
-        v[k].zero();
-        for (int c = lane; c < g.ncta; c += 32) v[k].unpack_add(__ldcg(P + (size_t)k * g.ncta + c));
-      }
-#pragma unroll
-      for (int k = 0; k < NS; k++) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[k].shfl_down_add(off);
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < NS; k++) s_tot[k] = v[k].to_double();
-        update(s_tot);
-      }
-    }
-    if (lane == 0) s_ok = ok;
+    for (int off = 16; off > 0; off >>= 1) v.shfl_down_add(off);
+    if (lane == 0) __stcg(P + (size_t)k * g.ncta + g.rank, v.pack());
   }
   __syncthreads();
-  return s_ok != 0;
+  if (threadIdx.x == 0) s_ok = barrier_arrive_wait(g);
+  __syncthreads();
+  const int ok = s_ok;
+  if (ok) {
+    for (int k = warp; k < NS; k += nw) {
+      const double* src = P + (size_t)k * g.ncta;
+      Acc<real> v;
+      v.zero();
+      for (int base = 0; base < g.ncta; base += 32 * GATHER_UNROLL) {
+        double w[GATHER_UNROLL];
+#pragma unroll
+        for (int u = 0; u < GATHER_UNROLL; u++) {
+          const int c = base + lane + 32 * u;
+          w[u] = c < g.ncta ? __ldcg(src + c) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < GATHER_UNROLL; u++)
+          if (base + lane + 32 * u < g.ncta) v.unpack_add(w[u]);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v.shfl_down_add(off);
+      if (lane == 0) s_tot[k] = v.to_double();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) update(s_tot);
+  }
+  __syncthreads();
+  return ok != 0;
 }
 
 // A phase boundary without a reduction.

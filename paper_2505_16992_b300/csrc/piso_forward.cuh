@@ -41,6 +41,9 @@ struct FwdCall {
   real* t;                   // [d][N]
   real* Poff;                // [d][N] + faces
   real* Pdiag;               // [N]
+  real* Pinv;                // [N]    1 / diag(-P)
+  real* invA;                // [N]    1 / A
+  real* Aw;                  // [d][N] alpha_jj / A
   real* Fh;                  // [d][N] J T . h
   real* b;                   // [N]
   real* cx;                  // [N]
@@ -94,8 +97,9 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   copy_to_smem(&D, A.dom);
   __syncthreads();
   const int32_t N = D.N;
-  const Ctx<real, ND> X{D, g, (int32_t)(((int64_t)N * g.rank) / g.ncta),
-                        (int32_t)(((int64_t)N * (g.rank + 1)) / g.ncta), N};
+  const int32_t lo = (int32_t)(((int64_t)N * g.rank) / g.ncta);
+  const int32_t hi = (int32_t)(((int64_t)N * (g.rank + 1)) / g.ncta);
+  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap)};
   const real* J = reinterpret_cast<const real*>(D.J);
   const real* T = reinterpret_cast<const real*>(D.T);
   const real* AL = reinterpret_cast<const real*>(D.alpha);
@@ -220,6 +224,10 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
         A.Coff[(size_t)s * N + P] = off[s];
       }
       A.Cdiag[P] = diag;
+      const real ia = real(1) / diag;
+      A.invA[P] = ia;
+#pragma unroll
+      for (int j = 0; j < ND; j++) A.Aw[(size_t)j * N + P] = AL[(size_t)j * N + P] * ia;
       real gp[ND];
 #pragma unroll
       for (int k = 0; k < ND; k++) gp[k] = 0;
@@ -281,7 +289,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
     // Fh = J T . h; (kc > 0) also the previous corrector's mean-free pressure.
     X.cells([&](const Cell& c) {
       const int32_t P = c.i;
-      const real aP = A.Cdiag[P];
+      const real ia = A.invA[P];
       if (kc == 0) {
         real pd = 0;
 #pragma unroll
@@ -289,11 +297,12 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
           const int j = s >> 1;
           const int32_t F = c.nb[s];
           real pf = 0;
-          if (F >= 0) pf = real(0.5) * (AL[(size_t)j * N + P] / aP + AL[(size_t)j * N + F] / A.Cdiag[F]);
+          if (F >= 0) pf = real(0.5) * (A.Aw[(size_t)j * N + P] + A.Aw[(size_t)j * N + F]);
           pd -= pf;
           if (s & 1) A.Poff[(size_t)j * N + P] = pf;
         }
         A.Pdiag[P] = pd;
+        A.Pinv[P] = real(1) / (-pd);
       } else {
         A.xk[kc - 1][P] = A.cx[P] - (real)s_mean;
       }
@@ -305,7 +314,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
 #pragma unroll
         for (int s = 0; s < NSD; s++)
           if (c.nb[s] >= 0) hu += A.Coff[(size_t)s * N + P] * x[c.nb[s]];
-        hv[k] = (A.rhs0[(size_t)k * N + P] - hu) / aP;
+        hv[k] = (A.rhs0[(size_t)k * N + P] - hu) * ia;
         h[(size_t)k * N + P] = hv[k];
       }
 #pragma unroll
@@ -346,8 +355,8 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       if (!reduce_sync<real, 1>(g, a, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
     }
     // pressure solve (App. A.5: CG; Chronopoulos-Gear form)
-    if (!cg_pressure<real, ND>(X, cs, o.p_rtol, o.atol, o.p_maxit, A.Pdiag, A.Poff, A.b, s_mean, A.cx, A.crb,
-                               A.cwb, A.csb, A.cp))
+    if (!cg_pressure<real, ND>(X, cs, o.p_rtol, o.atol, o.p_maxit, A.Pdiag, A.Pinv, A.Poff, A.b, s_mean, A.cx,
+                               A.crb, A.cwb, A.csb, A.cp))
       return;
     if (threadIdx.x == 0 && g.rank == 0) {
       A.istats[4 + kc] = cs.it;
@@ -373,9 +382,9 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
 #pragma unroll
           for (int k = 0; k < ND; k++) gp[k] += Tm(j, k, P) * dd;
         }
-        const real aP = A.Cdiag[P];
+        const real ia = A.invA[P];
 #pragma unroll
-        for (int k = 0; k < ND; k++) uo[(size_t)k * N + P] = h[(size_t)k * N + P] - gp[k] / aP;
+        for (int k = 0; k < ND; k++) uo[(size_t)k * N + P] = h[(size_t)k * N + P] - gp[k] * ia;
         a[0].add(xP);
       });
       if (!reduce_sync<real, 1>(g, a, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
@@ -407,6 +416,7 @@ __global__ void __launch_bounds__(512, 1) fwd_kernel(const __grid_constant__ Lau
   g.rank = blockIdx.x - A.cta0;
   g.epoch = 0;
   g.timeout_ns = L.o.timeout_ns;
+  g.withhold = (L.o.withhold_cta == g.rank) ? 1 : 0;
   fwd_group<real, ND>(A, L.o, g);
 }
 

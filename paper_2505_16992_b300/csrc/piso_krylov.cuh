@@ -12,7 +12,25 @@ struct SolverOpts {
   int32_t n_corr, pred_grad_p, adv_maxit, p_maxit;
   double adv_rtol, p_rtol, atol;
   uint64_t timeout_ns;
+  int32_t nbt_cap;           // cells per CTA the shared neighbour table can hold
+  int32_t withhold_cta;      // fault injection: group rank that skips its first barrier arrival (-1 off)
 };
+
+// Fill the CTA's neighbour table (dynamic shared memory) when its cell range
+// fits; returns the table or nullptr.
+template <int ND>
+__device__ __forceinline__ const int32_t* build_nbt(const DomStatic& D, int32_t lo, int32_t hi, int32_t cap) {
+  extern __shared__ int32_t s_nbt[];
+  const int32_t n = hi - lo;
+  if (n > cap) return nullptr;
+  for (int32_t l = threadIdx.x; l < n; l += blockDim.x) {
+    const Cell c = locate<ND>(D, lo + l);
+#pragma unroll
+    for (int s = 0; s < 2 * ND; s++) s_nbt[s * n + l] = c.nb[s];
+  }
+  __syncthreads();
+  return s_nbt;
+}
 
 // Execution context of one CTA inside its group.
 template <typename real, int ND>
@@ -20,11 +38,23 @@ struct Ctx {
   const DomStatic& D;   // shared-memory copy
   Group& g;
   int32_t lo, hi, N;
+  const int32_t* nbt;   // [2*ND][hi-lo] neighbour table in shared memory, or nullptr
   template <typename F>
   __device__ __forceinline__ void cells(F&& f) const {
-    for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += blockDim.x) {
-      const Cell c = locate<ND>(D, i);
-      f(c);
+    if (nbt) {
+      const int32_t n = hi - lo;
+      for (int32_t l = (int32_t)threadIdx.x; l < n; l += blockDim.x) {
+        Cell c;
+        c.i = lo + l;
+#pragma unroll
+        for (int s = 0; s < 2 * ND; s++) c.nb[s] = nbt[s * n + l];
+        f(c);
+      }
+    } else {
+      for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += blockDim.x) {
+        const Cell c = locate<ND>(D, i);
+        f(c);
+      }
     }
   }
   template <typename F>
@@ -282,8 +312,9 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
 // rb, wb, sb are ping-pong buffers for r, w = A u and s = A p; pdir holds p.
 template <typename real, int ND>
 __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, double atol, int maxit,
-                            const real* Pdiag, const real* Poff, const real* b, double bmean, real* x,
-                            real* const (&rb)[2], real* const (&wb)[2], real* const (&sb)[2], real* pdir) {
+                            const real* Pdiag, const real* Pinv, const real* Poff, const real* b, double bmean,
+                            real* x, real* const (&rb)[2], real* const (&wb)[2], real* const (&sb)[2],
+                            real* pdir) {
   const int32_t N = X.N;
   // I1: r0 = b' - A' x0 with b' = -(b - mean), A' = -P
   {
@@ -330,12 +361,12 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
       real pf[2 * ND];
       p_row<real, ND>(c, N, Poff, pf);
       const real rP = r0[c.i];
-      const real uP = rP / (-Pdiag[c.i]);
+      const real uP = rP * Pinv[c.i];
       real w = rP;
 #pragma unroll
       for (int s = 0; s < 2 * ND; s++) {
         const int32_t Q = c.nb[s];
-        if (Q >= 0) w -= pf[s] * (r0[Q] / (-Pdiag[Q]));
+        if (Q >= 0) w -= pf[s] * (r0[Q] * Pinv[Q]);
       }
       wb[0][c.i] = w;
       a[0].add_prod(rP, uP);
@@ -372,10 +403,10 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
       real pf[2 * ND];
       p_row<real, ND>(c, N, Poff, pf);
       auto sQ = [&](int32_t Q) -> real { return first ? w_i[Q] : w_i[Q] + be * s_o[Q]; };
-      auto u1 = [&](int32_t Q) -> real { return (r_i[Q] - al * sQ(Q)) / (-Pdiag[Q]); };
+      auto u1 = [&](int32_t Q) -> real { return (r_i[Q] - al * sQ(Q)) * Pinv[Q]; };
       const int32_t P = c.i;
-      const real dP = -Pdiag[P];
-      const real uP = r_i[P] / dP;
+      const real iP = Pinv[P];
+      const real uP = r_i[P] * iP;
       const real p = first ? uP : uP + be * pdir[P];
       pdir[P] = p;
       x[P] += al * p;
@@ -383,7 +414,7 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
       s_n[P] = sP;
       const real r1 = r_i[P] - al * sP;
       r_n[P] = r1;
-      const real u1P = r1 / dP;
+      const real u1P = r1 * iP;
       real w1 = r1;
 #pragma unroll
       for (int s = 0; s < 2 * ND; s++)

@@ -1,0 +1,108 @@
+"""Batched persistent launch: independent simulations of uneven size stepped in
+one cooperative launch (one CTA group per domain), checked member by member
+against the FP64 oracle; adjoint; CUDA-graph capture of a batched step."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2505_16992_b300 import capi
+from paper_2505_16992_b300 import workloads as W
+from paper_2505_16992_b300.solver import Batch
+from gpu_util import gpu_domain, host, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _members(cases, precision="fp64", **opts):
+    doms = [gpu_domain(c, precision, **opts) for c in cases]
+    us = [to_dev(d, c.u0, c.ndim) for d, c in zip(doms, cases)]
+    ps = [to_dev(d, c.p0) for d, c in zip(doms, cases)]
+    Ss = [None if c.S is None else to_dev(d, c.S, c.ndim) for d, c in zip(doms, cases)]
+    return doms, us, ps, Ss
+
+
+def test_batch_forward_matches_oracle_per_member():
+    cases = W.batch2d(count=7, seed=5, nmin=6, nmax=40)
+    doms, us, ps, Ss = _members(cases)
+    b = Batch(doms, capi.default_options(adv_rtol=1e-13, p_rtol=1e-13))
+    uo, po, st = b.step(us, ps, [c.dt for c in cases], [c.nu for c in cases], Ss)
+    for i, c in enumerate(cases):
+        assert st[i]["status"] == "PISO_OK", (i, st[i])
+        m = O.mesh_from_case(c)
+        u1, p1, _ = O.piso_step(m, c.u0, c.p0, c.dt, c.nu, c.S)
+        assert rel_err(host(uo[i]), u1) <= 1e-10, i
+        assert rel_err(host(po[i]), p1) <= 1e-9, i
+
+
+def test_batch_equals_single_domain_launches():
+    """A member's result in the batch equals its own single-domain launch up to
+    the summation order of its reductions (different CTA split)."""
+    cases = W.batch2d(count=5, seed=6, nmin=8, nmax=48)
+    doms, us, ps, Ss = _members(cases)
+    b = Batch(doms, capi.default_options(adv_rtol=1e-13, p_rtol=1e-13))
+    uo, po, _ = b.step(us, ps, [c.dt for c in cases], [c.nu for c in cases], Ss)
+    for i, (d, c) in enumerate(zip(doms, cases)):
+        u1, p1, _ = d.step(us[i], ps[i], c.dt, c.nu, Ss[i])
+        assert rel_err(host(uo[i]), host(u1)) <= 1e-11
+
+
+def test_batch_adjoint_matches_oracle():
+    cases = W.batch2d(count=4, seed=8, nmin=6, nmax=24)
+    doms, us, ps, Ss = _members(cases)
+    b = Batch(doms, capi.default_options(adv_rtol=1e-13, p_rtol=1e-13))
+    b.step(us, ps, [c.dt for c in cases], [c.nu for c in cases], Ss)
+    rng = np.random.default_rng(1)
+    gus = [rng.standard_normal((2, c.ncells)) for c in cases]
+    du, dp, dS, dnu, st = b.step_adjoint([to_dev(d, g, 2) for d, g in zip(doms, gus)])
+    for i, c in enumerate(cases):
+        assert st[i]["status"] == "PISO_OK"
+        m = O.mesh_from_case(c)
+        _, _, tape = O.piso_step(m, c.u0, c.p0, c.dt, c.nu, c.S)
+        gu, gp, gS, gnu = O.piso_step_adjoint(m, tape, gus[i], np.zeros(c.ncells))
+        assert rel_err(host(du[i]), gu) <= 1e-8, i
+        assert abs(dnu[i] - gnu) <= 1e-8 * abs(gnu), i
+
+
+def test_batch_config5_full_size_sampled_parity():
+    """Config 5: 64 independent 2D cavity/channel simulations, sides uniform in
+    32..256, Re in [100, 2000], FP32 bulk; sampled members against the oracle."""
+    cases = W.batch2d()
+    assert len(cases) == 64
+    doms, us, ps, Ss = _members(cases, "fp32", adv_rtol=1e-6, p_rtol=1e-6)
+    b = Batch(doms, capi.default_options(adv_rtol=1e-6, p_rtol=1e-6))
+    uo, po, st = b.step(us, ps, [c.dt for c in cases], [c.nu for c in cases], Ss)
+    assert all(s["status"] == "PISO_OK" for s in st)
+    sizes = [c.ncells for c in cases]
+    pick = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 1, 10})
+    for i in pick:
+        c = cases[i]
+        m = O.mesh_from_case(c)
+        u1, p1, _ = O.piso_step(m, c.u0, c.p0, c.dt, c.nu, c.S)
+        assert rel_err(host(uo[i]), u1) <= 1e-4, (i, c.ncells)
+
+
+def test_batch_step_in_cuda_graph():
+    """The batched forward step captured in a CUDA graph replays bit-identically
+    to the eager launch."""
+    cases = W.batch2d(count=6, seed=9, nmin=16, nmax=64)
+    doms, us, ps, Ss = _members(cases, "fp32", adv_rtol=1e-6, p_rtol=1e-6)
+    b = Batch(doms, capi.default_options(adv_rtol=1e-6, p_rtol=1e-6))
+    dts, nus = [c.dt for c in cases], [c.nu for c in cases]
+    uo = [torch.empty_like(u) for u in us]
+    po = [torch.empty_like(p) for p in ps]
+    ref_u, ref_p, _ = b.step(us, ps, dts, nus, Ss)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.step(us, ps, dts, nus, Ss, u_out=uo, p_out=po, sync=False)     # warm-up on the side stream
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.step(us, ps, dts, nus, Ss, u_out=uo, p_out=po, sync=False)
+    for t in uo + po:
+        t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for i in range(len(cases)):
+        assert torch.equal(uo[i], ref_u[i]) and torch.equal(po[i], ref_p[i]), i

@@ -188,3 +188,18 @@ def test_errors_reported_not_trapped():
     # the context is still usable afterwards
     u1, p1, st = dom.step(u, p, c.dt, c.nu)
     assert st["status"] == "PISO_OK"
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    """Failure detection without a GPU fault: one CTA withholds its first
+    barrier arrival (fault injection); every bounded wait runs out after
+    timeout_s, the step returns PISO_ETIMEOUT, and the next step succeeds."""
+    c = W.cavity2d(32)
+    dom = gpu_domain(c, ctas=4, block_threads=128, timeout_s=0.2, fault_withhold_cta=2)
+    u, p = to_dev(dom, c.u0, 2), to_dev(dom, c.p0)
+    with pytest.raises(capi.PisoError) as e:
+        dom.step(u, p, c.dt, c.nu)
+    assert e.value.status == 6          # PISO_ETIMEOUT
+    dom.set_options(capi.default_options(ctas=4, block_threads=128))
+    u1, p1, st = dom.step(u, p, c.dt, c.nu)
+    assert st["status"] == "PISO_OK"
