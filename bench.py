@@ -70,7 +70,7 @@ def clocks_sampler_start(path):
     try:
         f = open(path, "w")
         return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                 "-lms", "100"], stdout=f, stderr=subprocess.DEVNULL), f
+                                 "-lms", "20"], stdout=f, stderr=subprocess.DEVNULL), f
     except Exception:
         return None, None
 
@@ -176,12 +176,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--mode", default="fwdadj", choices=["fwd", "fwdadj"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--threads", type=int, default=0, help="CTA width; 0 = autotune")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -206,7 +207,8 @@ def main():
     case = W.channel3d()
     prec = args.precision
     rtol = 1e-6 if prec == "fp32" else 1e-10
-    opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000)
+    opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
+                                block_threads=args.threads)
     dom = Domain.from_case(case, prec, opts)
     d, N = case.ndim, case.ncells
     w = 4 if prec == "fp32" else 8
@@ -218,6 +220,10 @@ def main():
     gu = torch.ones_like(u)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    if args.threads == 0:
+        shape = dom.autotune(u, p, case.dt, case.nu, S)
+    else:
+        shape = (args.threads, None, None)
     with_adj = args.mode == "fwdadj"
 
     def one_step():
@@ -308,7 +314,8 @@ def main():
                                    "laminar + N(0,0.1^2) perturbation (seed 0)",
                        "cells": N, "precision": prec, "krylov_rtol": rtol,
                        "l2": "flushed between timed steps (256 MB write, untimed)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "launch": {"threads": shape[0], "ctas": shape[1], "autotuned": args.threads == 0}},
             "iterations": {"adv": st["adv_iters"][:d], "p": st["p_iters"][:2],
                            "adj_adv": adj_st["adv_iters"][:d] if adj_st else None,
                            "adj_p": adj_st["p_iters"][:2] if adj_st else None},

@@ -73,7 +73,7 @@ typedef struct {
   double atol;           /* absolute tolerance for both */
   int32_t adv_maxit;     /* BiCGStab iteration limit */
   int32_t p_maxit;       /* CG iteration limit per corrector */
-  int32_t block_threads; /* threads per CTA (multiple of 32, <= 512); 0 = auto */
+  int32_t block_threads; /* threads per CTA (multiple of 32, <= 768); 0 = 512 (see piso_autotune) */
   int32_t ctas;          /* CTAs for this domain; 0 = auto (one per SM, capped by size) */
   double timeout_s;      /* group-barrier wait limit in seconds (default 5) */
   int32_t fault_withhold_cta; /* fault injection for tests: this CTA of the domain skips its
@@ -155,6 +155,18 @@ size_t piso_tape_bytes(const piso_domain* d);
 piso_status piso_step(piso_domain* d, const void* u_in, const void* p_in, void* u_out,
                       void* p_out, double dt, double nu, const void* S, void* tape,
                       void* stream, piso_stats* stats);
+
+/* Launch-shape autotuner (no counterpart in the paper; a B300 execution
+ * choice): time one forward step of the given state (device u, p, S as for
+ * piso_step; the inputs are not modified and the outflow boundary state is
+ * restored) for each candidate shape - CTA width 512 or 768 threads, CTA count
+ * one per SM or one cell per thread - and make the fastest the domain's shape.
+ * Results are cached per process by (ndim, precision, cells, blocks,
+ * correctors).  threads_out, ctas_out, ms_out (host, may be NULL) receive the
+ * choice and its time (-1 when it came from the cache).  Synchronises the
+ * stream. */
+piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double dt, double nu, const void* S,
+                          void* stream, int32_t* threads_out, int32_t* ctas_out, double* ms_out);
 
 /* Wait for the last enqueued step (or adjoint) of the domain and report it. */
 piso_status piso_last_stats(piso_domain* d, piso_stats* stats);

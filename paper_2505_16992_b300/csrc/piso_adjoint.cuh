@@ -372,8 +372,8 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   });
 }
 
-template <typename real, int ND>
-__global__ void __launch_bounds__(512, 1) adj_kernel(const __grid_constant__ Launch<AdjCall<real>> L) {
+template <typename real, int ND, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) adj_kernel(const __grid_constant__ Launch<AdjCall<real>> L) {
   __shared__ AdjCall<real> A;
   const int gi = find_group(L.ngroups, L.cta_first);
   copy_to_smem(&A, L.calls ? L.calls + gi : &L.call0);

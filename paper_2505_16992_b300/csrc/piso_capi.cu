@@ -11,6 +11,9 @@
 #include <string>
 #include <vector>
 
+#include <map>
+#include <tuple>
+
 #include "../../include/piso.h"
 #include "piso_adjoint.cuh"
 #include "piso_forward.cuh"
@@ -337,8 +340,7 @@ size_t nbt_bytes(int ndim, int64_t N, int ncta, int32_t* cap) {
   return b;
 }
 
-template <typename K>
-cudaError_t coop_launch(K kernel, int grid, int threads, void** args, cudaStream_t st, size_t smem = 0) {
+cudaError_t coop_launch(const void* kernel, int grid, int threads, void** args, cudaStream_t st, size_t smem = 0) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(threads);
@@ -349,17 +351,35 @@ cudaError_t coop_launch(K kernel, int grid, int threads, void** args, cudaStream
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, (const void*)kernel, args);
+  return cudaLaunchKernelExC(&cfg, kernel, args);
 }
 
-const void* fwd_kernel_ptr(int prec, int nd) {
-  if (prec == PISO_FP64) return nd == 2 ? (const void*)fwd_kernel<double, 2> : (const void*)fwd_kernel<double, 3>;
-  return nd == 2 ? (const void*)fwd_kernel<float, 2> : (const void*)fwd_kernel<float, 3>;
+// Kernel variants: precision x dimension x CTA width (launch bound 512 or 768
+// threads; the wider variant holds one cell per thread for ~98k-cell domains
+// at 80 registers).
+constexpr int WIDE = 768;
+inline int width_class(int threads) { return threads > 512 ? WIDE : 512; }
+
+template <typename real>
+const void* fwd_ptr_t(int nd, int threads) {
+  if (width_class(threads) == WIDE)
+    return nd == 2 ? (const void*)fwd_kernel<real, 2, WIDE> : (const void*)fwd_kernel<real, 3, WIDE>;
+  return nd == 2 ? (const void*)fwd_kernel<real, 2, 512> : (const void*)fwd_kernel<real, 3, 512>;
 }
 
-const void* adj_kernel_ptr(int prec, int nd) {
-  if (prec == PISO_FP64) return nd == 2 ? (const void*)adj_kernel<double, 2> : (const void*)adj_kernel<double, 3>;
-  return nd == 2 ? (const void*)adj_kernel<float, 2> : (const void*)adj_kernel<float, 3>;
+template <typename real>
+const void* adj_ptr_t(int nd, int threads) {
+  if (width_class(threads) == WIDE)
+    return nd == 2 ? (const void*)adj_kernel<real, 2, WIDE> : (const void*)adj_kernel<real, 3, WIDE>;
+  return nd == 2 ? (const void*)adj_kernel<real, 2, 512> : (const void*)adj_kernel<real, 3, 512>;
+}
+
+const void* fwd_kernel_ptr(int prec, int nd, int threads = 512) {
+  return prec == PISO_FP64 ? fwd_ptr_t<double>(nd, threads) : fwd_ptr_t<float>(nd, threads);
+}
+
+const void* adj_kernel_ptr(int prec, int nd, int threads = 512) {
+  return prec == PISO_FP64 ? adj_ptr_t<double>(nd, threads) : adj_ptr_t<float>(nd, threads);
 }
 
 int max_coresident(const void* kernel, int threads, int* sms_out) {
@@ -374,11 +394,11 @@ int max_coresident(const void* kernel, int threads, int* sms_out) {
 
 piso_status choose_shape(piso_domain* d) {
   int threads = d->opts.block_threads > 0 ? d->opts.block_threads : 512;
-  if (threads % 32 || threads > 512 || threads < 32)
-    return fail(d, PISO_EINVAL, "block_threads must be a multiple of 32 in [32, 512]");
+  if (threads % 32 || threads > WIDE || threads < 32)
+    return fail(d, PISO_EINVAL, "block_threads must be a multiple of 32 in [32, %d]", WIDE);
   int sms = 148;
-  int cap_f = max_coresident(fwd_kernel_ptr(d->prec, d->ndim), threads, &sms);
-  int cap_a = max_coresident(adj_kernel_ptr(d->prec, d->ndim), threads, nullptr);
+  int cap_f = max_coresident(fwd_kernel_ptr(d->prec, d->ndim, threads), threads, &sms);
+  int cap_a = max_coresident(adj_kernel_ptr(d->prec, d->ndim, threads), threads, nullptr);
   int cap = std::min(cap_f, cap_a);
   if (cap <= 0) return fail(d, PISO_ECUDA, "kernel cannot be resident with %d threads", threads);
   int want = d->opts.ctas > 0 ? d->opts.ctas : std::min(sms, (int)((d->N + threads - 1) / threads));
@@ -446,8 +466,7 @@ piso_status launch_fwd(piso_domain* d, const void* u_in, const void* p_in, void*
   CUDA_TRY(d, cudaMemsetAsync(d->status, 0, 64, st));
   CUDA_TRY(d, cudaMemsetAsync(d->istats, 0, 64, st));
   void* args[] = {&L};
-  CUDA_TRY(d, coop_launch(d->ndim == 2 ? fwd_kernel<real, 2> : fwd_kernel<real, 3>, d->ncta, d->threads, args, st,
-                          smem));
+  CUDA_TRY(d, coop_launch(fwd_ptr_t<real>(d->ndim, d->threads), d->ncta, d->threads, args, st, smem));
   return PISO_OK;
 }
 
@@ -804,6 +823,90 @@ piso_status piso_step(piso_domain* d, const void* u_in, const void* p_in, void* 
   d->pending_kind = 1;
   d->pending_stream = st;
   if (stats) return collect_stats(d, stats);
+  return PISO_OK;
+}
+
+// Launch-shape autotuner: times one forward step of the caller's state for
+// each candidate (CTA width 512 or 768 threads; CTA count = one per SM, or
+// just enough CTAs for one cell per thread) and keeps the fastest.  Results
+// are cached per process by (ndim, precision, cells, blocks, correctors).
+static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>>& tune_cache() {
+  static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> c;
+  return c;
+}
+
+piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double dt, double nu, const void* S,
+                          void* stream, int32_t* threads_out, int32_t* ctas_out, double* ms_out) {
+  if (!d || !u || !p) return fail(d, PISO_EINVAL, "NULL argument");
+  if (!d->finalized) return fail(d, PISO_ESTATE, "autotune before finalize");
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto key = std::make_tuple(d->ndim, d->prec, (int)d->N, (int)d->blocks.size(), d->opts.n_correctors);
+  auto it = tune_cache().find(key);
+  double best_ms = -1.0;
+  if (it == tune_cache().end()) {
+    const size_t vb = (size_t)d->ndim * d->N * d->elem, sb = (size_t)d->N * d->elem;
+    const size_t bb = (size_t)d->ndim * std::max(d->nbf, 1) * d->elem;
+    char* tmp = nullptr;
+    CUDA_TRY(d, cudaMalloc((void**)&tmp, vb + sb + bb + 1024));
+    char* uo = tmp;
+    char* po = tmp + ((vb + 255) / 256) * 256;
+    char* bk = po + ((sb + 255) / 256) * 256;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const piso_options saved = d->opts;
+    const int saved_threads = d->threads, saved_ncta = d->ncta;
+    std::vector<std::pair<int, int>> cand;
+    for (int w : {512, WIDE}) {
+      int sms = 148;
+      const int cap = std::min(max_coresident(fwd_kernel_ptr(d->prec, d->ndim, w), w, &sms),
+                               max_coresident(adj_kernel_ptr(d->prec, d->ndim, w), w, nullptr));
+      const int one_per_thread = (int)std::min<int64_t>(cap, (d->N + w - 1) / w);
+      for (int nc : {std::min(cap, sms), one_per_thread})
+        if (nc >= 1 && std::find(cand.begin(), cand.end(), std::make_pair(w, nc)) == cand.end())
+          cand.push_back({w, nc});
+    }
+    std::pair<int, int> best = {saved_threads, saved_ncta};
+    piso_status s = PISO_OK;
+    CUDA_TRY(d, cudaMemcpyAsync(bk, d->bval, bb, cudaMemcpyDeviceToDevice, st));
+    for (auto& c : cand) {
+      d->threads = c.first;
+      d->ncta = c.second;
+      double t = 1e300;
+      for (int rep = 0; rep < 3 && s == PISO_OK; rep++) {
+        cudaEventRecord(e0, st);
+        s = d->prec == PISO_FP64 ? launch_fwd<double>(d, u, p, uo, po, dt, nu, S, nullptr, st)
+                                 : launch_fwd<float>(d, u, p, uo, po, dt, nu, S, nullptr, st);
+        cudaEventRecord(e1, st);
+        cudaMemcpyAsync(d->bval, bk, bb, cudaMemcpyDeviceToDevice, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) s = PISO_ECUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) t = std::min(t, (double)ms);
+      }
+      if (s != PISO_OK) break;
+      if (best_ms < 0 || t < best_ms) {
+        best_ms = t;
+        best = c;
+      }
+    }
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(tmp);
+    d->opts = saved;
+    d->threads = saved_threads;
+    d->ncta = saved_ncta;
+    if (s != PISO_OK) return fail(d, s, "autotune trial step failed");
+    it = tune_cache().emplace(key, best).first;
+  }
+  d->threads = it->second.first;
+  d->ncta = it->second.second;
+  d->opts.block_threads = d->threads;
+  d->opts.ctas = d->ncta;
+  if (threads_out) *threads_out = d->threads;
+  if (ctas_out) *ctas_out = d->ncta;
+  if (ms_out) *ms_out = best_ms;
   return PISO_OK;
 }
 

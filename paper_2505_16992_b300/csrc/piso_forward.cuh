@@ -402,8 +402,8 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   }
 }
 
-template <typename real, int ND>
-__global__ void __launch_bounds__(512, 1) fwd_kernel(const __grid_constant__ Launch<FwdCall<real>> L) {
+template <typename real, int ND, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const __grid_constant__ Launch<FwdCall<real>> L) {
   __shared__ FwdCall<real> A;
   const int gi = find_group(L.ngroups, L.cta_first);
   copy_to_smem(&A, L.calls ? L.calls + gi : &L.call0);

@@ -134,6 +134,14 @@ class Domain:
         capi.check(rc, self.h)
         return u_out, p_out, (st.as_dict() if st is not None else None)
 
+    def autotune(self, u, p, dt, nu, S=None, stream=None):
+        """Pick the fastest launch shape on this state; returns (threads, ctas, ms)."""
+        t, c, ms = C.c_int32(), C.c_int32(), C.c_double()
+        rc = self.lib.piso_autotune(self.h, capi.dptr(u), capi.dptr(p), float(dt), float(nu), capi.dptr(S),
+                                    _stream_ptr(stream), C.byref(t), C.byref(c), C.byref(ms))
+        capi.check(rc, self.h)
+        return t.value, c.value, ms.value
+
     def last_stats(self):
         st = capi.Stats()
         rc = self.lib.piso_last_stats(self.h, C.byref(st))

@@ -17,10 +17,12 @@ pytestmark = pytest.mark.gpu
 
 
 class Corrector(nn.Module):
-    """2 -> ch -> ch -> 2 channels, 3x3 kernels, circular padding, ReLU."""
+    """2 -> ch -> ch -> 2 channels, 3x3 kernels, circular padding, ReLU (tanh
+    for the finite-difference check, which needs a smooth network)."""
 
-    def __init__(self, ch, dtype):
+    def __init__(self, ch, dtype, act=torch.relu):
         super().__init__()
+        self.act = act
         self.c1 = nn.Conv2d(2, ch, 3, dtype=dtype)
         self.c2 = nn.Conv2d(ch, ch, 3, dtype=dtype)
         self.c3 = nn.Conv2d(ch, 2, 3, dtype=dtype)
@@ -30,7 +32,7 @@ class Corrector(nn.Module):
         for k, c in enumerate((self.c1, self.c2, self.c3)):
             x = c(F.pad(x, (1, 1, 1, 1), mode="circular"))
             if k < 2:
-                x = torch.relu(x)
+                x = self.act(x)
         return 0.1 * x.reshape(2, n * n)
 
 
@@ -47,7 +49,7 @@ def test_corrector_gradients_match_finite_differences():
     case = W.turbulence2d(n, nu=0.01, dt=0.02)
     dom = gpu_domain(case)
     torch.manual_seed(2)
-    net = Corrector(6, torch.float64).cuda()
+    net = Corrector(6, torch.float64, act=torch.tanh).cuda()
     rng = np.random.default_rng(3)
     target = to_dev(dom, rng.standard_normal((2, n * n)), 2)
     loss = _loss(dom, case, net, n, steps, target)

@@ -203,3 +203,22 @@ def test_barrier_timeout_is_reported_and_context_survives():
     dom.set_options(capi.default_options(ctas=4, block_threads=128))
     u1, p1, st = dom.step(u, p, c.dt, c.nu)
     assert st["status"] == "PISO_OK"
+
+
+def test_autotuned_shape_keeps_parity():
+    c = W.channel3d(16, 12, 8)
+    m = O.mesh_from_case(c)
+    dom = gpu_domain(c)
+    u, p, S = to_dev(dom, c.u0, 3), to_dev(dom, c.p0), to_dev(dom, c.S, 3)
+    threads, ctas, ms = dom.autotune(u, p, c.dt, c.nu, S)
+    assert threads in (512, 768) and ctas >= 1
+    u1, p1, st = dom.step(u, p, c.dt, c.nu, S)
+    uo, po, _ = oracle_step(m, c, c.u0, c.p0, c.S)
+    assert rel_err(host(u1), uo) <= FP64_REL
+    assert np.array_equal(host(u), c.u0)          # inputs untouched by the trials
+
+
+@pytest.mark.parametrize("threads", [768])
+def test_wide_cta_variant(threads):
+    c = W.channel3d(16, 12, 8)
+    _per_step_parity(c, 2, block_threads=threads)
