@@ -173,6 +173,40 @@ def run_reference(args):
     return 0
 
 
+def time_variant(case, prec, kw, steps, with_adj, flush):
+    """Steps/s of one precision/tolerance variant on the same workload (used to
+    compare FP32, refined FP32 and FP64 at matched pressure tolerances)."""
+    import torch
+    from paper_2505_16992_b300 import capi
+    from paper_2505_16992_b300.solver import Domain
+    o = capi.default_options(p_maxit=20000, adv_maxit=2000, **kw)
+    dom = Domain.from_case(case, prec, o)
+    d = case.ndim
+    u, p, S = dom.field(case.u0, d), dom.field(case.p0), dom.field(case.S, d)
+    dom.autotune(u, p, case.dt, case.nu, S)
+    uo, po = torch.empty_like(u), torch.empty_like(p)
+    g = torch.ones_like(u)
+    for _ in range(3):
+        dom.step(u, p, case.dt, case.nu, S, u_out=uo, p_out=po, sync=False)
+        if with_adj:
+            dom.step_adjoint(g, None)
+    st = dom.step(u, p, case.dt, case.nu, S, u_out=uo, p_out=po)[2]
+    stream = torch.cuda.current_stream()
+    tot = 0.0
+    for _ in range(steps):
+        flush.fill_(0.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dom.step(u, p, case.dt, case.nu, S, u_out=uo, p_out=po, sync=False)
+        if with_adj:
+            dom.step_adjoint(g, None)
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b) / 1e3
+    return {"steps_per_s": steps / tot, "p_iters": st["p_iters"][:2], "p_rounds": st["p_rounds"][:2],
+            "p_resid": st["p_resid"][:2]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,6 +217,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="CTA width; 0 = autotune")
+    ap.add_argument("--refine", type=float, default=0.0, help="FP32: FP64-refined pressure tolerance")
+    ap.add_argument("--compare", action="store_true",
+                    help="also time FP64 and refined FP32 at matched pressure tolerances")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -208,7 +245,7 @@ def main():
     prec = args.precision
     rtol = 1e-6 if prec == "fp32" else 1e-10
     opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
-                                block_threads=args.threads)
+                                block_threads=args.threads, p_refine_rtol=args.refine)
     dom = Domain.from_case(case, prec, opts)
     d, N = case.ndim, case.ncells
     w = 4 if prec == "fp32" else 8
@@ -303,6 +340,16 @@ def main():
         except Exception:
             traffic = None
 
+    compare = None
+    if args.compare:
+        compare = {}
+        for name, pr, kw in (("fp64_rtol1e-6", "fp64", dict(adv_rtol=1e-6, p_rtol=1e-6)),
+                             ("fp64_rtol1e-10", "fp64", dict(adv_rtol=1e-10, p_rtol=1e-10)),
+                             ("fp32_refined1e-10", "fp32", dict(adv_rtol=1e-6, p_rtol=1e-6, p_refine_rtol=1e-10))):
+            compare[name] = time_variant(case, pr, kw, max(5, args.steps // 3), with_adj, flush)
+        compare["fp32_rtol1e-6"] = {"steps_per_s": value, "p_iters": st["p_iters"][:2],
+                                    "p_resid": st["p_resid"][:2]}
+
     if rank == 0:
         line = {
             "metric": "PISO steps/s (fwd+adjoint), 64x48x32 channel" if with_adj else
@@ -329,6 +376,8 @@ def main():
                          "kernel": "fwd_kernel", "words_per_cell": words},
             "clocks": clocks,
         }
+        if compare is not None:
+            line["precision_compare"] = compare
         if world == 1 and not args.no_cpu_baseline:
             v, n, dt = cpu_baseline(case)
             line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",

@@ -79,6 +79,11 @@ typedef struct {
   int32_t fault_withhold_cta; /* fault injection for tests: this CTA of the domain skips its
                                  first barrier arrival, so every wait of the step runs out and
                                  the call returns PISO_ETIMEOUT; -1 (default) = off */
+  double p_refine_rtol;  /* PISO_FP32 only: > 0 refines every pressure solve against a residual
+                            b - P p evaluated in FP64 with the solution accumulated in FP64,
+                            until ||b - P p|| <= p_refine_rtol ||b|| (each round an FP32 CG to
+                            p_inner_rtol); 0 (default) = a single FP32 CG to p_rtol */
+  double p_inner_rtol;   /* inner tolerance per refinement round (default 1e-4) */
 } piso_options;
 
 /* Per-step statistics (read back when a stats pointer is given). */
@@ -88,7 +93,8 @@ typedef struct {
   int32_t adv_iters[3];   /* BiCGStab iterations per velocity component */
   int32_t p_iters[4];     /* CG iterations per corrector */
   double adv_resid[3];    /* final BiCGStab residual norms */
-  double p_resid[4];      /* final CG residual norms */
+  double p_resid[4];      /* final CG residual norms (the FP64 outer residual when refining) */
+  int32_t p_rounds[4];    /* refinement rounds per corrector (0 without refinement) */
 } piso_stats;
 
 /* Fill *o with the defaults listed above. */

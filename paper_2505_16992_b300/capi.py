@@ -19,17 +19,19 @@ class Options(C.Structure):
     _fields_ = [("n_correctors", C.c_int32), ("pred_grad_p", C.c_int32), ("adv_rtol", C.c_double),
                 ("p_rtol", C.c_double), ("atol", C.c_double), ("adv_maxit", C.c_int32),
                 ("p_maxit", C.c_int32), ("block_threads", C.c_int32), ("ctas", C.c_int32),
-                ("timeout_s", C.c_double), ("fault_withhold_cta", C.c_int32)]
+                ("timeout_s", C.c_double), ("fault_withhold_cta", C.c_int32), ("p_refine_rtol", C.c_double),
+                ("p_inner_rtol", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("error_bits", C.c_int32), ("adv_iters", C.c_int32 * 3),
-                ("p_iters", C.c_int32 * 4), ("adv_resid", C.c_double * 3), ("p_resid", C.c_double * 4)]
+                ("p_iters", C.c_int32 * 4), ("adv_resid", C.c_double * 3), ("p_resid", C.c_double * 4),
+                ("p_rounds", C.c_int32 * 4)]
 
     def as_dict(self):
         return dict(status=STATUS.get(self.status, self.status), error_bits=self.error_bits,
                     adv_iters=list(self.adv_iters), p_iters=list(self.p_iters),
-                    adv_resid=list(self.adv_resid), p_resid=list(self.p_resid))
+                    adv_resid=list(self.adv_resid), p_resid=list(self.p_resid), p_rounds=list(self.p_rounds))
 
 
 class PisoError(RuntimeError):

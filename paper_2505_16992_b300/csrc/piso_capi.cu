@@ -203,7 +203,7 @@ void put(std::vector<char>& buf, size_t i, double v) {
 // --- workspace layout ------------------------------------------------------
 enum WsIdx {
   W_U, W_RHS0, W_R, W_RHAT, W_P0, W_P1, W_V0, W_V1, W_T, W_POFF, W_PDIAG, W_FH, W_B, W_CX,
-  W_CRB0, W_CRB1, W_CWB0, W_CWB1, W_CSB0, W_CSB1, W_CP, W_PINV, W_INVA, W_AW,
+  W_CRB0, W_CRB1, W_CWB0, W_CWB1, W_CSB0, W_CSB1, W_CP, W_PINV, W_INVA, W_AW, W_X64, W_RIN, W_CE,
   // adjoint scratch
   A_GA, A_GCOFF, A_GRHS0, A_GW, A_W, A_GG, A_GU, A_GX, A_Z, A_DU,
   W_COUNT
@@ -213,8 +213,10 @@ enum WsIdx {
 int ws_units(int k, int nd) {
   switch (k) {
     case W_PDIAG: case W_B: case W_CX: case W_CRB0: case W_CRB1: case W_CWB0: case W_CWB1: case W_CSB0:
-    case W_CSB1: case W_CP: case A_GA: case A_GX: case W_PINV: case W_INVA:
+    case W_CSB1: case W_CP: case A_GA: case A_GX: case W_PINV: case W_INVA: case W_RIN: case W_CE:
       return 1;
+    case W_X64:
+      return 2;     // N doubles (two float units; the FP64 mode over-allocates)
     case A_GCOFF:
       return 2 * nd;
     default:
@@ -301,6 +303,9 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
   c.csb[0] = (real*)d->ws[W_CSB0];
   c.csb[1] = (real*)d->ws[W_CSB1];
   c.cp = (real*)d->ws[W_CP];
+  c.x64 = (double*)d->ws[W_X64];
+  c.rin = (real*)d->ws[W_RIN];
+  c.ce = (real*)d->ws[W_CE];
   c.bar = d->bar;
   c.partials = d->partials;
   c.status = d->status;
@@ -322,6 +327,8 @@ SolverOpts solver_opts(const piso_options& o) {
   s.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
   s.nbt_cap = 0;
   s.withhold_cta = o.fault_withhold_cta;
+  s.p_refine_rtol = o.p_refine_rtol;
+  s.p_inner_rtol = o.p_inner_rtol;
   return s;
 }
 
@@ -432,6 +439,7 @@ piso_status collect_stats(piso_domain* d, piso_stats* st) {
     for (int k = 0; k < 4; k++) {
       st->p_iters[k] = d->h_istats[4 + k];
       st->p_resid[k] = d->h_dstats[4 + k];
+      st->p_rounds[k] = d->h_istats[8 + k];
     }
   }
   if (s != PISO_OK) {
@@ -492,6 +500,8 @@ void piso_default_options(piso_options* o) {
   o->ctas = 0;
   o->timeout_s = 5.0;
   o->fault_withhold_cta = -1;
+  o->p_refine_rtol = 0.0;
+  o->p_inner_rtol = 1e-4;
 }
 
 piso_status piso_domain_create(int32_t ndim, int32_t prec, piso_domain** out) {

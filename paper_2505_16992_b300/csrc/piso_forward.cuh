@@ -51,6 +51,9 @@ struct FwdCall {
   real* cwb[2];              // [N]
   real* csb[2];              // [N]
   real* cp;                  // [N]
+  double* x64;               // [N]    refined pressure (FP32 mode)
+  real* rin;                 // [N]    refinement residual
+  real* ce;                  // [N]    refinement correction
   // group control
   uint32_t* bar;
   double* partials;
@@ -93,6 +96,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   __shared__ DomStatic D;
   __shared__ BiState bs;
   __shared__ CgState cs;
+  __shared__ RefState rs;
   __shared__ double s_scale, s_mean;
   copy_to_smem(&D, A.dom);
   __syncthreads();
@@ -354,14 +358,28 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       });
       if (!reduce_sync<real, 1>(g, a, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
     }
-    // pressure solve (App. A.5: CG; Chronopoulos-Gear form)
-    if (!cg_pressure<real, ND>(X, cs, o.p_rtol, o.atol, o.p_maxit, A.Pdiag, A.Pinv, A.Poff, A.b, s_mean, A.cx,
-                               A.crb, A.cwb, A.csb, A.cp))
-      return;
-    if (threadIdx.x == 0 && g.rank == 0) {
-      A.istats[4 + kc] = cs.it;
-      A.dstats[4 + kc] = sqrt(cs.res2);
-      if (!cs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
+    // pressure solve (App. A.5: CG; Chronopoulos-Gear form), in the FP32 mode
+    // optionally refined against an FP64 residual
+    if (sizeof(real) == 4 && o.p_refine_rtol > 0) {
+      if (!cg_pressure_refined<real, ND>(X, cs, rs, o.p_refine_rtol, o.p_inner_rtol, o.atol, o.p_maxit, 20,
+                                         A.Pdiag, A.Pinv, A.Poff, A.b, s_mean, A.cx, A.x64, A.rin, A.ce, A.crb,
+                                         A.cwb, A.csb, A.cp))
+        return;
+      if (threadIdx.x == 0 && g.rank == 0) {
+        A.istats[4 + kc] = rs.inner_it;
+        A.istats[8 + kc] = rs.rounds;
+        A.dstats[4 + kc] = sqrt(rs.res2);
+        if (!rs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
+      }
+    } else {
+      if (!cg_pressure<real, ND>(X, cs, o.p_rtol, o.atol, o.p_maxit, A.Pdiag, A.Pinv, A.Poff, A.b, s_mean, A.cx,
+                                 A.crb, A.cwb, A.csb, A.cp))
+        return;
+      if (threadIdx.x == 0 && g.rank == 0) {
+        A.istats[4 + kc] = cs.it;
+        A.dstats[4 + kc] = sqrt(cs.res2);
+        if (!cs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
+      }
     }
     // C4: u = h - A^-1 grad x (Eq. velCorrDiscrete, R5); mean of x (R7)
     {

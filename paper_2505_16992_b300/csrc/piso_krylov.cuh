@@ -14,6 +14,8 @@ struct SolverOpts {
   uint64_t timeout_ns;
   int32_t nbt_cap;           // cells per CTA the shared neighbour table can hold
   int32_t withhold_cta;      // fault injection: group rank that skips its first barrier arrival (-1 off)
+  double p_refine_rtol;      // FP32 mode: outer FP64 residual tolerance of the pressure solve (0 = off)
+  double p_inner_rtol;       // FP32 mode: inner CG tolerance per refinement round
 };
 
 // Fill the CTA's neighbour table (dynamic shared memory) when its cell range
@@ -101,6 +103,12 @@ struct BiState {
 struct CgState {
   double gam, gam_old, delta, alpha, alpha_old, beta, tol2, res2;
   int active, it, first, conv;
+};
+
+// Outer state of the iteratively refined pressure solve.
+struct RefState {
+  double bn2, res2, tol2;
+  int rounds, conv, inner_it;
 };
 
 // Thread 0: BiCGStab start from the reduced ||b||^2 and ||r0||^2 per component.
@@ -453,6 +461,72 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     cur ^= 1;
   }
   return true;
+}
+
+// Iteratively refined pressure solve for the FP32 mode: the solution x64 and
+// the outer residual r = b' - A' x64 (b' = -(b - mean), A' = -P) live in FP64;
+// each round solves A' e = r in FP32 with cg_pressure to inner_rtol and adds e
+// to x64 in FP64, until ||r|| <= max(outer_rtol ||b'||, atol).  Every residual
+// phase also writes x = (float) x64, so x holds the refined solution after the
+// final (converged) residual phase and its barrier.  e, rin: FP32 scratch.
+template <typename real, int ND>
+__device__ bool cg_pressure_refined(const Ctx<real, ND>& X, CgState& cs, RefState& rs, double outer_rtol,
+                                    double inner_rtol, double atol, int maxit, int max_rounds, const real* Pdiag,
+                                    const real* Pinv, const real* Poff, const real* b, double bmean, real* x,
+                                    double* x64, real* rin, real* e, real* const (&rb)[2], real* const (&wb)[2],
+                                    real* const (&sb)[2], real* pdir) {
+  const int32_t N = X.N;
+  for (int round = 0;; round++) {
+    // residual in FP64
+    {
+      Acc<double> a[2];
+      a[0].zero();
+      a[1].zero();
+      X.cells([&](const Cell& c) {
+        real pf[2 * ND];
+        p_row<real, ND>(c, N, Poff, pf);
+        auto xs = [&](int32_t Q) -> double { return round == 0 ? (double)x[Q] : x64[Q]; };
+        const int32_t P = c.i;
+        const double bp = -((double)b[P] - bmean);
+        double px = (double)Pdiag[P] * xs(P);
+#pragma unroll
+        for (int s = 0; s < 2 * ND; s++)
+          if (c.nb[s] >= 0) px += (double)pf[s] * xs(c.nb[s]);
+        const double r = bp + px;
+        const double xP = xs(P);
+        if (round == 0) x64[P] = xP;
+        else x[P] = (real)xP;
+        rin[P] = (real)(-r);
+        e[P] = real(0);
+        a[0].add_prod(r, r);
+        a[1].add_prod(bp, bp);
+      });
+      const bool ok = reduce_sync<double, 2>(X.g, a, [&](const double* q) {
+        if (round == 0) {
+          rs.bn2 = q[1];
+          rs.tol2 = fmax(outer_rtol * outer_rtol * q[1], atol * atol);
+          rs.inner_it = 0;
+        }
+        rs.res2 = q[0];
+        rs.rounds = round;
+        rs.conv = !(rs.res2 > rs.tol2);
+        if (rs.res2 != rs.res2) {
+          rs.conv = 0;
+          atomicOr(X.g.status, PISO_ERR_NAN);
+        }
+      });
+      if (!ok) return false;
+    }
+    if (rs.conv || rs.res2 != rs.res2 || round >= max_rounds || rs.inner_it >= maxit) return true;
+    // inner FP32 solve of A' e = r
+    if (!cg_pressure<real, ND>(X, cs, inner_rtol, 0.0, maxit - rs.inner_it, Pdiag, Pinv, Poff, rin, 0.0, e, rb,
+                               wb, sb, pdir))
+      return false;
+    if (threadIdx.x == 0) rs.inner_it += cs.it;
+    // x64 += e
+    X.own([&](int32_t P) { x64[P] += (double)e[P]; });
+    if (!plain_sync(X.g)) return false;
+  }
 }
 
 }  // namespace piso
