@@ -69,8 +69,13 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   __shared__ BiState bs;
   __shared__ CgState cs;
   __shared__ RefState rs;
-  __shared__ double s_mean;
+  __shared__ double s_mean, s_idt;
+  __shared__ float s_idt_f;
   copy_to_smem(&D, A.dom);
+  if (threadIdx.x == 0) {
+    s_idt = 1.0 / A.hdr[0];
+    s_idt_f = (float)s_idt;
+  }
   __syncthreads();
   const int32_t N = D.N;
   const int32_t lo = (int32_t)(((int64_t)N * g.rank) / g.ncta);
@@ -82,7 +87,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   const int NSD = 2 * ND;
   const int32_t nbf = D.nbf;
   auto Tm = [&](int j, int k, int32_t i) -> real { return T[(size_t)(j * ND + k) * N + i]; };
-  const real inv_dt = (real)(1.0 / A.hdr[0]);
+  const real inv_dt = pick<real>(s_idt, s_idt_f);
   const int K = o.n_corr;
 
   // (G^T W)_P for the cell-centred central gradient with the R5 boundary rule:

@@ -98,7 +98,15 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   __shared__ CgState cs;
   __shared__ RefState rs;
   __shared__ double s_scale, s_mean;
+  __shared__ float s_scale_f, s_mean_f, s_cf[3];
+  __shared__ double s_cd[3];
   copy_to_smem(&D, A.dom);
+  if (threadIdx.x == 0) {           // step constants in both precisions (no per-thread FP64 work)
+    s_cd[0] = A.dt;
+    s_cd[1] = A.nu;
+    s_cd[2] = 1.0 / A.dt;
+    for (int q = 0; q < 3; q++) s_cf[q] = (float)s_cd[q];
+  }
   __syncthreads();
   const int32_t N = D.N;
   const int32_t lo = (int32_t)(((int64_t)N * g.rank) / g.ncta);
@@ -108,7 +116,8 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   const real* T = reinterpret_cast<const real*>(D.T);
   const real* AL = reinterpret_cast<const real*>(D.alpha);
   const int NSD = 2 * ND;
-  const real dt = (real)A.dt, nu = (real)A.nu, inv_dt = (real)(1.0 / A.dt);
+  const real dt = pick<real>(s_cd[0], s_cf[0]), nu = pick<real>(s_cd[1], s_cf[1]);
+  const real inv_dt = pick<real>(s_cd[2], s_cf[2]);
   auto Tm = [&](int j, int k, int32_t i) -> real { return T[(size_t)(j * ND + k) * N + i]; };
   const int32_t nbf = D.nbf;
   const int32_t flo = (int32_t)(((int64_t)nbf * g.rank) / g.ncta);
@@ -148,9 +157,12 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       if (D.bf_out[f]) a[1].add(fl);
       else a[0].add(-fl);
     }
-    if (!reduce_sync<real, 2>(g, a, [&](const double* q) { s_scale = (q[1] != 0.0) ? q[0] / q[1] : 1.0; }))
+    if (!reduce_sync<real, 2>(g, a, [&](const double* q) {
+          s_scale = (q[1] != 0.0) ? q[0] / q[1] : 1.0;
+          s_scale_f = (float)s_scale;
+        }))
       return;
-    const real sc = (real)s_scale;
+    const real sc = pick<real>(s_scale, s_scale_f);
     for (int32_t f = flo + threadIdx.x; f < fhi; f += blockDim.x)
       if (D.bf_out[f]) {
 #pragma unroll
@@ -308,7 +320,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
         A.Pdiag[P] = pd;
         A.Pinv[P] = real(1) / (-pd);
       } else {
-        A.xk[kc - 1][P] = A.cx[P] - (real)s_mean;
+        A.xk[kc - 1][P] = A.cx[P] - pick<real>(s_mean, s_mean_f);
       }
       real hv[ND];
 #pragma unroll
@@ -356,7 +368,11 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
         A.cx[P] = xprev[P];
         a[0].add(b);
       });
-      if (!reduce_sync<real, 1>(g, a, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
+      if (!reduce_sync<real, 1>(g, a, [&](const double* q) {
+            s_mean = q[0] / (double)N;
+            s_mean_f = (float)s_mean;
+          }))
+        return;
     }
     // pressure solve (App. A.5: CG; Chronopoulos-Gear form), in the FP32 mode
     // optionally refined against an FP64 residual
@@ -405,12 +421,16 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
         for (int k = 0; k < ND; k++) uo[(size_t)k * N + P] = h[(size_t)k * N + P] - gp[k] * ia;
         a[0].add(xP);
       });
-      if (!reduce_sync<real, 1>(g, a, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
+      if (!reduce_sync<real, 1>(g, a, [&](const double* q) {
+            s_mean = q[0] / (double)N;
+            s_mean_f = (float)s_mean;
+          }))
+        return;
     }
   }
   // final pressure (mean-free) and the tape record of the last corrector
   {
-    const real m = (real)s_mean;
+    const real m = pick<real>(s_mean, s_mean_f);
     const int kl = o.n_corr - 1;
     X.own([&](int32_t P) {
       const real x = A.cx[P] - m;

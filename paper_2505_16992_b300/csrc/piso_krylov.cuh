@@ -94,20 +94,40 @@ __device__ __forceinline__ void p_row(const Cell& c, int32_t N, const real* Poff
 }
 
 // Krylov scalar state, owned by thread 0 and broadcast through shared memory.
+// Thread 0 also stores the coefficients the cell loops need in both storage
+// precisions (the *_f copies), so no other thread converts or divides in FP64.
 struct BiState {
   double rho[3], rho_old[3], alpha[3], omega[3], tol2[3], res2[3];
+  double beta_d[3];
+  float beta_f[3], alpha_f[3], omega_f[3];
   int active[3], sconv[3], iters[3], conv[3];
   int any, it, first;
 };
 
 struct CgState {
   double gam, gam_old, delta, alpha, alpha_old, beta, tol2, res2;
+  float alpha_f, beta_f;
   int active, it, first, conv;
 };
 
+// A scalar in the storage precision: the float copy for FP32, the double for FP64.
+template <typename real>
+__device__ __forceinline__ real pick(double d, float f) {
+  if constexpr (sizeof(real) == 4) return f;
+  else return d;
+}
+
+// Thread 0: BiCGStab beta for the next BA phase, both precisions.
+__device__ __forceinline__ void bicg_set_beta(BiState& bs, int k) {
+  const double b = bs.first ? 0.0 : (bs.rho[k] / bs.rho_old[k]) * (bs.alpha[k] / bs.omega[k]);
+  bs.beta_d[k] = b;
+  bs.beta_f[k] = (float)b;
+  bs.omega_f[k] = (float)bs.omega[k];
+}
+
 // Outer state of the iteratively refined pressure solve.
 struct RefState {
-  double bn2, res2, tol2;
+  double bn2, res2, tol2, rmean;
   int rounds, conv, inner_it;
 };
 
@@ -132,6 +152,7 @@ __device__ __forceinline__ void bicg_start(BiState& bs, const double* q, double 
       atomicOr(status, PISO_ERR_NAN);
     }
     bs.any |= bs.active[k];
+    bicg_set_beta(bs, k);
   }
 }
 
@@ -154,8 +175,8 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       for (int k = 0; k < ND; k++) {
         a[k].zero();
         act[k] = bs.active[k];
-        beta[k] = bs.first ? real(0) : (real)((bs.rho[k] / bs.rho_old[k]) * (bs.alpha[k] / bs.omega[k]));
-        om[k] = (real)bs.omega[k];
+        beta[k] = pick<real>(bs.beta_d[k], bs.beta_f[k]);
+        om[k] = pick<real>(bs.omega[k], bs.omega_f[k]);
       }
       const int first = bs.first;
       const real* pold = pv[cur ^ 1];
@@ -194,6 +215,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
             continue;
           }
           bs.alpha[k] = bs.rho[k] / q[k];
+          bs.alpha_f[k] = (float)bs.alpha[k];
         }
       });
       if (!ok) return false;
@@ -206,7 +228,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
 #pragma unroll
       for (int k = 0; k < ND; k++) {
         act[k] = bs.active[k];
-        al[k] = (real)bs.alpha[k];
+        al[k] = pick<real>(bs.alpha[k], bs.alpha_f[k]);
       }
 #pragma unroll
       for (int k = 0; k < 3 * ND; k++) a[k].zero();
@@ -241,6 +263,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
             atomicOr(X.g.status, q[ND + k] == 0.0 ? PISO_ERR_BREAKDOWN : PISO_ERR_NAN);
           } else {
             bs.omega[k] = q[k] / q[ND + k];
+            bs.omega_f[k] = (float)bs.omega[k];
           }
         }
       });
@@ -255,8 +278,8 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       for (int k = 0; k < ND; k++) {
         act[k] = bs.active[k];
         sc[k] = bs.sconv[k];
-        al[k] = (real)bs.alpha[k];
-        om[k] = (real)bs.omega[k];
+        al[k] = pick<real>(bs.alpha[k], bs.alpha_f[k]);
+        om[k] = pick<real>(bs.omega[k], bs.omega_f[k]);
         a[k].zero();
         a[ND + k].zero();
       }
@@ -305,6 +328,8 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
           bs.any |= bs.active[k];
         }
         bs.first = 0;
+        for (int k = 0; k < ND; k++)
+          if (bs.active[k]) bicg_set_beta(bs, k);
       });
       if (!ok) return false;
     }
@@ -329,7 +354,14 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     Acc<real> a[2];
     a[0].zero();
     a[1].zero();
-    const real mb = (real)bmean;
+    __shared__ double s_mb;
+    __shared__ float s_mbf;
+    if (threadIdx.x == 0) {
+      s_mb = bmean;
+      s_mbf = (float)bmean;
+    }
+    __syncthreads();
+    const real mb = pick<real>(s_mb, s_mbf);
     X.cells([&](const Cell& c) {
       real pf[2 * ND];
       p_row<real, ND>(c, N, Poff, pf);
@@ -389,6 +421,8 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
       } else {
         cs.alpha = cs.gam / cs.delta;
         cs.beta = 0.0;
+        cs.alpha_f = (float)cs.alpha;
+        cs.beta_f = 0.f;
       }
     });
     if (!ok) return false;
@@ -399,7 +433,7 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     a[0].zero();
     a[1].zero();
     a[2].zero();
-    const real al = (real)cs.alpha, be = (real)cs.beta;
+    const real al = pick<real>(cs.alpha, cs.alpha_f), be = pick<real>(cs.beta, cs.beta_f);
     const int first = cs.first;
     const real* r_i = rb[cur];
     const real* w_i = wb[cur];
@@ -454,6 +488,8 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
           atomicOr(X.g.status, PISO_ERR_BREAKDOWN);
         } else {
           cs.alpha = cs.gam / den;
+          cs.alpha_f = (float)cs.alpha;
+          cs.beta_f = (float)cs.beta;
         }
       }
     });
@@ -477,11 +513,14 @@ __device__ bool cg_pressure_refined(const Ctx<real, ND>& X, CgState& cs, RefStat
                                     real* const (&sb)[2], real* pdir) {
   const int32_t N = X.N;
   for (int round = 0;; round++) {
-    // residual in FP64
+    // residual in FP64, measured and corrected in the zero-mean subspace (R7:
+    // the rounded P has row sums of order the FP32 unit roundoff, so the
+    // constant mode of r is not reducible and carries no pressure gradient)
     {
-      Acc<double> a[2];
+      Acc<double> a[3];
       a[0].zero();
       a[1].zero();
+      a[2].zero();
       X.cells([&](const Cell& c) {
         real pf[2 * ND];
         p_row<real, ND>(c, N, Poff, pf);
@@ -498,16 +537,19 @@ __device__ bool cg_pressure_refined(const Ctx<real, ND>& X, CgState& cs, RefStat
         else x[P] = (real)xP;
         rin[P] = (real)(-r);
         e[P] = real(0);
-        a[0].add_prod(r, r);
-        a[1].add_prod(bp, bp);
+        a[0].add(r);
+        a[1].add_prod(r, r);
+        a[2].add_prod(bp, bp);
       });
-      const bool ok = reduce_sync<double, 2>(X.g, a, [&](const double* q) {
+      const bool ok = reduce_sync<double, 3>(X.g, a, [&](const double* q) {
         if (round == 0) {
-          rs.bn2 = q[1];
-          rs.tol2 = fmax(outer_rtol * outer_rtol * q[1], atol * atol);
+          rs.bn2 = q[2];
+          rs.tol2 = fmax(outer_rtol * outer_rtol * q[2], atol * atol);
           rs.inner_it = 0;
         }
-        rs.res2 = q[0];
+        const double mean = q[0] / (double)N;
+        rs.rmean = mean;
+        rs.res2 = fmax(q[1] - (double)N * mean * mean, 0.0);
         rs.rounds = round;
         rs.conv = !(rs.res2 > rs.tol2);
         if (rs.res2 != rs.res2) {
@@ -519,8 +561,8 @@ __device__ bool cg_pressure_refined(const Ctx<real, ND>& X, CgState& cs, RefStat
     }
     if (rs.conv || rs.res2 != rs.res2 || round >= max_rounds || rs.inner_it >= maxit) return true;
     // inner FP32 solve of A' e = r
-    if (!cg_pressure<real, ND>(X, cs, inner_rtol, 0.0, maxit - rs.inner_it, Pdiag, Pinv, Poff, rin, 0.0, e, rb,
-                               wb, sb, pdir))
+    if (!cg_pressure<real, ND>(X, cs, inner_rtol, 0.0, maxit - rs.inner_it, Pdiag, Pinv, Poff, rin, -rs.rmean, e,
+                               rb, wb, sb, pdir))
       return false;
     if (threadIdx.x == 0) rs.inner_it += cs.it;
     // x64 += e
