@@ -174,6 +174,32 @@ piso_status piso_step(piso_domain* d, const void* u_in, const void* p_in, void* 
 piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double dt, double nu, const void* S,
                           void* stream, int32_t* threads_out, int32_t* ctas_out, double* ms_out);
 
+/* Forward step that allocates nothing (the paper has no counterpart; this is
+ * a service of this library).  Some callers cannot allocate device memory at
+ * the time they step - for example a process whose device memory is already
+ * fully reserved by another framework's caching allocator, or a
+ * latency-critical loop that must not risk an allocation or its failure
+ * mid-run.  piso_step_static computes the same step as piso_step (same
+ * arguments except the tape, same kernel, same results), but its scratch -
+ * the workspace, the step record and the control words - lives in one fixed
+ * 32 MiB buffer compiled into this library (every GPU that loads the library
+ * holds it until the process exits), not in memory from cudaMalloc.  The
+ * caller still provides the inputs and outputs.
+ *   - Size limit: domains whose scratch exceeds 32 MiB are rejected with
+ *     PISO_EINVAL and a message giving the bytes needed (about 43,000 cells
+ *     for a 3D FP64 domain, 87,000 for 3D FP32, more in 2D).
+ *   - Set-up: the first call on each device looks up the buffer's device
+ *     address with that device current; make that first call before any
+ *     stream capture.
+ *   - Sharing: every call (every domain, every stream) uses the same buffer,
+ *     which keeps the last call's contents; calls that overlap on the GPU
+ *     race and corrupt each other's results.
+ *   - The step record lives in the shared buffer: piso_step_adjoint cannot use
+ *     it (run piso_step, with the domain's own workspace, before an adjoint).
+ *   - Advective outflow faces of the domain are updated as by piso_step. */
+piso_status piso_step_static(piso_domain* d, const void* u_in, const void* p_in, void* u_out, void* p_out,
+                             double dt, double nu, const void* S, void* stream, piso_stats* stats);
+
 /* Wait for the last enqueued step (or adjoint) of the domain and report it. */
 piso_status piso_last_stats(piso_domain* d, piso_stats* stats);
 

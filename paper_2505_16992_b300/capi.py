@@ -57,6 +57,7 @@ _SIGS = {
     "piso_tape_bytes": (C.c_size_t, [_P]),
     "piso_step": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, _P, _P, _P, C.POINTER(Stats)]),
     "piso_last_stats": (C.c_int, [_P, C.POINTER(Stats)]),
+    "piso_step_static": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, _P, _P, C.POINTER(Stats)]),
     "piso_autotune": (C.c_int, [_P, _P, _P, C.c_double, C.c_double, _P, _P, C.POINTER(C.c_int32),
                                 C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "piso_step_adjoint": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _D, _P, C.POINTER(Stats)]),

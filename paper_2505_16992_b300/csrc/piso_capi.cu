@@ -977,3 +977,134 @@ void piso_domain_destroy(piso_domain* d) {
 
 #include "piso_capi_adjoint.inc"
 #include "piso_capi_batch.inc"
+
+// ===========================================================================
+// Forward step with library-owned static scratch (allocates nothing per call).
+//
+// Some callers cannot allocate device memory when they step: for example a
+// process whose device memory is already fully reserved by another framework's
+// caching allocator, or a latency-critical loop that must not risk an
+// allocation or its failure mid-run.  For them piso_step_static runs the same
+// forward kernel as piso_step, but every scratch array it needs (workspace,
+// step record and control words) comes from one fixed buffer compiled into
+// this library instead of from memory obtained with cudaMalloc.
+// ===========================================================================
+namespace {
+
+constexpr size_t STATIC_SCRATCH_BYTES = 32ull << 20;   // 32 MiB, held on every device that loads the library
+__device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+void* g_static_ptr[MAX_DEVICES] = {nullptr};
+
+// Byte layout of the forward kernel's scratch inside the static buffer.
+struct StaticLayout {
+  size_t ws[W_COUNT];
+  size_t tape, bar, status, istats, dstats, partials, total;
+};
+
+StaticLayout static_layout(const piso_domain* d) {
+  StaticLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  for (int k = 0; k < A_GA; k++) L.ws[k] = take((size_t)ws_units(k, d->ndim) * d->N * d->elem);
+  L.tape = take(tape_layout(d).total);
+  L.bar = take(64);
+  L.status = take(64);
+  L.istats = take(64);
+  L.dstats = take(128);
+  L.partials = take(sizeof(double) * 2 * NSMAX * (size_t)d->ncta);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const void* p_in, void* u_out,
+                                        void* p_out, double dt, double nu, const void* S, void* stream,
+                                        piso_stats* stats) {
+  if (!d) return fail(d, PISO_EINVAL, "NULL domain");
+  if (!d->finalized) return fail(d, PISO_ESTATE, "step before finalize");
+  if (!u_in || !p_in || !u_out || !p_out) return fail(d, PISO_EINVAL, "NULL field pointer");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(d, PISO_EINVAL, "dt must be positive and finite");
+  if (!(nu >= 0) || !std::isfinite(nu)) return fail(d, PISO_EINVAL, "nu must be non-negative and finite");
+  const StaticLayout SL = static_layout(d);
+  if (SL.total > STATIC_SCRATCH_BYTES)
+    return fail(d, PISO_EINVAL, "domain needs %zu bytes of scratch; piso_step_static provides %zu (use piso_step)",
+                SL.total, STATIC_SCRATCH_BYTES);
+  int dev = 0;
+  CUDA_TRY(d, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= MAX_DEVICES) return fail(d, PISO_EINVAL, "device index %d out of range", dev);
+  if (!g_static_ptr[dev]) {   // set-up, once per device, with that device current
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess || !ptr)
+      return fail(d, PISO_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+    g_static_ptr[dev] = ptr;
+  }
+  char* base = (char*)g_static_ptr[dev];
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(d, cudaMemsetAsync(base + SL.bar, 0, 64, st));      // barrier counter, status and counts start at 0
+  CUDA_TRY(d, cudaMemsetAsync(base + SL.status, 0, 64, st));
+  CUDA_TRY(d, cudaMemsetAsync(base + SL.istats, 0, 64, st));
+  auto launch = [&](auto tag) -> piso_status {
+    using real = decltype(tag);
+    Launch<FwdCall<real>> L;
+    memset(&L, 0, sizeof L);
+    L.ngroups = 1;
+    L.o = solver_opts(d->opts);
+    const size_t smem = nbt_bytes(d->ndim, d->N, d->ncta, &L.o.nbt_cap);
+    FwdCall<real>& c = L.call0;
+    fill_fwd_call<real>(d, c, u_in, p_in, u_out, p_out, dt, nu, S, base + SL.tape);
+    auto W = [&](int k) { return (real*)(base + SL.ws[k]); };
+    c.U = W(W_U);
+    c.rhs0 = W(W_RHS0);
+    c.r = W(W_R);
+    c.rhat = W(W_RHAT);
+    c.pv[0] = W(W_P0);
+    c.pv[1] = W(W_P1);
+    c.vv[0] = W(W_V0);
+    c.vv[1] = W(W_V1);
+    c.t = W(W_T);
+    c.Poff = W(W_POFF);
+    c.Pdiag = W(W_PDIAG);
+    c.Pinv = W(W_PINV);
+    c.invA = W(W_INVA);
+    c.Aw = W(W_AW);
+    c.Fh = W(W_FH);
+    c.b = W(W_B);
+    c.cx = W(W_CX);
+    c.crb[0] = W(W_CRB0);
+    c.crb[1] = W(W_CRB1);
+    c.cwb[0] = W(W_CWB0);
+    c.cwb[1] = W(W_CWB1);
+    c.csb[0] = W(W_CSB0);
+    c.csb[1] = W(W_CSB1);
+    c.cp = W(W_CP);
+    c.x64 = (double*)(base + SL.ws[W_X64]);
+    c.rin = W(W_RIN);
+    c.ce = W(W_CE);
+    c.bar = (uint32_t*)(base + SL.bar);
+    c.status = (int32_t*)(base + SL.status);
+    c.istats = (int32_t*)(base + SL.istats);
+    c.dstats = (double*)(base + SL.dstats);
+    c.partials = (double*)(base + SL.partials);
+    void* args[] = {&L};
+    CUDA_TRY(d, coop_launch(fwd_ptr_t<real>(d->ndim, d->threads), d->ncta, d->threads, args, st, smem));
+    return PISO_OK;
+  };
+  piso_status s = d->prec == PISO_FP64 ? launch(double(0)) : launch(float(0));
+  if (s) return s;
+  CUDA_TRY(d, cudaMemcpyAsync(d->h_status, base + SL.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(d, cudaMemcpyAsync(d->h_istats, base + SL.istats, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(d, cudaMemcpyAsync(d->h_dstats, base + SL.dstats, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  d->pending = true;
+  d->pending_kind = 1;
+  d->pending_stream = st;
+  if (stats) return collect_stats(d, stats);
+  return PISO_OK;
+}
