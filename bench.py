@@ -115,6 +115,15 @@ def whole_job_value(total_s: float, steps: int, world: int, dist=None, device="c
     return world * steps / total_s
 
 
+def kernel_sources_hash() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2505_16992_b300", "csrc", "*.cuh"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -207,6 +216,74 @@ def time_variant(case, prec, kw, steps, with_adj, flush):
             "p_resid": st["p_resid"][:2]}
 
 
+def run_batch(args):
+    """Config 5: 64 independent 2D cavity/channel simulations (sides 32..256,
+    Re 100..2000, seed 4) advanced together: one persistent launch for the
+    forward step of all members and one for their adjoint."""
+    import numpy as np
+    import torch
+    from paper_2505_16992_b300 import capi, workloads as W
+    from paper_2505_16992_b300.solver import Batch, Domain
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cases = W.batch2d()
+    prec = args.precision
+    rtol = 1e-6 if prec == "fp32" else 1e-10
+    opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
+                                block_threads=args.threads or 512)
+    doms = [Domain.from_case(c, prec, opts) for c in cases]
+    us = [d.field(c.u0, 2) for d, c in zip(doms, cases)]
+    ps = [d.field(c.p0) for d, c in zip(doms, cases)]
+    Ss = [None if c.S is None else d.field(c.S, 2) for d, c in zip(doms, cases)]
+    uo = [torch.empty_like(u) for u in us]
+    po = [torch.empty_like(p) for p in ps]
+    g0 = torch.Generator(device="cpu").manual_seed(7)
+    gs = [torch.randn(u.shape, generator=g0, dtype=u.dtype).cuda() for u in us]   # seeded adjoint seeds
+    b = Batch(doms, opts)
+    dts, nus = [c.dt for c in cases], [c.nu for c in cases]
+    with_adj = args.mode == "fwdadj"
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def one():
+        b.step(us, ps, dts, nus, Ss, u_out=uo, p_out=po, sync=False)
+        if with_adj:
+            b.step_adjoint(gs)
+
+    for _ in range(args.warmup):
+        one()
+    _, _, st = b.step(us, ps, dts, nus, Ss, u_out=uo, p_out=po)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    tot = 0.0
+    clk_path = os.path.join(tempfile.gettempdir(), f"piso_clocks_{os.getpid()}.csv")
+    proc, fh = clocks_sampler_start(clk_path)
+    for _ in range(args.steps):
+        flush.fill_(0.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1) / 1e3
+    clocks = clocks_sampler_stop(proc, fh, clk_path, 0)
+    cells = sum(c.ncells for c in cases)
+    value = len(cases) * args.steps / tot
+    line = {"metric": "batched PISO sim-steps/s (64 independent 2D sims, fwd+adjoint)" if with_adj else
+                      "batched PISO sim-steps/s (64 independent 2D sims, fwd)",
+            "value": value, "unit": "sim-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "batch64: 2D cavities/channels, side U{32..256}, Re U[100,2000], seed 4",
+                       "cells": cells, "krylov_rtol": rtol, "ctas": b.total_ctas if hasattr(b, "total_ctas") else None,
+                       "l2": "flushed between timed steps (256 MB write, untimed)"},
+            "cell_updates_per_s": cells * args.steps / tot,
+            "p_iters_max": max(max(s["p_iters"][:2]) for s in st),
+            "p_iters_min": min(min(s["p_iters"][:2]) for s in st),
+            "gpu_launches": args.steps * (2 if with_adj else 1),
+            "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -220,11 +297,17 @@ def main():
     ap.add_argument("--refine", type=float, default=0.0, help="FP32: FP64-refined pressure tolerance")
     ap.add_argument("--compare", action="store_true",
                     help="also time FP64 and refined FP32 at matched pressure tolerances")
+    ap.add_argument("--workload", default="channel3d",
+                    choices=["channel3d", "channel3d-mid", "channel3d-large", "batch64"],
+                    help="channel3d: 64x48x32 (default); channel3d-large: 256x192x128 (HBM-bound sizes); "
+                         "batch64: 64 independent 2D simulations in one launch")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
 
     import numpy as np
     import torch
@@ -241,7 +324,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    case = W.channel3d()
+    sizes = {"channel3d": (64, 48, 32), "channel3d-mid": (160, 120, 80), "channel3d-large": (256, 192, 128)}
+    case = W.channel3d(*sizes[args.workload])
     prec = args.precision
     rtol = 1e-6 if prec == "fp32" else 1e-10
     opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
@@ -334,9 +418,12 @@ def main():
     achieved = alg_bytes / fwd_avg_s / 1e9
     traffic = None
     prof = os.path.join(ROOT, "profiles", f"traffic_fwd_kernel_channel3d_{prec}.json")
-    if os.path.exists(prof):
+    if os.path.exists(prof) and args.workload == "channel3d":
         try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+            tj = json.load(open(prof))
+            # counters are valid only for the kernel sources they were taken on
+            if tj.get("kernel_sources_sha256_16") == kernel_sources_hash():
+                traffic = tj.get("dram_bytes_per_launch")
         except Exception:
             traffic = None
 
@@ -378,7 +465,11 @@ def main():
         }
         if compare is not None:
             line["precision_compare"] = compare
-        if world == 1 and not args.no_cpu_baseline:
+        if args.workload != "channel3d":
+            tag = "x".join(str(v) for v in sizes[args.workload])
+            line["config"]["workload"] = line["config"]["workload"].replace("64x48x32", tag)
+            line["metric"] = line["metric"].replace("64x48x32", tag)
+        if world == 1 and not args.no_cpu_baseline and args.workload == "channel3d":
             v, n, dt = cpu_baseline(case)
             line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
                                     "sample": f"{n} fwd+adjoint steps of the same workload in {dt:.1f} s"}

@@ -95,6 +95,7 @@ typedef struct {
   double adv_resid[3];    /* final BiCGStab residual norms */
   double p_resid[4];      /* final CG residual norms (the FP64 outer residual when refining) */
   int32_t p_rounds[4];    /* refinement rounds per corrector (0 without refinement) */
+  double p_rhs_norm[4];   /* norm of each pressure solve's (projected) right-hand side */
 } piso_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -26,12 +26,13 @@ class Options(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("error_bits", C.c_int32), ("adv_iters", C.c_int32 * 3),
                 ("p_iters", C.c_int32 * 4), ("adv_resid", C.c_double * 3), ("p_resid", C.c_double * 4),
-                ("p_rounds", C.c_int32 * 4)]
+                ("p_rounds", C.c_int32 * 4), ("p_rhs_norm", C.c_double * 4)]
 
     def as_dict(self):
         return dict(status=STATUS.get(self.status, self.status), error_bits=self.error_bits,
                     adv_iters=list(self.adv_iters), p_iters=list(self.p_iters),
-                    adv_resid=list(self.adv_resid), p_resid=list(self.p_resid), p_rounds=list(self.p_rounds))
+                    adv_resid=list(self.adv_resid), p_resid=list(self.p_resid), p_rounds=list(self.p_rounds),
+                    p_rhs_norm=list(self.p_rhs_norm))
 
 
 class PisoError(RuntimeError):

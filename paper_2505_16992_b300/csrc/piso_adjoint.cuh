@@ -186,6 +186,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
         A.istats[4 + k] = rs.inner_it;
         A.istats[8 + k] = rs.rounds;
         A.dstats[4 + k] = sqrt(rs.res2);
+        A.dstats[8 + k] = sqrt(rs.bn2);
         if (!rs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
       }
     } else {
@@ -195,6 +196,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       if (threadIdx.x == 0 && g.rank == 0) {
         A.istats[4 + k] = cs.it;
         A.dstats[4 + k] = sqrt(cs.res2);
+        A.dstats[8 + k] = sqrt(cs.tol2) / fmax(o.p_rtol, 1e-300);
         if (!cs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
       }
     }

@@ -440,6 +440,7 @@ piso_status collect_stats(piso_domain* d, piso_stats* st) {
       st->p_iters[k] = d->h_istats[4 + k];
       st->p_resid[k] = d->h_dstats[4 + k];
       st->p_rounds[k] = d->h_istats[8 + k];
+      st->p_rhs_norm[k] = d->h_dstats[8 + k];
     }
   }
   if (s != PISO_OK) {
@@ -1108,3 +1109,12 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
   if (stats) return collect_stats(d, stats);
   return PISO_OK;
 }
+
+#ifdef PISO_TRACE
+// Copy the phase-timing trace (trace builds only): n entries of 4 stamps.
+extern "C" int piso_trace_read(uint64_t* out, int n) {
+  if (n > PISO_TRACE_LEN) n = PISO_TRACE_LEN;
+  if (cudaMemcpyFromSymbol(out, g_piso_trace, sizeof(uint64_t) * 4 * n) != cudaSuccess) return -1;
+  return n;
+}
+#endif

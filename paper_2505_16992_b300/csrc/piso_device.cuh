@@ -230,6 +230,28 @@ struct Group {
   int32_t withhold;     // fault injection: this CTA skips its first arrival (1) or not (0)
 };
 
+// Optional phase-timing trace (build with -DPISO_TRACE): CTA 0 of the launch
+// records globaltimer stamps at four points of every phase boundary — work
+// done, partials published, barrier passed, totals gathered — into a ring of
+// PISO_TRACE_LEN entries.  Off by default; it changes no computation.
+#ifdef PISO_TRACE
+constexpr int PISO_TRACE_LEN = 8192;
+__device__ uint64_t g_piso_trace[PISO_TRACE_LEN][4];
+__device__ uint32_t g_piso_trace_n;
+#define PISO_STAMP(slot, k)                                                   \
+  do {                                                                        \
+    if (blockIdx.x == 0 && threadIdx.x == 0) {                                \
+      uint64_t t_;                                                            \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                  \
+      g_piso_trace[(slot) % PISO_TRACE_LEN][k] = t_;                          \
+    }                                                                         \
+  } while (0)
+#else
+#define PISO_STAMP(slot, k) \
+  do {                      \
+  } while (0)
+#endif
+
 __device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -288,6 +310,7 @@ __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& up
     if (lane == 0) s_w[warp * NSMAX + k] = a[k].pack();
   }
   __syncthreads();
+  PISO_STAMP(g.epoch, 0);
   g.epoch++;
   double* P = g.partials + (size_t)(g.epoch & 1) * NSMAX * g.ncta;
   for (int k = warp; k < NS; k += nw) {
@@ -299,7 +322,9 @@ __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& up
     if (lane == 0) __stcg(P + (size_t)k * g.ncta + g.rank, v.pack());
   }
   __syncthreads();
+  PISO_STAMP(g.epoch - 1, 1);
   if (threadIdx.x == 0) s_ok = barrier_arrive_wait(g);
+  PISO_STAMP(g.epoch - 1, 2);
   __syncthreads();
   const int ok = s_ok;
   if (ok) {
@@ -325,6 +350,7 @@ __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& up
     __syncthreads();
     if (threadIdx.x == 0) update(s_tot);
   }
+  PISO_STAMP(g.epoch - 1, 3);
   __syncthreads();
   return ok != 0;
 }
@@ -333,8 +359,12 @@ __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& up
 __device__ __forceinline__ bool plain_sync(Group& g) {
   __shared__ int s_ok2;
   __syncthreads();
+  PISO_STAMP(g.epoch, 0);
+  PISO_STAMP(g.epoch, 1);
   g.epoch++;
   if (threadIdx.x == 0) s_ok2 = barrier_arrive_wait(g);
+  PISO_STAMP(g.epoch - 1, 2);
+  PISO_STAMP(g.epoch - 1, 3);
   __syncthreads();
   return s_ok2 != 0;
 }

@@ -385,6 +385,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
         A.istats[4 + kc] = rs.inner_it;
         A.istats[8 + kc] = rs.rounds;
         A.dstats[4 + kc] = sqrt(rs.res2);
+        A.dstats[8 + kc] = sqrt(rs.bn2);
         if (!rs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
       }
     } else {
@@ -394,6 +395,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       if (threadIdx.x == 0 && g.rank == 0) {
         A.istats[4 + kc] = cs.it;
         A.dstats[4 + kc] = sqrt(cs.res2);
+        A.dstats[8 + kc] = sqrt(cs.tol2) / fmax(o.p_rtol, 1e-300);
         if (!cs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
       }
     }
