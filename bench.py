@@ -229,7 +229,7 @@ def run_batch(args):
     prec = args.precision
     rtol = 1e-6 if prec == "fp32" else 1e-10
     opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
-                                block_threads=args.threads or 512)
+                                block_threads=args.threads or 768)
     doms = [Domain.from_case(c, prec, opts) for c in cases]
     us = [d.field(c.u0, 2) for d, c in zip(doms, cases)]
     ps = [d.field(c.p0) for d, c in zip(doms, cases)]

@@ -41,6 +41,30 @@ struct Ctx {
   Group& g;
   int32_t lo, hi, N;
   const int32_t* nbt;   // [2*ND][hi-lo] neighbour table in shared memory, or nullptr
+  // cells with an L2 prefetch of the cell this thread visits next: when a CTA
+  // owns more cells than threads, the next cell's streams are requested a full
+  // cell-visit ahead (memory-level parallelism for the bandwidth-bound sizes)
+  template <typename F, typename PF>
+  __device__ __forceinline__ void cells_pf(F&& f, PF&& pf) const {
+    const int32_t T = blockDim.x;
+    if (hi - lo <= T) {
+      cells(f);
+      return;
+    }
+    for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += T) {
+      if (i + T < hi) pf(i + T);
+      Cell c;
+      if (nbt) {
+        const int32_t n = hi - lo, l = i - lo;
+        c.i = i;
+#pragma unroll
+        for (int s = 0; s < 2 * ND; s++) c.nb[s] = nbt[s * n + l];
+      } else {
+        c = locate<ND>(D, i);
+      }
+      f(c);
+    }
+  }
   template <typename F>
   __device__ __forceinline__ void cells(F&& f) const {
     if (nbt) {
@@ -64,6 +88,10 @@ struct Ctx {
     for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += blockDim.x) f(i);
   }
 };
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 // Row coefficients of C (TR = false) or C^T (TR = true) for cell c:
 // (M y)_P = diag * y_P + sum_s cf[s] * y_{nb(P,s)} over inner faces.  The
@@ -193,7 +221,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       const real* vold = vv[cur ^ 1];
       real* pnew = pv[cur];
       real* vnew = vv[cur];
-      X.cells([&](const Cell& c) {
+      X.cells_pf([&](const Cell& c) {
         real diag, cf[2 * ND];
         c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
 #pragma unroll
@@ -212,6 +240,17 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
           pnew[o_ + c.i] = pP;
           vnew[o_ + c.i] = v;
           a[k].add_prod(rhat[o_ + c.i], v);
+        }
+      }, [&](int32_t i) {
+        prefetch_l2(Cdiag + i);
+#pragma unroll
+        for (int s = 0; s < 2 * ND; s++) prefetch_l2(Coff + (size_t)s * N + i);
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+          prefetch_l2(r + (size_t)k * N + i);
+          prefetch_l2(pold + (size_t)k * N + i);
+          prefetch_l2(vold + (size_t)k * N + i);
+          prefetch_l2(rhat + (size_t)k * N + i);
         }
       });
       const bool ok = reduce_sync<real, ND>(X.g, a, [&](const double* q) {
@@ -243,7 +282,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
 #pragma unroll
       for (int k = 0; k < 3 * ND; k++) a[k].zero();
       const real* vnew = vv[cur];
-      X.cells([&](const Cell& c) {
+      X.cells_pf([&](const Cell& c) {
         real diag, cf[2 * ND];
         c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
 #pragma unroll
@@ -260,6 +299,15 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
           a[k].add_prod(tt, sP);
           a[ND + k].add_prod(tt, tt);
           a[2 * ND + k].add_prod(sP, sP);
+        }
+      }, [&](int32_t i) {
+        prefetch_l2(Cdiag + i);
+#pragma unroll
+        for (int s = 0; s < 2 * ND; s++) prefetch_l2(Coff + (size_t)s * N + i);
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+          prefetch_l2(r + (size_t)k * N + i);
+          prefetch_l2(vnew + (size_t)k * N + i);
         }
       });
       const bool ok = reduce_sync<real, 3 * ND>(X.g, a, [&](const double* q) {
@@ -452,7 +500,7 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     real* s_n = sb[cur];
     real* r_n = rb[cur ^ 1];
     real* w_n = wb[cur ^ 1];
-    X.cells([&](const Cell& c) {
+    X.cells_pf([&](const Cell& c) {
       real pf[2 * ND];
       p_row<real, ND>(c, N, Poff, pf);
       auto sQ = [&](int32_t Q) -> real { return first ? w_i[Q] : w_i[Q] + be * s_o[Q]; };
@@ -476,6 +524,15 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
       a[0].add_prod(r1, u1P);
       a[1].add_prod(w1, u1P);
       a[2].add_prod(r1, r1);
+    }, [&](int32_t i) {
+      prefetch_l2(r_i + i);
+      prefetch_l2(w_i + i);
+      prefetch_l2(s_o + i);
+      prefetch_l2(Pinv + i);
+      prefetch_l2(pdir + i);
+      prefetch_l2(x + i);
+#pragma unroll
+      for (int j = 0; j < ND; j++) prefetch_l2(Poff + (size_t)j * N + i);
     });
     const bool ok = reduce_sync<real, 3>(X.g, a, [&](const double* q) {
       cs.it++;
