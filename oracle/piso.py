@@ -26,6 +26,10 @@ finite-volume PISO scheme of arXiv:2505.16992:
 * Sec. 2.3 and App. A.4 (gradients): linear solves are differentiated by the
   transposed solve  A^T db = dx,  dA = -db (x) x  on the sparsity pattern; every
   other operation by its exact transpose.
+* Sec. 2.4 (gradient paths, Eq. jnone): the paths through the advection solve
+  and through the pressure solves can each be left out of the backward pass
+  (that solve's output is then a constant of the backward pass), leaving the
+  bypass paths when both are left out.
 
 Readings of points the paper leaves open (the same readings the CUDA path
 implements; each is listed in the design notes):
@@ -74,6 +78,8 @@ class Options:
     maxit: int = 20000
     solver: str = "auto"         # "krylov" | "direct" | "auto" (direct where a sparse LU is cheap)
     update_outflow: bool = True  # App. A.3 advective outflow update before the step
+    grad_adv: bool = True        # Sec. 2.4: keep the gradient paths through the advection solve
+    grad_p: bool = True          # Sec. 2.4: keep the gradient paths through the pressure solves
 
 
 class Mesh:
@@ -503,7 +509,13 @@ def piso_step(mesh: Mesh, u, p, dt, nu, S=None, bval=None, opts: Optional[Option
 def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Options] = None):
     """Reverse of ``piso_step``: given dL/du^{n+1} and dL/dp^{n+1}, return
     dL/du^n, dL/dp^n, dL/dS and dL/dnu (the outflow update and the boundary
-    values are held fixed)."""
+    values are held fixed).
+
+    ``opts.grad_adv`` / ``opts.grad_p`` select the gradient paths of Sec. 2.4:
+    the full adjoint is J^Adv + J^P + J^none, and dropping a path treats that
+    solve's output (u*, or every corrector's pressure) as a constant of the
+    backward pass, i.e. its transposed solve contributes zero.  With both off
+    only the bypass paths of Eq. jnone remain."""
     opts = opts or Options()
     d, N = mesh.ndim, mesh.N
     C, Pm = tape["C"], tape["Pm"]
@@ -525,18 +537,21 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
         gA += np.sum(gu * grad_p(mesh, x), axis=0) / A ** 2
         if k == ncorr - 1:
             gx = gx + gp_last
-        # x = Pi(P^+ Pi b): transposed (symmetric) solve
-        gx = gx - gx.mean()
-        y, _ = solve_P(mesh, Pm, gx, np.zeros(N), opts)
-        gb = y - y.mean()
-        # dP = -y (x) x on the pattern -> d(alpha/A): 0.5 (y_P - y_F)(x_P - x_F) per inner face
-        for s in range(mesh.nsides):
-            j = s // 2
-            P = np.nonzero(mesh.inner[s])[0]
-            F = mesh.nb[s, P]
-            gw[j, P] += 0.5 * (y[P] - y[F]) * (x[P] - x[F])
-        # b = div(h) + boundary flux
-        gh += divergence_T(mesh, gb)
+        if opts.grad_p:
+            # x = Pi(P^+ Pi b): transposed (symmetric) solve
+            gx = gx - gx.mean()
+            y, _ = solve_P(mesh, Pm, gx, np.zeros(N), opts)
+            gb = y - y.mean()
+            # dP = -y (x) x on the pattern -> d(alpha/A): 0.5 (y_P - y_F)(x_P - x_F) per inner face
+            for s in range(mesh.nsides):
+                j = s // 2
+                P = np.nonzero(mesh.inner[s])[0]
+                F = mesh.nb[s, P]
+                gw[j, P] += 0.5 * (y[P] - y[F]) * (x[P] - x[F])
+            # b = div(h) + boundary flux
+            gh += divergence_T(mesh, gb)
+        # without the pressure path (Sec. 2.4) x is a constant of the backward
+        # pass: gx is dropped and neither b nor P receives a gradient
         # h = (rhs0 - H u_in) / A
         gg = gh / A[None, :]
         gA -= np.sum(gh * h, axis=0) / A
@@ -548,7 +563,9 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
     gA -= np.sum(gw * mesh.alpha, axis=0) / A ** 2
     # predictor: u* = C^-1 rhs
     ustar = tape["ustar"]
-    z = solve_C_T(mesh, C, gu, opts)
+    # without the advection path (Sec. 2.4) u* is a constant of the backward
+    # pass: the transposed solve is skipped and C, rhs receive nothing from it
+    z = solve_C_T(mesh, C, gu, opts) if opts.grad_adv else np.zeros_like(gu)
     grhs = z
     gA -= np.sum(z * ustar, axis=0)
     for s in range(mesh.nsides):
