@@ -427,6 +427,35 @@ def main():
         except Exception:
             traffic = None
 
+    # gradient-path variants of the adjoint (Sec. 2.4): the same fwd+adjoint
+    # step with the advection and/or pressure solves left out of the backward pass
+    paths = None
+    if with_adj:
+        adj_ms = [t - f for t, f in zip(step_ms, fwd_ms)]
+        paths = {"adv+p": {"steps_per_s": value, "adj_ms": sum(adj_ms) / len(adj_ms)}}
+        nvar = max(5, args.steps // 3)
+        for name, bits in (("adv", capi.PISO_GRAD_ADV), ("p", capi.PISO_GRAD_P), ("none", 0)):
+            dom.set_options(capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
+                                                 block_threads=shape[0], ctas=shape[1] or 0,
+                                                 p_refine_rtol=args.refine, grad_paths=bits))
+            for _ in range(3):
+                one_step()
+            vst = dom.step_adjoint(gu, None)[4]
+            tf = ta = 0.0
+            for k in range(nvar):
+                flush.fill_(float(k))
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+                dom.step(u, p, case.dt, case.nu, S, u_out=u_out, p_out=p_out, sync=False)
+                e[1].record(stream)
+                dom.step_adjoint(gu, None)
+                e[2].record(stream)
+                e[2].synchronize()
+                tf += e[0].elapsed_time(e[1])
+                ta += e[1].elapsed_time(e[2])
+            paths[name] = {"steps_per_s": 1e3 * nvar / (tf + ta), "adj_ms": ta / nvar,
+                           "adj_iters": {"adv": vst["adv_iters"][:d], "p": vst["p_iters"][:2]}}
+
     compare = None
     if args.compare:
         compare = {}
@@ -465,6 +494,8 @@ def main():
         }
         if compare is not None:
             line["precision_compare"] = compare
+        if paths is not None:
+            line["grad_paths"] = paths
         if args.workload != "channel3d":
             tag = "x".join(str(v) for v in sizes[args.workload])
             line["config"]["workload"] = line["config"]["workload"].replace("64x48x32", tag)

@@ -84,7 +84,16 @@ typedef struct {
                             until ||b - P p|| <= p_refine_rtol ||b|| (each round an FP32 CG to
                             p_inner_rtol); 0 (default) = a single FP32 CG to p_rtol */
   double p_inner_rtol;   /* inner tolerance per refinement round (default 1e-4) */
+  int32_t grad_paths;    /* gradient paths kept by piso_step_adjoint (Sec. 2.4, Eq. jnone): a bit
+                            set of PISO_GRAD_ADV and PISO_GRAD_P, default both (the exact adjoint).
+                            A path left out treats that solve's output (u*, or every corrector's
+                            pressure) as a constant of the backward pass, so its transposed solve
+                            is skipped; 0 keeps only the bypass paths.  The forward step ignores it. */
 } piso_options;
+
+/* Bits of piso_options.grad_paths. */
+#define PISO_GRAD_ADV 1   /* paths through the advection (predictor) solve */
+#define PISO_GRAD_P 2     /* paths through the pressure solves */
 
 /* Per-step statistics (read back when a stats pointer is given). */
 typedef struct {

@@ -11,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpiso.so")
 
 PISO_FP64, PISO_FP32 = 0, 1
+PISO_GRAD_ADV, PISO_GRAD_P = 1, 2          # piso_options.grad_paths bits (Sec. 2.4 gradient paths)
 STATUS = {0: "PISO_OK", 1: "PISO_EINVAL", 2: "PISO_ECUDA", 3: "PISO_ENOCONV", 4: "PISO_EBREAKDOWN",
           5: "PISO_ENAN", 6: "PISO_ETIMEOUT", 7: "PISO_ESTATE", 8: "PISO_ENOMEM"}
 
@@ -20,7 +21,7 @@ class Options(C.Structure):
                 ("p_rtol", C.c_double), ("atol", C.c_double), ("adv_maxit", C.c_int32),
                 ("p_maxit", C.c_int32), ("block_threads", C.c_int32), ("ctas", C.c_int32),
                 ("timeout_s", C.c_double), ("fault_withhold_cta", C.c_int32), ("p_refine_rtol", C.c_double),
-                ("p_inner_rtol", C.c_double)]
+                ("p_inner_rtol", C.c_double), ("grad_paths", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -4,7 +4,9 @@
 // sparsity pattern; App. A.5: the forward solvers with the transposed matrix),
 // every other operation by its exact transpose, read off the implemented
 // forward operator (reading R9).  Boundary values and the outflow update are
-// held fixed.
+// held fixed.  The gradient paths of Sec. 2.4 (Eq. jnone) are selectable: a
+// path left out makes its solve's output a constant of the backward pass, so
+// the transposed solve and the terms it feeds are skipped.
 #pragma once
 #include "piso_forward.cuh"
 
@@ -89,6 +91,8 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   auto Tm = [&](int j, int k, int32_t i) -> real { return T[(size_t)(j * ND + k) * N + i]; };
   const real inv_dt = pick<real>(s_idt, s_idt_f);
   const int K = o.n_corr;
+  const bool path_adv = (o.grad_paths & 1) != 0;   // Sec. 2.4: gradient through the advection solve
+  const bool path_p = (o.grad_paths & 2) != 0;     // Sec. 2.4: gradient through the pressure solves
 
   // (G^T W)_P for the cell-centred central gradient with the R5 boundary rule:
   // G(p)_Q = sum_j T_Q,j . 0.5 (p_{nb(Q,+j)} - p_{nb(Q,-j)}), p_Q standing in
@@ -163,8 +167,9 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       A.gA[P] = (k == K - 1) ? ga : A.gA[P] + ga;
     });
     if (!plain_sync(g)) return;
-    // R1: gx = -G^T W (+ dL/dp^{n+1} after the last corrector); its mean
-    {
+    // R1: gx = -G^T W (+ dL/dp^{n+1} after the last corrector); its mean.
+    // Without the pressure path the pressure is a constant: no gx, no solve.
+    if (path_p) {
       Acc<real> a[1];
       a[0].zero();
       X.cells([&](const Cell& c) {
@@ -177,7 +182,8 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       if (!reduce_sync<real, 1>(g, a, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
     }
     // transposed pressure solve: P y = gx - mean (P is symmetric)
-    if (sizeof(real) == 4 && o.p_refine_rtol > 0) {
+    if (!path_p) {
+    } else if (sizeof(real) == 4 && o.p_refine_rtol > 0) {
       if (!cg_pressure_refined<real, ND>(X, cs, rs, o.p_refine_rtol, o.p_inner_rtol, o.atol, o.p_maxit, 20,
                                          A.Pdiag, A.Pinv, A.Poff, A.gx, s_mean, A.cx, A.x64, A.rin, A.ce, A.crb,
                                          A.cwb, A.csb, A.cp))
@@ -204,24 +210,28 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
     //     gg = h_bar / A; dL/dA and dL/drhs0 from h = A^-1 (rhs0 - H u)
     X.cells([&](const Cell& c) {
       const int32_t P = c.i;
-      const real yP = A.cx[P], xP = xk[P];
+      const real yP = path_p ? A.cx[P] : real(0), xP = path_p ? xk[P] : real(0);
       const real aP = A.Cdiag[P];
       real Fb[ND];
 #pragma unroll
-      for (int j = 0; j < ND; j++) {
-        real gwj = 0, fb = 0;
+      for (int j = 0; j < ND; j++) Fb[j] = 0;
+      if (path_p) {
 #pragma unroll
-        for (int e = 0; e < 2; e++) {
-          const int s = 2 * j + e;
-          const int32_t F = c.nb[s];
-          if (F < 0) continue;
-          const real n = e ? real(1) : real(-1);
-          const real dy = yP - A.cx[F];
-          gwj += real(0.5) * dy * (xP - xk[F]);
-          fb += real(0.5) * n * dy;
+        for (int j = 0; j < ND; j++) {
+          real gwj = 0, fb = 0;
+#pragma unroll
+          for (int e = 0; e < 2; e++) {
+            const int s = 2 * j + e;
+            const int32_t F = c.nb[s];
+            if (F < 0) continue;
+            const real n = e ? real(1) : real(-1);
+            const real dy = yP - A.cx[F];
+            gwj += real(0.5) * dy * (xP - xk[F]);
+            fb += real(0.5) * n * dy;
+          }
+          A.gw[(size_t)j * N + P] += gwj;
+          Fb[j] = fb * J[P];
         }
-        A.gw[(size_t)j * N + P] += gwj;
-        Fb[j] = fb * J[P];
       }
       real ga = 0;
 #pragma unroll
@@ -279,20 +289,26 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       for (int j = 0; j < ND; j++) s += A.gw[(size_t)j * N + P] * AL[(size_t)j * N + P];
       A.gA[P] -= s / (aP * aP);
 #pragma unroll
-      for (int i = 0; i < ND; i++) {
-        const real b = A.gu[(size_t)i * N + P];
-        A.z[(size_t)i * N + P] = 0;
-        A.r[(size_t)i * N + P] = b;
-        A.rhat[(size_t)i * N + P] = b;
-        a[i].add_prod(b, b);
-        a[ND + i].add_prod(b, b);
+      if (path_adv) {
+#pragma unroll
+        for (int i = 0; i < ND; i++) {
+          const real b = A.gu[(size_t)i * N + P];
+          A.z[(size_t)i * N + P] = 0;
+          A.r[(size_t)i * N + P] = b;
+          A.rhat[(size_t)i * N + P] = b;
+          a[i].add_prod(b, b);
+          a[ND + i].add_prod(b, b);
+        }
       }
     });
-    if (!reduce_sync<real, 2 * ND>(g, a, [&](const double* q) { bicg_start<ND>(bs, q, o.adv_rtol, o.atol, g.status); }))
+    // without the advection path u* is a constant: z = 0 and no solve
+    if (path_adv &&
+        !reduce_sync<real, 2 * ND>(g, a, [&](const double* q) { bicg_start<ND>(bs, q, o.adv_rtol, o.atol, g.status); }))
       return;
   }
-  if (!bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t)) return;
-  if (threadIdx.x == 0 && g.rank == 0) {
+  if (path_adv && !bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t))
+    return;
+  if (path_adv && threadIdx.x == 0 && g.rank == 0) {
     int nc = 0;
     for (int k = 0; k < ND; k++) {
       A.istats[k] = bs.iters[k];
@@ -308,21 +324,25 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   X.cells([&](const Cell& c) {
     const int32_t P = c.i;
     real zP[ND];
-    real ga = 0;
 #pragma unroll
-    for (int i = 0; i < ND; i++) {
-      zP[i] = A.z[(size_t)i * N + P];
-      ga += zP[i] * A.ustar[(size_t)i * N + P];
-    }
-    A.gA[P] -= ga;
+    for (int i = 0; i < ND; i++) zP[i] = 0;
+    if (path_adv) {
+      real ga = 0;
 #pragma unroll
-    for (int s = 0; s < NSD; s++) {
-      const int32_t F = c.nb[s];
-      if (F < 0) continue;
-      real acc = 0;
+      for (int i = 0; i < ND; i++) {
+        zP[i] = A.z[(size_t)i * N + P];
+        ga += zP[i] * A.ustar[(size_t)i * N + P];
+      }
+      A.gA[P] -= ga;
 #pragma unroll
-      for (int i = 0; i < ND; i++) acc += zP[i] * A.ustar[(size_t)i * N + F];
-      A.gCoff[(size_t)s * N + P] -= acc;
+      for (int s = 0; s < NSD; s++) {
+        const int32_t F = c.nb[s];
+        if (F < 0) continue;
+        real acc = 0;
+#pragma unroll
+        for (int i = 0; i < ND; i++) acc += zP[i] * A.ustar[(size_t)i * N + F];
+        A.gCoff[(size_t)s * N + P] -= acc;
+      }
     }
     real gr[ND];
 #pragma unroll

@@ -329,6 +329,7 @@ SolverOpts solver_opts(const piso_options& o) {
   s.withhold_cta = o.fault_withhold_cta;
   s.p_refine_rtol = o.p_refine_rtol;
   s.p_inner_rtol = o.p_inner_rtol;
+  s.grad_paths = o.grad_paths;
   return s;
 }
 
@@ -503,6 +504,7 @@ void piso_default_options(piso_options* o) {
   o->fault_withhold_cta = -1;
   o->p_refine_rtol = 0.0;
   o->p_inner_rtol = 1e-4;
+  o->grad_paths = PISO_GRAD_ADV | PISO_GRAD_P;
 }
 
 piso_status piso_domain_create(int32_t ndim, int32_t prec, piso_domain** out) {
@@ -599,6 +601,7 @@ static piso_status validate_options(piso_domain* d, const piso_options* o) {
   if (o->adv_maxit < 0 || o->p_maxit < 0) return fail(d, PISO_EINVAL, "negative iteration limit");
   if (!(o->timeout_s > 0)) return fail(d, PISO_EINVAL, "timeout_s must be positive");
   if (o->adv_rtol < 0 || o->p_rtol < 0 || o->atol < 0) return fail(d, PISO_EINVAL, "negative tolerance");
+  if (o->grad_paths & ~(PISO_GRAD_ADV | PISO_GRAD_P)) return fail(d, PISO_EINVAL, "grad_paths: unknown bits");
   return PISO_OK;
 }
 

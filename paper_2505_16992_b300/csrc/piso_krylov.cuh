@@ -16,6 +16,7 @@ struct SolverOpts {
   int32_t withhold_cta;      // fault injection: group rank that skips its first barrier arrival (-1 off)
   double p_refine_rtol;      // FP32 mode: outer FP64 residual tolerance of the pressure solve (0 = off)
   double p_inner_rtol;       // FP32 mode: inner CG tolerance per refinement round
+  int32_t grad_paths;        // adjoint: bit 1 keeps the advection-solve paths, bit 2 the pressure-solve paths
 };
 
 // Fill the CTA's neighbour table (dynamic shared memory) when its cell range

@@ -76,3 +76,25 @@ def test_fast_division_matches_integer_division():
         m, s = make(d)
         t = (n * m) >> 32
         assert (t + n) >> s == n // d, (n, d)
+
+
+def test_default_options_fill_every_field(lib):
+    """The ctypes mirror of piso_options lines up with the C struct: the
+    library's defaults land in the expected fields, the last one included."""
+    o = capi.default_options()
+    assert o.n_correctors == 2 and o.fault_withhold_cta == -1
+    assert o.p_inner_rtol == 1e-4
+    assert o.grad_paths == capi.PISO_GRAD_ADV | capi.PISO_GRAD_P
+
+
+def test_gradient_path_bits_are_validated(lib):
+    h = C.c_void_p()
+    assert lib.piso_domain_create(2, 0, C.byref(h)) == 0
+    res = (C.c_int32 * 3)(2, 2, 1)
+    verts = (C.c_double * 18)(*[0.0] * 18)
+    bid = C.c_int32()
+    assert lib.piso_block_add(h, res, verts, C.byref(bid)) == 0
+    o = capi.default_options(grad_paths=4)
+    assert lib.piso_finalize(h, C.byref(o)) == 1
+    assert b"grad_paths" in lib.piso_last_error(h)
+    lib.piso_domain_destroy(h)

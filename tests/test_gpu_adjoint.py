@@ -15,9 +15,9 @@ pytestmark = pytest.mark.gpu
 ADJ_REL = 1e-8
 
 
-def _adjoint_parity(case, seed=0, tol=ADJ_REL, precision="fp64", pred_grad_p=0, **opts):
+def _adjoint_parity(case, seed=0, tol=ADJ_REL, precision="fp64", pred_grad_p=0, grad_paths=3, **opts):
     m = O.mesh_from_case(case)
-    dom = gpu_domain(case, precision, pred_grad_p=pred_grad_p, **opts)
+    dom = gpu_domain(case, precision, pred_grad_p=pred_grad_p, grad_paths=grad_paths, **opts)
     d, N = case.ndim, case.ncells
     rng = np.random.default_rng(seed)
     u0 = case.u0 + 0.2 * rng.standard_normal((d, N))
@@ -32,7 +32,11 @@ def _adjoint_parity(case, seed=0, tol=ADJ_REL, precision="fp64", pred_grad_p=0, 
     uo, po, tape = O.piso_step(m, u0, p0, case.dt, case.nu, S0, None, oo)
     du, dp, dS, dnu, ast = dom.step_adjoint(to_dev(dom, ubar, d), to_dev(dom, pbar))
     assert ast["status"] == "PISO_OK", ast
-    gu, gp, gS, gnu = O.piso_step_adjoint(m, tape, ubar, pbar, oo)
+    oa = O.Options(pred_grad_p=bool(pred_grad_p), grad_adv=bool(grad_paths & 1), grad_p=bool(grad_paths & 2))
+    gu, gp, gS, gnu = O.piso_step_adjoint(m, tape, ubar, pbar, oa)
+    # a solve left out of the backward pass (Sec. 2.4) does not run at all
+    assert (sum(ast["adv_iters"]) > 0) == bool(grad_paths & 1), ast
+    assert (sum(ast["p_iters"]) > 0) == bool(grad_paths & 2), ast
     errs = dict(u=rel_err(host(du), gu), S=rel_err(host(dS), gS), nu=abs(dnu - gnu) / max(abs(gnu), 1e-300))
     if pred_grad_p:
         errs["p"] = rel_err(host(dp), gp)
@@ -75,6 +79,33 @@ def test_adjoint_ragged_ctas(ctas):
 
 def test_adjoint_fp32_mixed():
     _adjoint_parity(W.cavity2d(32, nu=0.01, dt=0.01), tol=2e-3, precision="fp32", adv_rtol=1e-6, p_rtol=1e-6)
+
+
+@pytest.mark.parametrize("paths", [0, capi.PISO_GRAD_ADV, capi.PISO_GRAD_P])
+@pytest.mark.parametrize("name", ["cavity", "bfs", "channel3d"])
+def test_adjoint_gradient_path_variants(name, paths):
+    """Sec. 2.4 gradient paths: adjoints with the advection and/or pressure
+    solves left out equal the oracle's variants (pinned there by FD of the step
+    with frozen solve outputs)."""
+    if name == "cavity":
+        c, kw = W.cavity2d(32, nu=0.01, dt=0.01), {}
+    elif name == "bfs":
+        c, kw = W.bfs2d(n_in=(16, 8), n_ch=64, n_out=16, half=8, dt=0.02), dict(p_rtol=1e-12)
+    else:
+        c, kw = W.channel3d(16, 12, 8), {}
+    _adjoint_parity(c, grad_paths=paths, **kw)
+
+
+@pytest.mark.parametrize("paths", [0, capi.PISO_GRAD_P])
+def test_adjoint_gradient_paths_with_predictor_pressure_gradient(paths):
+    """With -grad p^n in the predictor (reading R4), dL/dp^n flows only through
+    the advection solve: it must vanish when that path is left out."""
+    _adjoint_parity(W.cavity2d(16, nu=0.05, dt=0.05), pred_grad_p=1, grad_paths=paths)
+
+
+def test_adjoint_gradient_paths_fp32_full_channel():
+    _adjoint_parity(W.channel3d(), tol=2e-3, precision="fp32", adv_rtol=1e-6, p_rtol=1e-6,
+                    grad_paths=capi.PISO_GRAD_ADV)
 
 
 def test_adjoint_matches_gpu_finite_difference():

@@ -64,6 +64,24 @@ def test_batch_adjoint_matches_oracle():
         assert abs(dnu[i] - gnu) <= 1e-8 * abs(gnu), i
 
 
+def test_batch_adjoint_gradient_path_variant():
+    """The batched adjoint honours the gradient-path selection (Sec. 2.4)."""
+    cases = W.batch2d(count=3, seed=10, nmin=6, nmax=24)
+    doms, us, ps, Ss = _members(cases)
+    b = Batch(doms, capi.default_options(adv_rtol=1e-13, p_rtol=1e-13, grad_paths=capi.PISO_GRAD_ADV))
+    b.step(us, ps, [c.dt for c in cases], [c.nu for c in cases], Ss)
+    rng = np.random.default_rng(2)
+    gus = [rng.standard_normal((2, c.ncells)) for c in cases]
+    du, dp, dS, dnu, st = b.step_adjoint([to_dev(d, g, 2) for d, g in zip(doms, gus)])
+    for i, c in enumerate(cases):
+        assert st[i]["status"] == "PISO_OK" and sum(st[i]["p_iters"]) == 0, st[i]
+        m = O.mesh_from_case(c)
+        _, _, tape = O.piso_step(m, c.u0, c.p0, c.dt, c.nu, c.S)
+        gu, gp, gS, gnu = O.piso_step_adjoint(m, tape, gus[i], np.zeros(c.ncells), O.Options(grad_p=False))
+        assert rel_err(host(du[i]), gu) <= 1e-8, i
+        assert abs(dnu[i] - gnu) <= 1e-8 * abs(gnu), i
+
+
 def test_batch_config5_full_size_sampled_parity():
     """Config 5: 64 independent 2D cavity/channel simulations, sides uniform in
     32..256, Re in [100, 2000], FP32 bulk; sampled members against the oracle."""
