@@ -82,7 +82,8 @@ typedef struct {
   double p_refine_rtol;  /* PISO_FP32 only: > 0 refines every pressure solve against a residual
                             b - P p evaluated in FP64 with the solution accumulated in FP64,
                             until ||b - P p|| <= p_refine_rtol ||b|| (each round an FP32 CG to
-                            p_inner_rtol); 0 (default) = a single FP32 CG to p_rtol */
+                            p_inner_rtol); 0 (default) = a single FP32 CG to p_rtol, finished
+                            by such rounds (to p_rtol) only if it stalls */
   double p_inner_rtol;   /* inner tolerance per refinement round (default 1e-4) */
   int32_t grad_paths;    /* gradient paths kept by piso_step_adjoint (Sec. 2.4, Eq. jnone): a bit
                             set of PISO_GRAD_ADV and PISO_GRAD_P, default both (the exact adjoint).
@@ -100,10 +101,12 @@ typedef struct {
   int32_t status;         /* piso_status of the step */
   int32_t error_bits;     /* 1 adv no-conv, 2 pressure no-conv, 4 breakdown, 8 NaN, 16 timeout */
   int32_t adv_iters[3];   /* BiCGStab iterations per velocity component */
-  int32_t p_iters[4];     /* CG iterations per corrector */
+  int32_t p_iters[4];     /* CG iterations per corrector (all rounds) */
   double adv_resid[3];    /* final BiCGStab residual norms */
   double p_resid[4];      /* final CG residual norms (the FP64 outer residual when refining) */
-  int32_t p_rounds[4];    /* refinement rounds per corrector (0 without refinement) */
+  int32_t p_rounds[4];    /* FP64 refinement rounds per corrector: 0 for a plain CG; a plain FP32
+                             CG that stalled (its best residual norm did not halve in 200
+                             iterations) and was finished by refinement counts as round 1 */
   double p_rhs_norm[4];   /* norm of each pressure solve's (projected) right-hand side */
 } piso_stats;
 

@@ -182,30 +182,9 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       if (!reduce_sync<real, 1>(g, a, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
     }
     // transposed pressure solve: P y = gx - mean (P is symmetric)
-    if (!path_p) {
-    } else if (sizeof(real) == 4 && o.p_refine_rtol > 0) {
-      if (!cg_pressure_refined<real, ND>(X, cs, rs, o.p_refine_rtol, o.p_inner_rtol, o.atol, o.p_maxit, 20,
-                                         A.Pdiag, A.Pinv, A.Poff, A.gx, s_mean, A.cx, A.x64, A.rin, A.ce, A.crb,
-                                         A.cwb, A.csb, A.cp))
-        return;
-      if (threadIdx.x == 0 && g.rank == 0) {
-        A.istats[4 + k] = rs.inner_it;
-        A.istats[8 + k] = rs.rounds;
-        A.dstats[4 + k] = sqrt(rs.res2);
-        A.dstats[8 + k] = sqrt(rs.bn2);
-        if (!rs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
-      }
-    } else {
-      if (!cg_pressure<real, ND>(X, cs, o.p_rtol, o.atol, o.p_maxit, A.Pdiag, A.Pinv, A.Poff, A.gx, s_mean, A.cx,
-                                 A.crb, A.cwb, A.csb, A.cp))
-        return;
-      if (threadIdx.x == 0 && g.rank == 0) {
-        A.istats[4 + k] = cs.it;
-        A.dstats[4 + k] = sqrt(cs.res2);
-        A.dstats[8 + k] = sqrt(cs.tol2) / fmax(o.p_rtol, 1e-300);
-        if (!cs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
-      }
-    }
+    if (path_p && !pressure_solve<real, ND>(X, cs, rs, o, A.Pdiag, A.Pinv, A.Poff, A.gx, s_mean, A.cx, A.x64, A.rin,
+                                            A.ce, A.crb, A.cwb, A.csb, A.cp, A.istats, A.dstats, k))
+      return;
     // R3: dP = -y (x) x on the pattern -> d(alpha/A); h_bar = gu + div^T y;
     //     gg = h_bar / A; dL/dA and dL/drhs0 from h = A^-1 (rhs0 - H u)
     X.cells([&](const Cell& c) {

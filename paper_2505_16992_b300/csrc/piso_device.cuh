@@ -164,6 +164,43 @@ __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
   return r;
 }
 
+// Float-pair (double-word) operations for the FP32 mode's Krylov scalars, so
+// thread 0's per-iteration update stays on the FP32 pipe (an FP64 instruction
+// issues at ~64 cycles per warp on this GPU).  The product follows Dekker's
+// double-length multiplication with an FMA for the exact partial product, the
+// quotient one correction step q1 + (a - q1 b) / b; relative accuracy ~2^-44.
+__device__ __forceinline__ f2 f2_norm(float s, float e) {   // fast two-sum, |s| >= |e|
+  f2 r;
+  r.hi = s + e;
+  r.lo = e - (r.hi - s);
+  return r;
+}
+__device__ __forceinline__ f2 f2_neg(f2 a) { return f2{-a.hi, -a.lo}; }
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return f2_norm(p, e);
+}
+__device__ __forceinline__ f2 f2_div(f2 a, f2 b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const f2 r = f2_add(a, f2_neg(f2_mul(f2{q1, 0.f}, b)));
+  return f2_norm(q1, __fdiv_rn(r.hi, b.hi));
+}
+__device__ __forceinline__ bool f2_gt(f2 a, f2 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ f2 f2_from_double(double d) {
+  f2 r;
+  r.hi = (float)d;
+  r.lo = (float)(d - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ double f2_to_double(f2 a) { return (double)a.hi + (double)a.lo; }
+// unpack a float pair transported in the bits of a double (Acc<float>::pack)
+__device__ __forceinline__ f2 f2_unpack(double w) {
+  return f2{__int_as_float(__double2hiint(w)), __int_as_float(__double2loint(w))};
+}
+
 template <typename real>
 struct Acc;
 
@@ -297,7 +334,9 @@ __device__ __noinline__ int barrier_arrive_wait(const Group& g) {
 // the barrier wait ran out.
 constexpr int GATHER_UNROLL = 8;
 
-template <typename real, int NS, typename F>
+// RAW: hand update() the totals in transport form (Acc::pack: the float pair's
+// bits in the FP32 mode) instead of converted to double.
+template <typename real, int NS, bool RAW = false, typename F>
 __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& update) {
   __shared__ double s_w[MAXW * NSMAX];
   __shared__ double s_tot[NSMAX];
@@ -345,7 +384,7 @@ __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& up
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) v.shfl_down_add(off);
-      if (lane == 0) s_tot[k] = v.to_double();
+      if (lane == 0) s_tot[k] = RAW ? v.pack() : v.to_double();
     }
     __syncthreads();
     if (threadIdx.x == 0) update(s_tot);

@@ -375,30 +375,10 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
         return;
     }
     // pressure solve (App. A.5: CG; Chronopoulos-Gear form), in the FP32 mode
-    // optionally refined against an FP64 residual
-    if (sizeof(real) == 4 && o.p_refine_rtol > 0) {
-      if (!cg_pressure_refined<real, ND>(X, cs, rs, o.p_refine_rtol, o.p_inner_rtol, o.atol, o.p_maxit, 20,
-                                         A.Pdiag, A.Pinv, A.Poff, A.b, s_mean, A.cx, A.x64, A.rin, A.ce, A.crb,
-                                         A.cwb, A.csb, A.cp))
-        return;
-      if (threadIdx.x == 0 && g.rank == 0) {
-        A.istats[4 + kc] = rs.inner_it;
-        A.istats[8 + kc] = rs.rounds;
-        A.dstats[4 + kc] = sqrt(rs.res2);
-        A.dstats[8 + kc] = sqrt(rs.bn2);
-        if (!rs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
-      }
-    } else {
-      if (!cg_pressure<real, ND>(X, cs, o.p_rtol, o.atol, o.p_maxit, A.Pdiag, A.Pinv, A.Poff, A.b, s_mean, A.cx,
-                                 A.crb, A.cwb, A.csb, A.cp))
-        return;
-      if (threadIdx.x == 0 && g.rank == 0) {
-        A.istats[4 + kc] = cs.it;
-        A.dstats[4 + kc] = sqrt(cs.res2);
-        A.dstats[8 + kc] = sqrt(cs.tol2) / fmax(o.p_rtol, 1e-300);
-        if (!cs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
-      }
-    }
+    // refined against an FP64 residual when asked or when the CG stalls
+    if (!pressure_solve<real, ND>(X, cs, rs, o, A.Pdiag, A.Pinv, A.Poff, A.b, s_mean, A.cx, A.x64, A.rin, A.ce,
+                                  A.crb, A.cwb, A.csb, A.cp, A.istats, A.dstats, kc))
+      return;
     // C4: u = h - A^-1 grad x (Eq. velCorrDiscrete, R5); mean of x (R7)
     {
       Acc<real> a[1];

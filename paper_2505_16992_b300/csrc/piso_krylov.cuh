@@ -144,10 +144,99 @@ struct BiState {
 constexpr int CG_REPLACE = PISO_CG_REPLACE;
 
 struct CgState {
-  double gam, gam_old, delta, alpha, alpha_old, beta, tol2, res2;
+  double gam, delta, alpha, beta, tol2, res2;
+  double inv_gam;   // 1 / gamma of the last iteration
+  double kappa;     // 1 / (gamma alpha) of the last iteration
+  double best;      // smallest ||r||^2 that was a 2x (norm) improvement, and its iteration
+  // FP32 mode: the loop's scalar state as float pairs (gamma, 1 / alpha, best,
+  // tolerance and residual ||r||^2); res2 is converted back when the loop ends
+  f2 fgam, finv_alpha, fbest, ftol2, fres2;
   float alpha_f, beta_f;
-  int active, it, first, conv;
+  int active, it, first, conv, best_it, stalled;
 };
+
+// Thread 0, end of one CG iteration (FP64 mode): convergence, stall and
+// breakdown tests on ||r||^2, then cg_coeffs from gamma = (r, u), delta = (w, u).
+__device__ __forceinline__ void cg_iter_update(CgState& cs, double gam, double delta, double res2, int stall_window,
+                                               int32_t* status);
+
+// Thread 0, end of one CG iteration (FP32 mode), all in float-pair arithmetic
+// on the FP32 pipe.  Only ratio-form quantities are kept (gamma / gamma_old,
+// gamma / alpha_old, den / gamma), which stay inside the float exponent range
+// even when ||r||^2 itself is far below 1e-20 (small adjoint right-hand sides).
+__device__ __forceinline__ void cg_iter_update_f2(CgState& cs, f2 gam, f2 delta, f2 res2, int stall_window,
+                                                  int32_t* status) {
+  cs.it++;
+  cs.first = 0;
+  cs.fres2 = res2;
+  if (res2.hi != res2.hi) {
+    cs.active = 0;
+    atomicOr(status, PISO_ERR_NAN);
+    return;
+  }
+  if (!f2_gt(res2, cs.ftol2)) {
+    cs.active = 0;
+    cs.conv = 1;
+    return;
+  }
+  const bool improved = f2_gt(f2{0.25f * cs.fbest.hi, 0.25f * cs.fbest.lo}, res2);
+  if (stall_window > 0 && !improved && cs.it - cs.best_it >= stall_window) {
+    cs.active = 0;
+    cs.stalled = 1;
+    return;
+  }
+  if (improved) {
+    cs.fbest = res2;
+    cs.best_it = cs.it;
+  }
+  const f2 beta = f2_div(gam, cs.fgam);
+  const f2 den = f2_add(delta, f2_neg(f2_mul(beta, f2_mul(gam, cs.finv_alpha))));
+  if (den.hi == 0.f || gam.hi == 0.f || den.hi != den.hi) {
+    cs.active = 0;
+    atomicOr(status, den.hi != den.hi ? PISO_ERR_NAN : PISO_ERR_BREAKDOWN);
+    return;
+  }
+  const f2 alpha = f2_div(gam, den);
+  cs.finv_alpha = f2_div(den, gam);
+  cs.fgam = gam;
+  cs.alpha_f = alpha.hi;
+  cs.beta_f = beta.hi;
+}
+
+// FP32 pressure CG: a solve whose best residual norm has not halved for this
+// many iterations is stalled (finite-precision plateau near the attainable
+// accuracy of FP32 vectors) and is finished by FP64-residual refinement rounds.
+constexpr int CG_STALL_WINDOW = 200;
+
+// Thread 0: Chronopoulos–Gear coefficients from gamma = (r, u), delta = (w, u):
+// beta = gamma / gamma_old and alpha = gamma / (delta - beta gamma / alpha_old).
+// The denominator is formed as delta - gamma^2 kappa with kappa = 1 / (gamma_old
+// alpha_old) carried over from the previous iteration, so a single division
+// (gamma / den) lies on the critical path of the update that every thread of
+// the CTA waits for; 1 / gamma for the next kappa is independent of it.  (A
+// dependent FP64 division costs ~600 cycles on this GPU, an FP64 FMA ~64.)
+// first: the start of the recurrence (beta = 0, alpha = gamma / delta).
+// Returns false on breakdown (den or gamma zero) or NaN, with the status set.
+__device__ __forceinline__ bool cg_coeffs(CgState& cs, double gam, double delta, bool first, int32_t* status) {
+  const double beta = first ? 0.0 : gam * cs.inv_gam;
+  const double den = first ? delta : fma(-gam * gam, cs.kappa, delta);
+  if (den == 0.0 || gam == 0.0 || den != den) {
+    cs.active = 0;
+    atomicOr(status, den != den ? PISO_ERR_NAN : PISO_ERR_BREAKDOWN);
+    return false;
+  }
+  const double alpha = gam / den;
+  const double ig = 1.0 / gam;
+  cs.kappa = den * ig * ig;
+  cs.inv_gam = ig;
+  cs.gam = gam;
+  cs.delta = delta;
+  cs.alpha = alpha;
+  cs.beta = beta;
+  cs.alpha_f = (float)alpha;
+  cs.beta_f = (float)beta;
+  return true;
+}
 
 // A scalar in the storage precision: the float copy for FP32, the double for FP64.
 template <typename real>
@@ -406,7 +495,7 @@ template <typename real, int ND>
 __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, double atol, int maxit,
                             const real* Pdiag, const real* Pinv, const real* Poff, const real* b, double bmean,
                             real* x, real* const (&rb)[2], real* const (&wb)[2], real* const (&sb)[2],
-                            real* pdir) {
+                            real* pdir, int stall_window = 0) {
   const int32_t N = X.N;
   // I1: r0 = b' - A' x0 with b' = -(b - mean), A' = -P
   __shared__ double s_mb;
@@ -438,6 +527,14 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     const bool ok = reduce_sync<real, 2>(X.g, a, [&](const double* q) {
       cs.tol2 = fmax(rtol * rtol * q[0], atol * atol);
       cs.res2 = q[1];
+      cs.best = q[1];
+      if (sizeof(real) == 4) {
+        cs.ftol2 = f2_from_double(cs.tol2);
+        cs.fbest = f2_from_double(q[1]);
+        cs.fres2 = cs.fbest;
+      }
+      cs.best_it = 0;
+      cs.stalled = 0;
       cs.it = 0;
       cs.first = 1;
       cs.conv = !(cs.res2 > cs.tol2);
@@ -473,16 +570,9 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
       a[1].add_prod(w, uP);
     });
     const bool ok = reduce_sync<real, 2>(X.g, a, [&](const double* q) {
-      cs.gam = q[0];
-      cs.delta = q[1];
-      if (cs.delta == 0.0 || cs.delta != cs.delta) {
-        cs.active = 0;
-        atomicOr(X.g.status, cs.delta == 0.0 ? PISO_ERR_BREAKDOWN : PISO_ERR_NAN);
-      } else {
-        cs.alpha = cs.gam / cs.delta;
-        cs.beta = 0.0;
-        cs.alpha_f = (float)cs.alpha;
-        cs.beta_f = 0.f;
+      if (cg_coeffs(cs, q[0], q[1], true, X.g.status) && sizeof(real) == 4) {
+        cs.fgam = f2_from_double(q[0]);
+        cs.finv_alpha = f2_div(f2_from_double(q[1]), cs.fgam);
       }
     });
     if (!ok) return false;
@@ -535,33 +625,14 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
 #pragma unroll
       for (int j = 0; j < ND; j++) prefetch_l2(Poff + (size_t)j * N + i);
     });
-    const bool ok = reduce_sync<real, 3>(X.g, a, [&](const double* q) {
-      cs.it++;
-      cs.res2 = q[2];
-      cs.first = 0;
-      if (cs.res2 != cs.res2) {
-        cs.active = 0;
-        atomicOr(X.g.status, PISO_ERR_NAN);
-      } else if (!(cs.res2 > cs.tol2)) {
-        cs.active = 0;
-        cs.conv = 1;
-      } else {
-        cs.gam_old = cs.gam;
-        cs.alpha_old = cs.alpha;
-        cs.gam = q[0];
-        cs.delta = q[1];
-        cs.beta = cs.gam / cs.gam_old;
-        const double den = cs.delta - cs.beta * cs.gam / cs.alpha_old;
-        if (den == 0.0 || cs.gam_old == 0.0) {
-          cs.active = 0;
-          atomicOr(X.g.status, PISO_ERR_BREAKDOWN);
-        } else {
-          cs.alpha = cs.gam / den;
-          cs.alpha_f = (float)cs.alpha;
-          cs.beta_f = (float)cs.beta;
-        }
-      }
-    });
+    bool ok;
+    if constexpr (sizeof(real) == 4)
+      ok = reduce_sync<real, 3, true>(X.g, a, [&](const double* q) {
+        cg_iter_update_f2(cs, f2_unpack(q[0]), f2_unpack(q[1]), f2_unpack(q[2]), stall_window, X.g.status);
+      });
+    else
+      ok = reduce_sync<real, 3>(
+          X.g, a, [&](const double* q) { cg_iter_update(cs, q[0], q[1], q[2], stall_window, X.g.status); });
     if (!ok) return false;
     cur ^= 1;
     // residual replacement (Cools & Vanroose): every CG_REPLACE iterations the
@@ -610,27 +681,21 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
       });
       const bool ok2 = reduce_sync<real, 3>(X.g, a2, [&](const double* q) {
         cs.res2 = q[2];
+        if (sizeof(real) == 4) cs.fres2 = f2_from_double(q[2]);
         if (!(cs.res2 > cs.tol2)) {
           cs.active = 0;
           cs.conv = 1;
           return;
         }
-        cs.gam = q[0];
-        cs.delta = q[1];
-        cs.beta = cs.gam / cs.gam_old;
-        const double den = cs.delta - cs.beta * cs.gam / cs.alpha_old;
-        if (den == 0.0 || den != den) {
-          cs.active = 0;
-          atomicOr(X.g.status, den == 0.0 ? PISO_ERR_BREAKDOWN : PISO_ERR_NAN);
-        } else {
-          cs.alpha = cs.gam / den;
-          cs.alpha_f = (float)cs.alpha;
-          cs.beta_f = (float)cs.beta;
+        if (cg_coeffs(cs, q[0], q[1], false, X.g.status) && sizeof(real) == 4) {
+          cs.fgam = f2_from_double(q[0]);
+          cs.finv_alpha = f2_from_double(1.0 / cs.alpha);
         }
       });
       if (!ok2) return false;
     }
   }
+  if (sizeof(real) == 4 && threadIdx.x == 0) cs.res2 = f2_to_double(cs.fres2);
   return true;
 }
 
@@ -695,15 +760,93 @@ __device__ bool cg_pressure_refined(const Ctx<real, ND>& X, CgState& cs, RefStat
       if (!ok) return false;
     }
     if (rs.conv || rs.res2 != rs.res2 || round >= max_rounds || rs.inner_it >= maxit) return true;
-    // inner FP32 solve of A' e = r
+    // inner FP32 solve of A' e = r (a stalled inner solve just ends the round)
     if (!cg_pressure<real, ND>(X, cs, inner_rtol, 0.0, maxit - rs.inner_it, Pdiag, Pinv, Poff, rin, -rs.rmean, e,
-                               rb, wb, sb, pdir))
+                               rb, wb, sb, pdir, CG_STALL_WINDOW))
       return false;
     if (threadIdx.x == 0) rs.inner_it += cs.it;
     // x64 += e
     X.own([&](int32_t P) { x64[P] += (double)e[P]; });
     if (!plain_sync(X.g)) return false;
   }
+}
+
+__device__ __forceinline__ void cg_iter_update(CgState& cs, double gam, double delta, double res2, int stall_window,
+                                               int32_t* status) {
+  cs.it++;
+  cs.res2 = res2;
+  cs.first = 0;
+  if (res2 != res2) {
+    cs.active = 0;
+    atomicOr(status, PISO_ERR_NAN);
+  } else if (!(res2 > cs.tol2)) {
+    cs.active = 0;
+    cs.conv = 1;
+  } else if (stall_window > 0 && !(res2 < 0.25 * cs.best) && cs.it - cs.best_it >= stall_window) {
+    cs.active = 0;
+    cs.stalled = 1;
+  } else {
+    if (res2 < 0.25 * cs.best) {
+      cs.best = res2;
+      cs.best_it = cs.it;
+    }
+    cg_coeffs(cs, gam, delta, false, status);
+  }
+}
+
+// One corrector's pressure solve P x = b - mean (forward or adjoint), x holding
+// the initial guess: a CG to rtol, or in the FP32 mode with p_refine_rtol > 0 an
+// FP64-refined solve; an FP32 CG that stalls is finished by refinement rounds
+// to the same tolerance from where it stopped.  Thread 0 of group rank 0
+// records iterations, refinement rounds, residual and right-hand-side norms in
+// stats slot k and flags non-convergence.  Returns false if the group aborted.
+template <typename real, int ND>
+__device__ bool pressure_solve(const Ctx<real, ND>& X, CgState& cs, RefState& rs, const SolverOpts& o,
+                               const real* Pdiag, const real* Pinv, const real* Poff, const real* b, double bmean,
+                               real* x, double* x64, real* rin, real* ce, real* const (&rb)[2],
+                               real* const (&wb)[2], real* const (&sb)[2], real* pdir, int32_t* istats,
+                               double* dstats, int k) {
+  constexpr bool F32 = sizeof(real) == 4;
+  const Group& g = X.g;
+  if (F32 && o.p_refine_rtol > 0) {
+    if (!cg_pressure_refined<real, ND>(X, cs, rs, o.p_refine_rtol, o.p_inner_rtol, o.atol, o.p_maxit, 20, Pdiag,
+                                       Pinv, Poff, b, bmean, x, x64, rin, ce, rb, wb, sb, pdir))
+      return false;
+    if (threadIdx.x == 0 && g.rank == 0) {
+      istats[4 + k] = rs.inner_it;
+      istats[8 + k] = rs.rounds;
+      dstats[4 + k] = sqrt(rs.res2);
+      dstats[8 + k] = sqrt(rs.bn2);
+      if (!rs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
+    }
+    return true;
+  }
+  if (!cg_pressure<real, ND>(X, cs, o.p_rtol, o.atol, o.p_maxit, Pdiag, Pinv, Poff, b, bmean, x, rb, wb, sb, pdir,
+                             F32 ? CG_STALL_WINDOW : 0))
+    return false;
+  if (F32 && cs.stalled) {
+    const int plain_it = cs.it;
+    if (!cg_pressure_refined<real, ND>(X, cs, rs, o.p_rtol, o.p_inner_rtol, o.atol, o.p_maxit - plain_it, 20, Pdiag,
+                                       Pinv, Poff, b, bmean, x, x64, rin, ce, rb, wb, sb, pdir))
+      return false;
+    // the refined result lives in x64; x holds it rounded (written by the last
+    // residual pass of the refinement)
+    if (threadIdx.x == 0 && g.rank == 0) {
+      istats[4 + k] = plain_it + rs.inner_it;
+      istats[8 + k] = 1 + rs.rounds;
+      dstats[4 + k] = sqrt(rs.res2);
+      dstats[8 + k] = sqrt(rs.bn2);
+      if (!rs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
+    }
+    return true;
+  }
+  if (threadIdx.x == 0 && g.rank == 0) {
+    istats[4 + k] = cs.it;
+    dstats[4 + k] = sqrt(cs.res2);
+    dstats[8 + k] = sqrt(cs.tol2) / fmax(o.p_rtol, 1e-300);
+    if (!cs.conv) atomicOr(g.status, PISO_ERR_NOCONV_P);
+  }
+  return true;
 }
 
 }  // namespace piso
