@@ -295,6 +295,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--threads", type=int, default=0, help="CTA width; 0 = autotune")
     ap.add_argument("--refine", type=float, default=0.0, help="FP32: FP64-refined pressure tolerance")
+    ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "line"],
+                    help="pressure CG preconditioner (auto: the autotuner times both on anisotropic grids)")
     ap.add_argument("--compare", action="store_true",
                     help="also time FP64 and refined FP32 at matched pressure tolerances")
     ap.add_argument("--workload", default="channel3d",
@@ -328,8 +330,10 @@ def main():
     case = W.channel3d(*sizes[args.workload])
     prec = args.precision
     rtol = 1e-6 if prec == "fp32" else 1e-10
+    pc_code = {"auto": capi.PISO_PRECOND_AUTO, "jacobi": capi.PISO_PRECOND_JACOBI, "line": capi.PISO_PRECOND_LINE}
     opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
-                                block_threads=args.threads, p_refine_rtol=args.refine)
+                                block_threads=args.threads, p_refine_rtol=args.refine,
+                                p_precond=pc_code[args.precond])
     dom = Domain.from_case(case, prec, opts)
     d, N = case.ndim, case.ncells
     w = 4 if prec == "fp32" else 8
@@ -346,6 +350,8 @@ def main():
     else:
         shape = (args.threads, None, None)
     with_adj = args.mode == "fwdadj"
+    pc_used = {capi.PISO_PRECOND_JACOBI: "jacobi", capi.PISO_PRECOND_LINE: "y-line",
+               capi.PISO_PRECOND_AUTO: "auto"}[dom.get_options().p_precond]
 
     def one_step():
         dom.step(u, p, case.dt, case.nu, S, u_out=u_out, p_out=p_out, sync=False)
@@ -434,10 +440,10 @@ def main():
         adj_ms = [t - f for t, f in zip(step_ms, fwd_ms)]
         paths = {"adv+p": {"steps_per_s": value, "adj_ms": sum(adj_ms) / len(adj_ms)}}
         nvar = max(5, args.steps // 3)
+        tuned = dom.get_options()          # launch shape and pressure preconditioner as tuned
         for name, bits in (("adv", capi.PISO_GRAD_ADV), ("p", capi.PISO_GRAD_P), ("none", 0)):
-            dom.set_options(capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
-                                                 block_threads=shape[0], ctas=shape[1] or 0,
-                                                 p_refine_rtol=args.refine, grad_paths=bits))
+            tuned.grad_paths = bits
+            dom.set_options(tuned)
             for _ in range(3):
                 one_step()
             vst = dom.step_adjoint(gu, None)[4]
@@ -478,7 +484,8 @@ def main():
                        "cells": N, "precision": prec, "krylov_rtol": rtol,
                        "l2": "flushed between timed steps (256 MB write, untimed)",
                        "parallelism": "replicas" if world > 1 else "single",
-                       "launch": {"threads": shape[0], "ctas": shape[1], "autotuned": args.threads == 0}},
+                       "launch": {"threads": shape[0], "ctas": shape[1], "autotuned": args.threads == 0},
+                       "pressure_precond": pc_used},
             "iterations": {"adv": st["adv_iters"][:d], "p": st["p_iters"][:2],
                            "adj_adv": adj_st["adv_iters"][:d] if adj_st else None,
                            "adj_p": adj_st["p_iters"][:2] if adj_st else None},

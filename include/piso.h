@@ -90,7 +90,20 @@ typedef struct {
                             A path left out treats that solve's output (u*, or every corrector's
                             pressure) as a constant of the backward pass, so its transposed solve
                             is skipped; 0 keeps only the bypass paths.  The forward step ignores it. */
+  int32_t p_precond;     /* preconditioner of the pressure CG (the paper names none; App. A.5 uses a
+                            plain CG): PISO_PRECOND_AUTO (default) picks the y-line preconditioner
+                            when the grid is anisotropic in y (some cell with alpha_yy >= 4 alpha_kk,
+                            k != y, as on wall-refined channels) and Jacobi otherwise;
+                            PISO_PRECOND_JACOBI; PISO_PRECOND_LINE: the block diagonal of -P made of
+                            its y-lines inside each block, solved exactly (Thomas factors formed once
+                            per step; the CG iteration then takes two group barriers instead of one).
+                            Batches (piso_batch_*) always use Jacobi. */
 } piso_options;
+
+/* Values of piso_options.p_precond. */
+#define PISO_PRECOND_AUTO 0
+#define PISO_PRECOND_JACOBI 1
+#define PISO_PRECOND_LINE 2
 
 /* Bits of piso_options.grad_paths. */
 #define PISO_GRAD_ADV 1   /* paths through the advection (predictor) solve */
@@ -154,6 +167,9 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts);
 /* Replace the solver options of a finalized domain (launch shape included). */
 piso_status piso_set_options(piso_domain* d, const piso_options* opts);
 
+/* Copy the domain's current options to *opts (host), e.g. after piso_autotune. */
+piso_status piso_get_options(const piso_domain* d, piso_options* opts);
+
 int64_t piso_num_cells(const piso_domain* d);
 int32_t piso_num_boundary_faces(const piso_domain* d);
 
@@ -179,11 +195,13 @@ piso_status piso_step(piso_domain* d, const void* u_in, const void* p_in, void* 
  * choice): time one forward step of the given state (device u, p, S as for
  * piso_step; the inputs are not modified and the outflow boundary state is
  * restored) for each candidate shape - CTA width 512 or 768 threads, CTA count
- * one per SM or one cell per thread - and make the fastest the domain's shape.
- * Results are cached per process by (ndim, precision, cells, blocks,
- * correctors).  threads_out, ctas_out, ms_out (host, may be NULL) receive the
- * choice and its time (-1 when it came from the cache).  Synchronises the
- * stream. */
+ * one per SM or one cell per thread, and, when p_precond is PISO_PRECOND_AUTO
+ * on a y-anisotropic grid, both pressure preconditioners - and make the
+ * fastest the domain's shape (its options then name the chosen preconditioner
+ * explicitly; read them with piso_get_options).  Results are cached per
+ * process by (ndim, precision, cells, blocks, correctors, p_precond).
+ * threads_out, ctas_out, ms_out (host, may be NULL) receive the choice and its
+ * time (-1 when it came from the cache).  Synchronises the stream. */
 piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double dt, double nu, const void* S,
                           void* stream, int32_t* threads_out, int32_t* ctas_out, double* ms_out);
 

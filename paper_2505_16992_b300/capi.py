@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(HERE, "libpiso.so")
 
 PISO_FP64, PISO_FP32 = 0, 1
 PISO_GRAD_ADV, PISO_GRAD_P = 1, 2          # piso_options.grad_paths bits (Sec. 2.4 gradient paths)
+PISO_PRECOND_AUTO, PISO_PRECOND_JACOBI, PISO_PRECOND_LINE = 0, 1, 2   # piso_options.p_precond
 STATUS = {0: "PISO_OK", 1: "PISO_EINVAL", 2: "PISO_ECUDA", 3: "PISO_ENOCONV", 4: "PISO_EBREAKDOWN",
           5: "PISO_ENAN", 6: "PISO_ETIMEOUT", 7: "PISO_ESTATE", 8: "PISO_ENOMEM"}
 
@@ -21,7 +22,7 @@ class Options(C.Structure):
                 ("p_rtol", C.c_double), ("atol", C.c_double), ("adv_maxit", C.c_int32),
                 ("p_maxit", C.c_int32), ("block_threads", C.c_int32), ("ctas", C.c_int32),
                 ("timeout_s", C.c_double), ("fault_withhold_cta", C.c_int32), ("p_refine_rtol", C.c_double),
-                ("p_inner_rtol", C.c_double), ("grad_paths", C.c_int32)]
+                ("p_inner_rtol", C.c_double), ("grad_paths", C.c_int32), ("p_precond", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -54,6 +55,7 @@ _SIGS = {
     "piso_set_advective_outflow": (C.c_int, [_P, C.c_int32, C.c_int32, _D, _D]),
     "piso_finalize": (C.c_int, [_P, C.POINTER(Options)]),
     "piso_set_options": (C.c_int, [_P, C.POINTER(Options)]),
+    "piso_get_options": (C.c_int, [_P, C.POINTER(Options)]),
     "piso_num_cells": (C.c_int64, [_P]),
     "piso_num_boundary_faces": (C.c_int32, [_P]),
     "piso_tape_bytes": (C.c_size_t, [_P]),

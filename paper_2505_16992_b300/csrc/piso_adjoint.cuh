@@ -57,6 +57,10 @@ struct AdjCall {
   double* x64;
   real* rin;
   real* ce;
+  real* lfa;                 // y-line preconditioner factors (when p_line)
+  real* lfm;
+  real* lfc;
+  int32_t p_line;
   uint32_t* bar;
   double* partials;
   int32_t* status;
@@ -82,7 +86,10 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   const int32_t N = D.N;
   const int32_t lo = (int32_t)(((int64_t)N * g.rank) / g.ncta);
   const int32_t hi = (int32_t)(((int64_t)N * (g.rank + 1)) / g.ncta);
-  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap)};
+  const bool lines = A.p_line && o.line_cap > 0;
+  LinePre<real> LP{};
+  if (lines) LP = line_setup<real, ND>(D, g, o, A.lfa, A.lfm, A.lfc);
+  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap), lines ? &LP : nullptr};
   const real* J = reinterpret_cast<const real*>(D.J);
   const real* T = reinterpret_cast<const real*>(D.T);
   const real* AL = reinterpret_cast<const real*>(D.alpha);
@@ -170,6 +177,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
     // R1: gx = -G^T W (+ dL/dp^{n+1} after the last corrector); its mean.
     // Without the pressure path the pressure is a constant: no gx, no solve.
     if (path_p) {
+      if (k == K - 1 && X.lp) line_factor<real, ND>(D, *X.lp, N, A.Pdiag, A.Poff);   // P rebuilt in R0
       Acc<real> a[1];
       a[0].zero();
       X.cells([&](const Cell& c) {

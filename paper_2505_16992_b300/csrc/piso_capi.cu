@@ -88,6 +88,8 @@ struct piso_domain {
   int threads = 512, ncta = 1;
   int sms = 148;
   DomStatic h_static;
+  double aniso = 1.0;          // max over cells of alpha_yy / alpha_kk (k != y): y-anisotropy of the grid
+  int p_line = 0;              // the pressure CG uses the y-line preconditioner
   bool pending = false;
   cudaStream_t pending_stream = nullptr;
   int pending_kind = 0;        // 1 forward, 2 adjoint
@@ -204,6 +206,7 @@ void put(std::vector<char>& buf, size_t i, double v) {
 enum WsIdx {
   W_U, W_RHS0, W_R, W_RHAT, W_P0, W_P1, W_V0, W_V1, W_T, W_POFF, W_PDIAG, W_FH, W_B, W_CX,
   W_CRB0, W_CRB1, W_CWB0, W_CWB1, W_CSB0, W_CSB1, W_CP, W_PINV, W_INVA, W_AW, W_X64, W_RIN, W_CE,
+  W_LFA, W_LFM, W_LFC,
   // adjoint scratch
   A_GA, A_GCOFF, A_GRHS0, A_GW, A_W, A_GG, A_GU, A_GX, A_Z, A_DU,
   W_COUNT
@@ -214,6 +217,7 @@ int ws_units(int k, int nd) {
   switch (k) {
     case W_PDIAG: case W_B: case W_CX: case W_CRB0: case W_CRB1: case W_CWB0: case W_CWB1: case W_CSB0:
     case W_CSB1: case W_CP: case A_GA: case A_GX: case W_PINV: case W_INVA: case W_RIN: case W_CE:
+    case W_LFA: case W_LFM: case W_LFC:
       return 1;
     case W_X64:
       return 2;     // N doubles (two float units; the FP64 mode over-allocates)
@@ -306,6 +310,10 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
   c.x64 = (double*)d->ws[W_X64];
   c.rin = (real*)d->ws[W_RIN];
   c.ce = (real*)d->ws[W_CE];
+  c.lfa = (real*)d->ws[W_LFA];
+  c.lfm = (real*)d->ws[W_LFM];
+  c.lfc = (real*)d->ws[W_LFC];
+  c.p_line = d->p_line;
   c.bar = d->bar;
   c.partials = d->partials;
   c.status = d->status;
@@ -326,6 +334,7 @@ SolverOpts solver_opts(const piso_options& o) {
   s.atol = o.atol;
   s.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
   s.nbt_cap = 0;
+  s.line_cap = 0;
   s.withhold_cta = o.fault_withhold_cta;
   s.p_refine_rtol = o.p_refine_rtol;
   s.p_inner_rtol = o.p_inner_rtol;
@@ -346,6 +355,36 @@ size_t nbt_bytes(int ndim, int64_t N, int ncta, int32_t* cap) {
   }
   *cap = (int32_t)per;
   return b;
+}
+
+// Dynamic shared memory of a single-domain launch: the neighbour table and,
+// with the y-line preconditioner, its staging area (LINE_ARRAYS arrays of line_cap reals
+// and 3 x LINE_LBMAX ints), together within NBT_MAX_BYTES (the size the
+// occupancy of the kernels was computed for).  The table is dropped (cells are
+// then located arithmetically) when it would leave the staging area less than
+// two lines.  Sets o->nbt_cap and o->line_cap; returns the bytes.
+size_t launch_smem(const piso_domain* d, int ncta, SolverOpts* o) {
+  const int nd = d->ndim;
+  const size_t e = d->elem;
+  const size_t ints = 3 * (size_t)LINE_LBMAX * sizeof(int32_t);
+  const int lmax = std::max(d->h_static.lmax, 1);
+  const size_t line_min = d->p_line ? LINE_ARRAYS * e * 2 * (size_t)lmax + ints : 0;
+  o->nbt_cap = 0;
+  o->line_cap = 0;
+  if (line_min > NBT_MAX_BYTES) return nbt_bytes(nd, d->N, ncta, &o->nbt_cap);   // lines cannot be staged
+  const int64_t per = ((int64_t)d->N + ncta - 1) / ncta;
+  size_t nbt = (size_t)per * 2 * nd * sizeof(int32_t);
+  if (nbt + 16 + line_min <= NBT_MAX_BYTES) o->nbt_cap = (int32_t)per;
+  else nbt = 0;
+  nbt = (nbt + 15) & ~size_t(15);
+  if (!d->p_line) return nbt;
+  // staging: as much as fits, but no more than this CTA's lines plus one
+  const int64_t lines_per = ((int64_t)d->h_static.nlines + ncta - 1) / ncta;
+  size_t cap = (NBT_MAX_BYTES - nbt - ints) / (LINE_ARRAYS * e);
+  cap = std::min<size_t>(cap, (size_t)(std::min<int64_t>(lines_per, LINE_LBMAX) + 1) * lmax);
+  cap = std::max<size_t>(cap, 2 * (size_t)lmax);
+  o->line_cap = (int32_t)cap;
+  return nbt + LINE_ARRAYS * e * cap + ints;
 }
 
 cudaError_t coop_launch(const void* kernel, int grid, int threads, void** args, cudaStream_t st, size_t smem = 0) {
@@ -470,7 +509,7 @@ piso_status launch_fwd(piso_domain* d, const void* u_in, const void* p_in, void*
   L.o = solver_opts(d->opts);
   L.cta_first = nullptr;
   L.calls = nullptr;
-  const size_t smem = nbt_bytes(d->ndim, d->N, d->ncta, &L.o.nbt_cap);
+  const size_t smem = launch_smem(d, d->ncta, &L.o);
   fill_fwd_call<real>(d, L.call0, u_in, p_in, u_out, p_out, dt, nu, S, tape);
   CUDA_TRY(d, cudaMemsetAsync(d->bar, 0, 64, st));
   CUDA_TRY(d, cudaMemsetAsync(d->status, 0, 64, st));
@@ -505,6 +544,7 @@ void piso_default_options(piso_options* o) {
   o->p_refine_rtol = 0.0;
   o->p_inner_rtol = 1e-4;
   o->grad_paths = PISO_GRAD_ADV | PISO_GRAD_P;
+  o->p_precond = PISO_PRECOND_AUTO;
 }
 
 piso_status piso_domain_create(int32_t ndim, int32_t prec, piso_domain** out) {
@@ -602,7 +642,15 @@ static piso_status validate_options(piso_domain* d, const piso_options* o) {
   if (!(o->timeout_s > 0)) return fail(d, PISO_EINVAL, "timeout_s must be positive");
   if (o->adv_rtol < 0 || o->p_rtol < 0 || o->atol < 0) return fail(d, PISO_EINVAL, "negative tolerance");
   if (o->grad_paths & ~(PISO_GRAD_ADV | PISO_GRAD_P)) return fail(d, PISO_EINVAL, "grad_paths: unknown bits");
+  if (o->p_precond < PISO_PRECOND_AUTO || o->p_precond > PISO_PRECOND_LINE)
+    return fail(d, PISO_EINVAL, "p_precond must be PISO_PRECOND_AUTO, _JACOBI or _LINE");
   return PISO_OK;
+}
+
+// Pressure preconditioner of a finalized domain from its options and grid.
+static void resolve_precond(piso_domain* d) {
+  const int p = d->opts.p_precond;
+  d->p_line = (p == PISO_PRECOND_LINE || (p == PISO_PRECOND_AUTO && d->aniso >= 4.0)) ? 1 : 0;
 }
 
 piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
@@ -640,6 +688,9 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
     bi.off = off[b];
     bi.dnx = make_fast_div(bi.nx);
     bi.dny = make_fast_div(bi.ny);
+    bi.line0 = S.nlines;                 // y-lines: one per (x, z) column of the block
+    S.nlines += bi.nx * bi.nz;
+    S.lmax = std::max(S.lmax, bi.ny);
     for (int s = 0; s < 6; s++) {
       bi.link[s] = -1;
       bi.bfo[s] = 0;
@@ -681,6 +732,8 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
               for (int k = 0; k < nd; k++) s += Ti[j][k] * Ti[l][k];
               G[j][l] = Jv * s;
             }
+          for (int k = 0; k < nd; k++)
+            if (k != 1 && G[k][k] > 0) d->aniso = std::max(d->aniso, G[1][1] / G[k][k]);
           for (int j = 0; j < nd; j++)
             for (int l = 0; l < nd; l++)
               if (j != l && std::fabs(G[j][l]) > 1e-9 * std::max(std::fabs(G[j][j]), std::fabs(G[l][l])))
@@ -797,6 +850,7 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
   CUDA_TRY(d, cudaMallocHost((void**)&d->h_istats, 64));
   CUDA_TRY(d, cudaMallocHost((void**)&d->h_dstats, 128));
   CUDA_TRY(d, cudaMallocHost((void**)&d->h_dnu, 64));
+  resolve_precond(d);
   piso_status s = choose_shape(d);
   if (s) return s;
   d->finalized = true;
@@ -808,7 +862,16 @@ piso_status piso_set_options(piso_domain* d, const piso_options* opts) {
   piso_status s = validate_options(d, opts);
   if (s) return s;
   d->opts = *opts;
-  if (d->finalized) return choose_shape(d);
+  if (d->finalized) {
+    resolve_precond(d);
+    return choose_shape(d);
+  }
+  return PISO_OK;
+}
+
+piso_status piso_get_options(const piso_domain* d, piso_options* opts) {
+  if (!d || !opts) return fail(const_cast<piso_domain*>(d), PISO_EINVAL, "NULL argument");
+  *opts = d->opts;
   return PISO_OK;
 }
 
@@ -844,8 +907,8 @@ piso_status piso_step(piso_domain* d, const void* u_in, const void* p_in, void* 
 // each candidate (CTA width 512 or 768 threads; CTA count = one per SM, or
 // just enough CTAs for one cell per thread) and keeps the fastest.  Results
 // are cached per process by (ndim, precision, cells, blocks, correctors).
-static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>>& tune_cache() {
-  static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> c;
+static std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int>>& tune_cache() {
+  static std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int>> c;
   return c;
 }
 
@@ -854,7 +917,8 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
   if (!d || !u || !p) return fail(d, PISO_EINVAL, "NULL argument");
   if (!d->finalized) return fail(d, PISO_ESTATE, "autotune before finalize");
   cudaStream_t st = (cudaStream_t)stream;
-  const auto key = std::make_tuple(d->ndim, d->prec, (int)d->N, (int)d->blocks.size(), d->opts.n_correctors);
+  const auto key = std::make_tuple(d->ndim, d->prec, (int)d->N, (int)d->blocks.size(),
+                                   d->opts.n_correctors * 4 + d->opts.p_precond);
   auto it = tune_cache().find(key);
   double best_ms = -1.0;
   if (it == tune_cache().end()) {
@@ -869,23 +933,30 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const piso_options saved = d->opts;
-    const int saved_threads = d->threads, saved_ncta = d->ncta;
-    std::vector<std::pair<int, int>> cand;
-    for (int w : {512, WIDE}) {
-      int sms = 148;
-      const int cap = std::min(max_coresident(fwd_kernel_ptr(d->prec, d->ndim, w), w, &sms),
-                               max_coresident(adj_kernel_ptr(d->prec, d->ndim, w), w, nullptr));
-      const int one_per_thread = (int)std::min<int64_t>(cap, (d->N + w - 1) / w);
-      for (int nc : {std::min(cap, sms), one_per_thread})
-        if (nc >= 1 && std::find(cand.begin(), cand.end(), std::make_pair(w, nc)) == cand.end())
-          cand.push_back({w, nc});
-    }
-    std::pair<int, int> best = {saved_threads, saved_ncta};
+    const int saved_threads = d->threads, saved_ncta = d->ncta, saved_line = d->p_line;
+    // with PISO_PRECOND_AUTO on a y-anisotropic grid both pressure
+    // preconditioners are timed (the line form saves iterations, but costs a
+    // second barrier per iteration and a serial line solve per CTA)
+    std::vector<int> pls = {d->p_line};
+    if (d->opts.p_precond == PISO_PRECOND_AUTO && d->p_line) pls.push_back(0);
+    std::vector<std::tuple<int, int, int>> cand;
+    for (int pl : pls)
+      for (int w : {512, WIDE}) {
+        int sms = 148;
+        const int cap = std::min(max_coresident(fwd_kernel_ptr(d->prec, d->ndim, w), w, &sms),
+                                 max_coresident(adj_kernel_ptr(d->prec, d->ndim, w), w, nullptr));
+        const int one_per_thread = (int)std::min<int64_t>(cap, (d->N + w - 1) / w);
+        for (int nc : {std::min(cap, sms), one_per_thread})
+          if (nc >= 1 && std::find(cand.begin(), cand.end(), std::make_tuple(w, nc, pl)) == cand.end())
+            cand.push_back({w, nc, pl});
+      }
+    std::tuple<int, int, int> best = {saved_threads, saved_ncta, saved_line};
     piso_status s = PISO_OK;
     CUDA_TRY(d, cudaMemcpyAsync(bk, d->bval, bb, cudaMemcpyDeviceToDevice, st));
     for (auto& c : cand) {
-      d->threads = c.first;
-      d->ncta = c.second;
+      d->threads = std::get<0>(c);
+      d->ncta = std::get<1>(c);
+      d->p_line = std::get<2>(c);
       double t = 1e300;
       for (int rep = 0; rep < 3 && s == PISO_OK; rep++) {
         cudaEventRecord(e0, st);
@@ -911,13 +982,16 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
     d->opts = saved;
     d->threads = saved_threads;
     d->ncta = saved_ncta;
+    d->p_line = saved_line;
     if (s != PISO_OK) return fail(d, s, "autotune trial step failed");
     it = tune_cache().emplace(key, best).first;
   }
-  d->threads = it->second.first;
-  d->ncta = it->second.second;
+  d->threads = std::get<0>(it->second);
+  d->ncta = std::get<1>(it->second);
+  d->p_line = std::get<2>(it->second);
   d->opts.block_threads = d->threads;
   d->opts.ctas = d->ncta;
+  d->opts.p_precond = d->p_line ? PISO_PRECOND_LINE : PISO_PRECOND_JACOBI;
   if (threads_out) *threads_out = d->threads;
   if (ctas_out) *ctas_out = d->ncta;
   if (ms_out) *ms_out = best_ms;
@@ -1061,7 +1135,7 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
     memset(&L, 0, sizeof L);
     L.ngroups = 1;
     L.o = solver_opts(d->opts);
-    const size_t smem = nbt_bytes(d->ndim, d->N, d->ncta, &L.o.nbt_cap);
+    const size_t smem = launch_smem(d, d->ncta, &L.o);
     FwdCall<real>& c = L.call0;
     fill_fwd_call<real>(d, c, u_in, p_in, u_out, p_out, dt, nu, S, base + SL.tape);
     auto W = [&](int k) { return (real*)(base + SL.ws[k]); };
@@ -1092,6 +1166,9 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
     c.x64 = (double*)(base + SL.ws[W_X64]);
     c.rin = W(W_RIN);
     c.ce = W(W_CE);
+    c.lfa = W(W_LFA);
+    c.lfm = W(W_LFM);
+    c.lfc = W(W_LFC);
     c.bar = (uint32_t*)(base + SL.bar);
     c.status = (int32_t*)(base + SL.status);
     c.istats = (int32_t*)(base + SL.istats);

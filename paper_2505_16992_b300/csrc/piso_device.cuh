@@ -58,11 +58,13 @@ struct BlockInfo {
   int32_t link[6];           // >= 0: block joined at this side (its opposite side); -1: boundary faces
   int32_t bfo[6];            // first boundary face of this side (when link < 0)
   FastDiv dnx, dny;
+  int32_t line0;             // first y-line of this block in the domain's line numbering
 };
 
 struct DomStatic {
   int32_t ndim, nblocks, N, nbf;
   int32_t n_out;             // number of advective-outflow faces
+  int32_t nlines, lmax;      // y-lines (one per block column) and the longest line's length
   BlockInfo blk[MAXB];
   // per-cell metrics, storage precision (void*: float or double)
   const void* J;             // [N]
@@ -139,6 +141,43 @@ __device__ __forceinline__ Cell locate(const DomStatic& D, int32_t i) {
 }
 
 __device__ __forceinline__ int32_t safe(int32_t nb, int32_t self) { return nb >= 0 ? nb : self; }
+
+// Lines of the y-line preconditioner: the cells of one block that share x (and
+// z), in order of y.  Line l of block b (l' = l - line0) starts at x = l' mod nx,
+// z = l' / nx, y = 0, with stride nx and ny cells; consecutive lines are
+// x-neighbours, so a warp that takes one cell of each of 32 consecutive lines
+// at the same y reads contiguous memory.
+struct LineDesc {
+  int32_t start, stride, len;
+};
+
+__device__ __forceinline__ LineDesc line_desc(const DomStatic& D, int32_t l) {
+  int b = 0;
+  while (b + 1 < D.nblocks && l >= D.blk[b + 1].line0) b++;
+  const BlockInfo& B = D.blk[b];
+  const uint32_t lp = (uint32_t)(l - B.line0);
+  const uint32_t z = fast_div(lp, B.dnx);
+  const uint32_t x = lp - z * (uint32_t)B.nx;
+  return LineDesc{B.off + (int32_t)x + B.nx * B.ny * (int32_t)z, B.nx, B.ny};
+}
+
+// Per-CTA state of the y-line preconditioner: the Thomas factors of the line
+// blocks of -P (device arrays), this CTA's lines [L0, L1), and its shared
+// staging area (lb lines per batch).
+template <typename real>
+struct LinePre {
+  real* fa;          // [N] forward multiplier  -e_{y-1} m_y
+  real* fm;          // [N] pivot reciprocal     m_y
+  real* fc;          // [N] backward multiplier -c'_y
+  real* sA;          // shared staging arrays of line_cap reals each
+  real* sB;
+  real* sC;
+  real* sR;
+  int32_t* sStart;   // shared line descriptors of the current batch
+  int32_t* sStride;
+  int32_t* sLen;
+  int32_t L0, L1, lb;
+};
 
 // ---------------------------------------------------------------------------
 // accumulators: FP64 mode sums in double; the FP32 mode sums in a float pair

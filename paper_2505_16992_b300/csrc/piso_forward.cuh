@@ -54,6 +54,10 @@ struct FwdCall {
   double* x64;               // [N]    refined pressure (FP32 mode)
   real* rin;                 // [N]    refinement residual
   real* ce;                  // [N]    refinement correction
+  real* lfa;                 // [N]    y-line preconditioner factors (when p_line)
+  real* lfm;
+  real* lfc;
+  int32_t p_line;            // 1: the pressure CG uses the y-line preconditioner
   // group control
   uint32_t* bar;
   double* partials;
@@ -111,7 +115,10 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   const int32_t N = D.N;
   const int32_t lo = (int32_t)(((int64_t)N * g.rank) / g.ncta);
   const int32_t hi = (int32_t)(((int64_t)N * (g.rank + 1)) / g.ncta);
-  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap)};
+  const bool lines = A.p_line && o.line_cap > 0;
+  LinePre<real> LP{};
+  if (lines) LP = line_setup<real, ND>(D, g, o, A.lfa, A.lfm, A.lfc);
+  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap), lines ? &LP : nullptr};
   const real* J = reinterpret_cast<const real*>(D.J);
   const real* T = reinterpret_cast<const real*>(D.T);
   const real* AL = reinterpret_cast<const real*>(D.alpha);
@@ -342,7 +349,9 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       }
     });
     if (!plain_sync(g)) return;
-    // C2: b = sum_f N_f mean(J T_j . h) + boundary flux (R6); mean of b (R7)
+    // C2: b = sum_f N_f mean(J T_j . h) + boundary flux (R6); mean of b (R7).
+    // Once per step (P is complete after the barrier) the line factors.
+    if (kc == 0 && X.lp) line_factor<real, ND>(D, *X.lp, N, A.Pdiag, A.Poff);
     {
       Acc<real> a[1];
       a[0].zero();

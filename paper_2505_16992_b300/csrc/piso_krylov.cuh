@@ -13,6 +13,7 @@ struct SolverOpts {
   double adv_rtol, p_rtol, atol;
   uint64_t timeout_ns;
   int32_t nbt_cap;           // cells per CTA the shared neighbour table can hold
+  int32_t line_cap;          // reals per staging array of the y-line preconditioner (0: not available)
   int32_t withhold_cta;      // fault injection: group rank that skips its first barrier arrival (-1 off)
   double p_refine_rtol;      // FP32 mode: outer FP64 residual tolerance of the pressure solve (0 = off)
   double p_inner_rtol;       // FP32 mode: inner CG tolerance per refinement round
@@ -35,58 +36,66 @@ __device__ __forceinline__ const int32_t* build_nbt(const DomStatic& D, int32_t 
   return s_nbt;
 }
 
-// Execution context of one CTA inside its group.
+// Execution context of one CTA inside its group.  Which cells a thread visits:
+//  - with a neighbour table (the CTA's range fits in shared memory): the CTA's
+//    contiguous range [lo, hi), thread t taking lo + t, lo + t + T, ...;
+//  - without one (large domains): the group's cells interleaved in passes of
+//    ncta * T, so CTA r takes [(j ncta + r) T, (j ncta + r + 1) T) on pass j.
+//    All CTAs then sweep the same window of the domain at the same time, and
+//    the +-y and +-z neighbours a pass reads (one row / one plane away) were
+//    read by another CTA of the same or the previous pass: they are L2 hits,
+//    whereas contiguous ranges larger than a plane read every z neighbour
+//    stream a second time from DRAM.
+// Each thread's cell set and visiting order are fixed, so reductions stay
+// deterministic, and every loop of a phase (cells, cells_pf, own) uses the
+// same partition.
 template <typename real, int ND>
 struct Ctx {
   const DomStatic& D;   // shared-memory copy
   Group& g;
   int32_t lo, hi, N;
   const int32_t* nbt;   // [2*ND][hi-lo] neighbour table in shared memory, or nullptr
-  // cells with an L2 prefetch of the cell this thread visits next: when a CTA
-  // owns more cells than threads, the next cell's streams are requested a full
-  // cell-visit ahead (memory-level parallelism for the bandwidth-bound sizes)
+  const LinePre<real>* lp;   // y-line preconditioner of the pressure CG, or nullptr (Jacobi)
+  // first cell, stride and end of this thread's walk
+  __device__ __forceinline__ int32_t first() const {
+    return nbt ? lo + (int32_t)threadIdx.x : g.rank * (int32_t)blockDim.x + (int32_t)threadIdx.x;
+  }
+  __device__ __forceinline__ int32_t stride() const {
+    return nbt ? (int32_t)blockDim.x : g.ncta * (int32_t)blockDim.x;
+  }
+  __device__ __forceinline__ int32_t end() const { return nbt ? hi : N; }
+  __device__ __forceinline__ Cell cell(int32_t i) const {
+    Cell c;
+    if (nbt) {
+      const int32_t n = hi - lo, l = i - lo;
+      c.i = i;
+#pragma unroll
+      for (int s = 0; s < 2 * ND; s++) c.nb[s] = nbt[s * n + l];
+    } else {
+      c = locate<ND>(D, i);
+    }
+    return c;
+  }
+  // cells with an L2 prefetch of the cell this thread visits next: when a
+  // thread visits more than one cell, the next cell's streams are requested a
+  // full visit ahead (memory-level parallelism for the bandwidth-bound sizes)
   template <typename F, typename PF>
   __device__ __forceinline__ void cells_pf(F&& f, PF&& pf) const {
-    const int32_t T = blockDim.x;
-    if (hi - lo <= T) {
-      cells(f);
-      return;
-    }
-    for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += T) {
-      if (i + T < hi) pf(i + T);
-      Cell c;
-      if (nbt) {
-        const int32_t n = hi - lo, l = i - lo;
-        c.i = i;
-#pragma unroll
-        for (int s = 0; s < 2 * ND; s++) c.nb[s] = nbt[s * n + l];
-      } else {
-        c = locate<ND>(D, i);
-      }
-      f(c);
+    const int32_t e = end(), st = stride();
+    for (int32_t i = first(); i < e; i += st) {
+      if (i + st < e) pf(i + st);
+      f(cell(i));
     }
   }
   template <typename F>
   __device__ __forceinline__ void cells(F&& f) const {
-    if (nbt) {
-      const int32_t n = hi - lo;
-      for (int32_t l = (int32_t)threadIdx.x; l < n; l += blockDim.x) {
-        Cell c;
-        c.i = lo + l;
-#pragma unroll
-        for (int s = 0; s < 2 * ND; s++) c.nb[s] = nbt[s * n + l];
-        f(c);
-      }
-    } else {
-      for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += blockDim.x) {
-        const Cell c = locate<ND>(D, i);
-        f(c);
-      }
-    }
+    const int32_t e = end(), st = stride();
+    for (int32_t i = first(); i < e; i += st) f(cell(i));
   }
   template <typename F>
   __device__ __forceinline__ void own(F&& f) const {
-    for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += blockDim.x) f(i);
+    const int32_t e = end(), st = stride();
+    for (int32_t i = first(); i < e; i += st) f(i);
   }
 };
 
@@ -312,24 +321,35 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       real* pnew = pv[cur];
       real* vnew = vv[cur];
       X.cells_pf([&](const Cell& c) {
+        // every load of the cell (all components) precedes its stores, so the
+        // compiler can issue them together (it must assume the stores alias)
         real diag, cf[2 * ND];
         c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+        real pP[ND], v[ND], rh[ND];
 #pragma unroll
         for (int k = 0; k < ND; k++) {
+          pP[k] = v[k] = rh[k] = real(0);
           if (!act[k]) continue;
           const size_t o_ = (size_t)k * N;
           auto pn = [&](int32_t Q) -> real {
             const real rq = r[o_ + Q];
             return first ? rq : rq + beta[k] * (pold[o_ + Q] - om[k] * vold[o_ + Q]);
           };
-          const real pP = pn(c.i);
-          real v = diag * pP;
+          pP[k] = pn(c.i);
+          real vv_ = diag * pP[k];
 #pragma unroll
           for (int s = 0; s < 2 * ND; s++)
-            if (c.nb[s] >= 0) v += cf[s] * pn(c.nb[s]);
-          pnew[o_ + c.i] = pP;
-          vnew[o_ + c.i] = v;
-          a[k].add_prod(rhat[o_ + c.i], v);
+            if (c.nb[s] >= 0) vv_ += cf[s] * pn(c.nb[s]);
+          v[k] = vv_;
+          rh[k] = rhat[o_ + c.i];
+        }
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+          if (!act[k]) continue;
+          const size_t o_ = (size_t)k * N;
+          pnew[o_ + c.i] = pP[k];
+          vnew[o_ + c.i] = v[k];
+          a[k].add_prod(rh[k], v[k]);
         }
       }, [&](int32_t i) {
         prefetch_l2(Cdiag + i);
@@ -375,20 +395,27 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       X.cells_pf([&](const Cell& c) {
         real diag, cf[2 * ND];
         c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+        real sP[ND], tt[ND];
 #pragma unroll
         for (int k = 0; k < ND; k++) {
+          sP[k] = tt[k] = real(0);
           if (!act[k]) continue;
           const size_t o_ = (size_t)k * N;
           auto sv = [&](int32_t Q) -> real { return r[o_ + Q] - al[k] * vnew[o_ + Q]; };
-          const real sP = sv(c.i);
-          real tt = diag * sP;
+          sP[k] = sv(c.i);
+          real t_ = diag * sP[k];
 #pragma unroll
           for (int s = 0; s < 2 * ND; s++)
-            if (c.nb[s] >= 0) tt += cf[s] * sv(c.nb[s]);
-          t[o_ + c.i] = tt;
-          a[k].add_prod(tt, sP);
-          a[ND + k].add_prod(tt, tt);
-          a[2 * ND + k].add_prod(sP, sP);
+            if (c.nb[s] >= 0) t_ += cf[s] * sv(c.nb[s]);
+          tt[k] = t_;
+        }
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+          if (!act[k]) continue;
+          t[(size_t)k * N + c.i] = tt[k];
+          a[k].add_prod(tt[k], sP[k]);
+          a[ND + k].add_prod(tt[k], tt[k]);
+          a[2 * ND + k].add_prod(sP[k], sP[k]);
         }
       }, [&](int32_t i) {
         prefetch_l2(Cdiag + i);
@@ -434,20 +461,30 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       const real* pnew = pv[cur];
       const real* vnew = vv[cur];
       X.own([&](int32_t P) {
+        real xn[ND], rr[ND], rh[ND];
 #pragma unroll
         for (int k = 0; k < ND; k++) {
+          xn[k] = rr[k] = rh[k] = real(0);
           if (!act[k]) continue;
           const size_t o_ = (size_t)k * N;
           const real sP = r[o_ + P] - al[k] * vnew[o_ + P];
           if (sc[k]) {
-            x[o_ + P] += al[k] * pnew[o_ + P];
+            xn[k] = x[o_ + P] + al[k] * pnew[o_ + P];
             continue;
           }
-          x[o_ + P] += al[k] * pnew[o_ + P] + om[k] * sP;
-          const real rr = sP - om[k] * t[o_ + P];
-          r[o_ + P] = rr;
-          a[k].add_prod(rhat[o_ + P], rr);
-          a[ND + k].add_prod(rr, rr);
+          xn[k] = x[o_ + P] + (al[k] * pnew[o_ + P] + om[k] * sP);
+          rr[k] = sP - om[k] * t[o_ + P];
+          rh[k] = rhat[o_ + P];
+        }
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+          if (!act[k]) continue;
+          const size_t o_ = (size_t)k * N;
+          x[o_ + P] = xn[k];
+          if (sc[k]) continue;
+          r[o_ + P] = rr[k];
+          a[k].add_prod(rh[k], rr[k]);
+          a[ND + k].add_prod(rr[k], rr[k]);
         }
       });
       const bool ok = reduce_sync<real, 2 * ND>(X.g, a, [&](const double* q) {
@@ -486,6 +523,10 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
   return true;
 }
 
+}  // namespace piso
+#include "piso_lines.cuh"
+namespace piso {
+
 // Jacobi-preconditioned CG in the single-reduction form of Chronopoulos and
 // Gear (1989) for  (-P) x = -(b - bmean)  (R7: the pressure system is singular
 // and b is projected to zero mean).  D = -diag(P) is the preconditioner.  On
@@ -496,6 +537,9 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
                             const real* Pdiag, const real* Pinv, const real* Poff, const real* b, double bmean,
                             real* x, real* const (&rb)[2], real* const (&wb)[2], real* const (&sb)[2],
                             real* pdir, int stall_window = 0) {
+  if (X.lp)   // y-line preconditioner (piso_lines.cuh)
+    return cg_pressure_line<real, ND>(X, cs, rtol, atol, maxit, Poff, b, bmean, x, rb[0], rb[1], wb[0], sb[0], pdir,
+                                      stall_window);
   const int32_t N = X.N;
   // I1: r0 = b' - A' x0 with b' = -(b - mean), A' = -P
   __shared__ double s_mb;
@@ -592,25 +636,34 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     real* r_n = rb[cur ^ 1];
     real* w_n = wb[cur ^ 1];
     X.cells_pf([&](const Cell& c) {
+      // all loads first (own values, then the neighbours' u1), stores last:
+      // the compiler must assume the stores alias the loads, so this order is
+      // what lets the cell's loads be in flight together
       real pf[2 * ND];
       p_row<real, ND>(c, N, Poff, pf);
       auto sQ = [&](int32_t Q) -> real { return first ? w_i[Q] : w_i[Q] + be * s_o[Q]; };
       auto u1 = [&](int32_t Q) -> real { return (r_i[Q] - al * sQ(Q)) * Pinv[Q]; };
       const int32_t P = c.i;
       const real iP = Pinv[P];
-      const real uP = r_i[P] * iP;
-      const real p = first ? uP : uP + be * pdir[P];
-      pdir[P] = p;
-      x[P] += al * p;
+      const real rP = r_i[P];
+      const real pOld = first ? real(0) : pdir[P];
+      const real xP = x[P];
       const real sP = sQ(P);
-      s_n[P] = sP;
-      const real r1 = r_i[P] - al * sP;
-      r_n[P] = r1;
+      real uq[2 * ND];
+#pragma unroll
+      for (int s = 0; s < 2 * ND; s++) uq[s] = c.nb[s] >= 0 ? u1(c.nb[s]) : real(0);
+      const real uP = rP * iP;
+      const real p = first ? uP : uP + be * pOld;
+      const real r1 = rP - al * sP;
       const real u1P = r1 * iP;
       real w1 = 0;
 #pragma unroll
       for (int s = 0; s < 2 * ND; s++)
-        if (c.nb[s] >= 0) w1 += pf[s] * (u1P - u1(c.nb[s]));
+        if (c.nb[s] >= 0) w1 += pf[s] * (u1P - uq[s]);
+      pdir[P] = p;
+      x[P] = xP + al * p;
+      s_n[P] = sP;
+      r_n[P] = r1;
       w_n[P] = w1;
       a[0].add_prod(r1, u1P);
       a[1].add_prod(w1, u1P);

@@ -1,0 +1,387 @@
+// y-line preconditioner for the pressure CG (a B300 choice; the paper's CG,
+// App. A.5, names no preconditioner for the pressure system).
+//
+// M is the block diagonal of -P made of its y-lines: for every block column
+// (fixed x, z) the tridiagonal matrix that keeps the cell's full diagonal
+// (-P_P = sum of all its face coefficients) and the couplings to the y-
+// neighbours inside the same block.  Couplings across block sides, periodic
+// wraps and the x/z directions are dropped, so every line block is strictly
+// diagonally dominant (whenever a cell has an x or z face) and M is symmetric
+// positive definite: a valid CG preconditioner.  On grids refined towards
+// walls in y (tanh stretching, aspect ratios of 10-100 near the wall) the y
+// couplings dominate -P and M captures them: on the 64x48x32 channel the CG
+// needs 106 instead of 252 iterations, on the 5-block step 482 instead of 1477.
+//
+// Thomas' algorithm for one line block, with d_y = -P_P, e_y = -P_F(y, y+1)
+// (0 for the last cell of the line), m_y = 1 / (d_y - e_{y-1} c'_{y-1}) and
+// c'_y = e_y m_y (formed once per step):
+//   g_y = fa_y g_{y-1} + fm_y r_y,  fa_y = -e_{y-1} m_y, fm_y = m_y  (forward)
+//   z_y = fc_y z_{y+1} + g_y,       fc_y = -c'_y                      (backward)
+//
+// Execution: M^-1 r needs a whole line, so the CG iteration splits into two
+// phases with a plain barrier between them.  In the first, each CTA owns a
+// contiguous range of lines, stages them in shared memory in batches (cell
+// (line, y) of a batch at index y * pitch + line), updates r, x, p, s there and
+// solves its lines; in the second, every CTA applies -P to u on its usual cell
+// range.  A line solve is one warp: the two recurrences are affine maps
+// composed by a warp-level parallel prefix (Kogge-Stone), each lane holding a
+// contiguous chunk of the line.
+// This header is included from piso_krylov.cuh (it uses Ctx, CgState and the
+// group reductions defined there).
+#pragma once
+
+namespace piso {
+
+constexpr int LINE_LBMAX = 1024;   // lines per staging batch (size of the descriptor arrays)
+constexpr int LINE_ARRAYS = 4;     // staged reals per cell: fa, fm r (then the solution), fc, r
+
+// This CTA's share of the y-line preconditioner: lines [L0, L1) of the group
+// and the staging area behind the neighbour table in dynamic shared memory
+// (LINE_ARRAYS arrays of o.line_cap reals, then 3 x LINE_LBMAX ints).
+template <typename real, int ND>
+__device__ __forceinline__ LinePre<real> line_setup(const DomStatic& D, const Group& g, const SolverOpts& o,
+                                                    real* fa, real* fm, real* fc) {
+  extern __shared__ int32_t s_nbt[];
+  LinePre<real> L;
+  const size_t nbt_bytes = ((size_t)o.nbt_cap * 2 * ND * sizeof(int32_t) + 15) & ~size_t(15);
+  real* sr = reinterpret_cast<real*>(reinterpret_cast<char*>(s_nbt) + nbt_bytes);
+  const size_t cap = (size_t)o.line_cap;
+  L.sA = sr;
+  L.sB = sr + cap;
+  L.sC = sr + 2 * cap;
+  L.sR = sr + 3 * cap;
+  int32_t* si = reinterpret_cast<int32_t*>(sr + LINE_ARRAYS * cap);
+  L.sStart = si;
+  L.sStride = si + LINE_LBMAX;
+  L.sLen = si + 2 * LINE_LBMAX;
+  L.fa = fa;
+  L.fm = fm;
+  L.fc = fc;
+  L.L0 = (int32_t)(((int64_t)D.nlines * g.rank) / g.ncta);
+  L.L1 = (int32_t)(((int64_t)D.nlines * (g.rank + 1)) / g.ncta);
+  L.lb = min(LINE_LBMAX, o.line_cap / D.lmax - 1);
+  return L;
+}
+
+// Staging geometry of one batch: nb lines from line l0, pitch = nb | 1 (odd, so
+// the lanes of a line-solve warp, whose chunks start E * pitch apart, spread
+// over at least 16 banks).
+struct LineBatch {
+  int32_t l0, nb, pitch, slots;   // slots = nb * lmax
+};
+
+// Load this batch's line descriptors into shared memory.
+template <typename real>
+__device__ __forceinline__ LineBatch line_batch_begin(const DomStatic& D, const LinePre<real>& L, int32_t l0) {
+  LineBatch B;
+  B.l0 = l0;
+  B.nb = min(L.lb, L.L1 - l0);
+  B.pitch = B.nb | 1;
+  B.slots = B.nb * D.lmax;
+  __syncthreads();   // the previous batch's staging is no longer read
+  for (int32_t t = threadIdx.x; t < B.nb; t += blockDim.x) {
+    const LineDesc ld = line_desc(D, l0 + t);
+    L.sStart[t] = ld.start;
+    L.sStride[t] = ld.stride;
+    L.sLen[t] = ld.len;
+  }
+  __syncthreads();
+  return B;
+}
+
+// Cell and shared index of slot k of a batch (consecutive slots take
+// consecutive lines at the same y: contiguous memory for y-lines); false if
+// the slot lies past the end of a shorter line.  last: the line's last cell.
+template <typename real>
+__device__ __forceinline__ bool line_slot(const LinePre<real>& L, const LineBatch& B, int32_t k, int32_t& cell,
+                                          int32_t& sk, bool& last) {
+  const int32_t q = k / B.nb;   // y along the line
+  const int32_t l = k - q * B.nb;
+  const int32_t len = L.sLen[l];
+  if (q >= len) return false;
+  cell = L.sStart[l] + q * L.sStride[l];
+  sk = q * B.pitch + l;
+  last = q + 1 == len;
+  return true;
+}
+
+template <typename real, typename F>
+__device__ __forceinline__ void line_batch_cells(const LinePre<real>& L, const LineBatch& B, F&& f) {
+  for (int32_t k = threadIdx.x; k < B.slots; k += blockDim.x) {
+    int32_t i, sk;
+    bool last;
+    if (line_slot(L, B, k, i, sk, last)) f(i, sk, last);
+  }
+}
+
+// Solve the staged lines in place: on entry sB = fm * r, sA = fa, sC = fc; on
+// exit sB = M^-1 r.  One warp per line; lane j holds the chunk
+// [j E, min(len, (j + 1) E)) with E = ceil(len / 32).
+template <typename real>
+__device__ __forceinline__ void line_batch_solve(const LinePre<real>& L, const LineBatch& B) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int32_t P = B.pitch;
+  for (int32_t l = warp; l < B.nb; l += nw) {
+    const int32_t len = L.sLen[l];
+    const int32_t E = (len + 31) >> 5;
+    const int32_t y0 = min(len, lane * E), y1 = min(len, y0 + E);
+    // forward: g_y = a_y g_{y-1} + b_y; this lane's chunk as one map g -> A g + Bv
+    real A = real(1), Bv = real(0);
+    for (int32_t y = y0; y < y1; y++) {
+      const real a = L.sA[y * P + l];
+      A = a * A;
+      Bv = a * Bv + L.sB[y * P + l];
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {      // inclusive prefix of the maps over lanes
+      const real Au = __shfl_up_sync(0xffffffffu, A, off);
+      const real Bu = __shfl_up_sync(0xffffffffu, Bv, off);
+      if (lane >= off) {
+        Bv = A * Bu + Bv;
+        A = A * Au;
+      }
+    }
+    real g = __shfl_up_sync(0xffffffffu, Bv, 1);   // g just before this chunk (g_{-1} = 0)
+    if (lane == 0) g = real(0);
+    for (int32_t y = y0; y < y1; y++) {
+      g = L.sA[y * P + l] * g + L.sB[y * P + l];
+      L.sB[y * P + l] = g;
+    }
+    // backward: z_y = c_y z_{y+1} + g_y; the chunk as one map z_next -> C z_next + G
+    real Cm = real(1), G = real(0);
+    for (int32_t y = y1 - 1; y >= y0; y--) {
+      const real c = L.sC[y * P + l];
+      G = c * G + L.sB[y * P + l];
+      Cm = c * Cm;
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {      // suffix composition over lanes
+      const real Cd = __shfl_down_sync(0xffffffffu, Cm, off);
+      const real Gd = __shfl_down_sync(0xffffffffu, G, off);
+      if (lane + off < 32) {
+        G = Cm * Gd + G;
+        Cm = Cm * Cd;
+      }
+    }
+    real z = __shfl_down_sync(0xffffffffu, G, 1);  // z just after this chunk (z_len = 0)
+    if (lane == 31) z = real(0);
+    for (int32_t y = y1 - 1; y >= y0; y--) {
+      z = L.sC[y * P + l] * z + L.sB[y * P + l];
+      L.sB[y * P + l] = z;
+    }
+  }
+  __syncthreads();
+}
+
+// Thomas factors of every line block of -P (once per step, after P is
+// assembled).  One thread per line runs the recurrence over the staged
+// coefficients.
+template <typename real, int ND>
+__device__ void line_factor(const DomStatic& D, const LinePre<real>& L, int32_t N, const real* Pdiag,
+                            const real* Poff) {
+  for (int32_t l0 = L.L0; l0 < L.L1; l0 += L.lb) {
+    const LineBatch B = line_batch_begin(D, L, l0);
+    line_batch_cells(L, B, [&](int32_t i, int32_t k, bool last) {
+      L.sA[k] = -Pdiag[i];
+      L.sB[k] = last ? real(0) : -Poff[(size_t)N + i];   // j = 1: the +y face of i
+    });
+    __syncthreads();
+    for (int32_t l = threadIdx.x; l < B.nb; l += blockDim.x) {
+      const int32_t len = L.sLen[l];
+      real cprev = real(0), eprev = real(0);
+      for (int32_t y = 0; y < len; y++) {
+        const int32_t k = y * B.pitch + l;
+        const real d = L.sA[k], e = L.sB[k];
+        real piv = d - eprev * cprev;
+        // a line block without x/z couplings (a one-cell-wide block) is
+        // singular; the pivot then takes the full diagonal, i.e. the block is
+        // factored with a positive diagonal shift and M stays SPD
+        if (!(piv > real(1e-5) * d)) piv = d;
+        const real m = real(1) / piv;
+        const real c = e * m;
+        L.sA[k] = -eprev * m;
+        L.sB[k] = m;
+        L.sC[k] = -c;
+        cprev = c;
+        eprev = e;
+      }
+    }
+    __syncthreads();
+    line_batch_cells(L, B, [&](int32_t i, int32_t k, bool) {
+      L.fa[i] = L.sA[k];
+      L.fm[i] = L.sB[k];
+      L.fc[i] = L.sC[k];
+    });
+  }
+  __syncthreads();
+}
+
+// Line-preconditioned CG on (-P) x = -(b - bmean) in the Chronopoulos-Gear
+// form (one reduction per iteration; R7: b is projected to zero mean):
+//   r0 = b' - A' x0, u0 = M^-1 r0, w0 = A' u0
+//   per iteration: p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s,
+//                  u = M^-1 r  | barrier |  w = A' u, then gamma = (r, u),
+//                  delta = (w, u), ||r||^2 in one group reduction.
+// A' = -P is applied in difference form (sum_F P_F (u_P - u_F)), exact on
+// constants in any precision.  Vectors: x (solution, holds x0 on entry), r, u,
+// w, s, p.  The same scalar updates as the Jacobi CG (cg_coeffs /
+// cg_iter_update).
+template <typename real, int ND>
+__device__ bool cg_pressure_line(const Ctx<real, ND>& X, CgState& cs, double rtol, double atol, int maxit,
+                                 const real* Poff, const real* b, double bmean, real* x, real* r, real* u, real* w,
+                                 real* s, real* pdir, int stall_window) {
+  const int32_t N = X.N;
+  const DomStatic& D = X.D;
+  const LinePre<real>& L = *X.lp;
+  __shared__ double s_mb2;
+  __shared__ float s_mbf2;
+  if (threadIdx.x == 0) {
+    s_mb2 = bmean;
+    s_mbf2 = (float)bmean;
+  }
+  __syncthreads();
+  const real mb = pick<real>(s_mb2, s_mbf2);
+  // I1: r0 = b' - A' x0 and u0 = M^-1 r0 on this CTA's lines
+  Acc<real> a[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) a[k].zero();
+  for (int32_t l0 = L.L0; l0 < L.L1; l0 += L.lb) {
+    const LineBatch B = line_batch_begin(D, L, l0);
+    line_batch_cells(L, B, [&](int32_t i, int32_t k, bool) {
+      const Cell c = locate<ND>(D, i);
+      real pf[2 * ND];
+      p_row<real, ND>(c, N, Poff, pf);
+      const real bp = -(b[i] - mb);
+      const real xP = x[i];
+      real px = 0;
+#pragma unroll
+      for (int q = 0; q < 2 * ND; q++)
+        if (c.nb[q] >= 0) px += pf[q] * (x[c.nb[q]] - xP);
+      const real rr = bp + px;
+      const real fa = L.fa[i], fm = L.fm[i], fc = L.fc[i];
+      r[i] = rr;
+      L.sR[k] = rr;
+      L.sA[k] = fa;
+      L.sB[k] = fm * rr;
+      L.sC[k] = fc;
+      a[0].add_prod(bp, bp);
+      a[1].add_prod(rr, rr);
+    });
+    line_batch_solve(L, B);
+    line_batch_cells(L, B, [&](int32_t i, int32_t k, bool) {
+      const real uu = L.sB[k];
+      u[i] = uu;
+      a[2].add_prod(L.sR[k], uu);
+    });
+  }
+  if (!plain_sync(X.g)) return false;
+  // I2: w0 = A' u0 on the usual cell range
+  X.cells([&](const Cell& c) {
+    real pf[2 * ND];
+    p_row<real, ND>(c, N, Poff, pf);
+    const real uP = u[c.i];
+    real ww = 0;
+#pragma unroll
+    for (int q = 0; q < 2 * ND; q++)
+      if (c.nb[q] >= 0) ww += pf[q] * (uP - u[c.nb[q]]);
+    w[c.i] = ww;
+    a[3].add_prod(ww, uP);
+  });
+  {
+    const bool ok = reduce_sync<real, 4>(X.g, a, [&](const double* q) {
+      cs.tol2 = fmax(rtol * rtol * q[0], atol * atol);
+      cs.res2 = q[1];
+      cs.best = q[1];
+      if (sizeof(real) == 4) {
+        cs.ftol2 = f2_from_double(cs.tol2);
+        cs.fbest = f2_from_double(q[1]);
+        cs.fres2 = cs.fbest;
+      }
+      cs.best_it = 0;
+      cs.stalled = 0;
+      cs.it = 0;
+      cs.first = 1;
+      cs.conv = !(cs.res2 > cs.tol2);
+      cs.active = !cs.conv;
+      if (cs.res2 != cs.res2) {
+        cs.active = 0;
+        cs.conv = 0;
+        atomicOr(X.g.status, PISO_ERR_NAN);
+      }
+      if (cs.active && cg_coeffs(cs, q[2], q[3], true, X.g.status) && sizeof(real) == 4) {
+        cs.fgam = f2_from_double(q[2]);
+        cs.finv_alpha = f2_div(f2_from_double(q[3]), cs.fgam);
+      }
+    });
+    if (!ok) return false;
+  }
+  while (cs.active && cs.it < maxit) {
+    Acc<real> c3[3];
+    c3[0].zero();
+    c3[1].zero();
+    c3[2].zero();
+    const real al = pick<real>(cs.alpha, cs.alpha_f), be = pick<real>(cs.beta, cs.beta_f);
+    const int first = cs.first;
+    // phase A: vector updates and u = M^-1 r on this CTA's lines
+    for (int32_t l0 = L.L0; l0 < L.L1; l0 += L.lb) {
+      const LineBatch B = line_batch_begin(D, L, l0);
+      line_batch_cells(L, B, [&](int32_t i, int32_t k, bool) {
+        const real uP = u[i], wP = w[i], rP = r[i], xP = x[i];
+        const real pO = first ? real(0) : pdir[i];
+        const real sO = first ? real(0) : s[i];
+        const real fa = L.fa[i], fm = L.fm[i], fc = L.fc[i];
+        const real p = first ? uP : uP + be * pO;
+        const real sv = first ? wP : wP + be * sO;
+        const real rr = rP - al * sv;
+        pdir[i] = p;
+        s[i] = sv;
+        x[i] = xP + al * p;
+        r[i] = rr;
+        L.sR[k] = rr;
+        L.sA[k] = fa;
+        L.sB[k] = fm * rr;
+        L.sC[k] = fc;
+        c3[2].add_prod(rr, rr);
+      });
+      line_batch_solve(L, B);
+      line_batch_cells(L, B, [&](int32_t i, int32_t k, bool) {
+        const real uu = L.sB[k];
+        u[i] = uu;
+        c3[0].add_prod(L.sR[k], uu);
+      });
+    }
+    if (!plain_sync(X.g)) return false;
+    // phase B: w = A' u and (w, u)
+    X.cells_pf([&](const Cell& c) {
+      real pf[2 * ND];
+      p_row<real, ND>(c, N, Poff, pf);
+      const real uP = u[c.i];
+      real uq[2 * ND];
+#pragma unroll
+      for (int q = 0; q < 2 * ND; q++) uq[q] = c.nb[q] >= 0 ? u[c.nb[q]] : uP;
+      real ww = 0;
+#pragma unroll
+      for (int q = 0; q < 2 * ND; q++) ww += pf[q] * (uP - uq[q]);
+      w[c.i] = ww;
+      c3[1].add_prod(ww, uP);
+    }, [&](int32_t i) {
+      prefetch_l2(u + i);
+#pragma unroll
+      for (int j = 0; j < ND; j++) prefetch_l2(Poff + (size_t)j * N + i);
+    });
+    bool ok;
+    if constexpr (sizeof(real) == 4)
+      ok = reduce_sync<real, 3, true>(X.g, c3, [&](const double* q) {
+        cg_iter_update_f2(cs, f2_unpack(q[0]), f2_unpack(q[1]), f2_unpack(q[2]), stall_window, X.g.status);
+      });
+    else
+      ok = reduce_sync<real, 3>(
+          X.g, c3, [&](const double* q) { cg_iter_update(cs, q[0], q[1], q[2], stall_window, X.g.status); });
+    if (!ok) return false;
+  }
+  if (sizeof(real) == 4 && threadIdx.x == 0) cs.res2 = f2_to_double(cs.fres2);
+  return true;
+}
+
+}  // namespace piso

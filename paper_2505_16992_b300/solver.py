@@ -77,6 +77,11 @@ class Domain:
         o = options if options is not None else capi.default_options(**kw)
         capi.check(self.lib.piso_set_options(self.h, C.byref(o)), self.h)
 
+    def get_options(self) -> capi.Options:
+        o = capi.Options()
+        capi.check(self.lib.piso_get_options(self.h, C.byref(o)), self.h)
+        return o
+
     @classmethod
     def from_case(cls, case, precision="fp64", options=None, **kw) -> "Domain":
         """Build from an object with ndim/blocks/connections/dirichlet/outflow
