@@ -28,7 +28,18 @@ L2_FLUSH_BYTES = 256 << 20          # > 126 MB L2
 # algorithmic traffic model: every array a phase touches, counted once per
 # phase (neighbour re-reads are cache hits), in words per cell
 # ---------------------------------------------------------------------------
-def fwd_words_per_cell(d: int, adv_iters, p_iters) -> float:
+def cg_words_per_cell(d: int, it_p: int, line: bool) -> float:
+    """Stored-array words per cell of one pressure CG solve (start + iterations).
+    Jacobi (one phase per iteration): r, w, s, 1/diag, p, x, P faces read; p, x,
+    s, r, w written.  y-line (two phases): phase A reads u, w, r, x, p, s and the
+    three line factors and writes p, s, x, r, u; phase B reads u and the P faces
+    and writes w."""
+    if line:
+        return (d + 7) + (d + 2) + it_p * (14 + d + 2)
+    return (d + 4) + (d + 3) + it_p * (d + 11)
+
+
+def fwd_words_per_cell(d: int, adv_iters, p_iters, line: bool = False) -> float:
     """Stored-array words per cell one forward launch touches (each array once
     per phase; neighbour re-reads are cache hits).  One line per kernel phase."""
     it_a = max(adv_iters) if adv_iters else 0
@@ -39,20 +50,23 @@ def fwd_words_per_cell(d: int, adv_iters, p_iters) -> float:
     for k, it_p in enumerate(p_iters):
         w += (d * d + 8 * d + 4) if k == 0 else (d * d + 6 * d + 4)   # C1: (P), h, J T.h
         w += d + 3                    # C2: divergence, x0
-        w += (d + 4) + (d + 3)        # CG start: r0, w0
-        w += it_p * (d + 11)          # CG (one phase per iteration)
+        if line and k == 0:
+            w += 5                    # line factors: diag P, +y faces -> fa, fm, fc
+        w += cg_words_per_cell(d, it_p, line)
         w += d * d + 2 * d + 2        # C4: correction
     w += 3                            # final pressure
     return w
 
 
-def adj_words_per_cell(d: int, adv_iters, p_iters) -> float:
+def adj_words_per_cell(d: int, adv_iters, p_iters, line: bool = False) -> float:
     it_a = max(adv_iters) if adv_iters else 0
     w = 6 * d + 3                     # R0 extra on the first pass: rebuild P, clear accumulators
+    if line and any(p_iters):
+        w += 5                        # line factors of the rebuilt P
     for it_p in p_iters:
         w += d * d + 2 * d + 4        # R0: W = T gu / A, dL/dA
         w += d + 3                    # R1: -G^T W
-        w += (d + 4) + (d + 3) + it_p * (d + 11)   # CG on P
+        w += cg_words_per_cell(d, it_p, line)   # CG on P
         w += d * d + 7 * d + 6        # R3: d(alpha/A), div^T y, gg, dL/dA, dL/drhs0
         w += 9 * d                    # R4: -H^T gg, dL/dH
     w += 6 * d + 3                    # R5: start of the C^T solve
@@ -350,8 +364,10 @@ def main():
     else:
         shape = (args.threads, None, None)
     with_adj = args.mode == "fwdadj"
-    pc_used = {capi.PISO_PRECOND_JACOBI: "jacobi", capi.PISO_PRECOND_LINE: "y-line",
-               capi.PISO_PRECOND_AUTO: "auto"}[dom.get_options().p_precond]
+    pc_opt = dom.get_options().p_precond
+    if pc_opt == capi.PISO_PRECOND_AUTO:     # no autotune: the library's choice from the grid
+        pc_opt = capi.PISO_PRECOND_LINE if dom.uses_line_precond() else capi.PISO_PRECOND_JACOBI
+    pc_used = "y-line" if pc_opt == capi.PISO_PRECOND_LINE else "jacobi"
 
     def one_step():
         dom.step(u, p, case.dt, case.nu, S, u_out=u_out, p_out=p_out, sync=False)
@@ -418,7 +434,7 @@ def main():
 
     # roofline of the dominant kernel (the persistent forward-step kernel)
     peak, peak_kind = measured_peaks()
-    words = fwd_words_per_cell(d, st["adv_iters"][:d], st["p_iters"][:2])
+    words = fwd_words_per_cell(d, st["adv_iters"][:d], st["p_iters"][:2], line=pc_used == "y-line")
     alg_bytes = words * N * w
     fwd_avg_s = sum(fwd_ms) / len(fwd_ms) / 1e3
     achieved = alg_bytes / fwd_avg_s / 1e9

@@ -170,6 +170,11 @@ piso_status piso_set_options(piso_domain* d, const piso_options* opts);
 /* Copy the domain's current options to *opts (host), e.g. after piso_autotune. */
 piso_status piso_get_options(const piso_domain* d, piso_options* opts);
 
+/* The pressure preconditioner the domain's next step uses (PISO_PRECOND_JACOBI
+ * or PISO_PRECOND_LINE; PISO_PRECOND_AUTO resolved from the grid), or -1 for a
+ * NULL or unfinalized domain. */
+int32_t piso_pressure_precond(const piso_domain* d);
+
 int64_t piso_num_cells(const piso_domain* d);
 int32_t piso_num_boundary_faces(const piso_domain* d);
 

@@ -56,6 +56,7 @@ _SIGS = {
     "piso_finalize": (C.c_int, [_P, C.POINTER(Options)]),
     "piso_set_options": (C.c_int, [_P, C.POINTER(Options)]),
     "piso_get_options": (C.c_int, [_P, C.POINTER(Options)]),
+    "piso_pressure_precond": (C.c_int32, [_P]),
     "piso_num_cells": (C.c_int64, [_P]),
     "piso_num_boundary_faces": (C.c_int32, [_P]),
     "piso_tape_bytes": (C.c_size_t, [_P]),

@@ -875,6 +875,11 @@ piso_status piso_get_options(const piso_domain* d, piso_options* opts) {
   return PISO_OK;
 }
 
+int32_t piso_pressure_precond(const piso_domain* d) {
+  if (!d || !d->finalized) return -1;
+  return d->p_line ? PISO_PRECOND_LINE : PISO_PRECOND_JACOBI;
+}
+
 int64_t piso_num_cells(const piso_domain* d) { return d ? d->N : -1; }
 int32_t piso_num_boundary_faces(const piso_domain* d) { return d ? d->nbf : -1; }
 

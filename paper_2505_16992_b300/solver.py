@@ -82,6 +82,10 @@ class Domain:
         capi.check(self.lib.piso_get_options(self.h, C.byref(o)), self.h)
         return o
 
+    def uses_line_precond(self) -> bool:
+        """True when the pressure CG of the next step uses the y-line preconditioner."""
+        return int(self.lib.piso_pressure_precond(self.h)) == capi.PISO_PRECOND_LINE
+
     @classmethod
     def from_case(cls, case, precision="fp64", options=None, **kw) -> "Domain":
         """Build from an object with ndim/blocks/connections/dirichlet/outflow

@@ -65,10 +65,12 @@ def test_auto_picks_line_on_wall_refined_grids_only():
     c = W.channel3d(16, 12, 8)
     d_auto = gpu_domain(c, p_precond=capi.PISO_PRECOND_AUTO)
     d_line = gpu_domain(c, p_precond=LINE)
+    assert d_auto.uses_line_precond() and d_line.uses_line_precond()
     a = gpu_step(d_auto, c, c.u0, c.p0, c.S)
     b = gpu_step(d_line, c, c.u0, c.p0, c.S)
     assert a[2]["p_iters"] == b[2]["p_iters"]
     cav = W.cavity2d(32)
+    assert not gpu_domain(cav, p_precond=capi.PISO_PRECOND_AUTO).uses_line_precond()
     e = gpu_step(gpu_domain(cav, p_precond=capi.PISO_PRECOND_AUTO), cav, cav.u0, cav.p0)
     f = gpu_step(gpu_domain(cav, p_precond=JACOBI), cav, cav.u0, cav.p0)
     assert e[2]["p_iters"] == f[2]["p_iters"]
