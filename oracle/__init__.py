@@ -7,3 +7,4 @@ from .piso import (Mesh, Options, Matrix, assemble_C, assemble_P, matvec, matvec
                    grad_p_T, divergence, divergence_T, pressure_rhs_vec, correct, outflow_update,
                    piso_step, piso_step_adjoint, mesh_from_case, rollout, rhie_chow_residual,
                    to_sparse)
+from . import stats
