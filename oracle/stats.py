@@ -109,9 +109,11 @@ def accumulate(records: Sequence[Dict[str, np.ndarray]]) -> Dict[str, np.ndarray
 
 def frame_record_adjoint(q: np.ndarray, res, rec: Dict[str, np.ndarray], g_mean: np.ndarray,
                          g_m2: np.ndarray, g_m3: Optional[np.ndarray] = None) -> np.ndarray:
-    """dL/dq [nq][N] of one frame, given dL/d(mean, m2, m3) of its record.
+    """dL/dq [nq][N] of one frame, given dL/d(mean, m2, m3) of a record that
+    contains the frame's samples: its own record, or a record accumulated over
+    several frames (time average), whose count n and moments are then used.
 
-    For a cell c of plane y with a = q(c) - mean (n cells per plane):
+    For a cell c of plane y with a = q(c) - mean (n samples in the record):
       d mean_i / d q_l = delta_il / n
       d m2_ij / d q_l  = (delta_il a_j + delta_jl a_i) / n        (sum of a is 0)
       d m3_ijk / d q_l = (delta_il (a_j a_k - m2_jk) + delta_jl (a_i a_k - m2_ik)
@@ -127,7 +129,7 @@ def frame_record_adjoint(q: np.ndarray, res, rec: Dict[str, np.ndarray], g_mean:
         # g3s[y, l, j, k] = g_ljk + g_jlk + g_jkl
         aa = np.einsum("jyc,kyc->yjkc", a, a) - rec["m2"][:, :, :, None]
         out = out + np.einsum("yljk,yjkc->lyc", g3s, aa)
-    out = out / n
+    out = out / rec["n"][None, :, None]
     # back to the cell order [nq][N]
     nx, ny_ = int(res[0]), int(res[1])
     nz = int(res[2]) if len(res) > 2 else 1

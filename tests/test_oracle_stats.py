@@ -108,6 +108,34 @@ def test_record_adjoint_matches_finite_differences():
     assert np.allclose(dq, fd, rtol=1e-8, atol=1e-9)
 
 
+def test_accumulated_record_adjoint_matches_finite_differences():
+    """The same adjoint applied with an accumulated record (time average over
+    frames) is the derivative of the accumulated statistics with respect to one
+    frame's samples: central differences through ``accumulate``."""
+    rng = np.random.default_rng(4)
+    res = (3, 2, 2)
+    frames = [rng.standard_normal((2, 12)) + f for f in range(3)]
+    acc = OS.accumulate([OS.frame_record(q, res) for q in frames])
+    gm = rng.standard_normal(acc["mean"].shape)
+    g2 = rng.standard_normal(acc["m2"].shape)
+    g3 = rng.standard_normal(acc["m3"].shape)
+
+    def L(q1):
+        r = OS.accumulate([OS.frame_record(q, res) for q in (frames[0], q1, frames[2])])
+        return np.sum(gm * r["mean"]) + np.sum(g2 * r["m2"]) + np.sum(g3 * r["m3"])
+
+    dq = OS.frame_record_adjoint(frames[1], res, acc, gm, g2, g3)
+    h = 1e-5
+    fd = np.zeros_like(frames[1])
+    for i in range(2):
+        for c in range(12):
+            e = np.zeros_like(frames[1])
+            e[i, c] = h
+            fd[i, c] = (-L(frames[1] + 2 * e) + 8 * L(frames[1] + e) - 8 * L(frames[1] - e) +
+                        L(frames[1] - 2 * e)) / (12 * h)
+    assert np.allclose(dq, fd, rtol=1e-8, atol=1e-9)
+
+
 def _channel(nx=8, ny=6, nz=4, gamma=1.5):
     c = W.channel3d(nx, ny, nz, gamma=gamma)
     return c, O.mesh_from_case(c)
