@@ -230,6 +230,63 @@ def time_variant(case, prec, kw, steps, with_adj, flush):
             "p_resid": st["p_resid"][:2]}
 
 
+def time_statistics(dom, u, p, nu, steps, flush, peak):
+    """Turbulence statistics of the step's fields (Sec. 2.5): per frame the
+    cell gradients and the records of u (order 3), grad u and (u, grad p)
+    (order 2) merged into their accumulators; the adjoint of the u record.
+    Returns per-frame times and the roofline of the u-record kernel
+    (algorithmic bytes: one read of the d fields)."""
+    import torch
+    from paper_2505_16992_b300 import solver as SV
+    d, N = dom.ndim, dom.N
+    w = 4 if dom.dtype == torch.float32 else 8
+    su, sg, sp = SV.PlaneStats(dom, d, 3), SV.PlaneStats(dom, d * d, 2), SV.PlaneStats(dom, 2 * d, 2)
+    au, ag, ap = su.empty(), sg.empty(), sp.empty()
+    up = torch.empty((2 * d, N), dtype=dom.dtype, device="cuda")
+    grad = torch.randn_like(au)
+    dq = torch.zeros_like(u)
+    stream = torch.cuda.current_stream()
+
+    def frame():
+        gu, gp = SV.cell_gradients(dom, u, p)
+        su.frame(u, au)
+        sg.frame(gu.reshape(d * d, N), ag)
+        up[:d].copy_(u)
+        up[d:].copy_(gp)
+        sp.frame(up, ap)
+
+    for _ in range(3):
+        frame()
+        su.frame_adjoint(u, au, grad, dq)
+    t_frame = t_rec = t_adj = 0.0
+    for k in range(steps):
+        flush.fill_(float(k))
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        e[0].record(stream)
+        frame()
+        e[1].record(stream)
+        flush.fill_(float(k) + 0.5)
+        e[2].record(stream)
+        su.frame(u)
+        e[3].record(stream)
+        flush.fill_(float(k) + 0.25)
+        e[4].record(stream)
+        su.frame_adjoint(u, au, grad, dq)
+        e[5].record(stream)
+        e[5].synchronize()
+        t_frame += e[0].elapsed_time(e[1])
+        t_rec += e[2].elapsed_time(e[3])
+        t_adj += e[4].elapsed_time(e[5])
+    B = SV.budget(su, au, sg, ag, sp, ap, nu)
+    torch.cuda.synchronize()
+    rec_ms = t_rec / steps
+    achieved = d * N * w / (rec_ms / 1e3) / 1e9
+    return {"frame_ms": t_frame / steps, "u_record_ms": rec_ms, "u_record_adjoint_ms": t_adj / steps,
+            "budget_finite": bool(all(torch.isfinite(v).all() for v in B.values())),
+            "roofline_u_record": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak, "bytes_per_launch": d * N * w}}
+
+
 def run_batch(args):
     """Config 5: 64 independent 2D cavity/channel simulations (sides 32..256,
     Re 100..2000, seed 4) advanced together: one persistent launch for the
@@ -307,6 +364,7 @@ def main():
     ap.add_argument("--mode", default="fwdadj", choices=["fwd", "fwdadj"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stats", action="store_true", help="skip the turbulence-statistics timing")
     ap.add_argument("--threads", type=int, default=0, help="CTA width; 0 = autotune")
     ap.add_argument("--refine", type=float, default=0.0, help="FP32: FP64-refined pressure tolerance")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "line"],
@@ -478,6 +536,10 @@ def main():
             paths[name] = {"steps_per_s": 1e3 * nvar / (tf + ta), "adj_ms": ta / nvar,
                            "adj_iters": {"adv": vst["adv_iters"][:d], "p": vst["p_iters"][:2]}}
 
+    statistics = None
+    if not args.no_stats:
+        statistics = time_statistics(dom, u_out, p_out, case.nu, max(5, args.steps // 3), flush, peak)
+
     compare = None
     if args.compare:
         compare = {}
@@ -519,6 +581,8 @@ def main():
             line["precision_compare"] = compare
         if paths is not None:
             line["grad_paths"] = paths
+        if statistics is not None:
+            line["statistics"] = statistics
         if args.workload != "channel3d":
             tag = "x".join(str(v) for v in sizes[args.workload])
             line["config"]["workload"] = line["config"]["workload"].replace("64x48x32", tag)

@@ -283,6 +283,70 @@ piso_status piso_batch_step_adjoint(piso_batch* b, const void* const* du_out,
 
 void piso_batch_destroy(piso_batch* b);
 
+/* ---- turbulence statistics (Sec. 2.5 "Operators for Turbulence Statistics";
+ * Sec. 3.3 "Losses from Turbulence Statistics") ----
+ * A record holds, for every plane y = const of a single-block domain (the
+ * homogeneous directions are x and, in 3D, z), in doubles:
+ *   [n, mean[nq], m2[nq][nq], m3[nq][nq][nq] (order 3 only)]
+ * with n the number of samples, mean_i = (1/n) sum q_i and the central moments
+ * m2_ij = (1/n) sum a_i a_j, m3_ijk = (1/n) sum a_i a_j a_k, a = q - mean; a
+ * domain's records are [ny][record_size] arrays in DEVICE memory, caller-owned.
+ * Averaging over time is merging frame records (an online pairwise update), so
+ * no frame needs to be stored.  Every call enqueues on the stream and returns
+ * a status; errors name the violated condition via piso_last_error(domain). */
+typedef struct piso_plane_stats piso_plane_stats;
+
+/* Statistics of nq per-cell fields (nq <= 12) up to order 2 or 3 (order 3
+ * needs nq <= 4) on a finalized single-block domain.  Ownership of *out passes
+ * to the caller (release with piso_stats_destroy). */
+piso_status piso_stats_create(piso_domain* d, int32_t nq, int32_t order, piso_plane_stats** out);
+
+/* Doubles per plane of a record, and the number of planes (ny); -1 for NULL. */
+int32_t piso_stats_record_size(const piso_plane_stats* s);
+int32_t piso_stats_planes(const piso_plane_stats* s);
+
+/* Record of one frame: q DEVICE [nq][N] in the domain's storage precision ->
+ * rec (device [ny][record_size]).  If acc is non-NULL it is merged with the
+ * frame (acc <- merge(acc, rec)); an acc plane with n = 0 starts empty.  Each
+ * plane is split over several CTAs whose partial records (in a scratch buffer
+ * of the statistics object: calls on one object must not overlap on the GPU)
+ * are merged in a fixed order, so results are deterministic. */
+piso_status piso_stats_frame(piso_plane_stats* s, const void* q, double* rec, double* acc, void* stream);
+
+/* a <- merge(a, b): the record of the union of both sample sets, per plane. */
+piso_status piso_stats_merge(piso_plane_stats* s, double* a, const double* b, void* stream);
+
+/* Adjoint of a record with respect to one frame's fields: dq += (d rec / d q)^T
+ * grad, with q the frame (device [nq][N]), rec its record or an accumulated
+ * record that contains it (then the derivative is that of the accumulated
+ * statistics with respect to this frame's samples), grad = dL/d(rec) in the
+ * record layout (the n entries are ignored), dq device [nq][N] accumulated. */
+piso_status piso_stats_frame_adjoint(piso_plane_stats* s, const void* q, const double* rec, const double* grad,
+                                     void* dq, void* stream);
+
+/* Cell-centred gradients of the velocity and pressure (the central
+ * differences of Eq. velCorrDiscrete mapped with T): grad_u [ndim][ndim][N]
+ * with grad_u[i][k] = d u_i / d x_k, grad_p [ndim][N] (device, storage
+ * precision, either may be NULL).  At Dirichlet faces the missing neighbour is
+ * the ghost 2 u_b - u_P for the velocity and p_P for the pressure. */
+piso_status piso_cell_gradients(piso_domain* d, const void* u, const void* p, void* grad_u, void* grad_p,
+                                void* stream);
+
+/* Turbulent energy budget per plane from three records of one domain: rec_u
+ * of the velocity (nq = ndim, order 3), rec_g of its gradient (nq = ndim^2,
+ * field i*ndim + k = d u_i / d x_k) and rec_p of (u, grad p) (nq = 2 ndim):
+ * out (device [5][ny][ndim][ndim] doubles) = production
+ * -(R_ik dU_j/dx_k + R_jk dU_i/dx_k), dissipation 2 nu <d_k u_i' d_k u_j'>,
+ * turbulent transport -d<u_i' u_j' v'>/dy, viscous diffusion nu d^2 R_ij/dy^2,
+ * velocity pressure-gradient -(<u_i' d_j p> + <u_j' d_i p>).  y-derivatives of
+ * the profiles use three-point formulas on {-y side, plane centres, +y side}
+ * with zero values at the sides (no-slip walls). */
+piso_status piso_stats_budget(const piso_plane_stats* su, const double* rec_u, const piso_plane_stats* sg,
+                              const double* rec_g, const piso_plane_stats* sp, const double* rec_p, double nu,
+                              double* out, void* stream);
+
+void piso_stats_destroy(piso_plane_stats* s);
+
 /* Library version string. */
 const char* piso_version(void);
 

@@ -76,6 +76,15 @@ _SIGS = {
     "piso_batch_step_adjoint": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                           C.POINTER(_P), _D, _P, C.POINTER(Stats)]),
     "piso_batch_destroy": (None, [_P]),
+    "piso_stats_create": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(_P)]),
+    "piso_stats_record_size": (C.c_int32, [_P]),
+    "piso_stats_planes": (C.c_int32, [_P]),
+    "piso_stats_frame": (C.c_int, [_P, _P, _P, _P, _P]),
+    "piso_stats_merge": (C.c_int, [_P, _P, _P, _P]),
+    "piso_stats_frame_adjoint": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "piso_cell_gradients": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "piso_stats_budget": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_double, _P, _P]),
+    "piso_stats_destroy": (None, [_P]),
 }
 
 _lib = None

@@ -17,6 +17,7 @@
 #include "../../include/piso.h"
 #include "piso_adjoint.cuh"
 #include "piso_forward.cuh"
+#include "piso_stats.cuh"
 
 using namespace piso;
 
@@ -1060,6 +1061,7 @@ void piso_domain_destroy(piso_domain* d) {
 
 #include "piso_capi_adjoint.inc"
 #include "piso_capi_batch.inc"
+#include "piso_capi_stats.inc"
 
 // ===========================================================================
 // Forward step with library-owned static scratch (allocates nothing per call).

@@ -277,3 +277,151 @@ def rollout(domain: Domain, u, p, dt, nu, steps: int, source_fn=None):
         S = source_fn(u) if source_fn is not None else None
         u, p = piso_step(domain, u, p, dt, nu, S)
     return u, p
+
+
+# ---------------------------------------------------------------------------
+# turbulence statistics (Sec. 2.5 "Operators for Turbulence Statistics";
+# Sec. 3.3 "Losses from Turbulence Statistics")
+# ---------------------------------------------------------------------------
+
+class PlaneStats:
+    """Plane records of nq per-cell fields of a single-block domain: count,
+    means and central moments up to ``order`` per plane y (homogeneous x, z),
+    as float64 tensors [ny][record_size] = [n, mean, m2, m3]."""
+
+    def __init__(self, domain: Domain, nq: int, order: int = 3):
+        self.lib = capi.load()
+        self.domain, self.nq, self.order = domain, nq, order
+        h = C.c_void_p()
+        capi.check(self.lib.piso_stats_create(domain.h, nq, order, C.byref(h)), domain.h)
+        self.h = h
+        self.rsize = int(self.lib.piso_stats_record_size(h))
+        self.ny = int(self.lib.piso_stats_planes(h))
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.lib.piso_stats_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def empty(self) -> torch.Tensor:
+        """An accumulator with no samples (n = 0 in every plane)."""
+        return torch.zeros((self.ny, self.rsize), dtype=torch.float64, device="cuda")
+
+    def _q(self, q):
+        q = q.detach().contiguous()
+        if q.dtype != self.domain.dtype or q.numel() != self.nq * self.domain.N:
+            raise ValueError(f"q must hold {self.nq} x {self.domain.N} {self.domain.dtype} values")
+        return q
+
+    def frame(self, q, acc: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        rec = torch.empty((self.ny, self.rsize), dtype=torch.float64, device="cuda")
+        capi.check(self.lib.piso_stats_frame(self.h, capi.dptr(self._q(q)), capi.dptr(rec), capi.dptr(acc),
+                                             _stream_ptr(stream)), self.domain.h)
+        return rec
+
+    def merge(self, a: torch.Tensor, b: torch.Tensor, stream=None) -> torch.Tensor:
+        capi.check(self.lib.piso_stats_merge(self.h, capi.dptr(a), capi.dptr(b), _stream_ptr(stream)),
+                   self.domain.h)
+        return a
+
+    def frame_adjoint(self, q, rec, grad, dq=None, stream=None) -> torch.Tensor:
+        q = self._q(q)
+        dq = torch.zeros_like(q) if dq is None else dq
+        capi.check(self.lib.piso_stats_frame_adjoint(self.h, capi.dptr(q), capi.dptr(rec.contiguous()),
+                                                     capi.dptr(grad.contiguous()), capi.dptr(dq),
+                                                     _stream_ptr(stream)), self.domain.h)
+        return dq
+
+    def split(self, rec: torch.Tensor):
+        """(n [ny], mean [ny][nq], m2 [ny][nq][nq], m3 [ny][nq][nq][nq] or None) views of a record."""
+        nq = self.nq
+        n = rec[:, 0]
+        mean = rec[:, 1:1 + nq]
+        m2 = rec[:, 1 + nq:1 + nq + nq * nq].reshape(-1, nq, nq)
+        m3 = rec[:, 1 + nq + nq * nq:].reshape(-1, nq, nq, nq) if self.order == 3 else None
+        return n, mean, m2, m3
+
+
+class FrameRecordFunction(torch.autograd.Function):
+    """record = plane statistics of one frame q (differentiable in q)."""
+
+    @staticmethod
+    def forward(ctx, q, stats: PlaneStats):
+        rec = stats.frame(q)
+        ctx.stats = stats
+        ctx.save_for_backward(q.detach(), rec)
+        return rec
+
+    @staticmethod
+    def backward(ctx, g):
+        q, rec = ctx.saved_tensors
+        return ctx.stats.frame_adjoint(q, rec, g.contiguous()), None
+
+
+class TimeAveragedRecordFunction(torch.autograd.Function):
+    """record of all samples of the frames qs (averaging over time and the
+    homogeneous directions), accumulated online; the derivative with respect
+    to each frame uses the accumulated record."""
+
+    @staticmethod
+    def forward(ctx, stats: PlaneStats, *qs):
+        acc = stats.empty()
+        tmp = torch.empty_like(acc)
+        for q in qs:
+            capi.check(stats.lib.piso_stats_frame(stats.h, capi.dptr(stats._q(q)), capi.dptr(tmp), capi.dptr(acc),
+                                                  _stream_ptr(None)), stats.domain.h)
+        ctx.stats = stats
+        ctx.save_for_backward(acc, *[q.detach() for q in qs])
+        return acc
+
+    @staticmethod
+    def backward(ctx, g):
+        acc, *qs = ctx.saved_tensors
+        g = g.contiguous()
+        return (None,) + tuple(ctx.stats.frame_adjoint(q, acc, g) for q in qs)
+
+
+def frame_record(stats: PlaneStats, q):
+    return FrameRecordFunction.apply(q, stats)
+
+
+def time_averaged_record(stats: PlaneStats, qs):
+    return TimeAveragedRecordFunction.apply(stats, *qs)
+
+
+def stats_loss(stats: PlaneStats, qs, ref_mean, ref_m2, lam_U=1.0, lam_uu=1.0, lam_frame=1.0):
+    """L_stats of Eq. TCFstatsLossGeneric (Sec. 3.3) with one weight per kind:
+    squared errors of the mean profiles and second-order statistics per plane
+    (averaged over the planes) for the time-averaged record of all frames plus
+    lam_frame times the same terms of every frame's own record."""
+    def terms(rec):
+        _, mean, m2, _ = stats.split(rec)
+        ny = mean.shape[0]
+        return (lam_U * ((mean - ref_mean) ** 2).sum() + lam_uu * ((m2 - ref_m2) ** 2).sum()) / ny
+    total = terms(time_averaged_record(stats, qs))
+    for q in qs:
+        total = total + lam_frame * terms(frame_record(stats, q))
+    return total
+
+
+def cell_gradients(domain: Domain, u, p=None, stream=None):
+    """(grad_u [d][d][N] with grad_u[i, k] = d u_i / d x_k, grad_p [d][N] or None)."""
+    d, N = domain.ndim, domain.N
+    gu = torch.empty((d, d, N), dtype=domain.dtype, device="cuda")
+    gp = torch.empty((d, N), dtype=domain.dtype, device="cuda") if p is not None else None
+    capi.check(domain.lib.piso_cell_gradients(domain.h, capi.dptr(u.contiguous()),
+                                              capi.dptr(None if p is None else p.contiguous()), capi.dptr(gu),
+                                              capi.dptr(gp), _stream_ptr(stream)), domain.h)
+    return gu, gp
+
+
+def budget(su: PlaneStats, rec_u, sg: PlaneStats, rec_g, sp: PlaneStats, rec_p, nu: float, stream=None):
+    """Budget terms per plane: dict of [ny][d][d] tensors P, eps, T, D, Pi."""
+    d = su.domain.ndim
+    out = torch.empty((5, su.ny, d, d), dtype=torch.float64, device="cuda")
+    capi.check(su.lib.piso_stats_budget(su.h, capi.dptr(rec_u), sg.h, capi.dptr(rec_g), sp.h, capi.dptr(rec_p),
+                                        float(nu), capi.dptr(out), _stream_ptr(stream)), su.domain.h)
+    return dict(P=out[0], eps=out[1], T=out[2], D=out[3], Pi=out[4])
