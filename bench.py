@@ -314,14 +314,32 @@ def run_batch(args):
     with_adj = args.mode == "fwdadj"
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    gdu = [torch.empty_like(g) for g in gs]
+    gdp = [torch.empty((d.N,), dtype=d.dtype, device="cuda") for d in doms]
+    gdS = [torch.empty_like(g) for g in gs]
+
     def one():
         b.step(us, ps, dts, nus, Ss, u_out=uo, p_out=po, sync=False)
         if with_adj:
-            b.step_adjoint(gs)
+            b.step_adjoint(gs, sync=False, du_in=gdu, dp_in=gdp, dS=gdS)
 
     for _ in range(args.warmup):
         one()
     _, _, st = b.step(us, ps, dts, nus, Ss, u_out=uo, p_out=po)
+    torch.cuda.synchronize()
+    # the forward and adjoint launches of a step captured once in a CUDA graph
+    # and replayed (the graph records the same arguments every replay)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        one()                          # warm the side stream once outside the capture
+        torch.cuda.current_stream().synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            one()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph.replay()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     tot = 0.0
@@ -331,11 +349,13 @@ def run_batch(args):
         flush.fill_(0.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        one()
+        graph.replay()
         e1.record(stream)
         e1.synchronize()
         tot += e0.elapsed_time(e1) / 1e3
     clocks = clocks_sampler_stop(proc, fh, clk_path, 0)
+    _, _, st_after = b.step(us, ps, dts, nus, Ss, u_out=uo, p_out=po)     # replayed steps still converge
+    assert all(s["status"] == "PISO_OK" for s in st_after), "batch step failed after graph replays"
     cells = sum(c.ncells for c in cases)
     value = len(cases) * args.steps / tot
     line = {"metric": "batched PISO sim-steps/s (64 independent 2D sims, fwd+adjoint)" if with_adj else
@@ -345,7 +365,8 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": "batch64: 2D cavities/channels, side U{32..256}, Re U[100,2000], seed 4",
                        "cells": cells, "krylov_rtol": rtol, "ctas": b.total_ctas if hasattr(b, "total_ctas") else None,
-                       "l2": "flushed between timed steps (256 MB write, untimed)"},
+                       "l2": "flushed between timed steps (256 MB write, untimed)",
+                       "cuda_graph": "forward + adjoint launches of a step captured once, replayed per step"},
             "cell_updates_per_s": cells * args.steps / tot,
             "p_iters_max": max(max(s["p_iters"][:2]) for s in st),
             "p_iters_min": min(min(s["p_iters"][:2]) for s in st),

@@ -220,18 +220,22 @@ class Batch:
         capi.check(rc, None)
         return u_out, p_out, ([s.as_dict() for s in st] if st is not None else None)
 
-    def step_adjoint(self, du_out, dp_out=None, stream=None):
+    def step_adjoint(self, du_out, dp_out=None, stream=None, sync=True, du_in=None, dp_in=None, dS=None):
+        """Adjoint of every member's last step.  sync=False enqueues only (no
+        statistics or dnu read back; usable inside CUDA-graph capture)."""
         n = len(self.domains)
         dp_out = [None] * n if dp_out is None else dp_out
-        du_in = [torch.empty_like(g) for g in du_out]
-        dp_in = [torch.empty((d.N,), dtype=d.dtype, device="cuda") for d in self.domains]
-        dS = [torch.empty_like(g) for g in du_out]
-        dnu = (C.c_double * n)()
-        st = (capi.Stats * n)()
+        du_in = [torch.empty_like(g) for g in du_out] if du_in is None else du_in
+        dp_in = [torch.empty((d.N,), dtype=d.dtype, device="cuda") for d in self.domains] if dp_in is None else dp_in
+        dS = [torch.empty_like(g) for g in du_out] if dS is None else dS
+        dnu = (C.c_double * n)() if sync else None
+        st = (capi.Stats * n)() if sync else None
         rc = self.lib.piso_batch_step_adjoint(self.h, self._ptrs(du_out), self._ptrs(dp_out),
                                               self._ptrs(du_in), self._ptrs(dp_in), self._ptrs(dS), dnu,
                                               _stream_ptr(stream), st)
         capi.check(rc, None)
+        if not sync:
+            return du_in, dp_in, dS, None, None
         return du_in, dp_in, dS, list(dnu), [s.as_dict() for s in st]
 
 
