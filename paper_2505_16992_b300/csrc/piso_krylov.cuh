@@ -293,6 +293,153 @@ __device__ __forceinline__ void bicg_start(BiState& bs, const double* q, double 
   }
 }
 
+// The three cell sweeps of a BiCGStab iteration.  Each array is touched
+// through one pointer only (ping-pong buffers), so the pointers are
+// __restrict__: after inlining the compiler knows a cell's stores cannot alias
+// the next cell's loads, and the 2x unrolled loops keep two cells' loads in
+// flight.
+// BA: p = r + beta (p - omega v), v = M p (p formed on the fly at the stencil), (rhat, v)
+template <typename real, int ND, bool TR>
+__device__ __forceinline__ void bicg_sweep_a(const Ctx<real, ND>& X, int first, const int (&act)[ND],
+                                             const real (&beta)[ND], const real (&om)[ND],
+                                             const real* __restrict__ Cdiag, const real* __restrict__ Coff,
+                                             const real* __restrict__ r, const real* __restrict__ pold,
+                                             const real* __restrict__ vold, const real* __restrict__ rhat,
+                                             real* __restrict__ pnew, real* __restrict__ vnew, Acc<real> (&a)[ND]) {
+  const int32_t N = X.N, e = X.end(), st = X.stride();
+#pragma unroll 2
+  for (int32_t i = X.first(); i < e; i += st) {
+    const int32_t nx_ = i + st;
+    if (nx_ < e) {
+      prefetch_l2(Cdiag + nx_);
+#pragma unroll
+      for (int s = 0; s < 2 * ND; s++) prefetch_l2(Coff + (size_t)s * N + nx_);
+#pragma unroll
+      for (int k = 0; k < ND; k++) {
+        prefetch_l2(r + (size_t)k * N + nx_);
+        prefetch_l2(pold + (size_t)k * N + nx_);
+        prefetch_l2(vold + (size_t)k * N + nx_);
+        prefetch_l2(rhat + (size_t)k * N + nx_);
+      }
+    }
+    const Cell c = X.cell(i);
+    real diag, cf[2 * ND];
+    c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+    real pP[ND], v[ND], rh[ND];
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+      pP[k] = v[k] = rh[k] = real(0);
+      if (!act[k]) continue;
+      const size_t o_ = (size_t)k * N;
+      auto pn = [&](int32_t Q) -> real {
+        const real rq = r[o_ + Q];
+        return first ? rq : rq + beta[k] * (pold[o_ + Q] - om[k] * vold[o_ + Q]);
+      };
+      pP[k] = pn(c.i);
+      real vv_ = diag * pP[k];
+#pragma unroll
+      for (int s = 0; s < 2 * ND; s++)
+        if (c.nb[s] >= 0) vv_ += cf[s] * pn(c.nb[s]);
+      v[k] = vv_;
+      rh[k] = rhat[o_ + c.i];
+    }
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+      if (!act[k]) continue;
+      const size_t o_ = (size_t)k * N;
+      pnew[o_ + c.i] = pP[k];
+      vnew[o_ + c.i] = v[k];
+      a[k].add_prod(rh[k], v[k]);
+    }
+  }
+}
+
+// BB: s = r - alpha v, t = M s (s formed on the fly), (t, s), (t, t), (s, s)
+template <typename real, int ND, bool TR>
+__device__ __forceinline__ void bicg_sweep_b(const Ctx<real, ND>& X, const int (&act)[ND], const real (&al)[ND],
+                                             const real* __restrict__ Cdiag, const real* __restrict__ Coff,
+                                             const real* __restrict__ r, const real* __restrict__ vnew,
+                                             real* __restrict__ t, Acc<real> (&a)[3 * ND]) {
+  const int32_t N = X.N, e = X.end(), st = X.stride();
+#pragma unroll 2
+  for (int32_t i = X.first(); i < e; i += st) {
+    const int32_t nx_ = i + st;
+    if (nx_ < e) {
+      prefetch_l2(Cdiag + nx_);
+#pragma unroll
+      for (int s = 0; s < 2 * ND; s++) prefetch_l2(Coff + (size_t)s * N + nx_);
+#pragma unroll
+      for (int k = 0; k < ND; k++) {
+        prefetch_l2(r + (size_t)k * N + nx_);
+        prefetch_l2(vnew + (size_t)k * N + nx_);
+      }
+    }
+    const Cell c = X.cell(i);
+    real diag, cf[2 * ND];
+    c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+    real sP[ND], tt[ND];
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+      sP[k] = tt[k] = real(0);
+      if (!act[k]) continue;
+      const size_t o_ = (size_t)k * N;
+      auto sv = [&](int32_t Q) -> real { return r[o_ + Q] - al[k] * vnew[o_ + Q]; };
+      sP[k] = sv(c.i);
+      real t_ = diag * sP[k];
+#pragma unroll
+      for (int s = 0; s < 2 * ND; s++)
+        if (c.nb[s] >= 0) t_ += cf[s] * sv(c.nb[s]);
+      tt[k] = t_;
+    }
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+      if (!act[k]) continue;
+      t[(size_t)k * N + c.i] = tt[k];
+      a[k].add_prod(tt[k], sP[k]);
+      a[ND + k].add_prod(tt[k], tt[k]);
+      a[2 * ND + k].add_prod(sP[k], sP[k]);
+    }
+  }
+}
+
+// BC: x += alpha p + omega s, r = s - omega t (own cell only), (rhat, r), (r, r)
+template <typename real, int ND>
+__device__ __forceinline__ void bicg_sweep_c(const Ctx<real, ND>& X, const int (&act)[ND], const int (&sc)[ND],
+                                             const real (&al)[ND], const real (&om)[ND],
+                                             const real* __restrict__ pnew, const real* __restrict__ vnew,
+                                             const real* __restrict__ t, const real* __restrict__ rhat,
+                                             real* __restrict__ x, real* __restrict__ r, Acc<real> (&a)[2 * ND]) {
+  const int32_t N = X.N, e = X.end(), st = X.stride();
+#pragma unroll 2
+  for (int32_t P = X.first(); P < e; P += st) {
+    real xn[ND], rr[ND], rh[ND];
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+      xn[k] = rr[k] = rh[k] = real(0);
+      if (!act[k]) continue;
+      const size_t o_ = (size_t)k * N;
+      const real sP = r[o_ + P] - al[k] * vnew[o_ + P];
+      if (sc[k]) {
+        xn[k] = x[o_ + P] + al[k] * pnew[o_ + P];
+        continue;
+      }
+      xn[k] = x[o_ + P] + (al[k] * pnew[o_ + P] + om[k] * sP);
+      rr[k] = sP - om[k] * t[o_ + P];
+      rh[k] = rhat[o_ + P];
+    }
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+      if (!act[k]) continue;
+      const size_t o_ = (size_t)k * N;
+      x[o_ + P] = xn[k];
+      if (sc[k]) continue;
+      r[o_ + P] = rr[k];
+      a[k].add_prod(rh[k], rr[k]);
+      a[ND + k].add_prod(rr[k], rr[k]);
+    }
+  }
+}
+
 // BiCGStab (van der Vorst 1992) on M x = b, M = C or C^T, for the ND velocity
 // components sharing M, each with its own scalars; converged components
 // freeze.  On entry x = x0, r = b - M x0, rhat = r and bs came from bicg_start.
@@ -320,49 +467,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       const real* vold = vv[cur ^ 1];
       real* pnew = pv[cur];
       real* vnew = vv[cur];
-      X.cells_pf([&](const Cell& c) {
-        // every load of the cell (all components) precedes its stores, so the
-        // compiler can issue them together (it must assume the stores alias)
-        real diag, cf[2 * ND];
-        c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
-        real pP[ND], v[ND], rh[ND];
-#pragma unroll
-        for (int k = 0; k < ND; k++) {
-          pP[k] = v[k] = rh[k] = real(0);
-          if (!act[k]) continue;
-          const size_t o_ = (size_t)k * N;
-          auto pn = [&](int32_t Q) -> real {
-            const real rq = r[o_ + Q];
-            return first ? rq : rq + beta[k] * (pold[o_ + Q] - om[k] * vold[o_ + Q]);
-          };
-          pP[k] = pn(c.i);
-          real vv_ = diag * pP[k];
-#pragma unroll
-          for (int s = 0; s < 2 * ND; s++)
-            if (c.nb[s] >= 0) vv_ += cf[s] * pn(c.nb[s]);
-          v[k] = vv_;
-          rh[k] = rhat[o_ + c.i];
-        }
-#pragma unroll
-        for (int k = 0; k < ND; k++) {
-          if (!act[k]) continue;
-          const size_t o_ = (size_t)k * N;
-          pnew[o_ + c.i] = pP[k];
-          vnew[o_ + c.i] = v[k];
-          a[k].add_prod(rh[k], v[k]);
-        }
-      }, [&](int32_t i) {
-        prefetch_l2(Cdiag + i);
-#pragma unroll
-        for (int s = 0; s < 2 * ND; s++) prefetch_l2(Coff + (size_t)s * N + i);
-#pragma unroll
-        for (int k = 0; k < ND; k++) {
-          prefetch_l2(r + (size_t)k * N + i);
-          prefetch_l2(pold + (size_t)k * N + i);
-          prefetch_l2(vold + (size_t)k * N + i);
-          prefetch_l2(rhat + (size_t)k * N + i);
-        }
-      });
+      bicg_sweep_a<real, ND, TR>(X, first, act, beta, om, Cdiag, Coff, r, pold, vold, rhat, pnew, vnew, a);
       const bool ok = reduce_sync<real, ND>(X.g, a, [&](const double* q) {
         bs.it++;
         for (int k = 0; k < ND; k++) {
@@ -391,42 +496,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       }
 #pragma unroll
       for (int k = 0; k < 3 * ND; k++) a[k].zero();
-      const real* vnew = vv[cur];
-      X.cells_pf([&](const Cell& c) {
-        real diag, cf[2 * ND];
-        c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
-        real sP[ND], tt[ND];
-#pragma unroll
-        for (int k = 0; k < ND; k++) {
-          sP[k] = tt[k] = real(0);
-          if (!act[k]) continue;
-          const size_t o_ = (size_t)k * N;
-          auto sv = [&](int32_t Q) -> real { return r[o_ + Q] - al[k] * vnew[o_ + Q]; };
-          sP[k] = sv(c.i);
-          real t_ = diag * sP[k];
-#pragma unroll
-          for (int s = 0; s < 2 * ND; s++)
-            if (c.nb[s] >= 0) t_ += cf[s] * sv(c.nb[s]);
-          tt[k] = t_;
-        }
-#pragma unroll
-        for (int k = 0; k < ND; k++) {
-          if (!act[k]) continue;
-          t[(size_t)k * N + c.i] = tt[k];
-          a[k].add_prod(tt[k], sP[k]);
-          a[ND + k].add_prod(tt[k], tt[k]);
-          a[2 * ND + k].add_prod(sP[k], sP[k]);
-        }
-      }, [&](int32_t i) {
-        prefetch_l2(Cdiag + i);
-#pragma unroll
-        for (int s = 0; s < 2 * ND; s++) prefetch_l2(Coff + (size_t)s * N + i);
-#pragma unroll
-        for (int k = 0; k < ND; k++) {
-          prefetch_l2(r + (size_t)k * N + i);
-          prefetch_l2(vnew + (size_t)k * N + i);
-        }
-      });
+      bicg_sweep_b<real, ND, TR>(X, act, al, Cdiag, Coff, r, vv[cur], t, a);
       const bool ok = reduce_sync<real, 3 * ND>(X.g, a, [&](const double* q) {
         for (int k = 0; k < ND; k++) {
           if (!bs.active[k]) continue;
@@ -458,35 +528,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
         a[k].zero();
         a[ND + k].zero();
       }
-      const real* pnew = pv[cur];
-      const real* vnew = vv[cur];
-      X.own([&](int32_t P) {
-        real xn[ND], rr[ND], rh[ND];
-#pragma unroll
-        for (int k = 0; k < ND; k++) {
-          xn[k] = rr[k] = rh[k] = real(0);
-          if (!act[k]) continue;
-          const size_t o_ = (size_t)k * N;
-          const real sP = r[o_ + P] - al[k] * vnew[o_ + P];
-          if (sc[k]) {
-            xn[k] = x[o_ + P] + al[k] * pnew[o_ + P];
-            continue;
-          }
-          xn[k] = x[o_ + P] + (al[k] * pnew[o_ + P] + om[k] * sP);
-          rr[k] = sP - om[k] * t[o_ + P];
-          rh[k] = rhat[o_ + P];
-        }
-#pragma unroll
-        for (int k = 0; k < ND; k++) {
-          if (!act[k]) continue;
-          const size_t o_ = (size_t)k * N;
-          x[o_ + P] = xn[k];
-          if (sc[k]) continue;
-          r[o_ + P] = rr[k];
-          a[k].add_prod(rh[k], rr[k]);
-          a[ND + k].add_prod(rr[k], rr[k]);
-        }
-      });
+      bicg_sweep_c<real, ND>(X, act, sc, al, om, pv[cur], vv[cur], t, rhat, x, r, a);
       const bool ok = reduce_sync<real, 2 * ND>(X.g, a, [&](const double* q) {
         bs.any = 0;
         for (int k = 0; k < ND; k++) {
@@ -526,6 +568,67 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
 }  // namespace piso
 #include "piso_lines.cuh"
 namespace piso {
+
+// One iteration's cell sweep of the Jacobi CG below (all of the CTA's cells):
+// p = u + beta p, x += alpha p, s = w + beta s, r1 = r - alpha s, w1 = A' u1
+// with u1 = D^-1 r1 formed on the fly at the neighbours, and the three dot
+// products.  The arrays are distinct (ping-pong buffers; p and x are touched
+// only at the own cell), so the pointer arguments are __restrict__: after
+// inlining the compiler still knows a cell's stores cannot alias the next
+// cell's loads, and the 2x unrolled loop keeps two cells' loads in flight.
+template <typename real, int ND>
+__device__ __forceinline__ void cg_jacobi_sweep(const Ctx<real, ND>& X, int first, real al, real be,
+                                                const real* __restrict__ r_i, const real* __restrict__ w_i,
+                                                const real* __restrict__ s_o, const real* __restrict__ Pinv,
+                                                const real* __restrict__ Poff, real* __restrict__ pdir,
+                                                real* __restrict__ x, real* __restrict__ s_n, real* __restrict__ r_n,
+                                                real* __restrict__ w_n, Acc<real> (&a)[3]) {
+  const int32_t N = X.N, e = X.end(), st = X.stride();
+#pragma unroll 2
+  for (int32_t i = X.first(); i < e; i += st) {
+    const int32_t nx_ = i + st;
+    if (nx_ < e) {
+      prefetch_l2(r_i + nx_);
+      prefetch_l2(w_i + nx_);
+      prefetch_l2(s_o + nx_);
+      prefetch_l2(Pinv + nx_);
+      prefetch_l2(pdir + nx_);
+      prefetch_l2(x + nx_);
+#pragma unroll
+      for (int j = 0; j < ND; j++) prefetch_l2(Poff + (size_t)j * N + nx_);
+    }
+    const Cell c = X.cell(i);
+    real pf[2 * ND];
+    p_row<real, ND>(c, N, Poff, pf);
+    auto sQ = [&](int32_t Q) -> real { return first ? w_i[Q] : w_i[Q] + be * s_o[Q]; };
+    auto u1 = [&](int32_t Q) -> real { return (r_i[Q] - al * sQ(Q)) * Pinv[Q]; };
+    const int32_t P = c.i;
+    const real iP = Pinv[P];
+    const real rP = r_i[P];
+    const real pOld = first ? real(0) : pdir[P];
+    const real xP = x[P];
+    const real sP = sQ(P);
+    real uq[2 * ND];
+#pragma unroll
+    for (int s = 0; s < 2 * ND; s++) uq[s] = c.nb[s] >= 0 ? u1(c.nb[s]) : real(0);
+    const real uP = rP * iP;
+    const real p = first ? uP : uP + be * pOld;
+    const real r1 = rP - al * sP;
+    const real u1P = r1 * iP;
+    real w1 = 0;
+#pragma unroll
+    for (int s = 0; s < 2 * ND; s++)
+      if (c.nb[s] >= 0) w1 += pf[s] * (u1P - uq[s]);
+    pdir[P] = p;
+    x[P] = xP + al * p;
+    s_n[P] = sP;
+    r_n[P] = r1;
+    w_n[P] = w1;
+    a[0].add_prod(r1, u1P);
+    a[1].add_prod(w1, u1P);
+    a[2].add_prod(r1, r1);
+  }
+}
 
 // Jacobi-preconditioned CG in the single-reduction form of Chronopoulos and
 // Gear (1989) for  (-P) x = -(b - bmean)  (R7: the pressure system is singular
@@ -635,49 +738,7 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     real* s_n = sb[cur];
     real* r_n = rb[cur ^ 1];
     real* w_n = wb[cur ^ 1];
-    X.cells_pf([&](const Cell& c) {
-      // all loads first (own values, then the neighbours' u1), stores last:
-      // the compiler must assume the stores alias the loads, so this order is
-      // what lets the cell's loads be in flight together
-      real pf[2 * ND];
-      p_row<real, ND>(c, N, Poff, pf);
-      auto sQ = [&](int32_t Q) -> real { return first ? w_i[Q] : w_i[Q] + be * s_o[Q]; };
-      auto u1 = [&](int32_t Q) -> real { return (r_i[Q] - al * sQ(Q)) * Pinv[Q]; };
-      const int32_t P = c.i;
-      const real iP = Pinv[P];
-      const real rP = r_i[P];
-      const real pOld = first ? real(0) : pdir[P];
-      const real xP = x[P];
-      const real sP = sQ(P);
-      real uq[2 * ND];
-#pragma unroll
-      for (int s = 0; s < 2 * ND; s++) uq[s] = c.nb[s] >= 0 ? u1(c.nb[s]) : real(0);
-      const real uP = rP * iP;
-      const real p = first ? uP : uP + be * pOld;
-      const real r1 = rP - al * sP;
-      const real u1P = r1 * iP;
-      real w1 = 0;
-#pragma unroll
-      for (int s = 0; s < 2 * ND; s++)
-        if (c.nb[s] >= 0) w1 += pf[s] * (u1P - uq[s]);
-      pdir[P] = p;
-      x[P] = xP + al * p;
-      s_n[P] = sP;
-      r_n[P] = r1;
-      w_n[P] = w1;
-      a[0].add_prod(r1, u1P);
-      a[1].add_prod(w1, u1P);
-      a[2].add_prod(r1, r1);
-    }, [&](int32_t i) {
-      prefetch_l2(r_i + i);
-      prefetch_l2(w_i + i);
-      prefetch_l2(s_o + i);
-      prefetch_l2(Pinv + i);
-      prefetch_l2(pdir + i);
-      prefetch_l2(x + i);
-#pragma unroll
-      for (int j = 0; j < ND; j++) prefetch_l2(Poff + (size_t)j * N + i);
-    });
+    cg_jacobi_sweep<real, ND>(X, first, al, be, r_i, w_i, s_o, Pinv, Poff, pdir, x, s_n, r_n, w_n, a);
     bool ok;
     if constexpr (sizeof(real) == 4)
       ok = reduce_sync<real, 3, true>(X.g, a, [&](const double* q) {

@@ -217,6 +217,71 @@ __device__ void line_factor(const DomStatic& D, const LinePre<real>& L, int32_t 
   __syncthreads();
 }
 
+// Phase A of an iteration for one staged batch: p = u + beta p, s = w + beta s,
+// x += alpha p, r -= alpha s at the batch's cells, and the staging of r and
+// the line factors; ||r||^2.  Every array is touched through one pointer only
+// (__restrict__: a slot's stores cannot alias the next slot's loads), the
+// loop is unrolled 2x.
+template <typename real>
+__device__ __forceinline__ void line_update_sweep(const LinePre<real>& L, const LineBatch& B, int first, real al, real be,
+                                                  const real* __restrict__ u, const real* __restrict__ w,
+                                                  const real* __restrict__ fa, const real* __restrict__ fm,
+                                                  const real* __restrict__ fc, real* __restrict__ r,
+                                                  real* __restrict__ x, real* __restrict__ pdir, real* __restrict__ s,
+                                                  real* __restrict__ sR, real* __restrict__ sA, real* __restrict__ sB,
+                                                  real* __restrict__ sC, Acc<real>& rr2) {
+#pragma unroll 2
+  for (int32_t k = threadIdx.x; k < B.slots; k += blockDim.x) {
+    int32_t i, sk;
+    bool last;
+    if (!line_slot(L, B, k, i, sk, last)) continue;
+    const real uP = u[i], wP = w[i], rP = r[i], xP = x[i];
+    const real pO = first ? real(0) : pdir[i];
+    const real sO = first ? real(0) : s[i];
+    const real fav = fa[i], fmv = fm[i], fcv = fc[i];
+    const real p = first ? uP : uP + be * pO;
+    const real sv = first ? wP : wP + be * sO;
+    const real rr = rP - al * sv;
+    pdir[i] = p;
+    s[i] = sv;
+    x[i] = xP + al * p;
+    r[i] = rr;
+    sR[sk] = rr;
+    sA[sk] = fav;
+    sB[sk] = fmv * rr;
+    sC[sk] = fcv;
+    rr2.add_prod(rr, rr);
+  }
+}
+
+// Phase B: w = A' u on the CTA's cell range (difference form) and (w, u).
+template <typename real, int ND>
+__device__ __forceinline__ void line_apply_sweep(const Ctx<real, ND>& X, const real* __restrict__ u,
+                                                 const real* __restrict__ Poff, real* __restrict__ w, Acc<real>& wu) {
+  const int32_t N = X.N, e = X.end(), st = X.stride();
+#pragma unroll 2
+  for (int32_t i = X.first(); i < e; i += st) {
+    const int32_t nx_ = i + st;
+    if (nx_ < e) {
+      prefetch_l2(u + nx_);
+#pragma unroll
+      for (int j = 0; j < ND; j++) prefetch_l2(Poff + (size_t)j * N + nx_);
+    }
+    const Cell c = X.cell(i);
+    real pf[2 * ND];
+    p_row<real, ND>(c, N, Poff, pf);
+    const real uP = u[c.i];
+    real uq[2 * ND];
+#pragma unroll
+    for (int q = 0; q < 2 * ND; q++) uq[q] = c.nb[q] >= 0 ? u[c.nb[q]] : uP;
+    real ww = 0;
+#pragma unroll
+    for (int q = 0; q < 2 * ND; q++) ww += pf[q] * (uP - uq[q]);
+    w[c.i] = ww;
+    wu.add_prod(ww, uP);
+  }
+}
+
 // Line-preconditioned CG on (-P) x = -(b - bmean) in the Chronopoulos-Gear
 // form (one reduction per iteration; R7: b is projected to zero mean):
 //   r0 = b' - A' x0, u0 = M^-1 r0, w0 = A' u0
@@ -326,24 +391,8 @@ __device__ bool cg_pressure_line(const Ctx<real, ND>& X, CgState& cs, double rto
     // phase A: vector updates and u = M^-1 r on this CTA's lines
     for (int32_t l0 = L.L0; l0 < L.L1; l0 += L.lb) {
       const LineBatch B = line_batch_begin(D, L, l0);
-      line_batch_cells(L, B, [&](int32_t i, int32_t k, bool) {
-        const real uP = u[i], wP = w[i], rP = r[i], xP = x[i];
-        const real pO = first ? real(0) : pdir[i];
-        const real sO = first ? real(0) : s[i];
-        const real fa = L.fa[i], fm = L.fm[i], fc = L.fc[i];
-        const real p = first ? uP : uP + be * pO;
-        const real sv = first ? wP : wP + be * sO;
-        const real rr = rP - al * sv;
-        pdir[i] = p;
-        s[i] = sv;
-        x[i] = xP + al * p;
-        r[i] = rr;
-        L.sR[k] = rr;
-        L.sA[k] = fa;
-        L.sB[k] = fm * rr;
-        L.sC[k] = fc;
-        c3[2].add_prod(rr, rr);
-      });
+      line_update_sweep<real>(L, B, first, al, be, u, w, L.fa, L.fm, L.fc, r, x, pdir, s, L.sR, L.sA, L.sB, L.sC,
+                              c3[2]);
       line_batch_solve(L, B);
       line_batch_cells(L, B, [&](int32_t i, int32_t k, bool) {
         const real uu = L.sB[k];
@@ -353,23 +402,7 @@ __device__ bool cg_pressure_line(const Ctx<real, ND>& X, CgState& cs, double rto
     }
     if (!plain_sync(X.g)) return false;
     // phase B: w = A' u and (w, u)
-    X.cells_pf([&](const Cell& c) {
-      real pf[2 * ND];
-      p_row<real, ND>(c, N, Poff, pf);
-      const real uP = u[c.i];
-      real uq[2 * ND];
-#pragma unroll
-      for (int q = 0; q < 2 * ND; q++) uq[q] = c.nb[q] >= 0 ? u[c.nb[q]] : uP;
-      real ww = 0;
-#pragma unroll
-      for (int q = 0; q < 2 * ND; q++) ww += pf[q] * (uP - uq[q]);
-      w[c.i] = ww;
-      c3[1].add_prod(ww, uP);
-    }, [&](int32_t i) {
-      prefetch_l2(u + i);
-#pragma unroll
-      for (int j = 0; j < ND; j++) prefetch_l2(Poff + (size_t)j * N + i);
-    });
+    line_apply_sweep<real, ND>(X, u, Poff, w, c3[1]);
     bool ok;
     if constexpr (sizeof(real) == 4)
       ok = reduce_sync<real, 3, true>(X.g, c3, [&](const double* q) {
