@@ -482,6 +482,8 @@ def piso_step(mesh: Mesh, u, p, dt, nu, S=None, bval=None, opts: Optional[Option
     boundary values after the outflow update (they carry over to the next step)."""
     opts = opts or Options()
     bval = mesh.bval if bval is None else bval
+    bval_in = bval
+    updated = bool(opts.update_outflow and mesh.has_outflow)
     if opts.update_outflow:
         bval = outflow_update(mesh, u, bval, dt)
     C, rhs0 = assemble_C(mesh, u, nu, dt, S, bval)
@@ -501,15 +503,72 @@ def piso_step(mesh: Mesh, u, p, dt, nu, S=None, bval=None, opts: Optional[Option
         unew = correct(mesh, h, A, x)
         corr.append(dict(u_in=uk, h=h, b=b, x=x))
         uk, pk = unew, x
-    tape = dict(u=u, p=p, S=S, nu=nu, dt=dt, bval=bval, C=C, rhs0=rhs0, rhs=rhs, ustar=ustar,
-                Pm=Pm, corr=corr, u_out=uk, p_out=pk, adv_info=adv_info, p_infos=p_infos)
+    tape = dict(u=u, p=p, S=S, nu=nu, dt=dt, bval=bval, bval_in=bval_in, outflow_updated=updated, C=C,
+                rhs0=rhs0, rhs=rhs, ustar=ustar, Pm=Pm, corr=corr, u_out=uk, p_out=pk, adv_info=adv_info,
+                p_infos=p_infos)
     return uk, pk, tape
 
 
-def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Options] = None):
+def outflow_update_adjoint(mesh: Mesh, u, bval_in, dt, g_used):
+    """Transpose of ``outflow_update`` at (u, bval_in): given dL/d(bval after
+    the update) per side, return (dL/d bval_in per side, dL/du).  Forward:
+    b1 = (1 - f) b + f u_O on outflow faces (f = c/(1+c)); q_out = sum of the
+    outflow faces' fluxes N J T_j . b1, q_in = -sum of the other Dirichlet
+    faces' fluxes of b; outflow faces become (q_in / q_out) b1 (when q_out is
+    not 0), the others are unchanged."""
+    d, N = mesh.ndim, mesh.N
+    g_in = [g.copy() for g in g_used]
+    gu = np.zeros((d, N))
+    if not mesh.has_outflow:
+        return g_in, gu
+    # forward quantities
+    b1 = [b.copy() for b in bval_in]
+    fac = [np.zeros(N) for _ in range(mesh.nsides)]
+    q_in = q_out = 0.0
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        O = np.nonzero(mesh.is_outflow[s])[0]
+        if len(O):
+            c = 2.0 * dt * np.abs(np.einsum("nk,kn->n", mesh.T[O, j, :], mesh.u_m[s][:, O]))
+            fac[s][O] = c / (1.0 + c)
+            b1[s][:, O] = bval_in[s][:, O] - fac[s][O][None, :] * (bval_in[s][:, O] - u[:, O])
+            q_out += float(np.sum(n * mesh.face_flux_b(s, b1[s])[O]))
+        D = np.nonzero(mesh.is_bface[s] & ~mesh.is_outflow[s])[0]
+        q_in -= float(np.sum(n * mesh.face_flux_b(s, bval_in[s])[D]))
+    scaled = q_out != 0.0
+    scale = q_in / q_out if scaled else 1.0
+    # dL/dscale = sum over outflow faces of g_used . b1
+    gscale = 0.0
+    for s in range(mesh.nsides):
+        O = np.nonzero(mesh.is_outflow[s])[0]
+        gscale += float(np.sum(g_used[s][:, O] * b1[s][:, O]))
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        O = np.nonzero(mesh.is_outflow[s])[0]
+        D = np.nonzero(mesh.is_bface[s] & ~mesh.is_outflow[s])[0]
+        JT = mesh.J[:, None] * mesh.T[:, j, :]          # d(flux)/d(face value): J T_j
+        g_in[s][:, O] = 0.0
+        if len(O):
+            gb1 = scale * g_used[s][:, O]
+            if scaled:
+                gb1 = gb1 - gscale * q_in / q_out ** 2 * n * JT[O].T
+            g_in[s][:, O] = (1.0 - fac[s][O])[None, :] * gb1
+            np.add.at(gu.T, O, (fac[s][O][None, :] * gb1).T)
+        if scaled and len(D):
+            g_in[s][:, D] += gscale / q_out * (-n) * JT[D].T
+    return g_in, gu
+
+
+def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Options] = None,
+                      want_bval: bool = False):
     """Reverse of ``piso_step``: given dL/du^{n+1} and dL/dp^{n+1}, return
-    dL/du^n, dL/dp^n, dL/dS and dL/dnu (the outflow update and the boundary
-    values are held fixed).
+    dL/du^n, dL/dp^n, dL/dS and dL/dnu, and with ``want_bval`` also dL/d(the
+    boundary values before the step's outflow update), per side [nsides][d][N].
+    The boundary values enter the momentum right-hand side (Dirichlet fluxes,
+    Eq. velRHSdiscrete: u_b (2 alpha nu - N_f U_b)/J with U_b = J T_j . u_b)
+    and every corrector's divergence (R6: N_f J T_j . u_b); the advective
+    outflow update (Eq. advOut) is differentiated too, contributing to dL/du^n
+    through the cell values it moves towards.
 
     ``opts.grad_adv`` / ``opts.grad_p`` select the gradient paths of Sec. 2.4:
     the full adjoint is J^Adv + J^P + J^none, and dropping a path treats that
@@ -527,6 +586,7 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
     gw = np.zeros((d, N))             # dL/d(alpha_jj / A)
     gu = np.array(du_out, dtype=np.float64, copy=True)
     gp_last = np.array(dp_out, dtype=np.float64, copy=True)
+    gbs = []                          # dL/db of every corrector (divergence right-hand sides)
     ncorr = len(tape["corr"])
     for k in reversed(range(ncorr)):
         cr = tape["corr"][k]
@@ -550,6 +610,7 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
                 gw[j, P] += 0.5 * (y[P] - y[F]) * (x[P] - x[F])
             # b = div(h) + boundary flux
             gh += divergence_T(mesh, gb)
+            gbs.append(gb)
         # without the pressure path (Sec. 2.4) x is a constant of the backward
         # pass: gx is dropped and neither b nor P receives a gradient
         # h = (rhs0 - H u_in) / A
@@ -592,6 +653,28 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
         ub = bval[s][:, B]
         gnu += float(np.sum(grhs0[:, B] * ub * (2.0 * mesh.alpha[j, B] / mesh.J[B])[None, :]))
     gu_in += np.einsum("n,njk,jn->kn", mesh.J, mesh.T, gU)
+    # boundary values used by the step: rhs0 (assembly) and the divergences
+    gbu = [np.zeros((d, N)) for _ in range(mesh.nsides)]
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        B = np.nonzero(mesh.is_bface[s])[0]
+        if not len(B):
+            continue
+        ub = bval[s][:, B]
+        TjB = mesh.T[B, j, :].T                                    # [d][nB]
+        tu = np.sum(TjB * ub, axis=0)                             # T_j . u_b
+        a = 2.0 * mesh.alpha[j, B] * nu / mesh.J[B] - n * tu
+        g = grhs0[:, B]
+        gbu[s][:, B] = g * a[None, :] - n * TjB * np.sum(g * ub, axis=0)[None, :]
+        for gbk in gbs:
+            gbu[s][:, B] += n * (mesh.J[B] * gbk[B])[None, :] * TjB
+    if tape.get("outflow_updated", False):
+        g_in, gu_o = outflow_update_adjoint(mesh, tape["u"], tape["bval_in"], dt, gbu)
+        gu_in = gu_in + gu_o
+    else:
+        g_in = gbu
+    if want_bval:
+        return gu_in, gp_in, gS, gnu, g_in
     return gu_in, gp_in, gS, gnu
 
 

@@ -27,18 +27,20 @@ def _fd_check(case, seed, eps=1e-4, rtol=1e-6):
     pbar = rng.standard_normal(N)
     du, dp, dS = rng.standard_normal((d, N)), rng.standard_normal(N), rng.standard_normal((d, N))
     dnu = 0.3 * nu0
-    # the adjoint holds boundary values fixed: freeze the outflow update
-    bval = O.outflow_update(m, u0, m.bval, case.dt)
-    opts = O.Options(update_outflow=False)
+    # boundary values (incl. the advective outflow faces, whose update the
+    # adjoint differentiates) perturbed on their faces only
+    bval = [b.copy() for b in m.bval]
+    dbv = [np.where(m.is_bface[s][None, :], rng.standard_normal((d, N)), 0.0) for s in range(m.nsides)]
 
     def L(t):
-        u1, p1, _ = O.piso_step(m, u0 + t * du, p0 + t * dp, case.dt, nu0 + t * dnu, S0 + t * dS,
-                                bval, opts)
+        bv = [b + t * db for b, db in zip(bval, dbv)]
+        u1, p1, _ = O.piso_step(m, u0 + t * du, p0 + t * dp, case.dt, nu0 + t * dnu, S0 + t * dS, bv)
         return float(np.sum(ubar * u1) + np.sum(pbar * p1))
 
-    _, _, tape = O.piso_step(m, u0, p0, case.dt, nu0, S0, bval, opts)
-    gu, gp, gS, gnu = O.piso_step_adjoint(m, tape, ubar, pbar)
-    adj = float(np.sum(gu * du) + np.sum(gp * dp) + np.sum(gS * dS) + gnu * dnu)
+    _, _, tape = O.piso_step(m, u0, p0, case.dt, nu0, S0, bval)
+    gu, gp, gS, gnu, gbv = O.piso_step_adjoint(m, tape, ubar, pbar, want_bval=True)
+    adj = float(np.sum(gu * du) + np.sum(gp * dp) + np.sum(gS * dS) + gnu * dnu +
+                sum(np.sum(g * db) for g, db in zip(gbv, dbv)))
     fd = fd4(L, eps)
     assert abs(adj - fd) <= rtol * max(abs(fd), 1e-12), (adj, fd)
     return adj, fd
@@ -46,6 +48,8 @@ def _fd_check(case, seed, eps=1e-4, rtol=1e-6):
 
 @pytest.mark.parametrize("name", ["cavity", "periodic", "bfs", "channel3d"])
 def test_adjoint_matches_central_fd(name):
+    """All inputs at once, boundary values included (through the Dirichlet
+    fluxes, the divergence and, on the step, the advective outflow update)."""
     if name == "cavity":
         c = W.cavity2d(6, nu=0.05, dt=0.05)
     elif name == "periodic":
@@ -122,3 +126,28 @@ def test_direct_optimisation_initial_scale():
         grad = float(np.sum(gu * base))
         scale -= lr * grad / max(float(np.mean(base ** 2)), 1e-12)
     assert loss < 1e-5, (it, loss, scale)
+
+
+def test_outflow_update_adjoint_alone():
+    """The transpose of the advective outflow update (Eq. advOut with the
+    inflow/outflow rescaling, R10) against central differences of the update."""
+    c = W.bfs2d(n_in=(4, 3), n_ch=6, n_out=3, half=3, nu=0.01, dt=0.05)
+    m = O.mesh_from_case(c)
+    d, N = m.ndim, m.N
+    rng = np.random.default_rng(21)
+    u0 = 0.5 + 0.3 * rng.standard_normal((d, N))
+    bval = [b + np.where(m.is_bface[s][None, :], 0.1 * rng.standard_normal((d, N)), 0.0)
+            for s, b in enumerate(m.bval)]
+    g_used = [np.where(m.is_bface[s][None, :], rng.standard_normal((d, N)), 0.0) for s in range(m.nsides)]
+    dbv = [np.where(m.is_bface[s][None, :], rng.standard_normal((d, N)), 0.0) for s in range(m.nsides)]
+    du = rng.standard_normal((d, N))
+
+    def L(t):
+        out = O.outflow_update(m, u0 + t * du, [b + t * db for b, db in zip(bval, dbv)], c.dt)
+        return float(sum(np.sum(g * o) for g, o in zip(g_used, out)))
+
+    g_in, gu = O.piso.outflow_update_adjoint(m, u0, bval, c.dt, g_used)
+    adj = float(np.sum(gu * du) + sum(np.sum(g * db) for g, db in zip(g_in, dbv)))
+    fd = fd4(L, 1e-5)
+    assert abs(adj - fd) <= 1e-8 * max(abs(fd), 1e-12), (adj, fd)
+    assert np.abs(gu).max() > 0          # the update does depend on the cell values
