@@ -245,8 +245,11 @@ piso_status piso_last_stats(piso_domain* d, piso_stats* stats);
  * may be NULL to skip) and *dnu = dL/dnu (host double, may be NULL).
  * tape is the buffer filled by the forward step (NULL = the domain's own
  * record of its last step).  Linear solves are differentiated by transposed
- * solves (C^T via BiCGStab, P symmetric via CG); boundary values and the
- * outflow update are held fixed. */
+ * solves (C^T via BiCGStab, P symmetric via CG).  Boundary velocities are
+ * differentiable too (App. A.4): dL/d(boundary values before the step's
+ * advective-outflow update) is kept in the domain (read it with
+ * piso_get_boundary_adjoint), and the outflow update (Eq. advOut) is
+ * differentiated, so du_in includes the path through the outflow faces. */
 piso_status piso_step_adjoint(piso_domain* d, const void* tape, const void* du_out,
                               const void* dp_out, void* du_in, void* dp_in, void* dS,
                               double* dnu, void* stream, piso_stats* stats);
@@ -255,6 +258,12 @@ piso_status piso_step_adjoint(piso_domain* d, const void* tape, const void* du_o
  * host array values ([ndim][nbf] doubles), or set them from it. */
 piso_status piso_get_boundary(piso_domain* d, double* values);
 piso_status piso_set_boundary(piso_domain* d, const double* values);
+
+/* dL/d(boundary-face values) computed by the domain's last piso_step_adjoint
+ * (or batch adjoint), with respect to the values the step started from (before
+ * its advective-outflow update): host [ndim][nbf] doubles, the face order of
+ * piso_set_dirichlet.  Synchronises with the device. */
+piso_status piso_get_boundary_adjoint(piso_domain* d, double* values);
 
 /* Last error message of the domain (or of the most recent failing creation
  * call when d is NULL).  The string is owned by the library. */

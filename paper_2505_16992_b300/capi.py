@@ -68,6 +68,7 @@ _SIGS = {
     "piso_step_adjoint": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _D, _P, C.POINTER(Stats)]),
     "piso_get_boundary": (C.c_int, [_P, _D]),
     "piso_set_boundary": (C.c_int, [_P, _D]),
+    "piso_get_boundary_adjoint": (C.c_int, [_P, _D]),
     "piso_last_error": (C.c_char_p, [_P]),
     "piso_domain_destroy": (None, [_P]),
     "piso_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.POINTER(Options), C.POINTER(_P)]),

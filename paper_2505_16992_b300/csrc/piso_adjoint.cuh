@@ -23,7 +23,9 @@ struct AdjCall {
   const real* h[4];
   const real* xk[4];
   const real* uc[4];
-  const real* bval;          // [d][nbf]
+  const real* bval;          // [d][nbf] boundary values used by the step
+  const real* bval_in;       // [d][nbf] boundary values before its outflow update
+  const real* un;            // [d][N]   u^n
   // seeds and results
   const real* du_out;        // [d][N]
   const real* dp_out;        // [N] or nullptr
@@ -31,6 +33,7 @@ struct AdjCall {
   real* dp_in;               // [N] or nullptr
   real* dS;                  // [d][N] or nullptr
   double* dnu;               // device scalar
+  real* gbval;               // [d][nbf] dL/d(boundary values before the outflow update)
   // scratch
   real* Poff;                // [d][N] pressure matrix rebuilt from A
   real* Pdiag;               // [N]
@@ -77,10 +80,13 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   __shared__ RefState rs;
   __shared__ double s_mean, s_idt;
   __shared__ float s_idt_f;
+  __shared__ double s_ymean;          // sum over correctors of mean(y) (the transposed pressure solutions)
+  __shared__ double s_ob[4];          // outflow adjoint: scale, dL/dscale, q_in, q_out
   copy_to_smem(&D, A.dom);
   if (threadIdx.x == 0) {
     s_idt = 1.0 / A.hdr[0];
     s_idt_f = (float)s_idt;
+    s_ymean = 0.0;
   }
   __syncthreads();
   const int32_t N = D.N;
@@ -142,6 +148,11 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
         A.Pdiag[P] = pd;
         A.Pinv[P] = real(1) / (-pd);
 #pragma unroll
+        for (int s = 0; s < NSD; s++)
+          if (c.nb[s] < 0)
+#pragma unroll
+            for (int i = 0; i < ND; i++) A.gbval[(size_t)i * nbf + (-1 - c.nb[s])] = 0;
+#pragma unroll
         for (int i = 0; i < ND; i++) {
           A.grhs0[(size_t)i * N + P] = 0;
           A.gw[(size_t)i * N + P] = 0;
@@ -194,10 +205,26 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
                                             A.ce, A.crb, A.cwb, A.csb, A.cp, A.istats, A.dstats, k))
       return;
     // R3: dP = -y (x) x on the pattern -> d(alpha/A); h_bar = gu + div^T y;
-    //     gg = h_bar / A; dL/dA and dL/drhs0 from h = A^-1 (rhs0 - H u)
+    //     gg = h_bar / A; dL/dA and dL/drhs0 from h = A^-1 (rhs0 - H u);
+    //     boundary values: b has the flux N_b J_P T_j . u_b (R6), so
+    //     dL/du_b += N_b J_P T_j (y_P - mean y) (the mean is subtracted at the end)
+    Acc<real> ay[1];
+    ay[0].zero();
     X.cells([&](const Cell& c) {
       const int32_t P = c.i;
       const real yP = path_p ? A.cx[P] : real(0), xP = path_p ? xk[P] : real(0);
+      if (path_p) {
+        ay[0].add(yP);
+#pragma unroll
+        for (int s = 0; s < NSD; s++) {
+          if (c.nb[s] >= 0) continue;
+          const int j = s >> 1;
+          const real nJy = ((s & 1) ? real(1) : real(-1)) * J[P] * yP;
+          const int32_t f = -1 - c.nb[s];
+#pragma unroll
+          for (int i = 0; i < ND; i++) A.gbval[(size_t)i * nbf + f] += nJy * Tm(j, i, P);
+        }
+      }
       const real aP = A.Cdiag[P];
       real Fb[ND];
 #pragma unroll
@@ -233,7 +260,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       }
       A.gA[P] -= ga / aP;
     });
-    if (!plain_sync(g)) return;
+    if (!reduce_sync<real, 1>(g, ay, [&](const double* q) { s_ymean += q[0] / (double)N; })) return;
     // R4: gu_in = -H^T gg; dL/dH = -gg (x) u_in on the pattern
     X.cells([&](const Cell& c) {
       const int32_t P = c.i;
@@ -347,18 +374,30 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
         A.W[(size_t)j * N + P] = w;
       }
     }
-    // nu from the Dirichlet terms of the right-hand side (Eq. velRHSdiscrete)
+    // nu from the Dirichlet terms of the right-hand side (Eq. velRHSdiscrete),
+    // and the boundary values there: rhs0_i += u_b,i (2 alpha nu / J - N_f T_j . u_b)
     const real invJ = real(1) / J[P];
+    const real nu_s = pick<real>(A.hdr[1], (float)A.hdr[1]);
 #pragma unroll
     for (int s = 0; s < NSD; s++) {
       const int32_t F = c.nb[s];
       if (F >= 0) continue;
       const int32_t f = -1 - F;
-      const real two_a = real(2) * AL[(size_t)(s >> 1) * N + P] * invJ;
-      real acc = 0;
+      const int j = s >> 1;
+      const real n = (s & 1) ? real(1) : real(-1);
+      const real two_a = real(2) * AL[(size_t)j * N + P] * invJ;
+      real acc = 0, tu = 0;
+      real ub[ND];
 #pragma unroll
-      for (int i = 0; i < ND; i++) acc += gr[i] * A.bval[(size_t)i * nbf + f];
+      for (int i = 0; i < ND; i++) {
+        ub[i] = A.bval[(size_t)i * nbf + f];
+        acc += gr[i] * ub[i];
+        tu += Tm(j, i, P) * ub[i];
+      }
       anu[0].add(acc * two_a);
+      const real a = two_a * nu_s - n * tu;
+#pragma unroll
+      for (int i = 0; i < ND; i++) A.gbval[(size_t)i * nbf + f] += gr[i] * a - n * Tm(j, i, P) * acc;
     }
   });
   if (!plain_sync(g)) return;
@@ -398,9 +437,109 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       A.du_in[(size_t)i * N + P] += J[P] * v;
     }
   });
-  reduce_sync<real, 1>(g, anu, [&](const double* q) {
-    if (g.rank == 0) *A.dnu = q[0];
-  });
+  if (!reduce_sync<real, 1>(g, anu, [&](const double* q) {
+        if (g.rank == 0) *A.dnu = q[0];
+      }))
+    return;
+  if (nbf == 0) return;
+  // Boundary values: finish dL/du_b (the divergence term used y, not y - mean y)
+  // and, with advective outflow faces, differentiate the outflow update
+  // (App. A.3, Eq. advOut, R10): b1 = (1 - f) b + f u_P on outflow faces,
+  // q_out = sum N J T_j . b1 over them, q_in = -sum N J T_j . b over the other
+  // Dirichlet faces, u_b = (q_in / q_out) b1 on outflow faces.
+  const real ym = pick<real>(s_ymean, (float)s_ymean);
+  const real* um = reinterpret_cast<const real*>(D.bf_um);
+  const real dt_s = pick<real>(A.hdr[0], (float)A.hdr[0]);
+  auto face_fac = [&](int32_t P, int j, int32_t f) -> real {
+    real tu = 0;
+#pragma unroll
+    for (int i = 0; i < ND; i++) tu += Tm(j, i, P) * um[(size_t)i * nbf + f];
+    const real cc = real(2) * dt_s * fabs(tu);
+    return cc / (real(1) + cc);
+  };
+  if (D.n_out > 0) {
+    Acc<real> ao[3];   // dL/dscale, q_in, q_out
+    ao[0].zero();
+    ao[1].zero();
+    ao[2].zero();
+    X.cells([&](const Cell& c) {
+      const int32_t P = c.i;
+#pragma unroll
+      for (int s = 0; s < NSD; s++) {
+        if (c.nb[s] >= 0) continue;
+        const int j = s >> 1;
+        const real nJ = ((s & 1) ? real(1) : real(-1)) * J[P];
+        const int32_t f = -1 - c.nb[s];
+        real flux_in = 0, flux_b1 = 0, gdot = 0;
+#pragma unroll
+        for (int i = 0; i < ND; i++) {
+          real* gb = A.gbval + (size_t)i * nbf + f;
+          *gb -= ym * nJ * Tm(j, i, P);
+          const real b = A.bval_in[(size_t)i * nbf + f];
+          flux_in += nJ * Tm(j, i, P) * b;
+          if (D.bf_out[f]) {
+            const real fac = face_fac(P, j, f);
+            const real b1 = b - fac * (b - A.un[(size_t)i * N + P]);
+            flux_b1 += nJ * Tm(j, i, P) * b1;
+            gdot += *gb * b1;
+          }
+        }
+        if (D.bf_out[f]) {
+          ao[0].add(gdot);
+          ao[2].add(flux_b1);
+        } else {
+          ao[1].add(-flux_in);
+        }
+      }
+    });
+    if (!reduce_sync<real, 3>(g, ao, [&](const double* q) {
+          const bool scaled = q[2] != 0.0;
+          s_ob[0] = scaled ? q[1] / q[2] : 1.0;
+          s_ob[1] = scaled ? q[0] : 0.0;   // no rescaling when q_out = 0
+          s_ob[2] = q[1];
+          s_ob[3] = scaled ? q[2] : 1.0;
+        }))
+      return;
+    const real sc = pick<real>(s_ob[0], (float)s_ob[0]);
+    const real c_out = pick<real>(-s_ob[1] * s_ob[2] / (s_ob[3] * s_ob[3]), (float)(-s_ob[1] * s_ob[2] / (s_ob[3] * s_ob[3])));
+    const real c_in = pick<real>(-s_ob[1] / s_ob[3], (float)(-s_ob[1] / s_ob[3]));
+    X.cells([&](const Cell& c) {
+      const int32_t P = c.i;
+#pragma unroll
+      for (int s = 0; s < NSD; s++) {
+        if (c.nb[s] >= 0) continue;
+        const int j = s >> 1;
+        const real nJ = ((s & 1) ? real(1) : real(-1)) * J[P];
+        const int32_t f = -1 - c.nb[s];
+        if (D.bf_out[f]) {
+          const real fac = face_fac(P, j, f);
+#pragma unroll
+          for (int i = 0; i < ND; i++) {
+            real* gb = A.gbval + (size_t)i * nbf + f;
+            const real gb1 = sc * *gb + c_out * nJ * Tm(j, i, P);
+            *gb = (real(1) - fac) * gb1;
+            A.du_in[(size_t)i * N + P] += fac * gb1;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < ND; i++) A.gbval[(size_t)i * nbf + f] += c_in * nJ * Tm(j, i, P);
+        }
+      }
+    });
+  } else {
+    X.cells([&](const Cell& c) {
+      const int32_t P = c.i;
+#pragma unroll
+      for (int s = 0; s < NSD; s++) {
+        if (c.nb[s] >= 0) continue;
+        const int j = s >> 1;
+        const real nJ = ((s & 1) ? real(1) : real(-1)) * J[P];
+        const int32_t f = -1 - c.nb[s];
+#pragma unroll
+        for (int i = 0; i < ND; i++) A.gbval[(size_t)i * nbf + f] -= ym * nJ * Tm(j, i, P);
+      }
+    });
+  }
 }
 
 template <typename real, int ND, int MAXT>

@@ -71,6 +71,7 @@ struct piso_domain {
   int8_t* bf_out = nullptr;
   void* bf_um = nullptr;
   void* bval = nullptr;
+  void* gbval = nullptr;       // [d][nbf] dL/d(boundary values) of the last adjoint
   // workspace arrays (element pointers)
   void* ws[64] = {nullptr};
   void* tape_ws = nullptr;     // internal tape (last step)
@@ -230,7 +231,7 @@ int ws_units(int k, int nd) {
 }
 
 struct TapeLayout {
-  size_t hdr, un, cdiag, coff, ustar, h[4], xk[4], uc[4], bval, total;
+  size_t hdr, un, cdiag, coff, ustar, h[4], xk[4], uc[4], bval, bval_in, total;
 };
 
 TapeLayout tape_layout(const piso_domain* d) {
@@ -254,6 +255,7 @@ TapeLayout tape_layout(const piso_domain* d) {
     t.uc[k] = take(nd * N);
   }
   t.bval = take(nd * std::max(d->nbf, 1));
+  t.bval_in = take(nd * std::max(d->nbf, 1));
   t.total = off;
   return t;
 }
@@ -283,6 +285,7 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
     c.uc[k] = (real*)(tb + L.uc[k]);
   }
   c.bval_rec = (real*)(tb + L.bval);
+  c.bval_in_rec = (real*)(tb + L.bval_in);
   c.hdr = (double*)(tb + L.hdr);
   c.U = (real*)d->ws[W_U];
   c.rhs0 = (real*)d->ws[W_RHS0];
@@ -812,6 +815,7 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
     d->bf_out = (int8_t*)a.take(nbf1);
     d->bf_um = a.take((size_t)nd * nbf1 * e);
     d->bval = a.take((size_t)nd * nbf1 * e);
+    d->gbval = a.take((size_t)nd * nbf1 * e);
     for (int k = 0; k < W_COUNT; k++) d->ws[k] = a.take((size_t)ws_units(k, nd) * N * e);
     d->tape_ws = a.take(tape_layout(d).total);
     d->bar = (uint32_t*)a.take(64);
@@ -867,6 +871,21 @@ piso_status piso_set_options(piso_domain* d, const piso_options* opts) {
     resolve_precond(d);
     return choose_shape(d);
   }
+  return PISO_OK;
+}
+
+piso_status piso_get_boundary_adjoint(piso_domain* d, double* values) {
+  if (!d || !values) return fail(d, PISO_EINVAL, "NULL argument");
+  if (!d->finalized) return fail(d, PISO_ESTATE, "domain not finalized");
+  const int nbf1 = std::max(d->nbf, 1);
+  std::vector<char> buf((size_t)d->ndim * nbf1 * d->elem);
+  CUDA_TRY(d, cudaMemcpy(buf.data(), d->gbval, buf.size(), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < d->ndim; k++)
+    for (int f = 0; f < d->nbf; f++) {
+      const size_t i = (size_t)k * nbf1 + f;
+      values[(size_t)k * d->nbf + f] = d->prec == PISO_FP64 ? reinterpret_cast<double*>(buf.data())[i]
+                                                           : (double)reinterpret_cast<float*>(buf.data())[i];
+    }
   return PISO_OK;
 }
 

@@ -30,6 +30,7 @@ struct FwdCall {
   real* xk[4];               // [N]    mean-free pressure per corrector
   real* uc[4];               // [d][N] corrector outputs (last one unused)
   real* bval_rec;            // [d][nbf] boundary values used by this step
+  real* bval_in_rec;         // [d][nbf] boundary values before the outflow update
   double* hdr;               // tape header: dt, nu
   // scratch
   real* U;                   // [d][N]
@@ -144,7 +145,10 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       const real n = (s & 1) ? real(1) : real(-1);
       real ub[ND];
 #pragma unroll
-      for (int k = 0; k < ND; k++) ub[k] = A.bval[(size_t)k * nbf + f];
+      for (int k = 0; k < ND; k++) {
+        ub[k] = A.bval[(size_t)k * nbf + f];
+        A.bval_in_rec[(size_t)k * nbf + f] = ub[k];
+      }
       if (D.bf_out[f]) {
         real tu = 0;
 #pragma unroll
@@ -178,7 +182,11 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   }
   for (int32_t f = flo + threadIdx.x; f < fhi; f += blockDim.x)
 #pragma unroll
-    for (int k = 0; k < ND; k++) A.bval_rec[(size_t)k * nbf + f] = A.bval[(size_t)k * nbf + f];
+    for (int k = 0; k < ND; k++) {
+      const real v = A.bval[(size_t)k * nbf + f];
+      A.bval_rec[(size_t)k * nbf + f] = v;
+      if (D.n_out == 0) A.bval_in_rec[(size_t)k * nbf + f] = v;
+    }
   if (threadIdx.x == 0 && g.rank == 0) {
     A.hdr[0] = A.dt;
     A.hdr[1] = A.nu;

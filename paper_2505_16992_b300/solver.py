@@ -181,6 +181,14 @@ class Domain:
         a, vp = capi.dbuf(values)
         capi.check(self.lib.piso_set_boundary(self.h, vp), self.h)
 
+    def boundary_adjoint(self) -> np.ndarray:
+        """dL/d(boundary-face values) of the last adjoint, [ndim][nbf] (App. A.4:
+        boundary velocities are differentiable)."""
+        out = np.zeros((self.ndim, max(self.nbf, 0)))
+        capi.check(self.lib.piso_get_boundary_adjoint(self.h, out.ctypes.data_as(C.POINTER(C.c_double))),
+                   self.h)
+        return out
+
 
 class Batch:
     """Independent domains stepped together in one persistent launch."""

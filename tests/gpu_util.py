@@ -48,3 +48,15 @@ def oracle_step(mesh, case, u, p, S=None, bval=None, opts=None):
 
 def sync():
     torch.cuda.synchronize()
+
+
+def bval_faces(m, bval):
+    """Oracle boundary values (per cell side, [nsides][d][N]) -> the library's
+    face order [d][nbf] (blocks in order, sides in order, faces in side order)."""
+    faces = []
+    for bi in range(len(m.res)):
+        for s in range(m.nsides):
+            cells = m.side_cells(bi, s)
+            if m.is_bface[s, cells[0]]:
+                faces.append(bval[s][:, cells])
+    return np.concatenate(faces, axis=1) if faces else np.zeros((m.ndim, 0))

@@ -8,7 +8,7 @@ import oracle as O
 from paper_2505_16992_b300 import capi
 from paper_2505_16992_b300 import workloads as W
 from paper_2505_16992_b300.solver import piso_step, rollout
-from gpu_util import gpu_domain, host, rel_err, to_dev
+from gpu_util import bval_faces, gpu_domain, host, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -33,11 +33,13 @@ def _adjoint_parity(case, seed=0, tol=ADJ_REL, precision="fp64", pred_grad_p=0, 
     du, dp, dS, dnu, ast = dom.step_adjoint(to_dev(dom, ubar, d), to_dev(dom, pbar))
     assert ast["status"] == "PISO_OK", ast
     oa = O.Options(pred_grad_p=bool(pred_grad_p), grad_adv=bool(grad_paths & 1), grad_p=bool(grad_paths & 2))
-    gu, gp, gS, gnu = O.piso_step_adjoint(m, tape, ubar, pbar, oa)
+    gu, gp, gS, gnu, gbv = O.piso_step_adjoint(m, tape, ubar, pbar, oa, want_bval=True)
     # a solve left out of the backward pass (Sec. 2.4) does not run at all
     assert (sum(ast["adv_iters"]) > 0) == bool(grad_paths & 1), ast
     assert (sum(ast["p_iters"]) > 0) == bool(grad_paths & 2), ast
     errs = dict(u=rel_err(host(du), gu), S=rel_err(host(dS), gS), nu=abs(dnu - gnu) / max(abs(gnu), 1e-300))
+    if np.any(m.is_bface):
+        errs["bval"] = rel_err(dom.boundary_adjoint(), bval_faces(m, gbv))
     if pred_grad_p:
         errs["p"] = rel_err(host(dp), gp)
     else:
@@ -165,3 +167,33 @@ def test_autograd_rollout_checkpointed():
     assert rel_err(host(u0.grad), gu) <= 1e-7
     assert rel_err(host(S.grad), gS) <= 1e-7
     assert abs(float(nu.grad) - gnu) <= 1e-7 * abs(gnu)
+
+
+def test_boundary_adjoint_matches_gpu_finite_difference():
+    """dL/d(boundary values) on the multi-block step with inflow and advective
+    outflow (App. A.4: boundary velocities are differentiable; the outflow
+    update, Eq. advOut, is differentiated): <ubar, du1> along a perturbation
+    of every boundary-face value, 4th-order central differences of the GPU
+    forward, against the adjoint's directional derivative."""
+    c = W.bfs2d(n_in=(16, 8), n_ch=32, n_out=16, half=8, dt=0.02)
+    dom = gpu_domain(c, p_rtol=1e-12)
+    d, N = c.ndim, c.ncells
+    rng = np.random.default_rng(12)
+    u0 = to_dev(dom, c.u0 + 0.2 * rng.standard_normal((d, N)), d)
+    p0 = to_dev(dom, c.p0)
+    ubar = to_dev(dom, rng.standard_normal((d, N)), d)
+    b0 = dom.get_boundary()
+    db = rng.standard_normal(b0.shape)
+
+    def L(t):
+        dom.set_boundary(b0 + t * db)
+        u1, _, _ = dom.step(u0, p0, c.dt, c.nu)
+        return float((ubar * u1).sum())
+
+    dom.set_boundary(b0)
+    dom.step(u0, p0, c.dt, c.nu)
+    dom.step_adjoint(ubar, None)
+    adj = float(np.sum(dom.boundary_adjoint() * db))
+    e = 1e-4
+    fd = (8 * (L(e) - L(-e)) - (L(2 * e) - L(-2 * e))) / (12 * e)
+    assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
