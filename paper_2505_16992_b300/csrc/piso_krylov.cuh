@@ -584,7 +584,7 @@ __device__ __forceinline__ void cg_jacobi_sweep(const Ctx<real, ND>& X, int firs
                                                 real* __restrict__ x, real* __restrict__ s_n, real* __restrict__ r_n,
                                                 real* __restrict__ w_n, Acc<real> (&a)[3]) {
   const int32_t N = X.N, e = X.end(), st = X.stride();
-#pragma unroll 2
+#pragma unroll 4
   for (int32_t i = X.first(); i < e; i += st) {
     const int32_t nx_ = i + st;
     if (nx_ < e) {
