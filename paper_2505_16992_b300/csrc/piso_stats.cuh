@@ -66,6 +66,33 @@ __device__ __forceinline__ void st_block_sum(double (&v)[NV], double* s_red /* [
   __syncthreads();
 }
 
+// Deterministic block reduction of NV accumulators in their own arithmetic
+// (float pairs on the FP32 pipe in the FP32 mode; FP64 is a small fraction of
+// FP32 throughput on this GPU), converted to double once, in thread 0.
+template <typename real, int NV>
+__device__ __forceinline__ void st_acc_reduce(Acc<real> (&a)[NV], double* s_red /* [32][NV] */, double (&out)[NV]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a[k].shfl_down_add(off);
+    if (lane == 0) s_red[warp * NV + k] = a[k].pack();
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      Acc<real> t;
+      t.zero();
+      if (lane < nw) t.unpack_add(s_red[lane * NV + k]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t.shfl_down_add(off);
+      out[k] = t.to_double();
+    }
+  }
+  __syncthreads();
+}
+
 // grid (ny, chunks); writes the frame's record entries of this chunk (chunk 0
 // also n and the means)
 template <typename real>
@@ -299,9 +326,7 @@ __global__ void __launch_bounds__(256) stats_part_kernel(const __grid_constant__
       for (int i = 0; i < NQ; i++) s1[i].add(q[(size_t)i * G.N + cell]);
     }
     double v[NQ];
-#pragma unroll
-    for (int i = 0; i < NQ; i++) v[i] = s1[i].to_double();
-    st_block_sum<NQ>(v, s_red);
+    st_acc_reduce<real, NQ>(s1, s_red, v);
     if (threadIdx.x == 0)
 #pragma unroll
       for (int i = 0; i < NQ; i++) s_mean[i] = c1 > c0 ? v[i] / (double)(c1 - c0) : 0.0;
@@ -339,9 +364,12 @@ __global__ void __launch_bounds__(256) stats_part_kernel(const __grid_constant__
     }
   }
   double v[U];
+  {
+    Acc<real> ra[U];   // the same sums as reduction accumulators (same member type)
 #pragma unroll
-  for (int u = 0; u < U; u++) v[u] = acc[u].get();
-  st_block_sum<U>(v, s_red);
+    for (int u = 0; u < U; u++) ra[u].v = acc[u].v;
+    st_acc_reduce<real, U>(ra, s_red, v);
+  }
   if (threadIdx.x == 0) {
     double* R = part + ((size_t)y * S + sidx) * G.rsize;
     const double n = (double)(c1 - c0);
