@@ -26,6 +26,9 @@ finite-volume PISO scheme of arXiv:2505.16992:
 * Sec. 2.3 and App. A.4 (gradients): linear solves are differentiated by the
   transposed solve  A^T db = dx,  dA = -db (x) x  on the sparsity pattern; every
   other operation by its exact transpose.
+* App. A.5 (solvers): the advection-diffusion BiCGStab may be ILU(0)-
+  preconditioned, from the start or only after the plain solve failed; the
+  transposed solve of the adjoint uses the factorisation of C^T.
 * Sec. 2.4 (gradient paths, Eq. jnone): the paths through the advection solve
   and through the pressure solves can each be left out of the backward pass
   (that solve's output is then a constant of the backward pass), leaving the
@@ -80,6 +83,8 @@ class Options:
     update_outflow: bool = True  # App. A.3 advective outflow update before the step
     grad_adv: bool = True        # Sec. 2.4: keep the gradient paths through the advection solve
     grad_p: bool = True          # Sec. 2.4: keep the gradient paths through the pressure solves
+    adv_precond: str = "none"    # App. A.5: BiCGStab preconditioner "none" | "ilu" (ILU(0)) |
+                                 # "ilu_on_failure" (ILU(0) only after the plain solve failed)
 
 
 class Mesh:
@@ -434,6 +439,31 @@ def use_direct(mesh, opts: Options) -> bool:
     return opts.solver == "direct"
 
 
+def bicgstab_adv(A, matvec, b, x0, opts: Options):
+    """One advection-diffusion solve by BiCGStab with the preconditioning of
+    App. A.5: none, ILU(0) of the assembled matrix A throughout, or ILU(0) only
+    when the unpreconditioned solve did not converge (it then restarts from
+    x0).  info.precond is "none", "ilu" or "ilu_after_failure"; info.iters
+    counts the iterations of every attempt."""
+    if opts.adv_precond not in ("none", "ilu", "ilu_on_failure"):
+        raise ValueError(f"unknown adv_precond {opts.adv_precond!r}")
+    if opts.adv_precond == "ilu":
+        x, info = krylov.bicgstab(matvec, b, x0, opts.adv_rtol, opts.atol, opts.maxit,
+                                  precond=krylov.ilu0_preconditioner(A))
+        info.precond = "ilu"
+        return x, info
+    x, info = krylov.bicgstab(matvec, b, x0, opts.adv_rtol, opts.atol, opts.maxit)
+    info.precond = "none"
+    if info.converged or opts.adv_precond == "none":
+        return x, info
+    first = info.iters
+    x, info = krylov.bicgstab(matvec, b, x0, opts.adv_rtol, opts.atol, opts.maxit,
+                              precond=krylov.ilu0_preconditioner(A))
+    info.iters += first
+    info.precond = "ilu_after_failure"
+    return x, info
+
+
 def solve_C(mesh, C, rhs, x0, opts: Options):
     out = np.empty_like(rhs)
     infos = []
@@ -442,9 +472,9 @@ def solve_C(mesh, C, rhs, x0, opts: Options):
         for c in range(rhs.shape[0]):
             out[c] = krylov.direct_solve(Cs, rhs[c])
         return out, infos
+    Cs = to_sparse(mesh, C) if opts.adv_precond != "none" else None
     for c in range(rhs.shape[0]):
-        out[c], info = krylov.bicgstab(lambda v: matvec(mesh, C, v), rhs[c], x0[c],
-                                       opts.adv_rtol, opts.atol, opts.maxit)
+        out[c], info = bicgstab_adv(Cs, lambda v: matvec(mesh, C, v), rhs[c], x0[c], opts)
         infos.append(info)
     return out, infos
 
@@ -456,9 +486,9 @@ def solve_C_T(mesh, C, rhs, opts: Options):
         for c in range(rhs.shape[0]):
             out[c] = krylov.direct_solve(CsT, rhs[c])
         return out
+    CsT = to_sparse(mesh, C).T.tocsr() if opts.adv_precond != "none" else None
     for c in range(rhs.shape[0]):
-        out[c], _ = krylov.bicgstab(lambda v: matvec_T(mesh, C, v), rhs[c], np.zeros(mesh.N),
-                                    opts.adv_rtol, opts.atol, opts.maxit)
+        out[c], _ = bicgstab_adv(CsT, lambda v: matvec_T(mesh, C, v), rhs[c], np.zeros(mesh.N), opts)
     return out
 
 
