@@ -39,14 +39,27 @@ def cg_words_per_cell(d: int, it_p: int, line: bool) -> float:
     return (d + 4) + (d + 3) + it_p * (d + 11)
 
 
-def fwd_words_per_cell(d: int, adv_iters, p_iters, line: bool = False) -> float:
+def bicg_words_per_cell(d: int, it_a: int, ilu: bool) -> float:
+    """Stored-array words per cell of one BiCGStab solve.  Plain: BA 8d+1, BB
+    5d+1, BC 8d per iteration.  ILU(0)-preconditioned (five phases): PA r, p, v
+    in, p out, then the two triangular sweeps (level order, mask and pivot
+    1.5 + 1 words, the C row 2d+1, y written, read and rewritten) 11d+7; PB C,
+    y, rhat -> v 5d+1; PC r, v in and the sweeps 9d+7; PD C, z, r, v -> t 6d+1;
+    PE r, v, y, z, t, rhat, x -> x, r 9d; plus the factorisation once per solve
+    (level order, mask, C row and the transposed entries, pivot out) 4d+3.5."""
+    if ilu:
+        return (4 * d + 3.5) + it_a * (40 * d + 16)
+    return it_a * (21 * d + 2)
+
+
+def fwd_words_per_cell(d: int, adv_iters, p_iters, line: bool = False, ilu: bool = False) -> float:
     """Stored-array words per cell one forward launch touches (each array once
     per phase; neighbour re-reads are cache hits).  One line per kernel phase."""
     it_a = max(adv_iters) if adv_iters else 0
     w = 0.0
     w += d * d + 3 * d + 1            # F1: u, T, J -> u^n copy, U
     w += 11 * d + 3                   # F2: u, S, U, alpha, J -> C (2d+1), 1/A, alpha/A, rhs0, r, rhat, u*
-    w += it_a * (21 * d + 2)          # BiCGStab: BA 8d+1, BB 5d+1, BC 8d per iteration
+    w += bicg_words_per_cell(d, it_a, ilu)   # predictor BiCGStab
     for k, it_p in enumerate(p_iters):
         w += (d * d + 8 * d + 4) if k == 0 else (d * d + 6 * d + 4)   # C1: (P), h, J T.h
         w += d + 3                    # C2: divergence, x0
@@ -58,7 +71,7 @@ def fwd_words_per_cell(d: int, adv_iters, p_iters, line: bool = False) -> float:
     return w
 
 
-def adj_words_per_cell(d: int, adv_iters, p_iters, line: bool = False) -> float:
+def adj_words_per_cell(d: int, adv_iters, p_iters, line: bool = False, ilu: bool = False) -> float:
     it_a = max(adv_iters) if adv_iters else 0
     w = 6 * d + 3                     # R0 extra on the first pass: rebuild P, clear accumulators
     if line and any(p_iters):
@@ -70,7 +83,7 @@ def adj_words_per_cell(d: int, adv_iters, p_iters, line: bool = False) -> float:
         w += d * d + 7 * d + 6        # R3: d(alpha/A), div^T y, gg, dL/dA, dL/drhs0
         w += 9 * d                    # R4: -H^T gg, dL/dH
     w += 6 * d + 3                    # R5: start of the C^T solve
-    w += it_a * (21 * d + 2)          # BiCGStab on C^T
+    w += bicg_words_per_cell(d, it_a, ilu)   # BiCGStab on C^T
     w += 9 * d + 3                    # R6: dL/dC from the predictor, dS, du (1/dt part)
     w += d * d + 5 * d + 3            # R7: assembly adjoint
     return w
@@ -234,7 +247,8 @@ def time_variant(case, prec, kw, steps, with_adj, flush):
         b.synchronize()
         tot += a.elapsed_time(b) / 1e3
     return {"steps_per_s": steps / tot, "p_iters": st["p_iters"][:2], "p_rounds": st["p_rounds"][:2],
-            "p_resid": st["p_resid"][:2]}
+            "p_resid": st["p_resid"][:2], "adv_iters": st["adv_iters"][:d],
+            "adv_precond_used": st["adv_precond_used"]}
 
 
 def time_statistics(dom, u, p, nu, steps, flush, peak):
@@ -383,6 +397,23 @@ def run_batch(args):
     return 0
 
 
+ADV_PRECOND = {"none": 0, "ilu": 1, "ilu_on_failure": 2}     # piso_options.adv_precond
+
+
+def ilu_compare(prec, rtol, steps, with_adj, flush):
+    """Steps/s of the three BiCGStab preconditioner settings on a channel whose
+    cell sizes vary strongly (steeper tanh walls, gamma 3, and a 20x larger
+    time step than the headline channel), the case the incomplete-LU
+    preconditioner is meant for."""
+    from paper_2505_16992_b300 import workloads as W
+    case = W.channel3d(64, 48, 32, gamma=3.0, dt=0.2)
+    out = {"workload": "channel3d 64x48x32, tanh walls gamma 3, dt 0.2 (otherwise as the headline)"}
+    for name, code in ADV_PRECOND.items():
+        out[name] = time_variant(case, prec, dict(adv_rtol=rtol, p_rtol=rtol, adv_precond=code), steps, with_adj,
+                                 flush)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,11 +428,16 @@ def main():
     ap.add_argument("--refine", type=float, default=0.0, help="FP32: FP64-refined pressure tolerance")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "line"],
                     help="pressure CG preconditioner (auto: the autotuner times both on anisotropic grids)")
+    ap.add_argument("--adv-precond", default="none", choices=["none", "ilu", "ilu_on_failure"],
+                    help="BiCGStab preconditioner of the predictor solve (ILU(0), or ILU(0) after a failed plain solve)")
+    ap.add_argument("--no-ilu-compare", action="store_true",
+                    help="skip timing the BiCGStab preconditioners on the strongly stretched channel")
     ap.add_argument("--compare", action="store_true",
                     help="also time FP64 and refined FP32 at matched pressure tolerances")
     ap.add_argument("--workload", default="channel3d",
-                    choices=["channel3d", "channel3d-mid", "channel3d-large", "batch64"],
+                    choices=["channel3d", "channel3d-mid", "channel3d-large", "channel3d-stretched", "batch64"],
                     help="channel3d: 64x48x32 (default); channel3d-large: 256x192x128 (HBM-bound sizes); "
+                         "channel3d-stretched: 64x48x32 with tanh gamma 3 and dt 0.2 (for --adv-precond); "
                          "batch64: 64 independent 2D simulations in one launch")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -426,14 +462,16 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    sizes = {"channel3d": (64, 48, 32), "channel3d-mid": (160, 120, 80), "channel3d-large": (256, 192, 128)}
-    case = W.channel3d(*sizes[args.workload])
+    sizes = {"channel3d": (64, 48, 32), "channel3d-mid": (160, 120, 80), "channel3d-large": (256, 192, 128),
+             "channel3d-stretched": (64, 48, 32)}
+    stretched = args.workload == "channel3d-stretched"      # the case for the ILU(0) BiCGStab (App. A.5)
+    case = W.channel3d(*sizes[args.workload], **(dict(gamma=3.0, dt=0.2) if stretched else {}))
     prec = args.precision
     rtol = 1e-6 if prec == "fp32" else 1e-10
     pc_code = {"auto": capi.PISO_PRECOND_AUTO, "jacobi": capi.PISO_PRECOND_JACOBI, "line": capi.PISO_PRECOND_LINE}
     opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
                                 block_threads=args.threads, p_refine_rtol=args.refine,
-                                p_precond=pc_code[args.precond])
+                                p_precond=pc_code[args.precond], adv_precond=ADV_PRECOND[args.adv_precond])
     dom = Domain.from_case(case, prec, opts)
     d, N = case.ndim, case.ncells
     w = 4 if prec == "fp32" else 8
@@ -520,7 +558,8 @@ def main():
 
     # roofline of the dominant kernel (the persistent forward-step kernel)
     peak, peak_kind = measured_peaks()
-    words = fwd_words_per_cell(d, st["adv_iters"][:d], st["p_iters"][:2], line=pc_used == "y-line")
+    words = fwd_words_per_cell(d, st["adv_iters"][:d], st["p_iters"][:2], line=pc_used == "y-line",
+                               ilu=st["adv_precond_used"] == 1)
     alg_bytes = words * N * w
     fwd_avg_s = sum(fwd_ms) / len(fwd_ms) / 1e3
     achieved = alg_bytes / fwd_avg_s / 1e9
@@ -568,6 +607,10 @@ def main():
     if not args.no_stats:
         statistics = time_statistics(dom, u_out, p_out, case.nu, max(5, args.steps // 3), flush, peak)
 
+    ilu_cmp = None
+    if not args.no_ilu_compare and args.workload == "channel3d":
+        ilu_cmp = ilu_compare(prec, rtol, max(5, args.steps // 3), with_adj, flush)
+
     compare = None
     if args.compare:
         compare = {}
@@ -591,7 +634,7 @@ def main():
                        "l2": "flushed between timed steps (256 MB write, untimed)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "launch": {"threads": shape[0], "ctas": shape[1], "autotuned": args.threads == 0},
-                       "pressure_precond": pc_used},
+                       "pressure_precond": pc_used, "adv_precond": args.adv_precond},
             "iterations": {"adv": st["adv_iters"][:d], "p": st["p_iters"][:2],
                            "adj_adv": adj_st["adv_iters"][:d] if adj_st else None,
                            "adj_p": adj_st["p_iters"][:2] if adj_st else None},
@@ -607,11 +650,17 @@ def main():
         }
         if compare is not None:
             line["precision_compare"] = compare
+        if ilu_cmp is not None:
+            line["adv_precond_compare"] = ilu_cmp
         if paths is not None:
             line["grad_paths"] = paths
         if statistics is not None:
             line["statistics"] = statistics
-        if args.workload != "channel3d":
+        if stretched:
+            line["config"]["workload"] = line["config"]["workload"].replace("gamma 2", "gamma 3").replace(
+                "dt 0.01", "dt 0.2")
+            line["metric"] = line["metric"].replace("channel", "channel (tanh gamma 3, dt 0.2)")
+        elif args.workload != "channel3d":
             tag = "x".join(str(v) for v in sizes[args.workload])
             line["config"]["workload"] = line["config"]["workload"].replace("64x48x32", tag)
             line["metric"] = line["metric"].replace("64x48x32", tag)

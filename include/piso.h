@@ -98,12 +98,34 @@ typedef struct {
                             its y-lines inside each block, solved exactly (Thomas factors formed once
                             per step; the CG iteration then takes two group barriers instead of one).
                             Batches (piso_batch_*) always use Jacobi. */
+  int32_t adv_precond;   /* preconditioner of the advection-diffusion BiCGStab (App. A.5: incomplete
+                            LU, for grids with strongly varying cell sizes, enabled per case, and
+                            optionally only after the plain solve failed):
+                            PISO_ADV_PRECOND_NONE (default);
+                            PISO_ADV_PRECOND_ILU: right-preconditioned by zero-fill ILU of C, the
+                            factorisation formed once per step (the adjoint forms it again from the
+                            recorded C and applies its transpose to the transposed solve);
+                            PISO_ADV_PRECOND_ILU_ON_FAILURE: the plain BiCGStab first, and, if some
+                            component did not converge (iteration limit, breakdown or NaN), a restart
+                            from the same initial guess with the ILU preconditioner; the reported
+                            iterations count both attempts.
+                            Each CTA factors the diagonal block of C formed by the cells it owns
+                            (couplings between CTAs are left out of the preconditioner only), so the
+                            triangular solves need no grid-wide synchronisation; with ctas = 1 this
+                            is ILU(0) of the whole matrix in cell order.  The level tables are built
+                            on the host whenever the launch layout changes (finalize, set_options,
+                            autotune).  Batches reject any value but NONE (PISO_EINVAL). */
 } piso_options;
 
 /* Values of piso_options.p_precond. */
 #define PISO_PRECOND_AUTO 0
 #define PISO_PRECOND_JACOBI 1
 #define PISO_PRECOND_LINE 2
+
+/* Values of piso_options.adv_precond. */
+#define PISO_ADV_PRECOND_NONE 0
+#define PISO_ADV_PRECOND_ILU 1
+#define PISO_ADV_PRECOND_ILU_ON_FAILURE 2
 
 /* Bits of piso_options.grad_paths. */
 #define PISO_GRAD_ADV 1   /* paths through the advection (predictor) solve */
@@ -121,6 +143,8 @@ typedef struct {
                              CG that stalled (its best residual norm did not halve in 200
                              iterations) and was finished by refinement counts as round 1 */
   double p_rhs_norm[4];   /* norm of each pressure solve's (projected) right-hand side */
+  int32_t adv_precond_used; /* the BiCGStab ran ILU-preconditioned: 0 no, 1 from the start,
+                               2 after the plain attempt failed (PISO_ADV_PRECOND_ILU_ON_FAILURE) */
 } piso_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libpiso.so")
 PISO_FP64, PISO_FP32 = 0, 1
 PISO_GRAD_ADV, PISO_GRAD_P = 1, 2          # piso_options.grad_paths bits (Sec. 2.4 gradient paths)
 PISO_PRECOND_AUTO, PISO_PRECOND_JACOBI, PISO_PRECOND_LINE = 0, 1, 2   # piso_options.p_precond
+PISO_ADV_PRECOND_NONE, PISO_ADV_PRECOND_ILU, PISO_ADV_PRECOND_ILU_ON_FAILURE = 0, 1, 2   # .adv_precond
 STATUS = {0: "PISO_OK", 1: "PISO_EINVAL", 2: "PISO_ECUDA", 3: "PISO_ENOCONV", 4: "PISO_EBREAKDOWN",
           5: "PISO_ENAN", 6: "PISO_ETIMEOUT", 7: "PISO_ESTATE", 8: "PISO_ENOMEM"}
 
@@ -22,19 +23,20 @@ class Options(C.Structure):
                 ("p_rtol", C.c_double), ("atol", C.c_double), ("adv_maxit", C.c_int32),
                 ("p_maxit", C.c_int32), ("block_threads", C.c_int32), ("ctas", C.c_int32),
                 ("timeout_s", C.c_double), ("fault_withhold_cta", C.c_int32), ("p_refine_rtol", C.c_double),
-                ("p_inner_rtol", C.c_double), ("grad_paths", C.c_int32), ("p_precond", C.c_int32)]
+                ("p_inner_rtol", C.c_double), ("grad_paths", C.c_int32), ("p_precond", C.c_int32),
+                ("adv_precond", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("error_bits", C.c_int32), ("adv_iters", C.c_int32 * 3),
                 ("p_iters", C.c_int32 * 4), ("adv_resid", C.c_double * 3), ("p_resid", C.c_double * 4),
-                ("p_rounds", C.c_int32 * 4), ("p_rhs_norm", C.c_double * 4)]
+                ("p_rounds", C.c_int32 * 4), ("p_rhs_norm", C.c_double * 4), ("adv_precond_used", C.c_int32)]
 
     def as_dict(self):
         return dict(status=STATUS.get(self.status, self.status), error_bits=self.error_bits,
                     adv_iters=list(self.adv_iters), p_iters=list(self.p_iters),
                     adv_resid=list(self.adv_resid), p_resid=list(self.p_resid), p_rounds=list(self.p_rounds),
-                    p_rhs_norm=list(self.p_rhs_norm))
+                    p_rhs_norm=list(self.p_rhs_norm), adv_precond_used=self.adv_precond_used)
 
 
 class PisoError(RuntimeError):

@@ -64,6 +64,9 @@ struct AdjCall {
   real* lfm;
   real* lfc;
   int32_t p_line;
+  IluTab ilu;                // ILU(0) tables of the launch layout (when adv_ilu)
+  real* ilud;                // [N] ILU(0) reciprocal pivots (rebuilt here from the taped C)
+  int32_t adv_ilu;           // 0 none, 1 ILU(0), 2 ILU(0) after a failed plain solve
   uint32_t* bar;
   double* partials;
   int32_t* status;
@@ -320,16 +323,42 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
         !reduce_sync<real, 2 * ND>(g, a, [&](const double* q) { bicg_start<ND>(bs, q, o.adv_rtol, o.atol, g.status); }))
       return;
   }
-  if (path_adv && !bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t))
-    return;
+  // the transposed solve with the preconditioning of the forward one: the
+  // factors of C^T are the transposed factors of C (same pivots)
+  int ilu_used = 0;
+  if (path_adv) {
+    IluPre<real> IP{};
+    if (A.adv_ilu) IP = ilu_setup<real>(A.ilu, A.ilud, g.rank);
+    if (A.adv_ilu == 1) {
+      ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff);
+      ilu_used = 1;
+      if (!bicgstab_ilu<real, ND, true>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv[0], A.vv[0],
+                                        A.pv[1], A.vv[1], A.t))
+        return;
+    } else {
+      if (!bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t))
+        return;
+      if (A.adv_ilu == 2 && !bicg_all_conv<ND>(bs)) {
+        bicg_restart<real, ND>(X, bs, A.z, static_cast<const real*>(nullptr), A.r, A.rhat, o.adv_rtol, o.atol,
+                               g.status);
+        ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff);
+        ilu_used = 2;
+        if (!bicgstab_ilu<real, ND, true>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv[0],
+                                          A.vv[0], A.pv[1], A.vv[1], A.t))
+          return;
+      }
+    }
+  }
   if (path_adv && threadIdx.x == 0 && g.rank == 0) {
     int nc = 0;
     for (int k = 0; k < ND; k++) {
-      A.istats[k] = bs.iters[k];
+      A.istats[k] = bs.iters[k] + bs.iters_prev[k];
       A.dstats[k] = sqrt(bs.res2[k]);
       if (!bs.conv[k]) nc = 1;
     }
+    A.istats[3] = ilu_used;
     if (nc) atomicOr(g.status, PISO_ERR_NOCONV_ADV);
+    if (bs.err) atomicOr(g.status, bs.err);
   }
   // R6: dC = -z (x) u* on the pattern; dL/drhs0 += z; outputs dS and the
   //     1/dt part of du_in; W = T . z for the predictor pressure gradient

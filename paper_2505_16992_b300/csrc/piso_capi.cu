@@ -92,6 +92,11 @@ struct piso_domain {
   DomStatic h_static;
   double aniso = 1.0;          // max over cells of alpha_yy / alpha_kk (k != y): y-anisotropy of the grid
   int p_line = 0;              // the pressure CG uses the y-line preconditioner
+  // ILU(0) tables of the BiCGStab preconditioner for the current launch layout
+  void* ilu_buf = nullptr;
+  IluTab ilu_tab{};
+  bool ilu_ready = false;      // tables match (ncta, threads, ownership) of the launches
+  int ilu_key[3] = {-1, -1, -1};
   bool pending = false;
   cudaStream_t pending_stream = nullptr;
   int pending_kind = 0;        // 1 forward, 2 adjoint
@@ -208,7 +213,7 @@ void put(std::vector<char>& buf, size_t i, double v) {
 enum WsIdx {
   W_U, W_RHS0, W_R, W_RHAT, W_P0, W_P1, W_V0, W_V1, W_T, W_POFF, W_PDIAG, W_FH, W_B, W_CX,
   W_CRB0, W_CRB1, W_CWB0, W_CWB1, W_CSB0, W_CSB1, W_CP, W_PINV, W_INVA, W_AW, W_X64, W_RIN, W_CE,
-  W_LFA, W_LFM, W_LFC,
+  W_LFA, W_LFM, W_LFC, W_ILUD,
   // adjoint scratch
   A_GA, A_GCOFF, A_GRHS0, A_GW, A_W, A_GG, A_GU, A_GX, A_Z, A_DU,
   W_COUNT
@@ -219,7 +224,7 @@ int ws_units(int k, int nd) {
   switch (k) {
     case W_PDIAG: case W_B: case W_CX: case W_CRB0: case W_CRB1: case W_CWB0: case W_CWB1: case W_CSB0:
     case W_CSB1: case W_CP: case A_GA: case A_GX: case W_PINV: case W_INVA: case W_RIN: case W_CE:
-    case W_LFA: case W_LFM: case W_LFC:
+    case W_LFA: case W_LFM: case W_LFC: case W_ILUD:
       return 1;
     case W_X64:
       return 2;     // N doubles (two float units; the FP64 mode over-allocates)
@@ -318,6 +323,9 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
   c.lfm = (real*)d->ws[W_LFM];
   c.lfc = (real*)d->ws[W_LFC];
   c.p_line = d->p_line;
+  c.ilu = d->ilu_tab;
+  c.ilud = (real*)d->ws[W_ILUD];
+  c.adv_ilu = d->opts.adv_precond;
   c.bar = d->bar;
   c.partials = d->partials;
   c.status = d->status;
@@ -433,6 +441,112 @@ const void* adj_kernel_ptr(int prec, int nd, int threads = 512) {
   return prec == PISO_FP64 ? adj_ptr_t<double>(nd, threads) : adj_ptr_t<float>(nd, threads);
 }
 
+// ILU(0) tables for the current launch layout (App. A.5 preconditioner of the
+// BiCGStab).  Each CTA preconditions with the diagonal block of the cells it
+// owns, so the tables follow the kernels' ownership rule: contiguous ranges
+// [N r / ncta, N (r + 1) / ncta) when the neighbour table fits in shared
+// memory, otherwise chunks of `threads` cells dealt round-robin to the CTAs.
+// A cell's level is one more than the highest level among its neighbours in
+// the same block with a lower index (0 if none); the forward substitution
+// walks the levels upwards, the backward substitution downwards.
+template <int ND>
+void ilu_levels(const DomStatic& D, const std::vector<int32_t>& own, std::vector<int32_t>& lvl,
+                std::vector<uint16_t>& mask) {
+  const int32_t N = D.N;
+  for (int32_t i = 0; i < N; i++) {
+    const Cell c = locate<ND>(D, i);
+    int32_t L = 0;
+    uint16_t m = 0;
+    for (int s = 0; s < 2 * ND; s++) {
+      const int32_t k = c.nb[s];
+      if (k < 0 || k == i || own[k] != own[i]) continue;
+      if (k < i) {
+        m |= (uint16_t)(1u << s);
+        L = std::max(L, lvl[k] + 1);
+      } else {
+        m |= (uint16_t)(1u << (8 + s));
+      }
+    }
+    lvl[i] = L;
+    mask[i] = m;
+  }
+}
+
+piso_status build_ilu(piso_domain* d) {
+  if (d->opts.adv_precond == PISO_ADV_PRECOND_NONE) return PISO_OK;
+  SolverOpts so = solver_opts(d->opts);
+  launch_smem(d, d->ncta, &so);
+  const int contiguous = so.nbt_cap > 0 ? 1 : 0;
+  const int ncta = d->ncta, T = d->threads;
+  if (d->ilu_ready && d->ilu_key[0] == ncta && d->ilu_key[1] == T && d->ilu_key[2] == contiguous) return PISO_OK;
+  d->ilu_ready = false;
+  const int32_t N = d->N;
+  std::vector<int32_t> own(N);
+  if (contiguous) {
+    for (int r = 0; r < ncta; r++) {
+      const int32_t lo = (int32_t)(((int64_t)N * r) / ncta), hi = (int32_t)(((int64_t)N * (r + 1)) / ncta);
+      for (int32_t i = lo; i < hi; i++) own[i] = r;
+    }
+  } else {
+    for (int32_t i = 0; i < N; i++) own[i] = (int32_t)((i / T) % ncta);
+  }
+  std::vector<int32_t> lvl(N);
+  std::vector<uint16_t> mask(N);
+  if (d->ndim == 3) ilu_levels<3>(d->h_static, own, lvl, mask);
+  else ilu_levels<2>(d->h_static, own, lvl, mask);
+  std::vector<int32_t> cnt(ncta, 0), nlev(ncta, 0), base(ncta, 0), lidx(ncta + 1, 0);
+  for (int32_t i = 0; i < N; i++) {
+    cnt[own[i]]++;
+    nlev[own[i]] = std::max(nlev[own[i]], lvl[i] + 1);
+  }
+  for (int r = 1; r < ncta; r++) base[r] = base[r - 1] + cnt[r - 1];
+  for (int r = 0; r < ncta; r++) lidx[r + 1] = lidx[r] + nlev[r] + 1;
+  std::vector<int32_t> lstart(lidx[ncta], 0);
+  for (int32_t i = 0; i < N; i++) lstart[lidx[own[i]] + lvl[i] + 1]++;
+  for (int r = 0; r < ncta; r++)
+    for (int l = 1; l <= nlev[r]; l++) lstart[lidx[r] + l] += lstart[lidx[r] + l - 1];
+  std::vector<int32_t> cur(lstart), order(N);
+  for (int32_t i = 0; i < N; i++) order[base[own[i]] + cur[lidx[own[i]] + lvl[i]]++] = i;
+  // one device buffer: order | mask | lstart | lidx | base
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t o_order = 0, o_mask = al(sizeof(int32_t) * N), o_ls = o_mask + al(sizeof(uint16_t) * N),
+               o_lidx = o_ls + al(sizeof(int32_t) * lstart.size()), o_base = o_lidx + al(sizeof(int32_t) * (ncta + 1)),
+               total = o_base + al(sizeof(int32_t) * ncta);
+  if (d->ilu_buf) {
+    CUDA_TRY(d, cudaDeviceSynchronize());   // no launch in flight may still read the old tables
+    CUDA_TRY(d, cudaFree(d->ilu_buf));
+    d->ilu_buf = nullptr;
+  }
+  CUDA_TRY(d, cudaMalloc(&d->ilu_buf, total));
+  char* bb = (char*)d->ilu_buf;
+  CUDA_TRY(d, cudaMemcpy(bb + o_order, order.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(bb + o_mask, mask.data(), sizeof(uint16_t) * N, cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(bb + o_ls, lstart.data(), sizeof(int32_t) * lstart.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(bb + o_lidx, lidx.data(), sizeof(int32_t) * (ncta + 1), cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(bb + o_base, base.data(), sizeof(int32_t) * ncta, cudaMemcpyHostToDevice));
+  d->ilu_tab.order = (const int32_t*)(bb + o_order);
+  d->ilu_tab.mask = (const uint16_t*)(bb + o_mask);
+  d->ilu_tab.lstart = (const int32_t*)(bb + o_ls);
+  d->ilu_tab.lidx = (const int32_t*)(bb + o_lidx);
+  d->ilu_tab.base = (const int32_t*)(bb + o_base);
+  d->ilu_key[0] = ncta;
+  d->ilu_key[1] = T;
+  d->ilu_key[2] = contiguous;
+  d->ilu_ready = true;
+  return PISO_OK;
+}
+
+// A launch with the ILU(0) preconditioner needs tables of its own layout.
+piso_status check_ilu(piso_domain* d) {
+  if (d->opts.adv_precond == PISO_ADV_PRECOND_NONE) return PISO_OK;
+  SolverOpts so = solver_opts(d->opts);
+  launch_smem(d, d->ncta, &so);
+  if (!d->ilu_ready || d->ilu_key[0] != d->ncta || d->ilu_key[1] != d->threads ||
+      d->ilu_key[2] != (so.nbt_cap > 0 ? 1 : 0))
+    return fail(d, PISO_ESTATE, "ILU(0) tables do not match the launch layout");
+  return PISO_OK;
+}
+
 int max_coresident(const void* kernel, int threads, int* sms_out) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -459,7 +573,7 @@ piso_status choose_shape(piso_domain* d) {
   d->threads = threads;
   d->ncta = want;
   d->sms = sms;
-  return PISO_OK;
+  return build_ilu(d);
 }
 
 piso_status collect_stats(piso_domain* d, piso_stats* st) {
@@ -486,6 +600,7 @@ piso_status collect_stats(piso_domain* d, piso_stats* st) {
       st->p_rounds[k] = d->h_istats[8 + k];
       st->p_rhs_norm[k] = d->h_dstats[8 + k];
     }
+    st->adv_precond_used = d->h_istats[3];
   }
   if (s != PISO_OK) {
     const char* what = s == PISO_ETIMEOUT ? "group barrier timed out"
@@ -507,6 +622,8 @@ piso_status enqueue_readback(piso_domain* d, cudaStream_t st) {
 template <typename real>
 piso_status launch_fwd(piso_domain* d, const void* u_in, const void* p_in, void* u_out, void* p_out,
                               double dt, double nu, const void* S, void* tape, cudaStream_t st) {
+  const piso_status ci = check_ilu(d);
+  if (ci) return ci;
   Launch<FwdCall<real>> L;
   memset(&L, 0, sizeof L);
   L.ngroups = 1;
@@ -549,6 +666,7 @@ void piso_default_options(piso_options* o) {
   o->p_inner_rtol = 1e-4;
   o->grad_paths = PISO_GRAD_ADV | PISO_GRAD_P;
   o->p_precond = PISO_PRECOND_AUTO;
+  o->adv_precond = PISO_ADV_PRECOND_NONE;
 }
 
 piso_status piso_domain_create(int32_t ndim, int32_t prec, piso_domain** out) {
@@ -648,6 +766,8 @@ static piso_status validate_options(piso_domain* d, const piso_options* o) {
   if (o->grad_paths & ~(PISO_GRAD_ADV | PISO_GRAD_P)) return fail(d, PISO_EINVAL, "grad_paths: unknown bits");
   if (o->p_precond < PISO_PRECOND_AUTO || o->p_precond > PISO_PRECOND_LINE)
     return fail(d, PISO_EINVAL, "p_precond must be PISO_PRECOND_AUTO, _JACOBI or _LINE");
+  if (o->adv_precond < PISO_ADV_PRECOND_NONE || o->adv_precond > PISO_ADV_PRECOND_ILU_ON_FAILURE)
+    return fail(d, PISO_EINVAL, "adv_precond must be PISO_ADV_PRECOND_NONE, _ILU or _ILU_ON_FAILURE");
   return PISO_OK;
 }
 
@@ -943,7 +1063,7 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
   if (!d->finalized) return fail(d, PISO_ESTATE, "autotune before finalize");
   cudaStream_t st = (cudaStream_t)stream;
   const auto key = std::make_tuple(d->ndim, d->prec, (int)d->N, (int)d->blocks.size(),
-                                   d->opts.n_correctors * 4 + d->opts.p_precond);
+                                   (d->opts.n_correctors * 4 + d->opts.p_precond) * 4 + d->opts.adv_precond);
   auto it = tune_cache().find(key);
   double best_ms = -1.0;
   if (it == tune_cache().end()) {
@@ -982,6 +1102,8 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
       d->threads = std::get<0>(c);
       d->ncta = std::get<1>(c);
       d->p_line = std::get<2>(c);
+      s = build_ilu(d);
+      if (s != PISO_OK) break;
       double t = 1e300;
       for (int rep = 0; rep < 3 && s == PISO_OK; rep++) {
         cudaEventRecord(e0, st);
@@ -1017,6 +1139,8 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
   d->opts.block_threads = d->threads;
   d->opts.ctas = d->ncta;
   d->opts.p_precond = d->p_line ? PISO_PRECOND_LINE : PISO_PRECOND_JACOBI;
+  const piso_status sb = build_ilu(d);
+  if (sb) return sb;
   if (threads_out) *threads_out = d->threads;
   if (ctas_out) *ctas_out = d->ncta;
   if (ms_out) *ms_out = best_ms;
@@ -1070,6 +1194,7 @@ void piso_domain_destroy(piso_domain* d) {
   if (!d) return;
   if (d->dmem) cudaFree(d->dmem);
   if (d->h_status) cudaFreeHost(d->h_status);
+  if (d->ilu_buf) cudaFree(d->ilu_buf);
   if (d->h_istats) cudaFreeHost(d->h_istats);
   if (d->h_dstats) cudaFreeHost(d->h_dstats);
   if (d->h_dnu) cudaFreeHost(d->h_dnu);
@@ -1136,6 +1261,8 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
   if (!u_in || !p_in || !u_out || !p_out) return fail(d, PISO_EINVAL, "NULL field pointer");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(d, PISO_EINVAL, "dt must be positive and finite");
   if (!(nu >= 0) || !std::isfinite(nu)) return fail(d, PISO_EINVAL, "nu must be non-negative and finite");
+  const piso_status ci = check_ilu(d);
+  if (ci) return ci;
   const StaticLayout SL = static_layout(d);
   if (SL.total > STATIC_SCRATCH_BYTES)
     return fail(d, PISO_EINVAL, "domain needs %zu bytes of scratch; piso_step_static provides %zu (use piso_step)",
@@ -1195,6 +1322,7 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
     c.lfa = W(W_LFA);
     c.lfm = W(W_LFM);
     c.lfc = W(W_LFC);
+    c.ilud = W(W_ILUD);
     c.bar = (uint32_t*)(base + SL.bar);
     c.status = (int32_t*)(base + SL.status);
     c.istats = (int32_t*)(base + SL.istats);

@@ -87,7 +87,7 @@ struct Cell {
   int32_t nb[6];
 };
 
-__device__ __forceinline__ int32_t side_nbr(const DomStatic& D, const BlockInfo& B, int32_t i,
+__host__ __device__ __forceinline__ int32_t side_nbr(const DomStatic& D, const BlockInfo& B, int32_t i,
                                             int32_t x, int32_t y, int32_t z, int s) {
   switch (s) {
     case 0: if (x > 0) return i - 1; break;
@@ -117,7 +117,7 @@ __device__ __forceinline__ int32_t side_nbr(const DomStatic& D, const BlockInfo&
 }
 
 template <int ND>
-__device__ __forceinline__ Cell locate(const DomStatic& D, int32_t i) {
+__host__ __device__ __forceinline__ Cell locate(const DomStatic& D, int32_t i) {
   Cell c;
   c.i = i;
   int b = 0;

@@ -59,6 +59,9 @@ struct FwdCall {
   real* lfm;
   real* lfc;
   int32_t p_line;            // 1: the pressure CG uses the y-line preconditioner
+  IluTab ilu;                // ILU(0) tables of the launch layout (when adv_ilu)
+  real* ilud;                // [N]    ILU(0) reciprocal pivots
+  int32_t adv_ilu;           // BiCGStab preconditioner: 0 none, 1 ILU(0), 2 ILU(0) after a failed plain solve
   // group control
   uint32_t* bar;
   double* partials;
@@ -296,17 +299,43 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       return;
   }
 
-  // predictor solve (App. A.5: BiCGStab)
-  if (!bicgstab<real, ND, false>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv, A.vv, A.t))
-    return;
+  // predictor solve (App. A.5: BiCGStab, ILU(0)-preconditioned throughout or
+  // only after the plain solve failed)
+  int ilu_used = 0;
+  {
+    IluPre<real> IP{};
+    if (A.adv_ilu) IP = ilu_setup<real>(A.ilu, A.ilud, g.rank);
+    if (A.adv_ilu == 1) {
+      ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff);
+      ilu_used = 1;
+      if (!bicgstab_ilu<real, ND, false>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv[0],
+                                         A.vv[0], A.pv[1], A.vv[1], A.t))
+        return;
+    } else {
+      if (!bicgstab<real, ND, false>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv, A.vv, A.t))
+        return;
+      // bs is the same in every CTA (each runs the same updates on the same
+      // reduced values), so all CTAs take the same branch
+      if (A.adv_ilu == 2 && !bicg_all_conv<ND>(bs)) {
+        bicg_restart<real, ND>(X, bs, A.ustar, A.u_in, A.r, A.rhat, o.adv_rtol, o.atol, g.status);
+        ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff);
+        ilu_used = 2;
+        if (!bicgstab_ilu<real, ND, false>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv[0],
+                                           A.vv[0], A.pv[1], A.vv[1], A.t))
+          return;
+      }
+    }
+  }
   if (threadIdx.x == 0 && g.rank == 0) {
     int nc = 0;
     for (int k = 0; k < ND; k++) {
-      A.istats[k] = bs.iters[k];
+      A.istats[k] = bs.iters[k] + bs.iters_prev[k];
       A.dstats[k] = sqrt(bs.res2[k]);
       if (!bs.conv[k]) nc = 1;
     }
+    A.istats[3] = ilu_used;
     if (nc) atomicOr(g.status, PISO_ERR_NOCONV_ADV);
+    if (bs.err) atomicOr(g.status, bs.err);
   }
 
   // correctors (App. A.1 Eqs. pressureRHS, pressure, correction; App. A.2

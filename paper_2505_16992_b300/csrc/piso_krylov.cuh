@@ -137,9 +137,12 @@ __device__ __forceinline__ void p_row(const Cell& c, int32_t N, const real* Poff
 struct BiState {
   double rho[3], rho_old[3], alpha[3], omega[3], tol2[3], res2[3];
   double beta_d[3];
+  double q0[6];              // ||b||^2 and ||r0||^2 per component (a restart reuses them)
   float beta_f[3], alpha_f[3], omega_f[3];
   int active[3], sconv[3], iters[3], conv[3];
+  int iters_prev[3];         // iterations of an earlier, failed attempt (ILU(0) fallback)
   int any, it, first;
+  int err;                   // breakdown / NaN bits of the solve, passed to the step status by the caller
 };
 
 // Residual replacement period of the pressure CG (0 = off, the default).
@@ -274,12 +277,15 @@ __device__ __forceinline__ void bicg_start(BiState& bs, const double* q, double 
   bs.any = 0;
   bs.it = 0;
   bs.first = 1;
+  bs.err = 0;
+  for (int k = 0; k < 2 * ND; k++) bs.q0[k] = q[k];
   for (int k = 0; k < ND; k++) {
     bs.tol2[k] = fmax(rtol * rtol * q[k], atol * atol);
     bs.res2[k] = q[ND + k];
     bs.rho[k] = q[ND + k];
     bs.rho_old[k] = bs.alpha[k] = bs.omega[k] = 1.0;
     bs.iters[k] = 0;
+    bs.iters_prev[k] = 0;
     bs.sconv[k] = 0;
     bs.conv[k] = !(bs.res2[k] > bs.tol2[k]);
     bs.active[k] = !bs.conv[k];
@@ -291,6 +297,83 @@ __device__ __forceinline__ void bicg_start(BiState& bs, const double* q, double 
     bs.any |= bs.active[k];
     bicg_set_beta(bs, k);
   }
+}
+
+// Thread 0, after the reduction of (rhat, v): alpha per component.
+template <int ND>
+__device__ __forceinline__ void bicg_update_alpha(BiState& bs, const double* q) {
+  bs.it++;
+  for (int k = 0; k < ND; k++) {
+    if (!bs.active[k]) continue;
+    bs.iters[k]++;
+    if (q[k] == 0.0 || q[k] != q[k]) {
+      bs.active[k] = 0;
+      bs.err |= q[k] == 0.0 ? PISO_ERR_BREAKDOWN : PISO_ERR_NAN;
+      continue;
+    }
+    bs.alpha[k] = bs.rho[k] / q[k];
+    bs.alpha_f[k] = (float)bs.alpha[k];
+  }
+}
+
+// Thread 0, after the reduction of (t, s), (t, t), (s, s): the s-convergence
+// test, then omega.
+template <int ND>
+__device__ __forceinline__ void bicg_update_omega(BiState& bs, const double* q) {
+  for (int k = 0; k < ND; k++) {
+    if (!bs.active[k]) continue;
+    if (!(q[2 * ND + k] > bs.tol2[k])) {
+      bs.sconv[k] = 1;
+      bs.res2[k] = q[2 * ND + k];
+    } else if (q[ND + k] == 0.0 || q[ND + k] != q[ND + k]) {
+      bs.active[k] = 0;
+      bs.err |= q[ND + k] == 0.0 ? PISO_ERR_BREAKDOWN : PISO_ERR_NAN;
+    } else {
+      bs.omega[k] = q[k] / q[ND + k];
+      bs.omega_f[k] = (float)bs.omega[k];
+    }
+  }
+}
+
+// Thread 0, after the reduction of (rhat, r), (r, r): convergence, rho and the
+// next beta.
+template <int ND>
+__device__ __forceinline__ void bicg_update_rho(BiState& bs, const double* q) {
+  bs.any = 0;
+  for (int k = 0; k < ND; k++) {
+    if (!bs.active[k]) continue;
+    if (bs.sconv[k]) {
+      bs.active[k] = 0;
+      bs.conv[k] = 1;
+      continue;
+    }
+    bs.res2[k] = q[ND + k];
+    if (bs.res2[k] != bs.res2[k]) {
+      bs.active[k] = 0;
+      bs.err |= PISO_ERR_NAN;
+    } else if (!(bs.res2[k] > bs.tol2[k])) {
+      bs.active[k] = 0;
+      bs.conv[k] = 1;
+    } else if (q[k] == 0.0) {
+      bs.active[k] = 0;
+      bs.err |= PISO_ERR_BREAKDOWN;
+    } else {
+      bs.rho_old[k] = bs.rho[k];
+      bs.rho[k] = q[k];
+    }
+    bs.any |= bs.active[k];
+  }
+  bs.first = 0;
+  for (int k = 0; k < ND; k++)
+    if (bs.active[k]) bicg_set_beta(bs, k);
+}
+
+// Thread 0: every component converged?
+template <int ND>
+__device__ __forceinline__ bool bicg_all_conv(const BiState& bs) {
+  for (int k = 0; k < ND; k++)
+    if (!bs.conv[k]) return false;
+  return true;
 }
 
 // The three cell sweeps of a BiCGStab iteration.  Each array is touched
@@ -468,20 +551,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       real* pnew = pv[cur];
       real* vnew = vv[cur];
       bicg_sweep_a<real, ND, TR>(X, first, act, beta, om, Cdiag, Coff, r, pold, vold, rhat, pnew, vnew, a);
-      const bool ok = reduce_sync<real, ND>(X.g, a, [&](const double* q) {
-        bs.it++;
-        for (int k = 0; k < ND; k++) {
-          if (!bs.active[k]) continue;
-          bs.iters[k]++;
-          if (q[k] == 0.0 || q[k] != q[k]) {
-            bs.active[k] = 0;
-            atomicOr(X.g.status, q[k] == 0.0 ? PISO_ERR_BREAKDOWN : PISO_ERR_NAN);
-            continue;
-          }
-          bs.alpha[k] = bs.rho[k] / q[k];
-          bs.alpha_f[k] = (float)bs.alpha[k];
-        }
-      });
+      const bool ok = reduce_sync<real, ND>(X.g, a, [&](const double* q) { bicg_update_alpha<ND>(bs, q); });
       if (!ok) return false;
     }
     // BB: s = r - alpha v, t = M s
@@ -497,21 +567,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
 #pragma unroll
       for (int k = 0; k < 3 * ND; k++) a[k].zero();
       bicg_sweep_b<real, ND, TR>(X, act, al, Cdiag, Coff, r, vv[cur], t, a);
-      const bool ok = reduce_sync<real, 3 * ND>(X.g, a, [&](const double* q) {
-        for (int k = 0; k < ND; k++) {
-          if (!bs.active[k]) continue;
-          if (!(q[2 * ND + k] > bs.tol2[k])) {
-            bs.sconv[k] = 1;
-            bs.res2[k] = q[2 * ND + k];
-          } else if (q[ND + k] == 0.0 || q[ND + k] != q[ND + k]) {
-            bs.active[k] = 0;
-            atomicOr(X.g.status, q[ND + k] == 0.0 ? PISO_ERR_BREAKDOWN : PISO_ERR_NAN);
-          } else {
-            bs.omega[k] = q[k] / q[ND + k];
-            bs.omega_f[k] = (float)bs.omega[k];
-          }
-        }
-      });
+      const bool ok = reduce_sync<real, 3 * ND>(X.g, a, [&](const double* q) { bicg_update_omega<ND>(bs, q); });
       if (!ok) return false;
     }
     // BC: x += alpha p + omega s, r = s - omega t
@@ -529,35 +585,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
         a[ND + k].zero();
       }
       bicg_sweep_c<real, ND>(X, act, sc, al, om, pv[cur], vv[cur], t, rhat, x, r, a);
-      const bool ok = reduce_sync<real, 2 * ND>(X.g, a, [&](const double* q) {
-        bs.any = 0;
-        for (int k = 0; k < ND; k++) {
-          if (!bs.active[k]) continue;
-          if (bs.sconv[k]) {
-            bs.active[k] = 0;
-            bs.conv[k] = 1;
-            continue;
-          }
-          bs.res2[k] = q[ND + k];
-          if (bs.res2[k] != bs.res2[k]) {
-            bs.active[k] = 0;
-            atomicOr(X.g.status, PISO_ERR_NAN);
-          } else if (!(bs.res2[k] > bs.tol2[k])) {
-            bs.active[k] = 0;
-            bs.conv[k] = 1;
-          } else if (q[k] == 0.0) {
-            bs.active[k] = 0;
-            atomicOr(X.g.status, PISO_ERR_BREAKDOWN);
-          } else {
-            bs.rho_old[k] = bs.rho[k];
-            bs.rho[k] = q[k];
-          }
-          bs.any |= bs.active[k];
-        }
-        bs.first = 0;
-        for (int k = 0; k < ND; k++)
-          if (bs.active[k]) bicg_set_beta(bs, k);
-      });
+      const bool ok = reduce_sync<real, 2 * ND>(X.g, a, [&](const double* q) { bicg_update_rho<ND>(bs, q); });
       if (!ok) return false;
     }
     cur ^= 1;
@@ -567,6 +595,7 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
 
 }  // namespace piso
 #include "piso_lines.cuh"
+#include "piso_ilu.cuh"
 namespace piso {
 
 // One iteration's cell sweep of the Jacobi CG below (all of the CTA's cells):

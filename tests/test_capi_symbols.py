@@ -86,6 +86,7 @@ def test_default_options_fill_every_field(lib):
     assert o.p_inner_rtol == 1e-4
     assert o.grad_paths == capi.PISO_GRAD_ADV | capi.PISO_GRAD_P
     assert o.p_precond == capi.PISO_PRECOND_AUTO
+    assert o.adv_precond == capi.PISO_ADV_PRECOND_NONE
 
 
 def test_pressure_preconditioner_is_validated(lib):
@@ -98,6 +99,20 @@ def test_pressure_preconditioner_is_validated(lib):
     o = capi.default_options(p_precond=3)
     assert lib.piso_finalize(h, C.byref(o)) == 1
     assert b"p_precond" in lib.piso_last_error(h)
+    lib.piso_domain_destroy(h)
+
+
+def test_advection_preconditioner_is_validated(lib):
+    h = C.c_void_p()
+    assert lib.piso_domain_create(2, 0, C.byref(h)) == 0
+    res = (C.c_int32 * 3)(2, 2, 1)
+    verts = (C.c_double * 18)(*[0.0] * 18)
+    bid = C.c_int32()
+    assert lib.piso_block_add(h, res, verts, C.byref(bid)) == 0
+    for bad in (-1, 3):
+        o = capi.default_options(adv_precond=bad)
+        assert lib.piso_finalize(h, C.byref(o)) == 1
+        assert b"adv_precond" in lib.piso_last_error(h)
     lib.piso_domain_destroy(h)
 
 
