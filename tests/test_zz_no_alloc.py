@@ -57,6 +57,21 @@ def test_static_scratch_step_equals_piso_step_twice(name, precision):
         u, p = su, sp
 
 
+def test_static_scratch_step_with_ilu_preconditioned_predictor():
+    """The ILU(0) tables live with the domain (built when its launch layout is
+    chosen), so the static entry point runs the preconditioned solve without
+    allocating either."""
+    c = W.channel3d(10, 16, 4, gamma=3.0, dt=0.5)
+    dom = gpu_domain(c, adv_precond=capi.PISO_ADV_PRECOND_ILU)
+    u, p, S = to_dev(dom, c.u0, 3), to_dev(dom, c.p0), to_dev(dom, c.S, 3)
+    ref_u, ref_p, ref_st = dom.step(u, p, c.dt, c.nu, S)
+    su, sp, sst = _static_step(dom, u, p, c.dt, c.nu, S)
+    assert sst["status"] == "PISO_OK" and sst["adv_precond_used"] == 1, sst
+    assert sst["adv_iters"] == ref_st["adv_iters"]
+    assert rel_err(host(su), host(ref_u)) <= FP64_REL
+    assert rel_err(host(sp), host(ref_p)) <= 10 * FP64_REL
+
+
 def test_static_scratch_refuses_domains_that_do_not_fit():
     c = W.channel3d(64, 48, 32)            # 98,304 cells in FP64 need more than the 32 MiB buffer
     dom = gpu_domain(c)
