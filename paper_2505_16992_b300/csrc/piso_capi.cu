@@ -108,10 +108,8 @@ struct piso_batch {
   int total_cta = 0;
   std::vector<int32_t> cta_first;
   int32_t* d_cta_first = nullptr;
-  void* d_calls = nullptr;
-  void* h_calls = nullptr;     // pinned
-  size_t call_bytes = 0;
-  void* h_calls_aux = nullptr; // device/pinned control block of the batch launch
+  size_t call_bytes = 0;       // bytes of one group's call record (the larger of forward and adjoint)
+  void* dev = nullptr;         // piso_batch_dev: device and pinned buffers of the batch launches
   std::string err;
 };
 
