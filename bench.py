@@ -309,7 +309,7 @@ def time_statistics(dom, u, p, nu, steps, flush, peak):
 
 
 def run_batch(args):
-    """Config 5: 64 independent 2D cavity/channel simulations (sides 32..256,
+    """The batch of 64 independent 2D cavity/channel simulations (sides 32..256,
     Re 100..2000, seed 4) advanced together: one persistent launch for the
     forward step of all members and one for their adjoint."""
     import numpy as np

@@ -21,7 +21,7 @@ Layout conventions shared by every consumer:
 
 Case parameters follow the paper's scenarios (lid-driven cavity, backward-facing
 step channel, periodic turbulent channel, forced 2D turbulence; Sec. 4-5 and
-App. B) at the sizes the benchmark configurations name.
+App. B) at the sizes of the paper's workloads.
 """
 from __future__ import annotations
 

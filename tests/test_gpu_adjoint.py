@@ -57,7 +57,7 @@ def test_adjoint_cavity_pred_grad_p():
     _adjoint_parity(W.cavity2d(16, nu=0.05, dt=0.05), pred_grad_p=1)
 
 
-def test_adjoint_turbulence2d_config4_size():
+def test_adjoint_turbulence2d_128_squared():
     _adjoint_parity(W.turbulence2d(128))
 
 

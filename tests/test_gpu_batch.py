@@ -82,8 +82,8 @@ def test_batch_adjoint_gradient_path_variant():
         assert abs(dnu[i] - gnu) <= 1e-8 * abs(gnu), i
 
 
-def test_batch_config5_full_size_sampled_parity():
-    """Config 5: 64 independent 2D cavity/channel simulations, sides uniform in
+def test_batch_of_64_simulations_full_size_sampled_parity():
+    """The batch of 64 independent 2D cavity/channel simulations, sides uniform in
     32..256, Re in [100, 2000], FP32 bulk; sampled members against the oracle."""
     cases = W.batch2d()
     assert len(cases) == 64

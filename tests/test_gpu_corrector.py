@@ -1,4 +1,4 @@
-"""Config 4: a 3-layer 3x3-conv corrector produces the source S of every step
+"""The 128^2 periodic box with a learned corrector: a 3-layer 3x3-conv corrector produces the source S of every step
 of a differentiable rollout on 2D forced turbulence (Sec. 3: learned
 corrections enter as the source term; Sec. 2.3: gradients through the solver).
 Gradients w.r.t. the network parameters are checked against finite
@@ -71,7 +71,7 @@ def test_corrector_gradients_match_finite_differences():
     assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
 
 
-def test_corrector_training_config4_fp32():
+def test_corrector_training_periodic_box_fp32():
     """128x128 periodic forced turbulence, 16-step rollout, 32-channel FP32
     corrector, MSE to a seeded target: a few Adam steps reduce the loss."""
     n, steps = 128, 16

@@ -48,13 +48,13 @@ def _bval_faces(m, bval):
     return np.concatenate(faces, axis=1)
 
 
-def test_cavity_config1_per_step():
+def test_cavity_32_per_step():
     c = W.cavity2d(32)
     _per_step_parity(c, 4)
 
 
-def test_cavity_config1_rollout():
-    """Config 1 (32x32 cavity, Re 100, dt 0.005) over 50 steps."""
+def test_cavity_32_rollout():
+    """The 32x32 cavity (Re 100, dt 0.005) over 50 steps."""
     c = W.cavity2d(32)
     m = O.mesh_from_case(c)
     dom = gpu_domain(c)
@@ -88,7 +88,7 @@ def test_bfs_multiblock_outflow_small():
     _per_step_parity(c, 3, p_rtol=1e-12)
 
 
-def test_bfs_config2_full_size():
+def test_bfs_22528_cells_full_size():
     c = W.bfs2d()
     assert c.ncells == 22528
     _per_step_parity(c, 2, p_rtol=1e-12)
@@ -99,7 +99,7 @@ def test_channel3d_small():
     _per_step_parity(c, 3)
 
 
-def test_channel3d_config3_full_size():
+def test_channel3d_64x48x32_full_size():
     c = W.channel3d()
     assert c.ncells == 64 * 48 * 32
     _per_step_parity(c, 1)

@@ -52,7 +52,7 @@ def test_line_multiblock_bfs_with_outflow():
 
 
 def test_line_full_size_channel_fewer_iterations():
-    """Config 3 (64x48x32 channel, tanh walls): parity with the oracle and
+    """The 64x48x32 channel (tanh walls): parity with the oracle and
     fewer CG iterations than Jacobi for the same tolerance."""
     c = W.channel3d()
     st_l = _step_parity(c, LINE)

@@ -142,7 +142,7 @@ def _channel(nx=8, ny=6, nz=4, gamma=1.5):
 
 
 def _uniform_channel(nx=8, ny=6, nz=4):
-    """The channel of config 3 with uniform spacing in y (same sides)."""
+    """The 64x48x32 channel with uniform spacing in y (same sides)."""
     c = W.channel3d(nx, ny, nz)
     b = W.rect_block(W.uniform_vertices(nx, 0.0, 2 * math.pi), W.uniform_vertices(ny, -1.0, 1.0),
                      W.uniform_vertices(nz, 0.0, math.pi))
