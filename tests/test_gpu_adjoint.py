@@ -105,6 +105,16 @@ def test_adjoint_gradient_paths_with_predictor_pressure_gradient(paths):
     _adjoint_parity(W.cavity2d(16, nu=0.05, dt=0.05), pred_grad_p=1, grad_paths=paths)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", ADJ_REL), ("fp32", 2e-3)])
+def test_adjoint_with_ilu_preconditioned_solves(precision, tol):
+    """Every gradient of the step (u, S, nu, boundary values) with the
+    ILU(0)-preconditioned predictor and transposed predictor solves, on the
+    strongly stretched channel they are meant for."""
+    kw = dict(adv_rtol=1e-6, p_rtol=1e-6) if precision == "fp32" else {}
+    _adjoint_parity(W.channel3d(10, 16, 4, gamma=3.0, dt=0.5), tol=tol, precision=precision,
+                    adv_precond=capi.PISO_ADV_PRECOND_ILU, **kw)
+
+
 def test_adjoint_gradient_paths_fp32_full_channel():
     _adjoint_parity(W.channel3d(), tol=2e-3, precision="fp32", adv_rtol=1e-6, p_rtol=1e-6,
                     grad_paths=capi.PISO_GRAD_ADV)
