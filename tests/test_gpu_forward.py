@@ -160,6 +160,26 @@ def test_fp32_mixed_laminar_cavity():
     assert rel_err(host(u), uo) <= FP32_REL
 
 
+@pytest.mark.parametrize("make,steps", [
+    (lambda: W.bfs2d(n_in=(16, 8), n_ch=64, n_out=16, half=8, dt=0.02), 20),
+    (lambda: W.channel3d(16, 12, 8), 20),
+], ids=["bfs2d-outflow", "channel3d-16x12x8"])
+def test_fp32_mixed_laminar_after_n_steps(make, steps):
+    """Mixed precision against the FP64 oracle after N steps on the laminar
+    multi-block step (with its advective outflow) and the forced channel."""
+    c = make()
+    m = O.mesh_from_case(c)
+    dom = gpu_domain(c, "fp32", adv_rtol=1e-6, p_rtol=1e-6)
+    d = c.ndim
+    S = None if c.S is None else to_dev(dom, c.S, d)
+    u, p = to_dev(dom, c.u0, d), to_dev(dom, c.p0)
+    for _ in range(steps):
+        u, p, st = dom.step(u, p, c.dt, c.nu, S)
+        assert st["status"] == "PISO_OK", st
+    uo, po, _ = O.rollout(m, c.u0, c.p0, c.dt, c.nu, c.S, steps)
+    assert rel_err(host(u), uo) <= FP32_REL, rel_err(host(u), uo)
+
+
 def test_fp32_mixed_channel3d():
     c = W.channel3d(16, 12, 8)
     m = O.mesh_from_case(c)
