@@ -75,7 +75,7 @@ struct AdjCall {
   int32_t cta0, ncta;
 };
 
-template <typename real, int ND>
+template <typename real, int ND, bool ILU>
 __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g) {
   __shared__ DomStatic D;
   __shared__ BiState bs;
@@ -326,28 +326,33 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   // the transposed solve with the preconditioning of the forward one: the
   // factors of C^T are the transposed factors of C (same pivots)
   int ilu_used = 0;
-  if (path_adv) {
-    IluPre<real> IP{};
-    if (A.adv_ilu) IP = ilu_setup<real>(A.ilu, A.ilud, g.rank);
-    if (A.adv_ilu == 1) {
-      ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff);
-      ilu_used = 1;
-      if (!bicgstab_ilu<real, ND, true>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv[0], A.vv[0],
-                                        A.pv[1], A.vv[1], A.t))
-        return;
-    } else {
-      if (!bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t))
-        return;
-      if (A.adv_ilu == 2 && !bicg_all_conv<ND>(bs)) {
-        bicg_restart<real, ND>(X, bs, A.z, static_cast<const real*>(nullptr), A.r, A.rhat, o.adv_rtol, o.atol,
-                               g.status);
-        ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff);
-        ilu_used = 2;
+  if constexpr (ILU) {
+    if (path_adv) {
+      const IluPre<real> IP = ilu_setup<real>(A.ilu, A.ilud, g.rank);
+      const IluSmem<real, ND> IS = ilu_smem<real, ND>(X, o);
+      if (A.adv_ilu == 1) {
+        ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
+        ilu_used = 1;
         if (!bicgstab_ilu<real, ND, true>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv[0],
-                                          A.vv[0], A.pv[1], A.vv[1], A.t))
+                                          A.vv[0], A.pv[1], A.vv[1], A.t, IS))
           return;
+      } else {
+        if (!bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t))
+          return;
+        if (A.adv_ilu == 2 && !bicg_all_conv<ND>(bs)) {
+          bicg_restart<real, ND>(X, bs, A.z, static_cast<const real*>(nullptr), A.r, A.rhat, o.adv_rtol, o.atol,
+                                 g.status);
+          ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
+          ilu_used = 2;
+          if (!bicgstab_ilu<real, ND, true>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv[0],
+                                            A.vv[0], A.pv[1], A.vv[1], A.t, IS))
+            return;
+        }
       }
     }
+  } else {
+    if (path_adv && !bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t))
+      return;
   }
   if (path_adv && threadIdx.x == 0 && g.rank == 0) {
     int nc = 0;
@@ -571,7 +576,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   }
 }
 
-template <typename real, int ND, int MAXT>
+template <typename real, int ND, int MAXT, bool ILU>
 __global__ void __launch_bounds__(MAXT, 1) adj_kernel(const __grid_constant__ Launch<AdjCall<real>> L) {
   __shared__ AdjCall<real> A;
   const int gi = find_group(L.ngroups, L.cta_first);
@@ -586,7 +591,7 @@ __global__ void __launch_bounds__(MAXT, 1) adj_kernel(const __grid_constant__ La
   g.epoch = 0;
   g.timeout_ns = L.o.timeout_ns;
   g.withhold = (L.o.withhold_cta == g.rank) ? 1 : 0;
-  adj_group<real, ND>(A, L.o, g);
+  adj_group<real, ND, ILU>(A, L.o, g);
 }
 
 }  // namespace piso

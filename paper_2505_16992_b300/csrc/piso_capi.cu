@@ -349,6 +349,7 @@ SolverOpts solver_opts(const piso_options& o) {
   s.p_refine_rtol = o.p_refine_rtol;
   s.p_inner_rtol = o.p_inner_rtol;
   s.grad_paths = o.grad_paths;
+  s.ilu_soff = -1;
   return s;
 }
 
@@ -379,22 +380,39 @@ size_t launch_smem(const piso_domain* d, int ncta, SolverOpts* o) {
   const size_t ints = 3 * (size_t)LINE_LBMAX * sizeof(int32_t);
   const int lmax = std::max(d->h_static.lmax, 1);
   const size_t line_min = d->p_line ? LINE_ARRAYS * e * 2 * (size_t)lmax + ints : 0;
+  auto al16 = [](size_t b) { return (b + 15) & ~size_t(15); };
   o->nbt_cap = 0;
   o->line_cap = 0;
+  o->ilu_soff = -1;
   if (line_min > NBT_MAX_BYTES) return nbt_bytes(nd, d->N, ncta, &o->nbt_cap);   // lines cannot be staged
   const int64_t per = ((int64_t)d->N + ncta - 1) / ncta;
+  // ILU(0) sweep values and factor rows of one cell per thread, when the
+  // BiCGStab is preconditioned and every CTA owns at most one cell per thread
+  const size_t ilu_b = (d->opts.adv_precond != PISO_ADV_PRECOND_NONE && per <= d->threads)
+                           ? al16(ilu_smem_bytes(nd, (size_t)per, e)) : 0;
   size_t nbt = (size_t)per * 2 * nd * sizeof(int32_t);
-  if (nbt + 16 + line_min <= NBT_MAX_BYTES) o->nbt_cap = (int32_t)per;
+  if (nbt + 16 + line_min + ilu_b <= NBT_MAX_BYTES) o->nbt_cap = (int32_t)per;
+  else if (nbt + 16 + line_min <= NBT_MAX_BYTES && ilu_b) o->nbt_cap = (int32_t)per;   // table kept, no ILU area
   else nbt = 0;
-  nbt = (nbt + 15) & ~size_t(15);
-  if (!d->p_line) return nbt;
+  nbt = al16(nbt);
+  const size_t ilu = (o->nbt_cap > 0 && nbt + 16 + line_min + ilu_b <= NBT_MAX_BYTES) ? ilu_b : 0;
+  if (!d->p_line) {
+    if (ilu) o->ilu_soff = (int32_t)nbt;
+    return nbt + ilu;
+  }
   // staging: as much as fits, but no more than this CTA's lines plus one
   const int64_t lines_per = ((int64_t)d->h_static.nlines + ncta - 1) / ncta;
-  size_t cap = (NBT_MAX_BYTES - nbt - ints) / (LINE_ARRAYS * e);
+  size_t cap = (NBT_MAX_BYTES - nbt - ilu - ints - (ilu ? 16 : 0)) / (LINE_ARRAYS * e);
   cap = std::min<size_t>(cap, (size_t)(std::min<int64_t>(lines_per, LINE_LBMAX) + 1) * lmax);
   cap = std::max<size_t>(cap, 2 * (size_t)lmax);
   o->line_cap = (int32_t)cap;
-  return nbt + LINE_ARRAYS * e * cap + ints;
+  size_t total = nbt + LINE_ARRAYS * e * cap + ints;
+  if (ilu) {
+    total = al16(total);
+    o->ilu_soff = (int32_t)total;
+    total += ilu;
+  }
+  return total;
 }
 
 cudaError_t coop_launch(const void* kernel, int grid, int threads, void** args, cudaStream_t st, size_t smem = 0) {
@@ -417,27 +435,41 @@ cudaError_t coop_launch(const void* kernel, int grid, int threads, void** args, 
 constexpr int WIDE = 768;
 inline int width_class(int threads) { return threads > 512 ? WIDE : 512; }
 
-template <typename real>
-const void* fwd_ptr_t(int nd, int threads) {
+template <typename real, bool ILU>
+const void* fwd_ptr_ti(int nd, int threads) {
   if (width_class(threads) == WIDE)
-    return nd == 2 ? (const void*)fwd_kernel<real, 2, WIDE> : (const void*)fwd_kernel<real, 3, WIDE>;
-  return nd == 2 ? (const void*)fwd_kernel<real, 2, 512> : (const void*)fwd_kernel<real, 3, 512>;
+    return nd == 2 ? (const void*)fwd_kernel<real, 2, WIDE, ILU> : (const void*)fwd_kernel<real, 3, WIDE, ILU>;
+  return nd == 2 ? (const void*)fwd_kernel<real, 2, 512, ILU> : (const void*)fwd_kernel<real, 3, 512, ILU>;
+}
+
+template <typename real, bool ILU>
+const void* adj_ptr_ti(int nd, int threads) {
+  if (width_class(threads) == WIDE)
+    return nd == 2 ? (const void*)adj_kernel<real, 2, WIDE, ILU> : (const void*)adj_kernel<real, 3, WIDE, ILU>;
+  return nd == 2 ? (const void*)adj_kernel<real, 2, 512, ILU> : (const void*)adj_kernel<real, 3, 512, ILU>;
+}
+
+// ilu: the instantiation with the ILU(0)-preconditioned BiCGStab (domains
+// whose adv_precond is not NONE); batches always take the plain one.
+template <typename real>
+const void* fwd_ptr_t(int nd, int threads, bool ilu = false) {
+  return ilu ? fwd_ptr_ti<real, true>(nd, threads) : fwd_ptr_ti<real, false>(nd, threads);
 }
 
 template <typename real>
-const void* adj_ptr_t(int nd, int threads) {
-  if (width_class(threads) == WIDE)
-    return nd == 2 ? (const void*)adj_kernel<real, 2, WIDE> : (const void*)adj_kernel<real, 3, WIDE>;
-  return nd == 2 ? (const void*)adj_kernel<real, 2, 512> : (const void*)adj_kernel<real, 3, 512>;
+const void* adj_ptr_t(int nd, int threads, bool ilu = false) {
+  return ilu ? adj_ptr_ti<real, true>(nd, threads) : adj_ptr_ti<real, false>(nd, threads);
 }
 
-const void* fwd_kernel_ptr(int prec, int nd, int threads = 512) {
-  return prec == PISO_FP64 ? fwd_ptr_t<double>(nd, threads) : fwd_ptr_t<float>(nd, threads);
+const void* fwd_kernel_ptr(int prec, int nd, int threads = 512, bool ilu = false) {
+  return prec == PISO_FP64 ? fwd_ptr_t<double>(nd, threads, ilu) : fwd_ptr_t<float>(nd, threads, ilu);
 }
 
-const void* adj_kernel_ptr(int prec, int nd, int threads = 512) {
-  return prec == PISO_FP64 ? adj_ptr_t<double>(nd, threads) : adj_ptr_t<float>(nd, threads);
+const void* adj_kernel_ptr(int prec, int nd, int threads = 512, bool ilu = false) {
+  return prec == PISO_FP64 ? adj_ptr_t<double>(nd, threads, ilu) : adj_ptr_t<float>(nd, threads, ilu);
 }
+
+bool uses_ilu(const piso_domain* d) { return d->opts.adv_precond != PISO_ADV_PRECOND_NONE; }
 
 // ILU(0) tables for the current launch layout (App. A.5 preconditioner of the
 // BiCGStab).  Each CTA preconditions with the diagonal block of the cells it
@@ -560,8 +592,8 @@ piso_status choose_shape(piso_domain* d) {
   if (threads % 32 || threads > WIDE || threads < 32)
     return fail(d, PISO_EINVAL, "block_threads must be a multiple of 32 in [32, %d]", WIDE);
   int sms = 148;
-  int cap_f = max_coresident(fwd_kernel_ptr(d->prec, d->ndim, threads), threads, &sms);
-  int cap_a = max_coresident(adj_kernel_ptr(d->prec, d->ndim, threads), threads, nullptr);
+  int cap_f = max_coresident(fwd_kernel_ptr(d->prec, d->ndim, threads, uses_ilu(d)), threads, &sms);
+  int cap_a = max_coresident(adj_kernel_ptr(d->prec, d->ndim, threads, uses_ilu(d)), threads, nullptr);
   int cap = std::min(cap_f, cap_a);
   if (cap <= 0) return fail(d, PISO_ECUDA, "kernel cannot be resident with %d threads", threads);
   int want = d->opts.ctas > 0 ? d->opts.ctas : std::min(sms, (int)((d->N + threads - 1) / threads));
@@ -634,7 +666,7 @@ piso_status launch_fwd(piso_domain* d, const void* u_in, const void* p_in, void*
   CUDA_TRY(d, cudaMemsetAsync(d->status, 0, 64, st));
   CUDA_TRY(d, cudaMemsetAsync(d->istats, 0, 64, st));
   void* args[] = {&L};
-  CUDA_TRY(d, coop_launch(fwd_ptr_t<real>(d->ndim, d->threads), d->ncta, d->threads, args, st, smem));
+  CUDA_TRY(d, coop_launch(fwd_ptr_t<real>(d->ndim, d->threads, uses_ilu(d)), d->ncta, d->threads, args, st, smem));
   return PISO_OK;
 }
 
@@ -1086,8 +1118,8 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
     for (int pl : pls)
       for (int w : {512, WIDE}) {
         int sms = 148;
-        const int cap = std::min(max_coresident(fwd_kernel_ptr(d->prec, d->ndim, w), w, &sms),
-                                 max_coresident(adj_kernel_ptr(d->prec, d->ndim, w), w, nullptr));
+        const int cap = std::min(max_coresident(fwd_kernel_ptr(d->prec, d->ndim, w, uses_ilu(d)), w, &sms),
+                                 max_coresident(adj_kernel_ptr(d->prec, d->ndim, w, uses_ilu(d)), w, nullptr));
         const int one_per_thread = (int)std::min<int64_t>(cap, (d->N + w - 1) / w);
         for (int nc : {std::min(cap, sms), one_per_thread})
           if (nc >= 1 && std::find(cand.begin(), cand.end(), std::make_tuple(w, nc, pl)) == cand.end())
@@ -1327,7 +1359,7 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
     c.dstats = (double*)(base + SL.dstats);
     c.partials = (double*)(base + SL.partials);
     void* args[] = {&L};
-    CUDA_TRY(d, coop_launch(fwd_ptr_t<real>(d->ndim, d->threads), d->ncta, d->threads, args, st, smem));
+    CUDA_TRY(d, coop_launch(fwd_ptr_t<real>(d->ndim, d->threads, uses_ilu(d)), d->ncta, d->threads, args, st, smem));
     return PISO_OK;
   };
   piso_status s = d->prec == PISO_FP64 ? launch(double(0)) : launch(float(0));

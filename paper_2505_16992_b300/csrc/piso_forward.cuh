@@ -62,6 +62,7 @@ struct FwdCall {
   IluTab ilu;                // ILU(0) tables of the launch layout (when adv_ilu)
   real* ilud;                // [N]    ILU(0) reciprocal pivots
   int32_t adv_ilu;           // BiCGStab preconditioner: 0 none, 1 ILU(0), 2 ILU(0) after a failed plain solve
+                             // (read by the ILU instantiation of the kernel only)
   // group control
   uint32_t* bar;
   double* partials;
@@ -99,7 +100,7 @@ __device__ __forceinline__ int find_group(int ngroups, const int32_t* cta_first)
   return gi;
 }
 
-template <typename real, int ND>
+template <typename real, int ND, bool ILU>
 __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g) {
   __shared__ DomStatic D;
   __shared__ BiState bs;
@@ -302,14 +303,14 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   // predictor solve (App. A.5: BiCGStab, ILU(0)-preconditioned throughout or
   // only after the plain solve failed)
   int ilu_used = 0;
-  {
-    IluPre<real> IP{};
-    if (A.adv_ilu) IP = ilu_setup<real>(A.ilu, A.ilud, g.rank);
+  if constexpr (ILU) {
+    const IluPre<real> IP = ilu_setup<real>(A.ilu, A.ilud, g.rank);
+    const IluSmem<real, ND> IS = ilu_smem<real, ND>(X, o);
     if (A.adv_ilu == 1) {
-      ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff);
+      ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
       ilu_used = 1;
       if (!bicgstab_ilu<real, ND, false>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv[0],
-                                         A.vv[0], A.pv[1], A.vv[1], A.t))
+                                         A.vv[0], A.pv[1], A.vv[1], A.t, IS))
         return;
     } else {
       if (!bicgstab<real, ND, false>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv, A.vv, A.t))
@@ -318,13 +319,16 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       // reduced values), so all CTAs take the same branch
       if (A.adv_ilu == 2 && !bicg_all_conv<ND>(bs)) {
         bicg_restart<real, ND>(X, bs, A.ustar, A.u_in, A.r, A.rhat, o.adv_rtol, o.atol, g.status);
-        ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff);
+        ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
         ilu_used = 2;
         if (!bicgstab_ilu<real, ND, false>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv[0],
-                                           A.vv[0], A.pv[1], A.vv[1], A.t))
+                                           A.vv[0], A.pv[1], A.vv[1], A.t, IS))
           return;
       }
     }
+  } else {
+    if (!bicgstab<real, ND, false>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv, A.vv, A.t))
+      return;
   }
   if (threadIdx.x == 0 && g.rank == 0) {
     int nc = 0;
@@ -468,7 +472,9 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   }
 }
 
-template <typename real, int ND, int MAXT>
+// ILU: the instantiation with the ILU(0)-preconditioned predictor (App. A.5);
+// the plain one carries no preconditioner code at all.
+template <typename real, int ND, int MAXT, bool ILU>
 __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const __grid_constant__ Launch<FwdCall<real>> L) {
   __shared__ FwdCall<real> A;
   const int gi = find_group(L.ngroups, L.cta_first);
@@ -483,7 +489,7 @@ __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const __grid_constant__ La
   g.epoch = 0;
   g.timeout_ns = L.o.timeout_ns;
   g.withhold = (L.o.withhold_cta == g.rank) ? 1 : 0;
-  fwd_group<real, ND>(A, L.o, g);
+  fwd_group<real, ND, ILU>(A, L.o, g);
 }
 
 }  // namespace piso

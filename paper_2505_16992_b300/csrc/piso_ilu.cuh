@@ -36,6 +36,13 @@ struct IluTab {
   const int32_t* base;     // [ncta] start of CTA r's slice of order
 };
 
+// Bytes of the fast path's shared memory for n cells of d components (the
+// sweep values, the 2d row coefficients and the pivot in the storage type,
+// the 2d neighbour positions as int32); the host reserves this much.
+__host__ __device__ constexpr size_t ilu_smem_bytes(int nd, size_t n, size_t elem) {
+  return (size_t)(3 * nd + 1) * n * elem + (size_t)(2 * nd) * n * sizeof(int32_t);
+}
+
 template <typename real>
 struct IluPre {
   const int32_t* ord;      // this CTA's cells by level
@@ -61,7 +68,8 @@ __device__ __forceinline__ IluPre<real> ilu_setup(const IluTab& t, real* dinv, i
 // A pivot that is not safely positive (C has a positive diagonal; ILU(0) of
 // an M-matrix keeps its pivots positive) falls back to c_ii.
 template <typename real, int ND>
-__device__ void ilu_factor(const Ctx<real, ND>& X, const IluPre<real>& P, const real* Cdiag, const real* Coff) {
+__device__ void ilu_factor_levels(const Ctx<real, ND>& X, const IluPre<real>& P, const real* Cdiag,
+                                  const real* Coff) {
   const int32_t N = X.N;
   for (int l = 0; l < P.nlev; l++) {
     const int32_t e = P.ls[l + 1];
@@ -144,6 +152,200 @@ __device__ __forceinline__ void ilu_apply(const Ctx<real, ND>& X, const IluPre<r
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fast path.  When the CTA owns a contiguous range [lo, hi) of n <= blockDim
+// cells (its neighbour table is in shared memory), thread t takes the cell at
+// position t of the level order for every sweep of the solve.  The sweep
+// values (d x n, by cell position i - lo) and that cell's row of the factors
+// (2d coefficients and neighbour positions, the reciprocal pivot; by thread t,
+// one array per side) are staged in shared memory once per solve, so a level
+// step is a few shared-memory loads and one CTA barrier instead of a chain of
+// dependent global loads (level bound, cell, mask, row, values).  Only the
+// thread's cell, position, level and mask stay in registers.  This code is
+// compiled only into the kernels built for the preconditioned solve, so it
+// cannot change the register allocation of the plain ones.
+template <typename real, int ND>
+struct IluSmem {
+  real* zv;       // [ND][n]  sweep values by cell position
+  real* rc;       // [2ND][n] row coefficients by thread
+  real* rd;       // [n]      reciprocal pivot by thread
+  int32_t* rl;    // [2ND][n] neighbour position by thread
+  int32_t n;      // 0: no fast path
+};
+
+template <typename real, int ND>
+struct IluRow {
+  int32_t i;      // cell, -1 for a thread without one
+  int32_t self;   // its position i - lo
+  int32_t lvl;    // its level, -1 for a thread without a cell
+  uint32_t m;     // in-block mask (bit s: lower neighbour, bit 8 + s: upper)
+};
+
+// The fast path's shared memory, or n = 0 without one.
+template <typename real, int ND>
+__device__ __forceinline__ IluSmem<real, ND> ilu_smem(const Ctx<real, ND>& X, const SolverOpts& o) {
+  extern __shared__ int32_t s_nbt[];
+  IluSmem<real, ND> S{};
+  if (o.ilu_soff < 0 || X.nbt == nullptr || X.hi - X.lo > (int32_t)blockDim.x) return S;
+  const int32_t n = X.hi - X.lo;
+  real* b = reinterpret_cast<real*>(reinterpret_cast<char*>(s_nbt) + o.ilu_soff);
+  S.zv = b;
+  S.rc = b + (size_t)ND * n;
+  S.rd = b + (size_t)3 * ND * n;
+  S.rl = reinterpret_cast<int32_t*>(b + (size_t)(3 * ND + 1) * n);
+  S.n = n;
+  return S;
+}
+
+// The level l with ls[l] <= t < ls[l + 1] (ls[0] = 0 <= t < ls[nlev]).
+template <typename real>
+__device__ __forceinline__ int32_t ilu_level_of(const IluPre<real>& P, int32_t t) {
+  int32_t a = 0, b = P.nlev;
+  while (b - a > 1) {
+    const int32_t c = (a + b) >> 1;
+    if (P.ls[c] <= t) a = c;
+    else b = c;
+  }
+  return a;
+}
+
+template <typename real, int ND>
+__device__ __forceinline__ IluRow<real, ND> ilu_row_of(const Ctx<real, ND>& X, const IluPre<real>& P) {
+  IluRow<real, ND> R;
+  const int32_t t = (int32_t)threadIdx.x;
+  R.i = -1;
+  R.self = 0;
+  R.lvl = -1;
+  R.m = 0;
+  if (t < X.hi - X.lo) {
+    R.i = P.ord[t];
+    R.self = R.i - X.lo;
+    R.lvl = ilu_level_of(P, t);
+    R.m = P.mask[R.i];
+  }
+  return R;
+}
+
+// Stage this thread's row of M (C or C^T) and its pivot (after the pivots
+// are formed).
+template <typename real, int ND, bool TR>
+__device__ __forceinline__ void ilu_stage_rows(const Ctx<real, ND>& X, const IluPre<real>& P, const real* Cdiag,
+                                               const real* Coff, const IluRow<real, ND>& R,
+                                               const IluSmem<real, ND>& S) {
+  const int32_t t = (int32_t)threadIdx.x;
+  if (R.i >= 0) {
+    const Cell c = X.cell(R.i);
+    real diag, cf[2 * ND];
+    c_row<real, ND, TR>(c, X.N, Cdiag, Coff, diag, cf);
+#pragma unroll
+    for (int s = 0; s < 2 * ND; s++) {
+      const bool in = ((R.m >> s) | (R.m >> (8 + s))) & 1u;
+      S.rc[s * S.n + t] = in ? cf[s] : real(0);
+      S.rl[s * S.n + t] = in ? c.nb[s] - X.lo : 0;
+    }
+    S.rd[t] = P.dinv[R.i];
+  }
+  __syncthreads();
+}
+
+// Pivots, fast path.  Same arithmetic, in the same order, as
+// ilu_factor_levels: d_i = c_ii - sum (c_ik c_ki) / d_k.
+template <typename real, int ND>
+__device__ void ilu_factor_fast(const Ctx<real, ND>& X, const IluPre<real>& P, const real* Cdiag, const real* Coff,
+                                const IluSmem<real, ND>& S) {
+  const IluRow<real, ND> R = ilu_row_of<real, ND>(X, P);
+  const int32_t t = (int32_t)threadIdx.x, n = S.n;
+  const uint32_t m = R.m & 0xffu;
+  __syncthreads();   // the staging area may still be read by an earlier solve
+  if (R.i >= 0) {
+    const Cell c = X.cell(R.i);
+    real diag, cf[2 * ND], ct[2 * ND];
+    c_row<real, ND, false>(c, X.N, Cdiag, Coff, diag, cf);
+    c_row<real, ND, true>(c, X.N, Cdiag, Coff, diag, ct);
+#pragma unroll
+    for (int s = 0; s < 2 * ND; s++) {
+      S.rc[s * n + t] = ((m >> s) & 1u) ? cf[s] * ct[s] : real(0);
+      S.rl[s * n + t] = ((m >> s) & 1u) ? c.nb[s] - X.lo : 0;
+    }
+    S.rd[t] = diag;
+  }
+  __syncthreads();
+  for (int l = 0; l < P.nlev; l++) {
+    if (R.lvl == l) {
+      const real diag = S.rd[t];
+      real d = diag;
+#pragma unroll
+      for (int s = 0; s < 2 * ND; s++)
+        if ((m >> s) & 1u) d -= S.rc[s * n + t] * S.zv[S.rl[s * n + t]];
+      if (!(d > real(1e-5) * diag)) d = diag;
+      S.zv[R.self] = real(1) / d;
+    }
+    __syncthreads();
+  }
+  if (R.i >= 0) P.dinv[R.i] = S.zv[R.self];
+  __syncthreads();
+}
+
+// z = M^-1 w, fast path: the source values are staged first (one load round
+// trip for all cells), then the sweeps of ilu_apply run on shared memory and
+// the CTA's values are stored to z.  Rows staged by ilu_stage_rows.
+template <typename real, int ND, typename SRC>
+__device__ __forceinline__ void ilu_apply_fast(const Ctx<real, ND>& X, const IluPre<real>& P,
+                                               const IluRow<real, ND>& R, const IluSmem<real, ND>& S,
+                                               const int (&act)[ND], SRC&& src, real* z) {
+  const int32_t N = X.N, n = S.n, t = (int32_t)threadIdx.x;
+  __syncthreads();
+  if (R.i >= 0) {
+#pragma unroll
+    for (int k = 0; k < ND; k++)
+      if (act[k]) S.zv[k * n + R.self] = src(k, R.i);
+  }
+  __syncthreads();
+  for (int l = 0; l < P.nlev; l++) {
+    if (R.lvl == l) {
+      const real di = S.rd[t];
+#pragma unroll
+      for (int k = 0; k < ND; k++) {
+        if (!act[k]) continue;
+        real w = S.zv[k * n + R.self];
+#pragma unroll
+        for (int s = 0; s < 2 * ND; s++)
+          if ((R.m >> s) & 1u) w -= S.rc[s * n + t] * S.zv[k * n + S.rl[s * n + t]];
+        S.zv[k * n + R.self] = w * di;
+      }
+    }
+    __syncthreads();
+  }
+  for (int l = P.nlev - 1; l >= 0; l--) {
+    if (R.lvl == l && (R.m >> 8)) {
+      const real di = S.rd[t];
+#pragma unroll
+      for (int k = 0; k < ND; k++) {
+        if (!act[k]) continue;
+        real acc = 0;
+#pragma unroll
+        for (int s = 0; s < 2 * ND; s++)
+          if ((R.m >> (8 + s)) & 1u) acc += S.rc[s * n + t] * S.zv[k * n + S.rl[s * n + t]];
+        S.zv[k * n + R.self] -= di * acc;
+      }
+    }
+    __syncthreads();
+  }
+  if (R.i >= 0) {
+#pragma unroll
+    for (int k = 0; k < ND; k++)
+      if (act[k]) z[(size_t)k * N + R.i] = S.zv[k * n + R.self];
+  }
+}
+
+// Pivots of this CTA's block: the shared-memory sweep when S is set up.
+template <typename real, int ND>
+__device__ void ilu_factor(const Ctx<real, ND>& X, const IluPre<real>& P, const real* Cdiag, const real* Coff,
+                           const IluSmem<real, ND>& S) {
+  if (S.n) ilu_factor_fast<real, ND>(X, P, Cdiag, Coff, S);
+  else ilu_factor_levels<real, ND>(X, P, Cdiag, Coff);
+}
+
 // Restart of a BiCGStab that failed: x = x0 (zero when x0 is null), r = rhat
 // (the shadow residual is the initial residual b - M x0 and never changes),
 // and the scalars from the saved norms.  The iterations of the failed attempt
@@ -182,8 +384,13 @@ __device__ void bicg_restart(const Ctx<real, ND>& X, BiState& bs, real* x, const
 template <typename real, int ND, bool TR>
 __device__ bool bicgstab_ilu(const Ctx<real, ND>& X, const IluPre<real>& P, BiState& bs, int maxit,
                              const real* Cdiag, const real* Coff, real* x, real* r, const real* rhat, real* p,
-                             real* v, real* y, real* z, real* t) {
+                             real* v, real* y, real* z, real* t, const IluSmem<real, ND>& S) {
   const int32_t N = X.N;
+  IluRow<real, ND> R{};
+  if (S.n) {
+    R = ilu_row_of<real, ND>(X, P);
+    ilu_stage_rows<real, ND, TR>(X, P, Cdiag, Coff, R, S);
+  }
   while (bs.any && bs.it < maxit) {
     // PA
     {
@@ -196,12 +403,14 @@ __device__ bool bicgstab_ilu(const Ctx<real, ND>& X, const IluPre<real>& P, BiSt
         om[k] = pick<real>(bs.omega[k], bs.omega_f[k]);
       }
       const int first = bs.first;
-      ilu_apply<real, ND, TR>(X, P, Cdiag, Coff, act, [&](int k, int32_t i) -> real {
+      auto src = [&](int k, int32_t i) -> real {
         const size_t o_ = (size_t)k * N + i;
         const real pn = first ? r[o_] : r[o_] + beta[k] * (p[o_] - om[k] * v[o_]);
         p[o_] = pn;
         return pn;
-      }, y);
+      };
+      if (S.n) ilu_apply_fast<real, ND>(X, P, R, S, act, src, y);
+      else ilu_apply<real, ND, TR>(X, P, Cdiag, Coff, act, src, y);
       if (!plain_sync(X.g)) return false;
     }
     // PB
@@ -239,10 +448,12 @@ __device__ bool bicgstab_ilu(const Ctx<real, ND>& X, const IluPre<real>& P, BiSt
         act[k] = bs.active[k];
         al[k] = pick<real>(bs.alpha[k], bs.alpha_f[k]);
       }
-      ilu_apply<real, ND, TR>(X, P, Cdiag, Coff, act, [&](int k, int32_t i) -> real {
+      auto src = [&](int k, int32_t i) -> real {
         const size_t o_ = (size_t)k * N + i;
         return r[o_] - al[k] * v[o_];
-      }, z);
+      };
+      if (S.n) ilu_apply_fast<real, ND>(X, P, R, S, act, src, z);
+      else ilu_apply<real, ND, TR>(X, P, Cdiag, Coff, act, src, z);
       if (!plain_sync(X.g)) return false;
     }
     // PD

@@ -18,6 +18,7 @@ struct SolverOpts {
   double p_refine_rtol;      // FP32 mode: outer FP64 residual tolerance of the pressure solve (0 = off)
   double p_inner_rtol;       // FP32 mode: inner CG tolerance per refinement round
   int32_t grad_paths;        // adjoint: bit 1 keeps the advection-solve paths, bit 2 the pressure-solve paths
+  int32_t ilu_soff;          // byte offset of the ILU(0) sweep area in dynamic shared memory, -1: none
 };
 
 // Fill the CTA's neighbour table (dynamic shared memory) when its cell range
