@@ -5,9 +5,11 @@
  * finite-volume PISO scheme on structured multi-block grids with coordinate
  * transforms described in arXiv:2505.16992 (PICT), Sec. 2.1-2.3 and App. A:
  * assembly of the advection-diffusion matrix C = A + H, a BiCGStab predictor
- * solve, n pressure correctors (divergence of h, Jacobi-preconditioned CG on
- * the pressure matrix P, velocity correction), block-interface and boundary
- * handling, and the discrete adjoint of that step.
+ * solve (optionally ILU(0)-preconditioned, App. A.5), n pressure correctors
+ * (divergence of h, preconditioned CG on the pressure matrix P: Jacobi or
+ * y-line blocks, velocity correction), block-interface and boundary handling,
+ * and the discrete adjoint of that step; plus the turbulence-statistics
+ * operators of Sec. 2.5 (plane records, their merge and adjoint, budgets).
  *
  * Conventions (shared by every entry point):
  *   - Sides 0..5 = -x, +x, -y, +y, -z, +z (2D uses 0..3).
