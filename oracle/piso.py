@@ -51,8 +51,13 @@ implements; each is listed in the design notes):
 * R7 the pressure system is singular (constants); b is projected to zero mean
   and each solution is returned with zero mean.
 * R10 the outflow update uses the stable factor c/(1+c), c = 2 dt |T_j . u_m|.
-* Non-orthogonal cross terms (alpha_jk, j != k) are not part of this scheme;
-  meshes where they are non-zero are rejected.
+* App. A.2 "Non-Orthogonal Grids" (Eqs. difNonOrthoMatDiscrete,
+  velRHSnonOrtho, pressureRHSnonOrtho): on meshes whose cross metrics
+  alpha_jk (j != k) do not vanish (``allow_nonorthogonal=True``), the cross
+  derivatives of the diffusion and of the pressure Laplacian are deferred to
+  the right-hand sides with the previous iterate and the solves repeated
+  ``n_nonortho`` times (non-orthogonal corrector steps).  Forward step only:
+  the adjoint rejects such meshes.  Without the flag they are rejected.
 * Block connections join a side to the opposite side of the same axis with the
   same tangential ordering (no axis permutation).
 """
@@ -75,6 +80,7 @@ from . import krylov
 class Options:
     pred_grad_p: bool = False    # R4: predictor rhs of Eq. velRHSdiscrete (no grad p^n) by default
     n_correctors: int = 2        # App. A.1: two corrector rounds
+    n_nonortho: int = 1          # App. A.2: solves per predictor / pressure solve on non-orthogonal meshes
     adv_rtol: float = 1e-13
     p_rtol: float = 1e-13
     atol: float = 0.0
@@ -95,7 +101,7 @@ class Mesh:
     """
 
     def __init__(self, ndim: int, blocks: Sequence, connections: Sequence = (),
-                 dirichlet: Sequence = (), outflow: Sequence = ()):
+                 dirichlet: Sequence = (), outflow: Sequence = (), allow_nonorthogonal: bool = False):
         self.ndim = d = ndim
         self.nsides = 2 * d
         self.res = [tuple(int(v) for v in (b[0] if isinstance(b, tuple) else b.res)) for b in blocks]
@@ -115,8 +121,10 @@ class Mesh:
         self.T = np.linalg.inv(M)                     # T[i, j, k] = d xi^j / d x_k at cell i
         G = np.einsum("njk,nlk->njl", self.T, self.T) * self.J[:, None, None]
         self.alpha = np.stack([G[:, j, j] for j in range(d)])   # (d, N): alpha_jj
+        self.G = G                                    # (N, d, d): alpha_jk = J T_j . T_k
         off = np.abs(G - np.einsum("nj,jk->njk", self.alpha.T, np.eye(d)))
-        if off.max() > 1e-9 * np.abs(G).max():
+        self.has_cross = bool(off.max() > 1e-9 * np.abs(G).max())
+        if self.has_cross and not allow_nonorthogonal:
             raise ValueError("non-orthogonal mesh: cross-diffusion terms are not supported")
 
         # --- neighbours and boundary faces
@@ -398,6 +406,80 @@ def correct(mesh: Mesh, h, A, p):
     return h - grad_p(mesh, p) / A[None, :]
 
 
+# ----------------------------------------------------------------------------
+# non-orthogonal cross terms (App. A.2 "Non-Orthogonal Grids")
+# ----------------------------------------------------------------------------
+
+def _cell_diff(mesh: Mesh, q: np.ndarray, k: int, ghost) -> np.ndarray:
+    """Central difference of the cell values q (N,) along computational axis k:
+    (q_{k+} - q_{k-}) / 2, a missing neighbour (a boundary face on side s)
+    replaced by ghost(s) (N,)."""
+    hi = np.where(mesh.inner[2 * k + 1], q[mesh.safe_nb[2 * k + 1]], ghost(2 * k + 1))
+    lo = np.where(mesh.inner[2 * k], q[mesh.safe_nb[2 * k]], ghost(2 * k))
+    return 0.5 * (hi - lo)
+
+
+def _cross_flux_sum(mesh: Mesh, coef: np.ndarray, dq, bface_grad) -> np.ndarray:
+    """sum_j sum_{k != j} sum_{faces f of P on axis j} N_f c_jk,f g_k,f for one
+    scalar field: c_jk,f the face mean of coef (N, d, d) over P and its
+    neighbour, g_k,f the mean of the two cells' central differences dq[k] (N,).
+    Boundary faces: c_jk of P and g_k = bface_grad(s, k) (N,), or no flux when
+    bface_grad is None."""
+    d = mesh.ndim
+    out = np.zeros(mesh.N)
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        P = np.nonzero(mesh.inner[s])[0]
+        F = mesh.nb[s, P]
+        B = np.nonzero(mesh.is_bface[s])[0]
+        for k in range(d):
+            if k == j:
+                continue
+            cf = 0.5 * (coef[P, j, k] + coef[F, j, k])
+            out[P] += n * cf * 0.5 * (dq[k][P] + dq[k][F])
+            if bface_grad is not None and len(B):
+                out[B] += n * coef[B, j, k] * bface_grad(s, k)[B]
+    return out
+
+
+def cross_diffusion(mesh: Mesh, u: np.ndarray, nu: float, bval) -> np.ndarray:
+    """Cross-derivative part of the viscous term per unit volume, (nu / J_P)
+    sum_j sum_{k != j} sum_f N_f mean(alpha_jk) (d_k u)_f, for every velocity
+    component (the part of Eqs. difNonOrthoMatDiscrete / velRHSnonOrtho that
+    the orthogonal matrix C leaves out).  Cell differences use the ghost value
+    2 u_b - u_P at Dirichlet faces (linear through the face value); on a
+    Dirichlet face the tangential derivative is the central difference of the
+    boundary values of the neighbouring faces on the same side (a face whose
+    neighbour has none uses its own value in its place)."""
+    d = mesh.ndim
+    out = np.zeros((d, mesh.N))
+    for c in range(d):
+        q = u[c]
+        ghost = lambda s, c=c, q=q: 2.0 * bval[s][c] - q
+        dq = [_cell_diff(mesh, q, k, ghost) for k in range(d)]
+
+        def bgrad(s, k, c=c):
+            fb = bval[s][c]
+            hi_n, lo_n = mesh.safe_nb[2 * k + 1], mesh.safe_nb[2 * k]
+            hi = np.where(mesh.inner[2 * k + 1] & mesh.is_bface[s][hi_n], fb[hi_n], fb)
+            lo = np.where(mesh.inner[2 * k] & mesh.is_bface[s][lo_n], fb[lo_n], fb)
+            return 0.5 * (hi - lo)
+        out[c] = nu * _cross_flux_sum(mesh, mesh.G, dq, bgrad) / mesh.J
+    return out
+
+
+def cross_pressure(mesh: Mesh, p: np.ndarray, A: np.ndarray) -> np.ndarray:
+    """Cross-derivative part of the pressure operator, sum_j sum_{k != j} sum_f
+    N_f mean(alpha_jk / A) (d_k p)_f (cell-integrated like the matrix P of Eq.
+    pMatDiscrete; the part Eq. pressureRHSnonOrtho moves to the right-hand
+    side).  Cell differences take p_P for a missing neighbour and no cross flux
+    crosses a Dirichlet-velocity face (zero-Neumann pressure, App. A.3)."""
+    d = mesh.ndim
+    ghost = lambda s: p
+    dq = [_cell_diff(mesh, p, k, ghost) for k in range(d)]
+    return _cross_flux_sum(mesh, mesh.G / A[:, None, None], dq, None)
+
+
 def outflow_update(mesh: Mesh, u, bval, dt):
     """Advective outflow (App. A.3, Eq. advOut, reading R10): each outflow face
     moves towards its cell value with factor c/(1+c), c = 2 dt |T_j . u_m|; then
@@ -518,17 +600,27 @@ def piso_step(mesh: Mesh, u, p, dt, nu, S=None, bval=None, opts: Optional[Option
         bval = outflow_update(mesh, u, bval, dt)
     C, rhs0 = assemble_C(mesh, u, nu, dt, S, bval)
     rhs = rhs0 - grad_p(mesh, p) if opts.pred_grad_p else rhs0
-    ustar, adv_info = solve_C(mesh, C, rhs, u, opts)
+    X = mesh.has_cross
+    # non-orthogonal meshes: the cross-derivative terms are deferred to the
+    # right-hand side with the previous iterate, n_nonortho solves each
+    ustar = u
+    for _ in range(opts.n_nonortho if X else 1):
+        rhs_m = rhs + cross_diffusion(mesh, ustar, nu, bval) if X else rhs
+        ustar, adv_info = solve_C(mesh, C, rhs_m, ustar, opts)
     A = C.diag
     Pm = assemble_P(mesh, A)
     uk, pk = ustar, p
     corr = []
     p_infos = []
     for _ in range(opts.n_correctors):
-        h = pressure_rhs_vec(mesh, C, rhs0, uk)
+        rhs0_k = rhs0 + cross_diffusion(mesh, uk, nu, bval) if X else rhs0
+        h = pressure_rhs_vec(mesh, C, rhs0_k, uk)
         b = divergence(mesh, h, bval)
         b = b - b.mean()
-        x, info = solve_P(mesh, Pm, b, pk, opts)
+        x = pk
+        for _ in range(opts.n_nonortho if X else 1):
+            bm = b - cross_pressure(mesh, x, A) if X else b
+            x, info = solve_P(mesh, Pm, bm - bm.mean() if X else bm, x, opts)
         p_infos.append(info)
         unew = correct(mesh, h, A, x)
         corr.append(dict(u_in=uk, h=h, b=b, x=x))
@@ -605,6 +697,8 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
     solve's output (u*, or every corrector's pressure) as a constant of the
     backward pass, i.e. its transposed solve contributes zero.  With both off
     only the bypass paths of Eq. jnone remain."""
+    if mesh.has_cross:
+        raise NotImplementedError("the adjoint of the non-orthogonal step is not part of this oracle")
     opts = opts or Options()
     d, N = mesh.ndim, mesh.N
     C, Pm = tape["C"], tape["Pm"]
@@ -716,11 +810,11 @@ def offdiag_matvec_T(mesh: Mesh, M: Matrix, y):
 # convenience
 # ----------------------------------------------------------------------------
 
-def mesh_from_case(case) -> Mesh:
+def mesh_from_case(case, allow_nonorthogonal: bool = False) -> Mesh:
     """Build a Mesh from any object with ndim/blocks/connections/dirichlet/outflow
     attributes (the seeded input generators produce such objects)."""
     return Mesh(case.ndim, [(b.res, b.vertices) for b in case.blocks], case.connections,
-                case.dirichlet, case.outflow)
+                case.dirichlet, case.outflow, allow_nonorthogonal)
 
 
 def rollout(mesh: Mesh, u, p, dt, nu, S, steps, opts=None, bval=None):
