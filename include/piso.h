@@ -117,6 +117,16 @@ typedef struct {
                             is ILU(0) of the whole matrix in cell order.  The level tables are built
                             on the host whenever the launch layout changes (finalize, set_options,
                             autotune).  Batches reject any value but NONE (PISO_EINVAL). */
+  int32_t n_nonortho;    /* non-orthogonal meshes (App. A.2 "Non-Orthogonal Grids"): 0 (default)
+                            rejects blocks whose cross metrics alpha_jk = J T_j . T_k (j != k) do
+                            not vanish; n >= 1 accepts them: the cross derivatives of the viscous
+                            term and of the pressure operator are deferred to the right-hand sides
+                            with the previous iterate (the predictor's, each corrector's input
+                            velocity, the previous pressure) and every predictor and pressure solve
+                            is repeated n times (non-orthogonal corrector steps).  Forward step only
+                            on such meshes: piso_step_adjoint returns PISO_ESTATE, batches and
+                            pred_grad_p = 1 reject them (PISO_EINVAL).  Ignored on orthogonal
+                            meshes. */
 } piso_options;
 
 /* Values of piso_options.p_precond. */
@@ -147,6 +157,8 @@ typedef struct {
   double p_rhs_norm[4];   /* norm of each pressure solve's (projected) right-hand side */
   int32_t adv_precond_used; /* the BiCGStab ran ILU-preconditioned: 0 no, 1 from the start,
                                2 after the plain attempt failed (PISO_ADV_PRECOND_ILU_ON_FAILURE) */
+  /* on non-orthogonal meshes adv_iters and p_iters sum the iterations of all
+     non-orthogonal corrector steps */
 } piso_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -162,7 +174,8 @@ piso_status piso_domain_create(int32_t ndim, int32_t prec, piso_domain** out);
  * Metrics T = d xi / d x and J = det(d x / d xi) are formed at cell centres
  * from opposite face-centre differences (App. A.2 "Grid Transformations").
  * Grids whose cross metrics alpha_jk (j != k) do not vanish are rejected at
- * finalize.  *block_id receives the block's index. */
+ * finalize unless piso_options.n_nonortho >= 1.  *block_id receives the
+ * block's index. */
 piso_status piso_block_add(piso_domain* d, const int32_t res[3], const double* vertices,
                            int32_t* block_id);
 

@@ -67,6 +67,7 @@ struct AdjCall {
   IluTab ilu;                // ILU(0) tables of the launch layout (when adv_ilu)
   real* ilud;                // [N] ILU(0) reciprocal pivots (rebuilt here from the taped C)
   int32_t adv_ilu;           // 0 none, 1 ILU(0), 2 ILU(0) after a failed plain solve
+  int32_t n_nonortho;        // always 0: the adjoint is not provided on non-orthogonal meshes
   uint32_t* bar;
   double* partials;
   int32_t* status;
@@ -328,7 +329,8 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   int ilu_used = 0;
   if constexpr (ILU) {
     if (path_adv) {
-      const IluPre<real> IP = ilu_setup<real>(A.ilu, A.ilud, g.rank);
+      // the level tables exist only when the ILU(0) preconditioner is on
+      const IluPre<real> IP = A.adv_ilu ? ilu_setup<real>(A.ilu, A.ilud, g.rank) : IluPre<real>{};
       const IluSmem<real, ND> IS = ilu_smem<real, ND>(X, o);
       if (A.adv_ilu == 1) {
         ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);

@@ -97,6 +97,8 @@ struct piso_domain {
   IluTab ilu_tab{};
   bool ilu_ready = false;      // tables match (ncta, threads, ownership) of the launches
   int ilu_key[3] = {-1, -1, -1};
+  bool has_cross = false;      // some cell has non-zero cross metrics (accepted with n_nonortho >= 1)
+  void* gx = nullptr;          // [d(d-1)/2][N] cross metrics on the device
   bool pending = false;
   cudaStream_t pending_stream = nullptr;
   int pending_kind = 0;        // 1 forward, 2 adjoint
@@ -211,7 +213,7 @@ void put(std::vector<char>& buf, size_t i, double v) {
 enum WsIdx {
   W_U, W_RHS0, W_R, W_RHAT, W_P0, W_P1, W_V0, W_V1, W_T, W_POFF, W_PDIAG, W_FH, W_B, W_CX,
   W_CRB0, W_CRB1, W_CWB0, W_CWB1, W_CSB0, W_CSB1, W_CP, W_PINV, W_INVA, W_AW, W_X64, W_RIN, W_CE,
-  W_LFA, W_LFM, W_LFC, W_ILUD,
+  W_LFA, W_LFM, W_LFC, W_ILUD, W_BX,
   // adjoint scratch
   A_GA, A_GCOFF, A_GRHS0, A_GW, A_W, A_GG, A_GU, A_GX, A_Z, A_DU,
   W_COUNT
@@ -222,7 +224,7 @@ int ws_units(int k, int nd) {
   switch (k) {
     case W_PDIAG: case W_B: case W_CX: case W_CRB0: case W_CRB1: case W_CWB0: case W_CWB1: case W_CSB0:
     case W_CSB1: case W_CP: case A_GA: case A_GX: case W_PINV: case W_INVA: case W_RIN: case W_CE:
-    case W_LFA: case W_LFM: case W_LFC: case W_ILUD:
+    case W_LFA: case W_LFM: case W_LFC: case W_ILUD: case W_BX:
       return 1;
     case W_X64:
       return 2;     // N doubles (two float units; the FP64 mode over-allocates)
@@ -324,6 +326,8 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
   c.ilu = d->ilu_tab;
   c.ilud = (real*)d->ws[W_ILUD];
   c.adv_ilu = d->opts.adv_precond;
+  c.n_nonortho = d->has_cross ? d->opts.n_nonortho : 0;
+  c.bx = (real*)d->ws[W_BX];
   c.bar = d->bar;
   c.partials = d->partials;
   c.status = d->status;
@@ -469,7 +473,8 @@ const void* adj_kernel_ptr(int prec, int nd, int threads = 512, bool ilu = false
   return prec == PISO_FP64 ? adj_ptr_t<double>(nd, threads, ilu) : adj_ptr_t<float>(nd, threads, ilu);
 }
 
-bool uses_ilu(const piso_domain* d) { return d->opts.adv_precond != PISO_ADV_PRECOND_NONE; }
+// The extended instantiation: ILU(0) predictor or a non-orthogonal mesh.
+bool uses_ilu(const piso_domain* d) { return d->opts.adv_precond != PISO_ADV_PRECOND_NONE || d->has_cross; }
 
 // ILU(0) tables for the current launch layout (App. A.5 preconditioner of the
 // BiCGStab).  Each CTA preconditions with the diagonal block of the cells it
@@ -697,6 +702,7 @@ void piso_default_options(piso_options* o) {
   o->grad_paths = PISO_GRAD_ADV | PISO_GRAD_P;
   o->p_precond = PISO_PRECOND_AUTO;
   o->adv_precond = PISO_ADV_PRECOND_NONE;
+  o->n_nonortho = 0;
 }
 
 piso_status piso_domain_create(int32_t ndim, int32_t prec, piso_domain** out) {
@@ -798,6 +804,9 @@ static piso_status validate_options(piso_domain* d, const piso_options* o) {
     return fail(d, PISO_EINVAL, "p_precond must be PISO_PRECOND_AUTO, _JACOBI or _LINE");
   if (o->adv_precond < PISO_ADV_PRECOND_NONE || o->adv_precond > PISO_ADV_PRECOND_ILU_ON_FAILURE)
     return fail(d, PISO_EINVAL, "adv_precond must be PISO_ADV_PRECOND_NONE, _ILU or _ILU_ON_FAILURE");
+  if (o->n_nonortho < 0 || o->n_nonortho > 64) return fail(d, PISO_EINVAL, "n_nonortho must be 0..64");
+  if (d && d->has_cross && (o->n_nonortho < 1 || o->pred_grad_p))
+    return fail(d, PISO_EINVAL, "a non-orthogonal mesh needs n_nonortho >= 1 and pred_grad_p = 0");
   return PISO_OK;
 }
 
@@ -869,6 +878,8 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
   // metrics
   const size_t e = d->elem;
   std::vector<char> hJ(N * e), hT((size_t)nd * nd * N * e), hA((size_t)nd * N * e);
+  const int ncross = nd * (nd - 1) / 2;
+  std::vector<double> hX((size_t)ncross * N, 0.0);   // cross metrics, kept when some are non-zero
   for (size_t b = 0; b < d->blocks.size(); b++) {
     const HostBlock& hb = d->blocks[b];
     for (int z = 0; z < hb.res[2]; z++)
@@ -889,10 +900,16 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
           for (int k = 0; k < nd; k++)
             if (k != 1 && G[k][k] > 0) d->aniso = std::max(d->aniso, G[1][1] / G[k][k]);
           for (int j = 0; j < nd; j++)
-            for (int l = 0; l < nd; l++)
-              if (j != l && std::fabs(G[j][l]) > 1e-9 * std::max(std::fabs(G[j][j]), std::fabs(G[l][l])))
-                return fail(d, PISO_EINVAL,
-                            "non-orthogonal cell %zu: cross-diffusion metrics are not supported", i);
+            for (int l = j + 1; l < nd; l++) {
+              hX[(size_t)(j + l - 1) * N + i] = G[j][l];
+              if (std::fabs(G[j][l]) > 1e-9 * std::max(std::fabs(G[j][j]), std::fabs(G[l][l]))) {
+                if (d->opts.n_nonortho < 1 || d->opts.pred_grad_p)
+                  return fail(d, PISO_EINVAL,
+                              "non-orthogonal cell %zu: cross metrics need n_nonortho >= 1 (and pred_grad_p = 0)",
+                              i);
+                d->has_cross = true;
+              }
+            }
           if (d->prec == PISO_FP64) {
             put<double>(hJ, i, Jv);
             for (int j = 0; j < nd; j++) {
@@ -960,6 +977,7 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
     d->J = a.take(N * e);
     d->T = a.take((size_t)nd * nd * N * e);
     d->alpha = a.take((size_t)nd * N * e);
+    d->gx = d->has_cross ? a.take((size_t)ncross * N * e) : nullptr;
     d->bf_cell = (int32_t*)a.take(nbf1 * sizeof(int32_t));
     d->bf_side = (int8_t*)a.take(nbf1);
     d->bf_out = (int8_t*)a.take(nbf1);
@@ -988,6 +1006,7 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
   S.J = d->J;
   S.T = d->T;
   S.alpha = d->alpha;
+  S.Gx = d->gx;
   S.bf_cell = d->bf_cell;
   S.bf_side = d->bf_side;
   S.bf_out = d->bf_out;
@@ -996,6 +1015,14 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
   CUDA_TRY(d, cudaMemcpy(d->J, hJ.data(), hJ.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(d, cudaMemcpy(d->T, hT.data(), hT.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(d, cudaMemcpy(d->alpha, hA.data(), hA.size(), cudaMemcpyHostToDevice));
+  if (d->has_cross) {
+    std::vector<char> hx((size_t)ncross * N * e);
+    for (size_t q = 0; q < hX.size(); q++) {
+      if (d->prec == PISO_FP64) put<double>(hx, q, hX[q]);
+      else put<float>(hx, q, hX[q]);
+    }
+    CUDA_TRY(d, cudaMemcpy(d->gx, hx.data(), hx.size(), cudaMemcpyHostToDevice));
+  }
   CUDA_TRY(d, cudaMemcpy(d->bf_cell, bf_cell.data(), nbf1 * sizeof(int32_t), cudaMemcpyHostToDevice));
   CUDA_TRY(d, cudaMemcpy(d->bf_side, bf_side.data(), nbf1, cudaMemcpyHostToDevice));
   CUDA_TRY(d, cudaMemcpy(d->bf_out, bf_out.data(), nbf1, cudaMemcpyHostToDevice));
@@ -1353,6 +1380,7 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
     c.lfm = W(W_LFM);
     c.lfc = W(W_LFC);
     c.ilud = W(W_ILUD);
+    c.bx = W(W_BX);
     c.bar = (uint32_t*)(base + SL.bar);
     c.status = (int32_t*)(base + SL.status);
     c.istats = (int32_t*)(base + SL.istats);

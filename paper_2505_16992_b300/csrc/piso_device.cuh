@@ -70,6 +70,8 @@ struct DomStatic {
   const void* J;             // [N]
   const void* T;             // [d*d][N], T[(j*d+k)*N + i] = d xi^j / d x_k
   const void* alpha;         // [d][N]  alpha_jj = J T_j . T_j
+  const void* Gx;            // [d(d-1)/2][N] cross metrics alpha_jk, j < k, pairs (0,1) (0,2) (1,2); null
+                             // on orthogonal meshes
   // boundary faces
   const int32_t* bf_cell;    // [nbf] adjacent cell
   const int8_t* bf_side;     // [nbf] side of that cell

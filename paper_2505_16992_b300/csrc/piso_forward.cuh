@@ -6,6 +6,7 @@
 // range; phases are separated by the group barrier.
 #pragma once
 #include "piso_krylov.cuh"
+#include "piso_nonortho.cuh"
 
 namespace piso {
 
@@ -62,7 +63,9 @@ struct FwdCall {
   IluTab ilu;                // ILU(0) tables of the launch layout (when adv_ilu)
   real* ilud;                // [N]    ILU(0) reciprocal pivots
   int32_t adv_ilu;           // BiCGStab preconditioner: 0 none, 1 ILU(0), 2 ILU(0) after a failed plain solve
-                             // (read by the ILU instantiation of the kernel only)
+                             // (read by the extended instantiation of the kernel only)
+  int32_t n_nonortho;        // non-orthogonal mesh: solves per predictor / pressure solve (0: orthogonal)
+  real* bx;                  // [N]    pressure right-hand side with the cross terms (non-orthogonal)
   // group control
   uint32_t* bar;
   double* partials;
@@ -277,10 +280,17 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
           for (int k = 0; k < ND; k++) gp[k] += Tm(j, k, P) * dp;
         }
       }
+      real xv[ND];
+#pragma unroll
+      for (int k = 0; k < ND; k++) xv[k] = 0;
+      if constexpr (ILU) {
+        if (A.n_nonortho)
+          cross_visc<real, ND>(D, c, A.u_in, A.bval, nbf, reinterpret_cast<const real*>(D.Gx), J, nu, xv);
+      }
 #pragma unroll
       for (int k = 0; k < ND; k++) {
         A.rhs0[(size_t)k * N + P] = rhs[k];
-        const real b = rhs[k] - gp[k];
+        const real b = rhs[k] - gp[k] + xv[k];
         const real* x = A.u_in + (size_t)k * N;
         real cx = diag * x[P];
 #pragma unroll
@@ -303,28 +313,66 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   // predictor solve (App. A.5: BiCGStab, ILU(0)-preconditioned throughout or
   // only after the plain solve failed)
   int ilu_used = 0;
+  int adv_prev[3] = {0, 0, 0};   // thread 0: iterations of earlier non-orthogonal predictor solves
   if constexpr (ILU) {
-    const IluPre<real> IP = ilu_setup<real>(A.ilu, A.ilud, g.rank);
+    // the level tables exist only when the ILU(0) preconditioner is on (the extended
+    // instantiation also runs non-orthogonal meshes without it)
+    const IluPre<real> IP = A.adv_ilu ? ilu_setup<real>(A.ilu, A.ilud, g.rank) : IluPre<real>{};
     const IluSmem<real, ND> IS = ilu_smem<real, ND>(X, o);
-    if (A.adv_ilu == 1) {
-      ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
-      ilu_used = 1;
-      if (!bicgstab_ilu<real, ND, false>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv[0],
-                                         A.vv[0], A.pv[1], A.vv[1], A.t, IS))
-        return;
-    } else {
+    bool factored = false;
+    auto solve = [&]() -> bool {
+      if (A.adv_ilu == 1) {
+        if (!factored) ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
+        factored = true;
+        ilu_used = 1;
+        return bicgstab_ilu<real, ND, false>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv[0],
+                                             A.vv[0], A.pv[1], A.vv[1], A.t, IS);
+      }
       if (!bicgstab<real, ND, false>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv, A.vv, A.t))
-        return;
+        return false;
       // bs is the same in every CTA (each runs the same updates on the same
       // reduced values), so all CTAs take the same branch
       if (A.adv_ilu == 2 && !bicg_all_conv<ND>(bs)) {
         bicg_restart<real, ND>(X, bs, A.ustar, A.u_in, A.r, A.rhat, o.adv_rtol, o.atol, g.status);
-        ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
+        if (!factored) ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
+        factored = true;
         ilu_used = 2;
-        if (!bicgstab_ilu<real, ND, false>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv[0],
-                                           A.vv[0], A.pv[1], A.vv[1], A.t, IS))
-          return;
+        return bicgstab_ilu<real, ND, false>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv[0],
+                                             A.vv[0], A.pv[1], A.vv[1], A.t, IS);
       }
+      return true;
+    };
+    if (!solve()) return;
+    // non-orthogonal corrector steps: the cross terms of the latest u*, then
+    // the predictor solve again from it
+    for (int m = 1; m < A.n_nonortho; m++) {
+      if (threadIdx.x == 0)
+        for (int k = 0; k < ND; k++) adv_prev[k] += bs.iters[k] + bs.iters_prev[k];
+      Acc<real> a[2 * ND];
+#pragma unroll
+      for (int k = 0; k < 2 * ND; k++) a[k].zero();
+      X.cells([&](const Cell& c) {
+        const int32_t P = c.i;
+        real xv[ND];
+        cross_visc<real, ND>(D, c, A.ustar, A.bval, nbf, reinterpret_cast<const real*>(D.Gx), J, nu, xv);
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+          const real b = A.rhs0[(size_t)k * N + P] + xv[k];
+          const real* x = A.ustar + (size_t)k * N;
+          real cx = A.Cdiag[P] * x[P];
+#pragma unroll
+          for (int s = 0; s < NSD; s++)
+            if (c.nb[s] >= 0) cx += A.Coff[(size_t)s * N + P] * x[c.nb[s]];
+          const real r = b - cx;
+          A.r[(size_t)k * N + P] = r;
+          A.rhat[(size_t)k * N + P] = r;
+          a[k].add_prod(b, b);
+          a[ND + k].add_prod(r, r);
+        }
+      });
+      if (!reduce_sync<real, 2 * ND>(g, a, [&](const double* q) { bicg_start<ND>(bs, q, o.adv_rtol, o.atol, g.status); }))
+        return;
+      if (!solve()) return;
     }
   } else {
     if (!bicgstab<real, ND, false>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.ustar, A.r, A.rhat, A.pv, A.vv, A.t))
@@ -333,7 +381,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   if (threadIdx.x == 0 && g.rank == 0) {
     int nc = 0;
     for (int k = 0; k < ND; k++) {
-      A.istats[k] = bs.iters[k] + bs.iters_prev[k];
+      A.istats[k] = adv_prev[k] + bs.iters[k] + bs.iters_prev[k];
       A.dstats[k] = sqrt(bs.res2[k]);
       if (!bs.conv[k]) nc = 1;
     }
@@ -370,7 +418,13 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       } else {
         A.xk[kc - 1][P] = A.cx[P] - pick<real>(s_mean, s_mean_f);
       }
-      real hv[ND];
+      real hv[ND], xv[ND];
+#pragma unroll
+      for (int k = 0; k < ND; k++) xv[k] = 0;
+      if constexpr (ILU) {
+        if (A.n_nonortho)
+          cross_visc<real, ND>(D, c, uk, A.bval, nbf, reinterpret_cast<const real*>(D.Gx), J, nu, xv);
+      }
 #pragma unroll
       for (int k = 0; k < ND; k++) {
         const real* x = uk + (size_t)k * N;
@@ -378,7 +432,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
 #pragma unroll
         for (int s = 0; s < NSD; s++)
           if (c.nb[s] >= 0) hu += A.Coff[(size_t)s * N + P] * x[c.nb[s]];
-        hv[k] = (A.rhs0[(size_t)k * N + P] - hu) * ia;
+        hv[k] = (A.rhs0[(size_t)k * N + P] + xv[k] - hu) * ia;
         h[(size_t)k * N + P] = hv[k];
       }
 #pragma unroll
@@ -426,9 +480,38 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
     }
     // pressure solve (App. A.5: CG; Chronopoulos-Gear form), in the FP32 mode
     // refined against an FP64 residual when asked or when the CG stalls
-    if (!pressure_solve<real, ND>(X, cs, rs, o, A.Pdiag, A.Pinv, A.Poff, A.b, s_mean, A.cx, A.x64, A.rin, A.ce,
-                                  A.crb, A.cwb, A.csb, A.cp, A.istats, A.dstats, kc))
-      return;
+    bool nonortho = false;
+    if constexpr (ILU) nonortho = A.n_nonortho > 0;
+    if (!nonortho) {
+      if (!pressure_solve<real, ND>(X, cs, rs, o, A.Pdiag, A.Pinv, A.Poff, A.b, s_mean, A.cx, A.x64, A.rin, A.ce,
+                                    A.crb, A.cwb, A.csb, A.cp, A.istats, A.dstats, kc))
+        return;
+    } else {
+      // non-orthogonal corrector steps: b minus the cross terms of the
+      // previous pressure iterate (cx: the previous corrector's, then each
+      // solve's), then the pressure solve again from it
+      int p_tot = 0;
+      for (int m = 0; m < A.n_nonortho; m++) {
+        Acc<real> a[1];
+        a[0].zero();
+        X.cells([&](const Cell& c) {
+          const int32_t P = c.i;
+          const real bm = A.b[P] - cross_pres<real, ND>(D, c, A.cx, A.invA, reinterpret_cast<const real*>(D.Gx));
+          A.bx[P] = bm;
+          a[0].add(bm);
+        });
+        if (!reduce_sync<real, 1>(g, a, [&](const double* q) {
+              s_mean = q[0] / (double)N;
+              s_mean_f = (float)s_mean;
+            }))
+          return;
+        if (!pressure_solve<real, ND>(X, cs, rs, o, A.Pdiag, A.Pinv, A.Poff, A.bx, s_mean, A.cx, A.x64, A.rin,
+                                      A.ce, A.crb, A.cwb, A.csb, A.cp, A.istats, A.dstats, kc))
+          return;
+        if (threadIdx.x == 0 && g.rank == 0) p_tot += A.istats[4 + kc];
+      }
+      if (threadIdx.x == 0 && g.rank == 0) A.istats[4 + kc] = p_tot;
+    }
     // C4: u = h - A^-1 grad x (Eq. velCorrDiscrete, R5); mean of x (R7)
     {
       Acc<real> a[1];

@@ -87,6 +87,7 @@ def test_default_options_fill_every_field(lib):
     assert o.grad_paths == capi.PISO_GRAD_ADV | capi.PISO_GRAD_P
     assert o.p_precond == capi.PISO_PRECOND_AUTO
     assert o.adv_precond == capi.PISO_ADV_PRECOND_NONE
+    assert o.n_nonortho == 0
 
 
 def test_pressure_preconditioner_is_validated(lib):
@@ -114,6 +115,32 @@ def test_advection_preconditioner_is_validated(lib):
         assert lib.piso_finalize(h, C.byref(o)) == 1
         assert b"adv_precond" in lib.piso_last_error(h)
     lib.piso_domain_destroy(h)
+
+
+def test_nonorthogonal_block_needs_n_nonortho(lib):
+    """A sheared block (cross metrics alpha_xy != 0) is refused at finalize
+    unless n_nonortho >= 1; the check runs before any device work."""
+    h = C.c_void_p()
+    assert lib.piso_domain_create(2, 0, C.byref(h)) == 0
+    res = (C.c_int32 * 3)(3, 2, 1)
+    pts = [(x + 0.5 * y, y) for y in range(3) for x in range(4)]
+    verts = (C.c_double * 24)(*[v for pt in pts for v in pt])
+    bid = C.c_int32()
+    assert lib.piso_block_add(h, res, verts, C.byref(bid)) == 0
+    for s in range(4):
+        nf = 2 if s < 2 else 3
+        vals = (C.c_double * (2 * nf))(*([0.0] * (2 * nf)))
+        assert lib.piso_set_dirichlet(h, 0, s, vals) == 0
+    o = capi.default_options()
+    assert lib.piso_finalize(h, C.byref(o)) == 1
+    assert b"n_nonortho" in lib.piso_last_error(h)
+    lib.piso_domain_destroy(h)
+    bad = capi.default_options(n_nonortho=-1)
+    h2 = C.c_void_p()
+    assert lib.piso_domain_create(2, 0, C.byref(h2)) == 0
+    assert lib.piso_block_add(h2, res, verts, C.byref(bid)) == 0
+    assert lib.piso_finalize(h2, C.byref(bad)) == 1
+    lib.piso_domain_destroy(h2)
 
 
 def test_gradient_path_bits_are_validated(lib):
