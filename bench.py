@@ -430,14 +430,18 @@ def main():
                     help="pressure CG preconditioner (auto: the autotuner times both on anisotropic grids)")
     ap.add_argument("--adv-precond", default="none", choices=["none", "ilu", "ilu_on_failure"],
                     help="BiCGStab preconditioner of the predictor solve (ILU(0), or ILU(0) after a failed plain solve)")
+    ap.add_argument("--nonortho", type=int, default=1,
+                    help="non-orthogonal corrector steps on the sheared channel (piso_options.n_nonortho)")
     ap.add_argument("--no-ilu-compare", action="store_true",
                     help="skip timing the BiCGStab preconditioners on the strongly stretched channel")
     ap.add_argument("--compare", action="store_true",
                     help="also time FP64 and refined FP32 at matched pressure tolerances")
     ap.add_argument("--workload", default="channel3d",
-                    choices=["channel3d", "channel3d-mid", "channel3d-large", "channel3d-stretched", "batch64"],
+                    choices=["channel3d", "channel3d-mid", "channel3d-large", "channel3d-stretched",
+                             "channel3d-sheared", "batch64"],
                     help="channel3d: 64x48x32 (default); channel3d-large: 256x192x128 (HBM-bound sizes); "
                          "channel3d-stretched: 64x48x32 with tanh gamma 3 and dt 0.2 (for --adv-precond); "
+                         "channel3d-sheared: 64x48x32 with cells slanted by x += 0.5 y (non-orthogonal, forward only); "
                          "batch64: 64 independent 2D simulations in one launch")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -463,15 +467,20 @@ def main():
         dist.init_process_group("nccl")
 
     sizes = {"channel3d": (64, 48, 32), "channel3d-mid": (160, 120, 80), "channel3d-large": (256, 192, 128),
-             "channel3d-stretched": (64, 48, 32)}
+             "channel3d-stretched": (64, 48, 32), "channel3d-sheared": (64, 48, 32)}
     stretched = args.workload == "channel3d-stretched"      # the case for the ILU(0) BiCGStab (App. A.5)
-    case = W.channel3d(*sizes[args.workload], **(dict(gamma=3.0, dt=0.2) if stretched else {}))
+    sheared = args.workload == "channel3d-sheared"          # a non-orthogonal grid (App. A.2)
+    extra = dict(gamma=3.0, dt=0.2) if stretched else (dict(shear=0.5) if sheared else {})
+    case = W.channel3d(*sizes[args.workload], **extra)
+    if sheared:
+        args.mode = "fwd"              # the adjoint step is not provided on non-orthogonal meshes
     prec = args.precision
     rtol = 1e-6 if prec == "fp32" else 1e-10
     pc_code = {"auto": capi.PISO_PRECOND_AUTO, "jacobi": capi.PISO_PRECOND_JACOBI, "line": capi.PISO_PRECOND_LINE}
     opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
                                 block_threads=args.threads, p_refine_rtol=args.refine,
-                                p_precond=pc_code[args.precond], adv_precond=ADV_PRECOND[args.adv_precond])
+                                p_precond=pc_code[args.precond], adv_precond=ADV_PRECOND[args.adv_precond],
+                                n_nonortho=args.nonortho if sheared else 0)
     dom = Domain.from_case(case, prec, opts)
     d, N = case.ndim, case.ncells
     w = 4 if prec == "fp32" else 8
@@ -560,6 +569,14 @@ def main():
     peak, peak_kind = measured_peaks()
     words = fwd_words_per_cell(d, st["adv_iters"][:d], st["p_iters"][:2], line=pc_used == "y-line",
                                ilu=st["adv_precond_used"] == 1)
+    if sheared:
+        # cross terms: each viscous evaluation reads u, the cross metrics and J
+        # (predictor loops + each corrector's h); each pressure one reads x, the
+        # cross metrics and 1/A, reads b and writes the right-hand side; every
+        # further predictor solve restarts (rhs0, C, u* in, r, rhat out)
+        nx_ = d * (d - 1) // 2
+        words += (d + nx_ + 1) * (args.nonortho + 2) + (nx_ + 4) * 2 * args.nonortho
+        words += (args.nonortho - 1) * (4 * d + 2 * d + 1)
     alg_bytes = words * N * w
     fwd_avg_s = sum(fwd_ms) / len(fwd_ms) / 1e3
     achieved = alg_bytes / fwd_avg_s / 1e9
@@ -660,6 +677,10 @@ def main():
             line["config"]["workload"] = line["config"]["workload"].replace("gamma 2", "gamma 3").replace(
                 "dt 0.01", "dt 0.2")
             line["metric"] = line["metric"].replace("channel", "channel (tanh gamma 3, dt 0.2)")
+        elif sheared:
+            line["config"]["workload"] += ", cells slanted x += 0.5 y (non-orthogonal)"
+            line["config"]["n_nonortho"] = args.nonortho
+            line["metric"] = line["metric"].replace("channel", "sheared channel")
         elif args.workload != "channel3d":
             tag = "x".join(str(v) for v in sizes[args.workload])
             line["config"]["workload"] = line["config"]["workload"].replace("64x48x32", tag)

@@ -188,15 +188,19 @@ def cavity3d(n: int = 16, nu: float = 0.01, dt: float = 0.005, steps: int = 10,
 
 def channel3d(nx: int = 64, ny: int = 48, nz: int = 32, gamma: float = 2.0,
               nu: float = 1.0 / 180.0, dt: float = 0.01, amp: float = 0.1, seed: int = 0,
-              steps: int = 1000) -> Case:
+              steps: int = 1000, shear: float = 0.0) -> Case:
     """3D channel, periodic in x and z, no-slip walls at y = -1, 1 with tanh
     refinement; box 2pi x 2 x pi (App. B.4 geometry).  Constant streamwise
     forcing G = 2 nu makes u = 1 - y^2 the laminar steady state; the initial field
-    is that profile plus seeded Gaussian noise."""
+    is that profile plus seeded Gaussian noise.  shear != 0 slants the cells
+    (x += shear * y at every vertex): the same channel on a non-orthogonal grid
+    (cross metric alpha_xy != 0, App. A.2 "Non-Orthogonal Grids")."""
     xv = uniform_vertices(nx, 0.0, 2.0 * math.pi)
     yv = tanh_vertices(ny, -1.0, 1.0, gamma)
     zv = uniform_vertices(nz, 0.0, math.pi)
     b = rect_block(xv, yv, zv)
+    if shear:
+        b.vertices[..., 0] += shear * b.vertices[..., 1]
     N = b.ncells
     yc = cell_centres(b)[1]
     rng = np.random.default_rng(seed)
