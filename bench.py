@@ -144,7 +144,8 @@ def whole_job_value(total_s: float, steps: int, world: int, dist=None, device="c
 
 # the headers fwd_kernel and adj_kernel are compiled from (the statistics
 # kernels' header is not among them)
-STEP_KERNEL_HEADERS = ("piso_device.cuh", "piso_krylov.cuh", "piso_lines.cuh", "piso_ilu.cuh", "piso_forward.cuh",
+STEP_KERNEL_HEADERS = ("piso_device.cuh", "piso_krylov.cuh", "piso_lines.cuh", "piso_ilu.cuh", "piso_nonortho.cuh",
+                       "piso_forward.cuh",
                        "piso_adjoint.cuh")
 
 
