@@ -439,11 +439,11 @@ cudaError_t coop_launch(const void* kernel, int grid, int threads, void** args, 
 constexpr int WIDE = 768;
 inline int width_class(int threads) { return threads > 512 ? WIDE : 512; }
 
-template <typename real, bool ILU>
+template <typename real, int MODE>
 const void* fwd_ptr_ti(int nd, int threads) {
   if (width_class(threads) == WIDE)
-    return nd == 2 ? (const void*)fwd_kernel<real, 2, WIDE, ILU> : (const void*)fwd_kernel<real, 3, WIDE, ILU>;
-  return nd == 2 ? (const void*)fwd_kernel<real, 2, 512, ILU> : (const void*)fwd_kernel<real, 3, 512, ILU>;
+    return nd == 2 ? (const void*)fwd_kernel<real, 2, WIDE, MODE> : (const void*)fwd_kernel<real, 3, WIDE, MODE>;
+  return nd == 2 ? (const void*)fwd_kernel<real, 2, 512, MODE> : (const void*)fwd_kernel<real, 3, 512, MODE>;
 }
 
 template <typename real, bool ILU>
@@ -453,11 +453,13 @@ const void* adj_ptr_ti(int nd, int threads) {
   return nd == 2 ? (const void*)adj_kernel<real, 2, 512, ILU> : (const void*)adj_kernel<real, 3, 512, ILU>;
 }
 
-// ilu: the instantiation with the ILU(0)-preconditioned BiCGStab (domains
-// whose adv_precond is not NONE); batches always take the plain one.
+// Forward instantiation: mode 0 plain, 1 with the ILU(0) predictor, 2 also
+// with the non-orthogonal cross terms; the adjoint has plain and ILU(0) ones
+// (it is not provided on non-orthogonal meshes).  Batches take the plain ones.
 template <typename real>
-const void* fwd_ptr_t(int nd, int threads, bool ilu = false) {
-  return ilu ? fwd_ptr_ti<real, true>(nd, threads) : fwd_ptr_ti<real, false>(nd, threads);
+const void* fwd_ptr_t(int nd, int threads, int mode = 0) {
+  return mode == 2 ? fwd_ptr_ti<real, 2>(nd, threads)
+                   : (mode == 1 ? fwd_ptr_ti<real, 1>(nd, threads) : fwd_ptr_ti<real, 0>(nd, threads));
 }
 
 template <typename real>
@@ -465,16 +467,16 @@ const void* adj_ptr_t(int nd, int threads, bool ilu = false) {
   return ilu ? adj_ptr_ti<real, true>(nd, threads) : adj_ptr_ti<real, false>(nd, threads);
 }
 
-const void* fwd_kernel_ptr(int prec, int nd, int threads = 512, bool ilu = false) {
-  return prec == PISO_FP64 ? fwd_ptr_t<double>(nd, threads, ilu) : fwd_ptr_t<float>(nd, threads, ilu);
+const void* fwd_kernel_ptr(int prec, int nd, int threads = 512, int mode = 0) {
+  return prec == PISO_FP64 ? fwd_ptr_t<double>(nd, threads, mode) : fwd_ptr_t<float>(nd, threads, mode);
 }
 
 const void* adj_kernel_ptr(int prec, int nd, int threads = 512, bool ilu = false) {
   return prec == PISO_FP64 ? adj_ptr_t<double>(nd, threads, ilu) : adj_ptr_t<float>(nd, threads, ilu);
 }
 
-// The extended instantiation: ILU(0) predictor or a non-orthogonal mesh.
-bool uses_ilu(const piso_domain* d) { return d->opts.adv_precond != PISO_ADV_PRECOND_NONE || d->has_cross; }
+bool uses_ilu(const piso_domain* d) { return d->opts.adv_precond != PISO_ADV_PRECOND_NONE; }
+int fwd_mode(const piso_domain* d) { return d->has_cross ? 2 : (uses_ilu(d) ? 1 : 0); }
 
 // ILU(0) tables for the current launch layout (App. A.5 preconditioner of the
 // BiCGStab).  Each CTA preconditions with the diagonal block of the cells it
@@ -597,7 +599,7 @@ piso_status choose_shape(piso_domain* d) {
   if (threads % 32 || threads > WIDE || threads < 32)
     return fail(d, PISO_EINVAL, "block_threads must be a multiple of 32 in [32, %d]", WIDE);
   int sms = 148;
-  int cap_f = max_coresident(fwd_kernel_ptr(d->prec, d->ndim, threads, uses_ilu(d)), threads, &sms);
+  int cap_f = max_coresident(fwd_kernel_ptr(d->prec, d->ndim, threads, fwd_mode(d)), threads, &sms);
   int cap_a = max_coresident(adj_kernel_ptr(d->prec, d->ndim, threads, uses_ilu(d)), threads, nullptr);
   int cap = std::min(cap_f, cap_a);
   if (cap <= 0) return fail(d, PISO_ECUDA, "kernel cannot be resident with %d threads", threads);
@@ -671,7 +673,7 @@ piso_status launch_fwd(piso_domain* d, const void* u_in, const void* p_in, void*
   CUDA_TRY(d, cudaMemsetAsync(d->status, 0, 64, st));
   CUDA_TRY(d, cudaMemsetAsync(d->istats, 0, 64, st));
   void* args[] = {&L};
-  CUDA_TRY(d, coop_launch(fwd_ptr_t<real>(d->ndim, d->threads, uses_ilu(d)), d->ncta, d->threads, args, st, smem));
+  CUDA_TRY(d, coop_launch(fwd_ptr_t<real>(d->ndim, d->threads, fwd_mode(d)), d->ncta, d->threads, args, st, smem));
   return PISO_OK;
 }
 
@@ -1145,7 +1147,7 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
     for (int pl : pls)
       for (int w : {512, WIDE}) {
         int sms = 148;
-        const int cap = std::min(max_coresident(fwd_kernel_ptr(d->prec, d->ndim, w, uses_ilu(d)), w, &sms),
+        const int cap = std::min(max_coresident(fwd_kernel_ptr(d->prec, d->ndim, w, fwd_mode(d)), w, &sms),
                                  max_coresident(adj_kernel_ptr(d->prec, d->ndim, w, uses_ilu(d)), w, nullptr));
         const int one_per_thread = (int)std::min<int64_t>(cap, (d->N + w - 1) / w);
         for (int nc : {std::min(cap, sms), one_per_thread})
@@ -1387,7 +1389,7 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
     c.dstats = (double*)(base + SL.dstats);
     c.partials = (double*)(base + SL.partials);
     void* args[] = {&L};
-    CUDA_TRY(d, coop_launch(fwd_ptr_t<real>(d->ndim, d->threads, uses_ilu(d)), d->ncta, d->threads, args, st, smem));
+    CUDA_TRY(d, coop_launch(fwd_ptr_t<real>(d->ndim, d->threads, fwd_mode(d)), d->ncta, d->threads, args, st, smem));
     return PISO_OK;
   };
   piso_status s = d->prec == PISO_FP64 ? launch(double(0)) : launch(float(0));

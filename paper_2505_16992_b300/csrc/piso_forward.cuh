@@ -103,7 +103,7 @@ __device__ __forceinline__ int find_group(int ngroups, const int32_t* cta_first)
   return gi;
 }
 
-template <typename real, int ND, bool ILU>
+template <typename real, int ND, int MODE>
 __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g) {
   __shared__ DomStatic D;
   __shared__ BiState bs;
@@ -283,7 +283,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       real xv[ND];
 #pragma unroll
       for (int k = 0; k < ND; k++) xv[k] = 0;
-      if constexpr (ILU) {
+      if constexpr (MODE == 2) {
         if (A.n_nonortho)
           cross_visc<real, ND>(D, c, A.u_in, A.bval, nbf, reinterpret_cast<const real*>(D.Gx), J, nu, xv);
       }
@@ -314,7 +314,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   // only after the plain solve failed)
   int ilu_used = 0;
   int adv_prev[3] = {0, 0, 0};   // thread 0: iterations of earlier non-orthogonal predictor solves
-  if constexpr (ILU) {
+  if constexpr (MODE >= 1) {
     // the level tables exist only when the ILU(0) preconditioner is on (the extended
     // instantiation also runs non-orthogonal meshes without it)
     const IluPre<real> IP = A.adv_ilu ? ilu_setup<real>(A.ilu, A.ilud, g.rank) : IluPre<real>{};
@@ -345,6 +345,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
     if (!solve()) return;
     // non-orthogonal corrector steps: the cross terms of the latest u*, then
     // the predictor solve again from it
+    if constexpr (MODE == 2)
     for (int m = 1; m < A.n_nonortho; m++) {
       if (threadIdx.x == 0)
         for (int k = 0; k < ND; k++) adv_prev[k] += bs.iters[k] + bs.iters_prev[k];
@@ -421,7 +422,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       real hv[ND], xv[ND];
 #pragma unroll
       for (int k = 0; k < ND; k++) xv[k] = 0;
-      if constexpr (ILU) {
+      if constexpr (MODE == 2) {
         if (A.n_nonortho)
           cross_visc<real, ND>(D, c, uk, A.bval, nbf, reinterpret_cast<const real*>(D.Gx), J, nu, xv);
       }
@@ -481,7 +482,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
     // pressure solve (App. A.5: CG; Chronopoulos-Gear form), in the FP32 mode
     // refined against an FP64 residual when asked or when the CG stalls
     bool nonortho = false;
-    if constexpr (ILU) nonortho = A.n_nonortho > 0;
+    if constexpr (MODE == 2) nonortho = A.n_nonortho > 0;
     if (!nonortho) {
       if (!pressure_solve<real, ND>(X, cs, rs, o, A.Pdiag, A.Pinv, A.Poff, A.b, s_mean, A.cx, A.x64, A.rin, A.ce,
                                     A.crb, A.cwb, A.csb, A.cp, A.istats, A.dstats, kc))
@@ -555,9 +556,11 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   }
 }
 
-// ILU: the instantiation with the ILU(0)-preconditioned predictor (App. A.5);
-// the plain one carries no preconditioner code at all.
-template <typename real, int ND, int MAXT, bool ILU>
+// MODE 0: the plain step; 1: with the ILU(0)-preconditioned predictor (App.
+// A.5); 2: also the non-orthogonal cross terms (App. A.2).  Each mode carries
+// only its own code, so a feature's register pressure cannot reach the modes
+// without it.
+template <typename real, int ND, int MAXT, int MODE>
 __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const __grid_constant__ Launch<FwdCall<real>> L) {
   __shared__ FwdCall<real> A;
   const int gi = find_group(L.ngroups, L.cta_first);
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const __grid_constant__ La
   g.epoch = 0;
   g.timeout_ns = L.o.timeout_ns;
   g.withhold = (L.o.withhold_cta == g.rank) ? 1 : 0;
-  fwd_group<real, ND, ILU>(A, L.o, g);
+  fwd_group<real, ND, MODE>(A, L.o, g);
 }
 
 }  // namespace piso
