@@ -56,8 +56,9 @@ implements; each is listed in the design notes):
   alpha_jk (j != k) do not vanish (``allow_nonorthogonal=True``), the cross
   derivatives of the diffusion and of the pressure Laplacian are deferred to
   the right-hand sides with the previous iterate and the solves repeated
-  ``n_nonortho`` times (non-orthogonal corrector steps).  Forward step only:
-  the adjoint rejects such meshes.  Without the flag they are rejected.
+  ``n_nonortho`` times (non-orthogonal corrector steps), and the adjoint runs
+  those loops in reverse (the starting pressure p^n now matters through the
+  pressure cross terms).  Without the flag such meshes are rejected.
 * Block connections join a side to the opposite side of the same axis with the
   same tangential ordering (no axis permutation).
 """
@@ -480,6 +481,79 @@ def cross_pressure(mesh: Mesh, p: np.ndarray, A: np.ndarray) -> np.ndarray:
     return _cross_flux_sum(mesh, mesh.G / A[:, None, None], dq, None)
 
 
+def _cell_diff_T(mesh: Mesh, gd: np.ndarray, k: int, gq: np.ndarray, ghost_coef: float, gghost=None):
+    """Transpose of _cell_diff along k: add to gq (N,) the gradient of
+    sum_Q gd_Q dq_k(Q).  A missing neighbour's ghost is ghost_coef * q_Q + 2 q_b
+    (velocity: -1, pressure: +1 with no boundary term); gghost(s) receives the
+    boundary-value part (velocity only)."""
+    for s, w in ((2 * k + 1, 0.5), (2 * k, -0.5)):
+        inn = mesh.inner[s]
+        np.add.at(gq, mesh.nb[s, inn], w * gd[inn])
+        out = ~inn
+        gq[out] += w * ghost_coef * gd[out]
+        if gghost is not None:
+            gghost(s)[out] += w * 2.0 * gd[out]
+
+
+def cross_diffusion_T(mesh: Mesh, g: np.ndarray, nu: float):
+    """Transpose of cross_diffusion in u and in the boundary values: returns
+    (dL/du (d, N), dL/dbval per side [nsides](d, N)) for dL/dX = g."""
+    d, N = mesh.ndim, mesh.N
+    gu = np.zeros((d, N))
+    gb = [np.zeros((d, N)) for _ in range(mesh.nsides)]
+    for c in range(d):
+        w = nu * g[c] / mesh.J
+        gdk = [np.zeros(N) for _ in range(d)]
+        for s in range(mesh.nsides):
+            j, n = s // 2, sign(s)
+            P = np.nonzero(mesh.inner[s])[0]
+            F = mesh.nb[s, P]
+            B = np.nonzero(mesh.is_bface[s])[0]
+            for k in range(d):
+                if k == j:
+                    continue
+                t = n * 0.5 * (mesh.G[P, j, k] + mesh.G[F, j, k]) * 0.5 * w[P]
+                np.add.at(gdk[k], P, t)
+                np.add.at(gdk[k], F, t)
+                if len(B):
+                    tb = n * mesh.G[B, j, k] * w[B] * 0.5
+                    hi_n, lo_n = mesh.safe_nb[2 * k + 1][B], mesh.safe_nb[2 * k][B]
+                    hi_ok = mesh.inner[2 * k + 1][B] & mesh.is_bface[s][hi_n]
+                    lo_ok = mesh.inner[2 * k][B] & mesh.is_bface[s][lo_n]
+                    np.add.at(gb[s][c], np.where(hi_ok, hi_n, B), tb)
+                    np.add.at(gb[s][c], np.where(lo_ok, lo_n, B), -tb)
+        for k in range(d):
+            _cell_diff_T(mesh, gdk[k], k, gu[c], -1.0, lambda s, c=c: gb[s][c])
+    return gu, gb
+
+
+def cross_pressure_T(mesh: Mesh, g: np.ndarray, p: np.ndarray, A: np.ndarray):
+    """Transpose of cross_pressure: (dL/dp (N,), dL/dA (N,)) at (p, A) for
+    dL/dY = g."""
+    d, N = mesh.ndim, mesh.N
+    gp = np.zeros(N)
+    gA = np.zeros(N)
+    dq = [_cell_diff(mesh, p, k, lambda s: p) for k in range(d)]
+    gdk = [np.zeros(N) for _ in range(d)]
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        P = np.nonzero(mesh.inner[s])[0]
+        F = mesh.nb[s, P]
+        for k in range(d):
+            if k == j:
+                continue
+            cf = 0.5 * (mesh.G[P, j, k] / A[P] + mesh.G[F, j, k] / A[F])
+            t = n * cf * 0.5 * g[P]
+            np.add.at(gdk[k], P, t)
+            np.add.at(gdk[k], F, t)
+            gk = 0.5 * (dq[k][P] + dq[k][F])
+            np.add.at(gA, P, -n * 0.5 * mesh.G[P, j, k] / A[P] ** 2 * gk * g[P])
+            np.add.at(gA, F, -n * 0.5 * mesh.G[F, j, k] / A[F] ** 2 * gk * g[P])
+    for k in range(d):
+        _cell_diff_T(mesh, gdk[k], k, gp, 1.0)
+    return gp, gA
+
+
 def outflow_update(mesh: Mesh, u, bval, dt):
     """Advective outflow (App. A.3, Eq. advOut, reading R10): each outflow face
     moves towards its cell value with factor c/(1+c), c = 2 dt |T_j . u_m|; then
@@ -604,9 +678,11 @@ def piso_step(mesh: Mesh, u, p, dt, nu, S=None, bval=None, opts: Optional[Option
     # non-orthogonal meshes: the cross-derivative terms are deferred to the
     # right-hand side with the previous iterate, n_nonortho solves each
     ustar = u
+    ustar_it = [u]
     for _ in range(opts.n_nonortho if X else 1):
         rhs_m = rhs + cross_diffusion(mesh, ustar, nu, bval) if X else rhs
         ustar, adv_info = solve_C(mesh, C, rhs_m, ustar, opts)
+        ustar_it.append(ustar)
     A = C.diag
     Pm = assemble_P(mesh, A)
     uk, pk = ustar, p
@@ -618,15 +694,18 @@ def piso_step(mesh: Mesh, u, p, dt, nu, S=None, bval=None, opts: Optional[Option
         b = divergence(mesh, h, bval)
         b = b - b.mean()
         x = pk
+        x_it = [pk]
         for _ in range(opts.n_nonortho if X else 1):
             bm = b - cross_pressure(mesh, x, A) if X else b
             x, info = solve_P(mesh, Pm, bm - bm.mean() if X else bm, x, opts)
+            x_it.append(x)
         p_infos.append(info)
         unew = correct(mesh, h, A, x)
-        corr.append(dict(u_in=uk, h=h, b=b, x=x))
+        corr.append(dict(u_in=uk, h=h, b=b, x=x, x_it=x_it))
         uk, pk = unew, x
     tape = dict(u=u, p=p, S=S, nu=nu, dt=dt, bval=bval, bval_in=bval_in, outflow_updated=updated, C=C,
-                rhs0=rhs0, rhs=rhs, ustar=ustar, Pm=Pm, corr=corr, u_out=uk, p_out=pk, adv_info=adv_info,
+                rhs0=rhs0, rhs=rhs, ustar=ustar, ustar_it=ustar_it, Pm=Pm, corr=corr, u_out=uk, p_out=pk,
+                adv_info=adv_info,
                 p_infos=p_infos)
     return uk, pk, tape
 
@@ -697,9 +776,8 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
     solve's output (u*, or every corrector's pressure) as a constant of the
     backward pass, i.e. its transposed solve contributes zero.  With both off
     only the bypass paths of Eq. jnone remain."""
-    if mesh.has_cross:
-        raise NotImplementedError("the adjoint of the non-orthogonal step is not part of this oracle")
     opts = opts or Options()
+    X = mesh.has_cross
     d, N = mesh.ndim, mesh.N
     C, Pm = tape["C"], tape["Pm"]
     A = C.diag
@@ -711,6 +789,10 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
     gu = np.array(du_out, dtype=np.float64, copy=True)
     gp_last = np.array(dp_out, dtype=np.float64, copy=True)
     gbs = []                          # dL/db of every corrector (divergence right-hand sides)
+    gbX = [np.zeros((d, N)) for _ in range(mesh.nsides)]   # non-orthogonal: dL/dbval via the cross terms
+    gx_carry = np.zeros(N)            # non-orthogonal: dL/d(the next corrector's starting pressure)
+    gnu_x = 0.0                       # non-orthogonal: dL/dnu through the cross terms (linear in nu)
+    gp_in_x = np.zeros(N)
     ncorr = len(tape["corr"])
     for k in reversed(range(ncorr)):
         cr = tape["corr"][k]
@@ -721,7 +803,33 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
         gA += np.sum(gu * grad_p(mesh, x), axis=0) / A ** 2
         if k == ncorr - 1:
             gx = gx + gp_last
-        if opts.grad_p:
+        if X:
+            gx = gx + gx_carry
+        if X and opts.grad_p:
+            # x_m = Pi P^+ Pi (b - Y(x_{m-1})), m = 1..n, x_0 = this corrector's
+            # starting pressure: transposed solves in reverse order
+            gb = np.zeros(N)
+            gxm = gx
+            xs = cr["x_it"]
+            for m in range(len(xs) - 1, 0, -1):
+                g0 = gxm - gxm.mean()
+                y, _ = solve_P(mesh, Pm, g0, np.zeros(N), opts)
+                y = y - y.mean()
+                for s in range(mesh.nsides):
+                    j = s // 2
+                    P = np.nonzero(mesh.inner[s])[0]
+                    F = mesh.nb[s, P]
+                    gw[j, P] += 0.5 * (y[P] - y[F]) * (xs[m][P] - xs[m][F])
+                gb += y
+                gyx, gyA = cross_pressure_T(mesh, -y, xs[m - 1], A)
+                gA += gyA
+                gxm = gyx
+            gx_carry = gxm
+            gh += divergence_T(mesh, gb)
+            gbs.append(gb)
+        elif X:
+            gx_carry = np.zeros(N)
+        if opts.grad_p and not X:
             # x = Pi(P^+ Pi b): transposed (symmetric) solve
             gx = gx - gx.mean()
             y, _ = solve_P(mesh, Pm, gx, np.zeros(N), opts)
@@ -737,30 +845,61 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
             gbs.append(gb)
         # without the pressure path (Sec. 2.4) x is a constant of the backward
         # pass: gx is dropped and neither b nor P receives a gradient
-        # h = (rhs0 - H u_in) / A
+        # h = (rhs0 (+ X(u_in)) - H u_in) / A
         gg = gh / A[None, :]
         gA -= np.sum(gh * h, axis=0) / A
         grhs0 += gg
         gu = -offdiag_matvec_T(mesh, C, gg)
         for s in range(mesh.nsides):
             gCoff[s] -= np.sum(gg * uin[:, mesh.safe_nb[s]], axis=0) * mesh.inner[s]
+        if X:
+            gxu, gxb = cross_diffusion_T(mesh, gg, nu)
+            gu = gu + gxu
+            for s in range(mesh.nsides):
+                gbX[s] += gxb[s]
+            if nu:
+                gnu_x += float(np.sum(gg * cross_diffusion(mesh, uin, nu, bval))) / nu
+    if X:
+        gp_in_x = gx_carry
     # pressure matrix built from w = alpha / A
     gA -= np.sum(gw * mesh.alpha, axis=0) / A ** 2
     # predictor: u* = C^-1 rhs
     ustar = tape["ustar"]
     # without the advection path (Sec. 2.4) u* is a constant of the backward
     # pass: the transposed solve is skipped and C, rhs receive nothing from it
-    z = solve_C_T(mesh, C, gu, opts) if opts.grad_adv else np.zeros_like(gu)
-    grhs = z
-    gA -= np.sum(z * ustar, axis=0)
-    for s in range(mesh.nsides):
-        gCoff[s] -= np.sum(z * ustar[:, mesh.safe_nb[s]], axis=0) * mesh.inner[s]
+    gu_pred = np.zeros((d, N))
+    if X and opts.grad_adv:
+        # u*_m = C^-1 (rhs + X(u*_{m-1})), m = 1..n, u*_0 = u^n
+        its = tape["ustar_it"]
+        grhs = np.zeros((d, N))
+        gm = gu
+        for m in range(len(its) - 1, 0, -1):
+            z = solve_C_T(mesh, C, gm, opts)
+            grhs += z
+            gA -= np.sum(z * its[m], axis=0)
+            for s in range(mesh.nsides):
+                gCoff[s] -= np.sum(z * its[m][:, mesh.safe_nb[s]], axis=0) * mesh.inner[s]
+            gxu, gxb = cross_diffusion_T(mesh, z, nu)
+            for s in range(mesh.nsides):
+                gbX[s] += gxb[s]
+            if nu:
+                gnu_x += float(np.sum(z * cross_diffusion(mesh, its[m - 1], nu, bval))) / nu
+            gm = gxu
+        gu_pred = gm
+    else:
+        z = solve_C_T(mesh, C, gu, opts) if opts.grad_adv else np.zeros_like(gu)
+        grhs = z
+        gA -= np.sum(z * ustar, axis=0)
+        for s in range(mesh.nsides):
+            gCoff[s] -= np.sum(z * ustar[:, mesh.safe_nb[s]], axis=0) * mesh.inner[s]
     grhs0 += grhs
     gp_in = -grad_p_T(mesh, grhs) if opts.pred_grad_p else np.zeros(N)
+    if X:
+        gp_in = gp_in + gp_in_x
     # assembly
-    gu_in = grhs0 / dt
+    gu_in = grhs0 / dt + gu_pred
     gS = grhs0.copy()
-    gnu = 0.0
+    gnu = gnu_x if X else 0.0
     gU = np.zeros((d, N))
     for s in range(mesh.nsides):
         j, n = s // 2, sign(s)
@@ -792,6 +931,9 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
         gbu[s][:, B] = g * a[None, :] - n * TjB * np.sum(g * ub, axis=0)[None, :]
         for gbk in gbs:
             gbu[s][:, B] += n * (mesh.J[B] * gbk[B])[None, :] * TjB
+    if X:
+        for s in range(mesh.nsides):
+            gbu[s] = gbu[s] + gbX[s]
     if tape.get("outflow_updated", False):
         g_in, gu_o = outflow_update_adjoint(mesh, tape["u"], tape["bval_in"], dt, gbu)
         gu_in = gu_in + gu_o

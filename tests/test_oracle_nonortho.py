@@ -150,8 +150,6 @@ def test_corrector_loops_converge_to_the_full_discrete_system():
     # one step is not the same as the orthogonal scheme on this mesh
     u1a, _, _ = O.piso_step(m, u0, p0, dt, nu, S, None, OP.Options(n_nonortho=1, solver="direct"))
     assert np.abs(u1a - u1).max() > 0
-    with pytest.raises(NotImplementedError):
-        O.piso_step_adjoint(m, tape, np.ones((2, m.N)), np.zeros(m.N))
 
 
 def _tg_sheared(n, nu, dt):
@@ -187,3 +185,76 @@ def test_taylor_green_decay_on_a_sheared_periodic_grid():
     order = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(order) > 1.5, (errs, order)
     assert errs[-1] < 5e-3, errs
+
+
+def _fd4(f, eps):
+    return (-f(2 * eps) + 8 * f(eps) - 8 * f(-eps) + f(-2 * eps)) / (12 * eps)
+
+
+def test_cross_operator_transposes_are_exact():
+    """<X(u), g> = <u, X_u^T g> + <bval, X_b^T g> and <Y(p), g> = <p, Y^T g>,
+    with the A-derivative of Y checked by central differences."""
+    res, h, shear = (7, 6), (0.1, 0.12), (0.6,)
+    m = _walled_mesh(res, h, shear, seed=8)
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal((2, m.N))
+    g = rng.standard_normal((2, m.N))
+    nu = 0.3
+    gu, gb = OP.cross_diffusion_T(m, g, nu)
+    lhs = float(np.sum(OP.cross_diffusion(m, u, nu, m.bval) * g))
+    rhs = float(np.sum(gu * u)) + sum(float(np.sum(gb[s] * m.bval[s])) for s in range(m.nsides))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    p = rng.standard_normal(m.N)
+    A = 1.0 + rng.random(m.N)
+    gy = rng.standard_normal(m.N)
+    gp, gA = OP.cross_pressure_T(m, gy, p, A)
+    assert abs(float(np.sum(OP.cross_pressure(m, p, A) * gy)) - float(np.sum(gp * p))) <= 1e-12 * np.abs(gp).sum()
+    dA = rng.standard_normal(m.N)
+    fd = _fd4(lambda t: float(np.sum(OP.cross_pressure(m, p, A + t * dA) * gy)), 1e-4)
+    assert abs(float(np.sum(gA * dA)) - fd) <= 1e-8 * abs(fd)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_nonorthogonal_adjoint_matches_central_differences(periodic):
+    """The adjoint of the non-orthogonal step (two corrector steps): every
+    input's directional derivative (u^n, p^n, which now enters through the
+    pressure cross terms, S, nu and the boundary values) equals 4th-order
+    central differences of the forward step."""
+    res, h, shear = (7, 6), (0.1, 0.12), (0.6,)
+    if periodic:
+        m0 = _walled_mesh(res, h, shear, seed=10)
+        dirichlet = [(0, s, m0.side_values(m0.bval, 0, s)) for s in (2, 3)]
+        m = O.Mesh(2, [((7, 6, 1), _verts(res, h, shear))], [(0, 0, 0, 1)], dirichlet, allow_nonorthogonal=True)
+    else:
+        m = _walled_mesh(res, h, shear, seed=10)
+    d, N = 2, m.N
+    rng = np.random.default_rng(12)
+    u0 = 0.5 * rng.standard_normal((d, N))
+    p0 = rng.standard_normal(N)
+    S0 = rng.standard_normal((d, N))
+    nu, dt = 0.05, 0.03
+    opts = OP.Options(n_nonortho=2, solver="direct")
+    ubar, pbar = rng.standard_normal((d, N)), rng.standard_normal(N)
+    _, _, tape = O.piso_step(m, u0, p0, dt, nu, S0, None, opts)
+    gu, gp, gS, gnu, gbv = O.piso_step_adjoint(m, tape, ubar, pbar, opts, want_bval=True)
+    assert np.abs(gp).max() > 0
+    dirs = [rng.standard_normal((d, N)), rng.standard_normal(N), rng.standard_normal((d, N)), 0.01]
+    bdir = [rng.standard_normal((d, N)) * m.is_bface[s][None, :] for s in range(m.nsides)]
+    for k in range(5):
+        def L(t):
+            args = [u0, p0, S0, nu]
+            bv = m.bval
+            if k < 4:
+                args[k] = args[k] + t * dirs[k]
+            else:
+                bv = np.stack([m.bval[s] + t * bdir[s] for s in range(m.nsides)])
+            u1, p1, _ = O.piso_step(m, args[0], args[1], dt, args[3], args[2], bv, opts)
+            return float(np.sum(ubar * u1) + np.sum(pbar * p1))
+        fd = _fd4(L, 1e-4)
+        if k < 3:
+            adj = float(np.sum([gu, gp, gS][k] * dirs[k]))
+        elif k == 3:
+            adj = gnu * dirs[3]
+        else:
+            adj = sum(float(np.sum(gbv[s] * bdir[s])) for s in range(m.nsides))
+        assert abs(adj - fd) <= 1e-6 * max(abs(fd), 1e-12), (k, adj, fd)
