@@ -113,3 +113,19 @@ def test_nonorthogonal_refusals():
     assert e.value.status == 7
     with pytest.raises(capi.PisoError):
         Batch([dom])
+
+
+def test_sheared_channel_fp32_after_n_steps():
+    """The forced channel with slanted cells (the bench's non-orthogonal
+    workload at a small size): FP32 against the FP64 oracle after 10 steps."""
+    from paper_2505_16992_b300 import workloads as W
+    c = W.channel3d(12, 10, 6, shear=0.5)
+    m = O.mesh_from_case(c, allow_nonorthogonal=True)
+    assert m.has_cross
+    dom = gpu_domain(c, "fp32", n_nonortho=1, adv_rtol=1e-6, p_rtol=1e-6)
+    u, p, S = to_dev(dom, c.u0, 3), to_dev(dom, c.p0), to_dev(dom, c.S, 3)
+    for _ in range(10):
+        u, p, st = dom.step(u, p, c.dt, c.nu, S)
+        assert st["status"] == "PISO_OK", st
+    uo, po, _ = O.rollout(m, c.u0, c.p0, c.dt, c.nu, c.S, 10, OP.Options(n_nonortho=1))
+    assert rel_err(host(u), uo) <= FP32_REL, rel_err(host(u), uo)
