@@ -415,6 +415,20 @@ def ilu_compare(prec, rtol, steps, with_adj, flush):
     return out
 
 
+def nonortho_compare(prec, rtol, steps, flush):
+    """Forward steps/s of the 64x48x32 channel with slanted cells (x += 0.5 y,
+    a non-orthogonal grid, App. A.2) at one and two non-orthogonal corrector
+    steps, beside the same channel with rectangular cells."""
+    from paper_2505_16992_b300 import workloads as W
+    out = {"workload": "channel3d 64x48x32 with cells slanted x += 0.5 y (forward step only)"}
+    kw = dict(adv_rtol=rtol, p_rtol=rtol)
+    out["orthogonal"] = time_variant(W.channel3d(64, 48, 32), prec, kw, steps, False, flush)["steps_per_s"]
+    for n in (1, 2):
+        r = time_variant(W.channel3d(64, 48, 32, shear=0.5), prec, dict(kw, n_nonortho=n), steps, False, flush)
+        out[f"n_nonortho_{n}"] = {"steps_per_s": r["steps_per_s"], "p_iters": r["p_iters"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,6 +447,8 @@ def main():
                     help="BiCGStab preconditioner of the predictor solve (ILU(0), or ILU(0) after a failed plain solve)")
     ap.add_argument("--nonortho", type=int, default=1,
                     help="non-orthogonal corrector steps on the sheared channel (piso_options.n_nonortho)")
+    ap.add_argument("--no-nonortho", action="store_true",
+                    help="skip timing the forward step on the channel with slanted (non-orthogonal) cells")
     ap.add_argument("--no-ilu-compare", action="store_true",
                     help="skip timing the BiCGStab preconditioners on the strongly stretched channel")
     ap.add_argument("--compare", action="store_true",
@@ -628,6 +644,9 @@ def main():
     ilu_cmp = None
     if not args.no_ilu_compare and args.workload == "channel3d":
         ilu_cmp = ilu_compare(prec, rtol, max(5, args.steps // 3), with_adj, flush)
+    no_cmp = None
+    if not args.no_nonortho and args.workload == "channel3d":
+        no_cmp = nonortho_compare(prec, rtol, max(5, args.steps // 3), flush)
 
     compare = None
     if args.compare:
@@ -670,6 +689,8 @@ def main():
             line["precision_compare"] = compare
         if ilu_cmp is not None:
             line["adv_precond_compare"] = ilu_cmp
+        if no_cmp is not None:
+            line["nonortho"] = no_cmp
         if paths is not None:
             line["grad_paths"] = paths
         if statistics is not None:
