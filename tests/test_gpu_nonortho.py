@@ -129,3 +129,21 @@ def test_sheared_channel_fp32_after_n_steps():
         assert st["status"] == "PISO_OK", st
     uo, po, _ = O.rollout(m, c.u0, c.p0, c.dt, c.nu, c.S, 10, OP.Options(n_nonortho=1))
     assert rel_err(host(u), uo) <= FP32_REL, rel_err(host(u), uo)
+
+
+def test_sheared_multiblock_step_with_outflow():
+    """The 5-block backward-facing step under one affine shear x += 0.3 y (the
+    blocks stay conformal): cross terms across block connections (neighbours
+    of neighbours in other blocks) and at the advective-outflow faces."""
+    from paper_2505_16992_b300 import workloads as W
+    c = W.bfs2d(n_in=(8, 4), n_ch=16, n_out=8, half=4, dt=0.02)
+    for b in c.blocks:
+        b.vertices[..., 0] += 0.3 * b.vertices[..., 1]
+    m = O.mesh_from_case(c, allow_nonorthogonal=True)
+    assert m.has_cross and m.has_outflow
+    dom = gpu_domain(c, n_nonortho=2, p_rtol=1e-12)
+    ug, pg, st = gpu_step(dom, c, c.u0, c.p0, c.S)
+    assert st["status"] == "PISO_OK", st
+    uo, po, _ = O.piso_step(m, c.u0, c.p0, c.dt, c.nu, c.S, None, OP.Options(n_nonortho=2))
+    assert rel_err(ug, uo) <= FP64_REL, rel_err(ug, uo)
+    assert rel_err(pg, po) <= 10 * FP64_REL, rel_err(pg, po)
