@@ -21,6 +21,16 @@
 
 using namespace piso;
 
+// The step kernels live in translation units of their own
+// (piso_kernels_{fwd,adj}_{f32,f64}.cu, built in parallel); these return the
+// address of one instantiation (wide: the 768-thread variant).
+namespace piso {
+const void* fwd_kernel_addr_f32(int nd, bool wide, int mode);
+const void* fwd_kernel_addr_f64(int nd, bool wide, int mode);
+const void* adj_kernel_addr_f32(int nd, bool wide, bool ilu);
+const void* adj_kernel_addr_f64(int nd, bool wide, bool ilu);
+}  // namespace piso
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -436,35 +446,22 @@ cudaError_t coop_launch(const void* kernel, int grid, int threads, void** args, 
 // Kernel variants: precision x dimension x CTA width (launch bound 512 or 768
 // threads; the wider variant holds one cell per thread for ~98k-cell domains
 // at 80 registers).
-constexpr int WIDE = 768;
+constexpr int WIDE = 768;   // the wide instantiations of piso_kernels_*.cu
 inline int width_class(int threads) { return threads > 512 ? WIDE : 512; }
-
-template <typename real, int MODE>
-const void* fwd_ptr_ti(int nd, int threads) {
-  if (width_class(threads) == WIDE)
-    return nd == 2 ? (const void*)fwd_kernel<real, 2, WIDE, MODE> : (const void*)fwd_kernel<real, 3, WIDE, MODE>;
-  return nd == 2 ? (const void*)fwd_kernel<real, 2, 512, MODE> : (const void*)fwd_kernel<real, 3, 512, MODE>;
-}
-
-template <typename real, bool ILU>
-const void* adj_ptr_ti(int nd, int threads) {
-  if (width_class(threads) == WIDE)
-    return nd == 2 ? (const void*)adj_kernel<real, 2, WIDE, ILU> : (const void*)adj_kernel<real, 3, WIDE, ILU>;
-  return nd == 2 ? (const void*)adj_kernel<real, 2, 512, ILU> : (const void*)adj_kernel<real, 3, 512, ILU>;
-}
 
 // Forward instantiation: mode 0 plain, 1 with the ILU(0) predictor, 2 also
 // with the non-orthogonal cross terms; the adjoint has plain and ILU(0) ones
 // (it is not provided on non-orthogonal meshes).  Batches take the plain ones.
 template <typename real>
 const void* fwd_ptr_t(int nd, int threads, int mode = 0) {
-  return mode == 2 ? fwd_ptr_ti<real, 2>(nd, threads)
-                   : (mode == 1 ? fwd_ptr_ti<real, 1>(nd, threads) : fwd_ptr_ti<real, 0>(nd, threads));
+  const bool wide = width_class(threads) == WIDE;
+  return sizeof(real) == 4 ? fwd_kernel_addr_f32(nd, wide, mode) : fwd_kernel_addr_f64(nd, wide, mode);
 }
 
 template <typename real>
 const void* adj_ptr_t(int nd, int threads, bool ilu = false) {
-  return ilu ? adj_ptr_ti<real, true>(nd, threads) : adj_ptr_ti<real, false>(nd, threads);
+  const bool wide = width_class(threads) == WIDE;
+  return sizeof(real) == 4 ? adj_kernel_addr_f32(nd, wide, ilu) : adj_kernel_addr_f64(nd, wide, ilu);
 }
 
 const void* fwd_kernel_ptr(int prec, int nd, int threads = 512, int mode = 0) {

@@ -349,7 +349,7 @@ __device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
 // Arrival and bounded wait of one CTA at barrier g.epoch (called by one thread
 // after __syncthreads ordered the CTA's writes).  The release increment makes
 // those writes visible to every CTA whose acquire load sees the count.
-__device__ __noinline__ int barrier_arrive_wait(const Group& g) {
+static __device__ __noinline__ int barrier_arrive_wait(const Group& g) {
   const uint32_t target = g.epoch * (uint32_t)g.ncta;
   if (!(g.withhold && g.epoch == 1)) {
 #ifdef PISO_FULL_FENCES

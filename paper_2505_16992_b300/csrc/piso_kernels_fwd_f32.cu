@@ -1,0 +1,19 @@
+// Forward step kernels, float storage: every instantiation of fwd_kernel
+// (2D/3D, 512/768 threads, modes plain / ILU(0) / non-orthogonal) compiled
+// in a translation unit of its own, so the library's units build in parallel;
+// piso_capi.cu launches them through the addresses returned here.
+#include "piso_forward.cuh"
+
+namespace piso {
+
+template <int MODE>
+static const void* fwd_addr_f32(int nd, bool wide) {
+  if (wide) return nd == 2 ? (const void*)fwd_kernel<float, 2, 768, MODE> : (const void*)fwd_kernel<float, 3, 768, MODE>;
+  return nd == 2 ? (const void*)fwd_kernel<float, 2, 512, MODE> : (const void*)fwd_kernel<float, 3, 512, MODE>;
+}
+
+const void* fwd_kernel_addr_f32(int nd, bool wide, int mode) {
+  return mode == 2 ? fwd_addr_f32<2>(nd, wide) : (mode == 1 ? fwd_addr_f32<1>(nd, wide) : fwd_addr_f32<0>(nd, wide));
+}
+
+}  // namespace piso
