@@ -168,23 +168,73 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(case, seconds_budget=20.0, steps_cap=3):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+# the CPU oracle: single-core and all-core timings, and the fields the GPU
+# path is compared with (the oracle is test infrastructure; this leg is the
+# only place the benchmark runs it)
+# ---------------------------------------------------------------------------
+def _oracle_worker(job):
+    """Run the FP64 oracle, as it stands, on a bounded sample of the 64x48x32
+    channel: fwd+adjoint steps (adjoint seeds dL/du^{n+1} = 1, dL/dp^{n+1} = 0)
+    from the seeded initial state until the step cap or the time budget.
+    Returns (steps, seconds of the step loop, fields of the last step or None)."""
+    seconds_budget, steps_cap, want_fields, size = job
     import numpy as np
     import oracle as O
+    from paper_2505_16992_b300 import workloads as W
+    case = W.channel3d(*size)
     m = O.mesh_from_case(case)
     u, p = case.u0, case.p0
-    t0 = time.perf_counter()
     n = 0
+    fields = None
+    t0 = time.perf_counter()
     while n < steps_cap:
         u1, p1, tape = O.piso_step(m, u, p, case.dt, case.nu, case.S)
-        O.piso_step_adjoint(m, tape, np.ones_like(u1), np.zeros_like(p1))
+        gu, gp, gS, gnu = O.piso_step_adjoint(m, tape, np.ones_like(u1), np.zeros_like(p1))
         n += 1
+        if want_fields:
+            fields = dict(u=u1, p=p1, du=gu, dS=gS, dnu=gnu)
+        u, p = u1, p1
         if time.perf_counter() - t0 > seconds_budget:
             break
-        u, p = u1, p1
-    dt = time.perf_counter() - t0
-    return n / dt, n, dt
+    return n, time.perf_counter() - t0, fields
+
+
+def _oracle_pool(workers, job):
+    """Run ``workers`` copies of _oracle_worker(job) in fresh (spawned)
+    processes with single-threaded numerical libraries; returns the results."""
+    import multiprocessing as mp
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(workers) as pool:
+            return pool.map(_oracle_worker, [job] * workers)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def cpu_baseline(seconds_budget=20.0, steps_cap=3, size=(64, 48, 32)):
+    """The oracle on one host core (steps/s) and its fields after the last step."""
+    n, dt, fields = _oracle_pool(1, (seconds_budget, steps_cap, True, size))[0]
+    return n / dt, n, dt, fields
+
+
+def cpu_baseline_all_cores(seconds_budget=15.0, max_workers=64, size=(64, 48, 32)):
+    """Independent copies of the oracle on every host core (one process each,
+    capped at max_workers), one or more fwd+adjoint steps each: aggregate
+    steps/s = all steps / the slowest copy's step-loop time."""
+    nproc = os.cpu_count() or 1
+    workers = max(1, min(nproc, max_workers))
+    res = _oracle_pool(workers, (seconds_budget, 1, False, size))
+    steps = sum(r[0] for r in res)
+    slowest = max(r[1] for r in res)
+    return steps / slowest, workers, nproc, steps, slowest
 
 
 def run_reference(args):
@@ -194,14 +244,10 @@ def run_reference(args):
         return 0
     from paper_2505_16992_b300 import workloads as W
     case = W.channel3d()
-    for _ in range(args.warmup):
-        pass
     per_step = []
-    t_all = time.perf_counter()
     for _ in range(max(args.steps, 1)):
-        v, n, dt = cpu_baseline(case, seconds_budget=60.0 / max(args.steps, 1), steps_cap=1)
+        v, n, dt, _ = cpu_baseline(seconds_budget=60.0 / max(args.steps, 1), steps_cap=1)
         per_step.append(dt / n)
-    total = time.perf_counter() - t_all
     value = len(per_step) / sum(per_step)
     line = {"metric": "PISO steps/s (fwd+adjoint), 64x48x32 channel", "value": value,
             "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -217,39 +263,153 @@ def run_reference(args):
     return 0
 
 
+class Arm:
+    """One configuration of the step on one workload: its domain (launch shape
+    and pressure preconditioner autotuned unless a CTA width is given), the
+    seeded fields, and timing along the rollout."""
+
+    def __init__(self, case, prec, opts_kw, threads=0):
+        import torch
+        from paper_2505_16992_b300 import capi
+        from paper_2505_16992_b300.solver import Domain
+        self.case, self.prec = case, prec
+        kw = dict(p_maxit=20000, adv_maxit=2000, block_threads=threads)
+        kw.update(opts_kw)
+        self.dom = dom = Domain.from_case(case, prec, capi.default_options(**kw))
+        d = case.ndim
+        self.u0, self.p0 = dom.field(case.u0, d), dom.field(case.p0)
+        self.S = None if case.S is None else dom.field(case.S, d)
+        if threads == 0:
+            self.shape = dom.autotune(self.u0, self.p0, case.dt, case.nu, self.S)
+        else:
+            self.shape = (threads, None, None)
+        pc = dom.get_options().p_precond
+        if pc == capi.PISO_PRECOND_AUTO:
+            pc = capi.PISO_PRECOND_LINE if dom.uses_line_precond() else capi.PISO_PRECOND_JACOBI
+        self.pc_used = "y-line" if pc == capi.PISO_PRECOND_LINE else "jacobi"
+        self.g = torch.ones_like(self.u0)          # adjoint seed dL/du^{n+1} = 1
+        self.w = 4 if prec == "fp32" else 8
+
+    def _step(self, u, p, uo, po, with_adj, sync):
+        st = self.dom.step(u, p, self.case.dt, self.case.nu, self.S, u_out=uo, p_out=po, sync=sync)[2]
+        ast = self.dom.step_adjoint(self.g, None, sync=sync)[4] if with_adj else None
+        return st, ast
+
+    def run(self, steps, warmup, flush, with_adj, on_start=None, on_end=None):
+        """Warm-up steps, then ``steps`` timed steps, each starting from the
+        previous step's output (the flow advances as in a rollout), each
+        bracketed by CUDA events on the launching stream with an untimed L2
+        flush before it; then the same steps replayed untimed from the same
+        state with statistics read back (the kernels are deterministic, so the
+        replay has the timed steps' iteration counts)."""
+        import torch
+        stream = torch.cuda.current_stream()
+        u, p = self.u0.clone(), self.p0.clone()
+        uo, po = torch.empty_like(u), torch.empty_like(p)
+        for _ in range(warmup):
+            self._step(u, p, uo, po, with_adj, False)
+            u, uo, p, po = uo, u, po, p
+        start = (u.clone(), p.clone())
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        if on_start:
+            on_start()
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.fill_(float(k))                       # L2 flush between timed steps (not timed)
+            ev[k][0].record(stream)
+            self.dom.step(u, p, self.case.dt, self.case.nu, self.S, u_out=uo, p_out=po, sync=False)
+            ev[k][1].record(stream)
+            if with_adj:
+                self.dom.step_adjoint(self.g, None, sync=False)
+            ev[k][2].record(stream)
+            u, uo, p, po = uo, u, po, p
+        torch.cuda.synchronize()
+        if on_end:
+            on_end()
+        fwd_ms = [e[0].elapsed_time(e[1]) for e in ev]
+        step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+        u, p = start
+        uo, po = torch.empty_like(u), torch.empty_like(p)
+        sts, asts = [], []
+        for k in range(steps):
+            st, ast = self._step(u, p, uo, po, with_adj, True)
+            sts.append(st)
+            asts.append(ast)
+            u, uo, p, po = uo, u, po, p
+        return dict(fwd_ms=fwd_ms, step_ms=step_ms, stats=sts, adj_stats=asts)
+
+    def rollout_fields(self, n):
+        """n fwd+adjoint steps from the seeded state (untimed): host u, p after
+        the last step and dL/du^n, dL/dS, dL/dnu of its adjoint."""
+        import torch
+        u, p = self.u0.clone(), self.p0.clone()
+        out = None
+        for _ in range(n):
+            u1, p1, st = self.dom.step(u, p, self.case.dt, self.case.nu, self.S)
+            du, dp, dS, dnu, ast = self.dom.step_adjoint(self.g, None)
+            assert st["status"] == "PISO_OK" and ast["status"] == "PISO_OK", (st, ast)
+            out = (u1, p1, du, dS, dnu)
+            u, p = u1, p1
+        host = lambda t: t.detach().double().cpu().numpy()
+        return dict(u=host(out[0]), p=host(out[1]), du=host(out[2]), dS=host(out[3]), dnu=out[4])
+
+
+def iter_summary(stats, adj_stats, d):
+    """min / median / max over the timed steps of the Krylov iteration counts:
+    the BiCGStab (largest over the velocity components) and each corrector's
+    pressure CG, forward and adjoint."""
+    def mmm(v):
+        return [min(v), statistics.median(v), max(v)]
+    out = {"adv": mmm([max(s["adv_iters"][:d]) for s in stats]),
+           "p": [mmm([s["p_iters"][k] for s in stats]) for k in range(2)]}
+    if adj_stats and adj_stats[0] is not None:
+        out["adj_adv"] = mmm([max(s["adv_iters"][:d]) for s in adj_stats])
+        out["adj_p"] = [mmm([s["p_iters"][k] for s in adj_stats]) for k in range(2)]
+    return out
+
+
+def arm_summary(arm, res, with_adj):
+    d = arm.case.ndim
+    out = {"fwd_steps_per_s": 1e3 * len(res["fwd_ms"]) / sum(res["fwd_ms"]),
+           "fwd_ms": statistics.mean(res["fwd_ms"]),
+           "launch": {"threads": arm.shape[0], "ctas": arm.shape[1]}, "pressure_precond": arm.pc_used,
+           "iterations": iter_summary(res["stats"], res["adj_stats"], d)}
+    if with_adj:
+        out["fwdadj_steps_per_s"] = 1e3 * len(res["step_ms"]) / sum(res["step_ms"])
+        out["adj_ms"] = statistics.mean([t - f for t, f in zip(res["step_ms"], res["fwd_ms"])])
+    return out
+
+
+def fwd_roofline(arm, res, peak, peak_kind, traffic=None, extra_words=0.0):
+    """Roofline of the forward-step kernel: algorithmic bytes (the words-per-cell
+    model at each timed step's iteration counts, x cells x word size) over the
+    summed launch times."""
+    d, N = arm.case.ndim, arm.case.ncells
+    byts = 0.0
+    for st in res["stats"]:
+        words = fwd_words_per_cell(d, st["adv_iters"][:d], st["p_iters"][:2], line=arm.pc_used == "y-line",
+                                   ilu=st["adv_precond_used"] == 1) + extra_words
+        byts += words * N * arm.w
+    achieved = byts / (sum(res["fwd_ms"]) / 1e3) / 1e9
+    words_mean = byts / len(res["stats"]) / (N * arm.w)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind, "kernel": "fwd_kernel", "words_per_cell": words_mean,
+            "alg_bytes_per_launch": words_mean * N * arm.w}
+
+
 def time_variant(case, prec, kw, steps, with_adj, flush):
-    """Steps/s of one precision/tolerance variant on the same workload (used to
-    compare FP32, refined FP32 and FP64 at matched pressure tolerances)."""
-    import torch
-    from paper_2505_16992_b300 import capi
-    from paper_2505_16992_b300.solver import Domain
-    o = capi.default_options(p_maxit=20000, adv_maxit=2000, **kw)
-    dom = Domain.from_case(case, prec, o)
+    """Steps/s of one precision/tolerance/preconditioner variant on a workload."""
+    arm = Arm(case, prec, kw)
+    res = arm.run(steps, 3, flush, with_adj)
+    st = res["stats"][-1]
     d = case.ndim
-    u, p, S = dom.field(case.u0, d), dom.field(case.p0), dom.field(case.S, d)
-    dom.autotune(u, p, case.dt, case.nu, S)
-    uo, po = torch.empty_like(u), torch.empty_like(p)
-    g = torch.ones_like(u)
-    for _ in range(3):
-        dom.step(u, p, case.dt, case.nu, S, u_out=uo, p_out=po, sync=False)
-        if with_adj:
-            dom.step_adjoint(g, None)
-    st = dom.step(u, p, case.dt, case.nu, S, u_out=uo, p_out=po)[2]
-    stream = torch.cuda.current_stream()
-    tot = 0.0
-    for _ in range(steps):
-        flush.fill_(0.0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        dom.step(u, p, case.dt, case.nu, S, u_out=uo, p_out=po, sync=False)
-        if with_adj:
-            dom.step_adjoint(g, None)
-        b.record(stream)
-        b.synchronize()
-        tot += a.elapsed_time(b) / 1e3
-    return {"steps_per_s": steps / tot, "p_iters": st["p_iters"][:2], "p_rounds": st["p_rounds"][:2],
-            "p_resid": st["p_resid"][:2], "adv_iters": st["adv_iters"][:d],
-            "adv_precond_used": st["adv_precond_used"]}
+    out = arm_summary(arm, res, with_adj)
+    out["steps_per_s"] = out["fwdadj_steps_per_s"] if with_adj else out["fwd_steps_per_s"]
+    out.update({"p_rounds": st["p_rounds"][:2], "p_resid": st["p_resid"][:2],
+                "adv_precond_used": st["adv_precond_used"]})
+    del arm
+    return out
 
 
 def time_statistics(dom, u, p, nu, steps, flush, peak):
@@ -425,8 +585,17 @@ def nonortho_compare(prec, rtol, steps, flush):
     out["orthogonal"] = time_variant(W.channel3d(64, 48, 32), prec, kw, steps, False, flush)["steps_per_s"]
     for n in (1, 2):
         r = time_variant(W.channel3d(64, 48, 32, shear=0.5), prec, dict(kw, n_nonortho=n), steps, False, flush)
-        out[f"n_nonortho_{n}"] = {"steps_per_s": r["steps_per_s"], "p_iters": r["p_iters"]}
+        out[f"n_nonortho_{n}"] = {"steps_per_s": r["steps_per_s"], "iterations": r["iterations"]}
     return out
+
+
+def rel_err_per_component(a, b):
+    """max over components of max|a_c - b_c| / max|b_c| (a scalar field: one
+    component)."""
+    import numpy as np
+    a = np.asarray(a, dtype=np.float64).reshape(-1, np.asarray(b).shape[-1])
+    b = np.asarray(b, dtype=np.float64).reshape(a.shape)
+    return float(max(np.abs(a[c] - b[c]).max() / max(np.abs(b[c]).max(), 1e-300) for c in range(a.shape[0])))
 
 
 def main():
@@ -451,8 +620,9 @@ def main():
                     help="skip timing the forward step on the channel with slanted (non-orthogonal) cells")
     ap.add_argument("--no-ilu-compare", action="store_true",
                     help="skip timing the BiCGStab preconditioners on the strongly stretched channel")
-    ap.add_argument("--compare", action="store_true",
-                    help="also time FP64 and refined FP32 at matched pressure tolerances")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline arm only: skip the other precision arms, the above-L2 channel, the gradient "
+                         "paths, statistics and preconditioner comparisons")
     ap.add_argument("--workload", default="channel3d",
                     choices=["channel3d", "channel3d-mid", "channel3d-large", "channel3d-stretched",
                              "channel3d-sheared", "batch64"],
@@ -468,11 +638,9 @@ def main():
     if args.workload == "batch64":
         return run_batch(args)
 
-    import numpy as np
     import torch
 
     from paper_2505_16992_b300 import capi, workloads as W
-    from paper_2505_16992_b300.solver import Domain
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -485,6 +653,7 @@ def main():
 
     sizes = {"channel3d": (64, 48, 32), "channel3d-mid": (160, 120, 80), "channel3d-large": (256, 192, 128),
              "channel3d-stretched": (64, 48, 32), "channel3d-sheared": (64, 48, 32)}
+    headline = args.workload == "channel3d"
     stretched = args.workload == "channel3d-stretched"      # the case for the ILU(0) BiCGStab (App. A.5)
     sheared = args.workload == "channel3d-sheared"          # a non-orthogonal grid (App. A.2)
     extra = dict(gamma=3.0, dt=0.2) if stretched else (dict(shear=0.5) if sheared else {})
@@ -494,112 +663,74 @@ def main():
     prec = args.precision
     rtol = 1e-6 if prec == "fp32" else 1e-10
     pc_code = {"auto": capi.PISO_PRECOND_AUTO, "jacobi": capi.PISO_PRECOND_JACOBI, "line": capi.PISO_PRECOND_LINE}
-    opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
-                                block_threads=args.threads, p_refine_rtol=args.refine,
-                                p_precond=pc_code[args.precond], adv_precond=ADV_PRECOND[args.adv_precond],
-                                n_nonortho=args.nonortho if sheared else 0)
-    dom = Domain.from_case(case, prec, opts)
+    opts_kw = dict(adv_rtol=rtol, p_rtol=rtol, p_refine_rtol=args.refine, p_precond=pc_code[args.precond],
+                   adv_precond=ADV_PRECOND[args.adv_precond], n_nonortho=args.nonortho if sheared else 0)
     d, N = case.ndim, case.ncells
-    w = 4 if prec == "fp32" else 8
-    u0 = dom.field(case.u0, d)
-    p0 = dom.field(case.p0)
-    S = dom.field(case.S, d)
-    u, p = u0.clone(), p0.clone()
-    u_out, p_out = torch.empty_like(u), torch.empty_like(p)
-    gu = torch.ones_like(u)
-    stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    if args.threads == 0:
-        shape = dom.autotune(u, p, case.dt, case.nu, S)
-    else:
-        shape = (args.threads, None, None)
     with_adj = args.mode == "fwdadj"
-    pc_opt = dom.get_options().p_precond
-    if pc_opt == capi.PISO_PRECOND_AUTO:     # no autotune: the library's choice from the grid
-        pc_opt = capi.PISO_PRECOND_LINE if dom.uses_line_precond() else capi.PISO_PRECOND_JACOBI
-    pc_used = "y-line" if pc_opt == capi.PISO_PRECOND_LINE else "jacobi"
+    extras = headline and not args.no_extras
 
-    def one_step():
-        dom.step(u, p, case.dt, case.nu, S, u_out=u_out, p_out=p_out, sync=False)
-        if with_adj:
-            dom.step_adjoint(gu, None)
-
-    # warm-up (also records iteration counts)
-    for _ in range(args.warmup):
-        one_step()
-    st = dom.step(u, p, case.dt, case.nu, S, u_out=u_out, p_out=p_out)[2]
-    adj_st = dom.step_adjoint(gu, None)[4] if with_adj else None
-    torch.cuda.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+    # ---- the headline arm: timed region with clocks sampled, barrier + max over ranks
+    arm = Arm(case, prec, opts_kw, threads=args.threads)
     clk_path = os.path.join(tempfile.gettempdir(), f"piso_clocks_{os.getpid()}.csv")
-    proc, fh = clocks_sampler_start(clk_path)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.fill_(float(k))                       # L2 flush between timed steps (not timed)
-        ev[k][0].record(stream)
-        kev[k][0].record(stream)
-        dom.step(u, p, case.dt, case.nu, S, u_out=u_out, p_out=p_out, sync=False)
-        kev[k][1].record(stream)
-        if with_adj:
-            dom.step_adjoint(gu, None)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    clocks = clocks_sampler_stop(proc, fh, clk_path, local)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    fwd_ms = [a.elapsed_time(b) for a, b in kev]
+    clk = {}
+
+    def on_start():
+        clk["proc"], clk["fh"] = clocks_sampler_start(clk_path)
+        if dist is not None:
+            dist.barrier()
+
+    def on_end():
+        if dist is not None:
+            dist.barrier()
+        clk["clocks"] = clocks_sampler_stop(clk["proc"], clk["fh"], clk_path, local)
+
+    res = arm.run(args.steps, args.warmup, flush, with_adj, on_start, on_end)
+    step_ms = res["step_ms"] if with_adj else res["fwd_ms"]
     total_s = sum(step_ms) / 1e3
     value = whole_job_value(total_s, args.steps, world, dist)
     total_s = world * args.steps / value
+    summ = arm_summary(arm, res, with_adj)
 
-    # end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step copies
+    # its inputs from pinned host memory and its outputs back (the outputs feed
+    # the next step's inputs)
+    dom = arm.dom
+    stream = torch.cuda.current_stream()
     hu = torch.empty((d, N), dtype=dom.dtype, pin_memory=True)
     hp = torch.empty((N,), dtype=dom.dtype, pin_memory=True)
-    hu.copy_(u0.cpu())
-    hp.copy_(p0.cpu())
-    hu_o = torch.empty_like(hu).pin_memory()
-    hp_o = torch.empty_like(hp).pin_memory()
+    hu.copy_(arm.u0.cpu())
+    hp.copy_(arm.p0.cpu())
+    u, p = torch.empty_like(arm.u0), torch.empty_like(arm.p0)
+    uo, po = torch.empty_like(u), torch.empty_like(p)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
         u.copy_(hu, non_blocking=True)
         p.copy_(hp, non_blocking=True)
-        one_step()
-        hu_o.copy_(u_out, non_blocking=True)
-        hp_o.copy_(p_out, non_blocking=True)
+        arm._step(u, p, uo, po, with_adj, False)
+        hu.copy_(uo, non_blocking=True)
+        hp.copy_(po, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    e2e = whole_job_value(e2e_s, args.steps, world, dist)
-    io_bytes = (d + 1) * N * w
+    e2e = whole_job_value(e0.elapsed_time(e1) / 1e3, args.steps, world, dist)
+    io_bytes = (d + 1) * N * arm.w
 
-    # roofline of the dominant kernel (the persistent forward-step kernel)
+    # ---- roofline of the dominant kernel (the persistent forward-step kernel)
     peak, peak_kind = measured_peaks()
-    words = fwd_words_per_cell(d, st["adv_iters"][:d], st["p_iters"][:2], line=pc_used == "y-line",
-                               ilu=st["adv_precond_used"] == 1)
+    extra_words = 0.0
     if sheared:
         # cross terms: each viscous evaluation reads u, the cross metrics and J
         # (predictor loops + each corrector's h); each pressure one reads x, the
         # cross metrics and 1/A, reads b and writes the right-hand side; every
         # further predictor solve restarts (rhs0, C, u* in, r, rhat out)
         nx_ = d * (d - 1) // 2
-        words += (d + nx_ + 1) * (args.nonortho + 2) + (nx_ + 4) * 2 * args.nonortho
-        words += (args.nonortho - 1) * (4 * d + 2 * d + 1)
-    alg_bytes = words * N * w
-    fwd_avg_s = sum(fwd_ms) / len(fwd_ms) / 1e3
-    achieved = alg_bytes / fwd_avg_s / 1e9
+        extra_words += (d + nx_ + 1) * (args.nonortho + 2) + (nx_ + 4) * 2 * args.nonortho
+        extra_words += (args.nonortho - 1) * (4 * d + 2 * d + 1)
     traffic = None
     prof = os.path.join(ROOT, "profiles", f"traffic_fwd_kernel_channel3d_{prec}.json")
-    if os.path.exists(prof) and args.workload == "channel3d":
+    if os.path.exists(prof) and headline:
         try:
             tj = json.load(open(prof))
             # counters are valid only for the kernel sources they were taken on
@@ -607,56 +738,101 @@ def main():
                 traffic = tj.get("dram_bytes_per_launch")
         except Exception:
             traffic = None
+    roof = fwd_roofline(arm, res, peak, peak_kind, traffic, extra_words)
+    if headline:
+        roof["working_set"] = "L2-resident (about 60 MB in FP32 against a 126 MB L2): the achieved figure is " \
+                              "algorithmic bytes over time, mostly served from L2; roofline_above_l2 is the HBM case"
+        if traffic:
+            roof["dram_gbs"] = traffic / (summ["fwd_ms"] / 1e3) / 1e9
 
-    # gradient-path variants of the adjoint (Sec. 2.4): the same fwd+adjoint
+    # ---- gradient-path variants of the adjoint (Sec. 2.4): the same fwd+adjoint
     # step with the advection and/or pressure solves left out of the backward pass
     paths = None
-    if with_adj:
-        adj_ms = [t - f for t, f in zip(step_ms, fwd_ms)]
-        paths = {"adv+p": {"steps_per_s": value, "adj_ms": sum(adj_ms) / len(adj_ms)}}
+    if with_adj and extras:
+        paths = {"adv+p": {"steps_per_s": value, "adj_ms": summ.get("adj_ms")}}
         nvar = max(5, args.steps // 3)
         tuned = dom.get_options()          # launch shape and pressure preconditioner as tuned
         for name, bits in (("adv", capi.PISO_GRAD_ADV), ("p", capi.PISO_GRAD_P), ("none", 0)):
             tuned.grad_paths = bits
             dom.set_options(tuned)
-            for _ in range(3):
-                one_step()
-            vst = dom.step_adjoint(gu, None)[4]
-            tf = ta = 0.0
-            for k in range(nvar):
-                flush.fill_(float(k))
-                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                e[0].record(stream)
-                dom.step(u, p, case.dt, case.nu, S, u_out=u_out, p_out=p_out, sync=False)
-                e[1].record(stream)
-                dom.step_adjoint(gu, None)
-                e[2].record(stream)
-                e[2].synchronize()
-                tf += e[0].elapsed_time(e[1])
-                ta += e[1].elapsed_time(e[2])
-            paths[name] = {"steps_per_s": 1e3 * nvar / (tf + ta), "adj_ms": ta / nvar,
-                           "adj_iters": {"adv": vst["adv_iters"][:d], "p": vst["p_iters"][:2]}}
+            r = arm.run(nvar, 3, flush, True)
+            paths[name] = {"steps_per_s": 1e3 * nvar / sum(r["step_ms"]),
+                           "adj_ms": statistics.mean([t - f for t, f in zip(r["step_ms"], r["fwd_ms"])]),
+                           "adj_iters": {"adv": r["adj_stats"][-1]["adv_iters"][:d],
+                                         "p": r["adj_stats"][-1]["p_iters"][:2]}}
+        tuned.grad_paths = capi.PISO_GRAD_ADV | capi.PISO_GRAD_P
+        dom.set_options(tuned)
 
-    statistics = None
-    if not args.no_stats:
-        statistics = time_statistics(dom, u_out, p_out, case.nu, max(5, args.steps // 3), flush, peak)
+    # ---- the metric's other arms: forward and fwd+adjoint in FP32 and FP64, and
+    # the two precisions at matched pressure (divergence) tolerances
+    arms = compare = None
+    nsub = max(5, args.steps // 2)
+    if extras:
+        other = "fp64" if prec == "fp32" else "fp32"
+        orr = 1e-10 if other == "fp64" else 1e-6
+        oarm = Arm(case, other, dict(opts_kw, adv_rtol=orr, p_rtol=orr))
+        osum = arm_summary(oarm, oarm.run(nsub, 3, flush, True), True)
+        del oarm
+        arms = {prec: dict(summ, krylov_rtol=rtol), other: dict(osum, krylov_rtol=orr)}
+        compare = {"what": "fwd+adjoint steps/s at the same relative residual of every pressure solve (the "
+                           "Rhie-Chow divergence left by the correctors) and of the BiCGStab"}
+        for name, pr, kw in (("fp64_rtol1e-6", "fp64", dict(adv_rtol=1e-6, p_rtol=1e-6)),
+                             ("fp32_refined1e-10", "fp32", dict(adv_rtol=1e-6, p_rtol=1e-6, p_refine_rtol=1e-10))):
+            compare[name] = time_variant(case, pr, kw, nsub, True, flush)
+        compare["fp32_rtol1e-6"] = {"steps_per_s": arms["fp32"]["fwdadj_steps_per_s"]}
+        compare["fp64_rtol1e-10"] = {"steps_per_s": arms["fp64"]["fwdadj_steps_per_s"]}
+
+    # ---- the same step above L2: 256x192x128 (6.3 M cells, ~2.5 GB of FP32
+    # fields and workspace), where the forward kernel is bound by HBM
+    large = None
+    if extras:
+        lcase = W.channel3d(256, 192, 128)
+        larm = Arm(lcase, "fp32", dict(opts_kw, adv_rtol=1e-6, p_rtol=1e-6))
+        lres = larm.run(3, 3, flush, True)
+        ltraffic = None
+        lprof = os.path.join(ROOT, "profiles", "traffic_fwd_kernel_channel3d_256x192x128_fp32.json")
+        if os.path.exists(lprof):
+            try:
+                tj = json.load(open(lprof))
+                if tj.get("kernel_sources_sha256_16") == kernel_sources_hash():
+                    ltraffic = tj.get("dram_bytes_per_launch")
+            except Exception:
+                ltraffic = None
+        large = arm_summary(larm, lres, True)
+        large["workload"] = "channel3d 256x192x128 (same recipe), FP32, Krylov rtol 1e-6, autotuned"
+        large["cells"] = lcase.ncells
+        large["roofline"] = fwd_roofline(larm, lres, peak, peak_kind, ltraffic)
+        del larm
+
+    statistics_obj = None
+    if not args.no_stats and extras:
+        statistics_obj = time_statistics(dom, arm.u0, arm.p0, case.nu, max(5, args.steps // 3), flush, peak)
 
     ilu_cmp = None
-    if not args.no_ilu_compare and args.workload == "channel3d":
+    if not args.no_ilu_compare and extras:
         ilu_cmp = ilu_compare(prec, rtol, max(5, args.steps // 3), with_adj, flush)
     no_cmp = None
-    if not args.no_nonortho and args.workload == "channel3d":
+    if not args.no_nonortho and extras:
         no_cmp = nonortho_compare(prec, rtol, max(5, args.steps // 3), flush)
 
-    compare = None
-    if args.compare:
-        compare = {}
-        for name, pr, kw in (("fp64_rtol1e-6", "fp64", dict(adv_rtol=1e-6, p_rtol=1e-6)),
-                             ("fp64_rtol1e-10", "fp64", dict(adv_rtol=1e-10, p_rtol=1e-10)),
-                             ("fp32_refined1e-10", "fp32", dict(adv_rtol=1e-6, p_rtol=1e-6, p_refine_rtol=1e-10))):
-            compare[name] = time_variant(case, pr, kw, max(5, args.steps // 3), with_adj, flush)
-        compare["fp32_rtol1e-6"] = {"steps_per_s": value, "p_iters": st["p_iters"][:2],
-                                    "p_resid": st["p_resid"][:2]}
+    # ---- the oracle on the host cores, and the GPU path's error against it on
+    # the same steps (computed outside every timed region)
+    cpu = cpu_all = parity = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and headline:
+        v, n, dt, of = cpu_baseline()
+        cpu = {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} fwd+adjoint steps of the same workload from its seeded state in {dt:.1f} s"}
+        va, workers, nproc, steps_all, slow = cpu_baseline_all_cores()
+        cpu_all = {"value": va, "unit": "steps/s", "cores": workers, "nproc": nproc, "kind": "oracle",
+                   "sample": f"{workers} independent copies, {steps_all} fwd+adjoint steps in total, slowest "
+                             f"copy {slow:.1f} s"}
+        gf = arm.rollout_fields(n)
+        parity = {"against": f"FP64 oracle (Krylov rtol 1e-13), after {n} fwd+adjoint steps from the seeded state",
+                  "gpu": f"{prec}, Krylov rtol {rtol:g}, the timed launch shape",
+                  "u": rel_err_per_component(gf["u"], of["u"]), "p": rel_err_per_component(gf["p"], of["p"]),
+                  "du": rel_err_per_component(gf["du"], of["du"]), "dS": rel_err_per_component(gf["dS"], of["dS"]),
+                  "dnu": abs(gf["dnu"] - of["dnu"]) / max(abs(of["dnu"]), 1e-300),
+                  "norm": "per component: max|gpu - oracle| / max|oracle|"}
 
     if rank == 0:
         line = {
@@ -669,32 +845,39 @@ def main():
                                    "laminar + N(0,0.1^2) perturbation (seed 0)",
                        "cells": N, "precision": prec, "krylov_rtol": rtol,
                        "l2": "flushed between timed steps (256 MB write, untimed)",
+                       "state": "advances: each timed step starts from the previous step's output",
                        "parallelism": "replicas" if world > 1 else "single",
-                       "launch": {"threads": shape[0], "ctas": shape[1], "autotuned": args.threads == 0},
-                       "pressure_precond": pc_used, "adv_precond": args.adv_precond},
-            "iterations": {"adv": st["adv_iters"][:d], "p": st["p_iters"][:2],
-                           "adj_adv": adj_st["adv_iters"][:d] if adj_st else None,
-                           "adj_p": adj_st["p_iters"][:2] if adj_st else None},
-            "fwd_ms": sum(fwd_ms) / len(fwd_ms),
+                       "launch": {"threads": arm.shape[0], "ctas": arm.shape[1], "autotuned": args.threads == 0},
+                       "pressure_precond": arm.pc_used, "adv_precond": args.adv_precond},
+            "iterations": summ["iterations"],
+            "fwd_ms": summ["fwd_ms"],
             "cell_updates_per_s": value * N,
             "e2e": {"value": e2e, "unit": "steps/s", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
             "gpu_launches": args.steps * (2 if with_adj else 1),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "fwd_kernel", "words_per_cell": words},
-            "clocks": clocks,
+            "roofline": roof,
+            "clocks": clk.get("clocks"),
         }
+        if arms is not None:
+            line["arms"] = arms
         if compare is not None:
             line["precision_compare"] = compare
+        if large is not None:
+            line["roofline_above_l2"] = dict(large["roofline"], workload=large["workload"],
+                                             fwd_steps_per_s=large["fwd_steps_per_s"],
+                                             fwdadj_steps_per_s=large["fwdadj_steps_per_s"],
+                                             iterations=large["iterations"], launch=large["launch"],
+                                             pressure_precond=large["pressure_precond"])
+        if parity is not None:
+            line["parity"] = parity
         if ilu_cmp is not None:
             line["adv_precond_compare"] = ilu_cmp
         if no_cmp is not None:
             line["nonortho"] = no_cmp
         if paths is not None:
             line["grad_paths"] = paths
-        if statistics is not None:
-            line["statistics"] = statistics
+        if statistics_obj is not None:
+            line["statistics"] = statistics_obj
         if stretched:
             line["config"]["workload"] = line["config"]["workload"].replace("gamma 2", "gamma 3").replace(
                 "dt 0.01", "dt 0.2")
@@ -703,14 +886,13 @@ def main():
             line["config"]["workload"] += ", cells slanted x += 0.5 y (non-orthogonal)"
             line["config"]["n_nonortho"] = args.nonortho
             line["metric"] = line["metric"].replace("channel", "sheared channel")
-        elif args.workload != "channel3d":
+        elif not headline:
             tag = "x".join(str(v) for v in sizes[args.workload])
             line["config"]["workload"] = line["config"]["workload"].replace("64x48x32", tag)
             line["metric"] = line["metric"].replace("64x48x32", tag)
-        if world == 1 and not args.no_cpu_baseline and args.workload == "channel3d":
-            v, n, dt = cpu_baseline(case)
-            line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"{n} fwd+adjoint steps of the same workload in {dt:.1f} s"}
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+            line["cpu_baseline_all_cores"] = cpu_all
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -270,7 +270,9 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
  *     which keeps the last call's contents; calls that overlap on the GPU
  *     race and corrupt each other's results.
  *   - The step record lives in the shared buffer: piso_step_adjoint cannot use
- *     it (run piso_step, with the domain's own workspace, before an adjoint).
+ *     it, and a piso_step_adjoint with tape NULL after this call returns
+ *     PISO_ESTATE (run piso_step, with the domain's own workspace, before an
+ *     adjoint).
  *   - Advective outflow faces of the domain are updated as by piso_step. */
 piso_status piso_step_static(piso_domain* d, const void* u_in, const void* p_in, void* u_out, void* p_out,
                              double dt, double nu, const void* S, void* stream, piso_stats* stats);
@@ -282,8 +284,11 @@ piso_status piso_last_stats(piso_domain* d, piso_stats* stats);
  * dp_out = dL/dp^{n+1} (device; dp_out may be NULL for zero), write
  * du_in = dL/du^n, dp_in = dL/dp^n, dS = dL/dS (each device, caller-owned,
  * may be NULL to skip) and *dnu = dL/dnu (host double, may be NULL).
- * tape is the buffer filled by the forward step (NULL = the domain's own
- * record of its last step).  Linear solves are differentiated by transposed
+ * tape is the buffer filled by the forward step, or NULL for the domain's own
+ * record of its last forward step; that record exists only when the last
+ * forward step of the domain was a piso_step with tape NULL (or a batch step),
+ * otherwise (no step yet, or after piso_step_static, piso_autotune or a
+ * piso_step into a caller tape) a NULL tape returns PISO_ESTATE.  Linear solves are differentiated by transposed
  * solves (C^T via BiCGStab, P symmetric via CG).  Boundary velocities are
  * differentiable too (App. A.4): dL/d(boundary values before the step's
  * advective-outflow update) is kept in the domain (read it with

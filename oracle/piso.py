@@ -54,11 +54,16 @@ implements; each is listed in the design notes):
 * App. A.2 "Non-Orthogonal Grids" (Eqs. difNonOrthoMatDiscrete,
   velRHSnonOrtho, pressureRHSnonOrtho): on meshes whose cross metrics
   alpha_jk (j != k) do not vanish (``allow_nonorthogonal=True``), the cross
-  derivatives of the diffusion and of the pressure Laplacian are deferred to
-  the right-hand sides with the previous iterate and the solves repeated
-  ``n_nonortho`` times (non-orthogonal corrector steps), and the adjoint runs
-  those loops in reverse (the starting pressure p^n now matters through the
-  pressure cross terms).  Without the flag such meshes are rejected.
+  derivatives of the diffusion are split as the paper does: the terms on P's
+  direct neighbours join the matrix C (Eq. difNonOrthoMatDiscrete), those on
+  its diagonal neighbours go to the right-hand side with the previous iterate
+  (Eq. velRHSnonOrtho); the cross derivatives of the pressure Laplacian are
+  deferred to the right-hand side whole (Eq. pressureRHSnonOrtho; their
+  direct-neighbour part would make P unsymmetric for the CG).  The solves are
+  repeated ``n_nonortho`` times (non-orthogonal corrector steps) and the
+  adjoint runs those loops in reverse (the starting pressure p^n now matters
+  through the pressure cross terms).  ``nonortho_split="deferred"`` defers
+  the viscous terms whole as well.  Without the flag such meshes are rejected.
 * Block connections join a side to the opposite side of the same axis with the
   same tangential ordering (no axis permutation).
 """
@@ -92,6 +97,10 @@ class Options:
     grad_p: bool = True          # Sec. 2.4: keep the gradient paths through the pressure solves
     adv_precond: str = "none"    # App. A.5: BiCGStab preconditioner "none" | "ilu" (ILU(0)) |
                                  # "ilu_on_failure" (ILU(0) only after the plain solve failed)
+    nonortho_split: str = "paper"  # App. A.2: "paper" keeps the direct-neighbour part of the viscous cross
+                                 # terms in C (Eq. difNonOrthoMatDiscrete) and defers the diagonal-neighbour
+                                 # part (Eq. velRHSnonOrtho); "deferred" moves every cross term to the
+                                 # right-hand side.  The pressure cross terms are deferred in both.
 
 
 class Mesh:
@@ -420,12 +429,15 @@ def _cell_diff(mesh: Mesh, q: np.ndarray, k: int, ghost) -> np.ndarray:
     return 0.5 * (hi - lo)
 
 
-def _cross_flux_sum(mesh: Mesh, coef: np.ndarray, dq, bface_grad) -> np.ndarray:
+def _cross_flux_sum(mesh: Mesh, coef: np.ndarray, dq, bface_grad, part: str = "all") -> np.ndarray:
     """sum_j sum_{k != j} sum_{faces f of P on axis j} N_f c_jk,f g_k,f for one
     scalar field: c_jk,f the face mean of coef (N, d, d) over P and its
     neighbour, g_k,f the mean of the two cells' central differences dq[k] (N,).
     Boundary faces: c_jk of P and g_k = bface_grad(s, k) (N,), or no flux when
-    bface_grad is None."""
+    bface_grad is None.  part selects the terms: "all"; "own", the halves with
+    P's own differences dq[k][P] (its direct neighbours) and the boundary
+    faces; "nbr", the halves with the neighbour's differences dq[k][F] (P's
+    diagonal neighbours).  "own" + "nbr" = "all"."""
     d = mesh.ndim
     out = np.zeros(mesh.N)
     for s in range(mesh.nsides):
@@ -437,13 +449,18 @@ def _cross_flux_sum(mesh: Mesh, coef: np.ndarray, dq, bface_grad) -> np.ndarray:
             if k == j:
                 continue
             cf = 0.5 * (coef[P, j, k] + coef[F, j, k])
-            out[P] += n * cf * 0.5 * (dq[k][P] + dq[k][F])
-            if bface_grad is not None and len(B):
+            if part == "all":
+                out[P] += n * cf * 0.5 * (dq[k][P] + dq[k][F])
+            elif part == "own":
+                out[P] += n * cf * 0.5 * dq[k][P]
+            else:
+                out[P] += n * cf * 0.5 * dq[k][F]
+            if bface_grad is not None and len(B) and part != "nbr":
                 out[B] += n * coef[B, j, k] * bface_grad(s, k)[B]
     return out
 
 
-def cross_diffusion(mesh: Mesh, u: np.ndarray, nu: float, bval) -> np.ndarray:
+def cross_diffusion(mesh: Mesh, u: np.ndarray, nu: float, bval, part: str = "all") -> np.ndarray:
     """Cross-derivative part of the viscous term per unit volume, (nu / J_P)
     sum_j sum_{k != j} sum_f N_f mean(alpha_jk) (d_k u)_f, for every velocity
     component (the part of Eqs. difNonOrthoMatDiscrete / velRHSnonOrtho that
@@ -465,8 +482,38 @@ def cross_diffusion(mesh: Mesh, u: np.ndarray, nu: float, bval) -> np.ndarray:
             hi = np.where(mesh.inner[2 * k + 1] & mesh.is_bface[s][hi_n], fb[hi_n], fb)
             lo = np.where(mesh.inner[2 * k] & mesh.is_bface[s][lo_n], fb[lo_n], fb)
             return 0.5 * (hi - lo)
-        out[c] = nu * _cross_flux_sum(mesh, mesh.G, dq, bgrad) / mesh.J
+        out[c] = nu * _cross_flux_sum(mesh, mesh.G, dq, bgrad, part) / mesh.J
     return out
+
+
+def cross_matrix(mesh: Mesh, nu: float) -> Matrix:
+    """The direct-neighbour part of the viscous cross terms as matrix entries
+    (Eq. difNonOrthoMatDiscrete): in part "own" of cross_diffusion every face
+    tangential derivative uses P's own central difference (q_{k+} - q_{k-})/2,
+    so that part is W_k(P) (q_{k+} - q_{k-})/2 with W_k(P) = sum over P's inner
+    faces on the axes j != k of N_f mean(alpha_jk) / 2, times nu / J_P; a
+    missing k-neighbour's ghost 2 u_b - q_P puts -/+ W_k / 2 on the diagonal
+    (its 2 u_b part is a constant).  Returns M with cross_diffusion(u, "own") =
+    M u + cross_diffusion(0, "own") for each velocity component; the matrix of
+    the paper's split is C - M."""
+    d, N = mesh.ndim, mesh.N
+    W = np.zeros((d, N))
+    for s in range(mesh.nsides):
+        j, n = s // 2, sign(s)
+        P = np.nonzero(mesh.inner[s])[0]
+        F = mesh.nb[s, P]
+        for k in range(d):
+            if k != j:
+                W[k][P] += n * 0.5 * (mesh.G[P, j, k] + mesh.G[F, j, k]) * 0.5
+    diag = np.zeros(N)
+    off = np.zeros((mesh.nsides, N))
+    for k in range(d):
+        for s, w in ((2 * k + 1, 0.5), (2 * k, -0.5)):
+            inn = mesh.inner[s]
+            off[s, inn] += w * W[k][inn]
+            diag[~inn] -= w * W[k][~inn]
+    f = nu / mesh.J
+    return Matrix(f * diag, f[None, :] * off)
 
 
 def cross_pressure(mesh: Mesh, p: np.ndarray, A: np.ndarray) -> np.ndarray:
@@ -495,9 +542,10 @@ def _cell_diff_T(mesh: Mesh, gd: np.ndarray, k: int, gq: np.ndarray, ghost_coef:
             gghost(s)[out] += w * 2.0 * gd[out]
 
 
-def cross_diffusion_T(mesh: Mesh, g: np.ndarray, nu: float):
-    """Transpose of cross_diffusion in u and in the boundary values: returns
-    (dL/du (d, N), dL/dbval per side [nsides](d, N)) for dL/dX = g."""
+def cross_diffusion_T(mesh: Mesh, g: np.ndarray, nu: float, part: str = "all"):
+    """Transpose of cross_diffusion (the same part) in u and in the boundary
+    values: returns (dL/du (d, N), dL/dbval per side [nsides](d, N)) for
+    dL/dX = g."""
     d, N = mesh.ndim, mesh.N
     gu = np.zeros((d, N))
     gb = [np.zeros((d, N)) for _ in range(mesh.nsides)]
@@ -513,9 +561,11 @@ def cross_diffusion_T(mesh: Mesh, g: np.ndarray, nu: float):
                 if k == j:
                     continue
                 t = n * 0.5 * (mesh.G[P, j, k] + mesh.G[F, j, k]) * 0.5 * w[P]
-                np.add.at(gdk[k], P, t)
-                np.add.at(gdk[k], F, t)
-                if len(B):
+                if part != "nbr":
+                    np.add.at(gdk[k], P, t)
+                if part != "own":
+                    np.add.at(gdk[k], F, t)
+                if len(B) and part != "nbr":
                     tb = n * mesh.G[B, j, k] * w[B] * 0.5
                     hi_n, lo_n = mesh.safe_nb[2 * k + 1][B], mesh.safe_nb[2 * k][B]
                     hi_ok = mesh.inner[2 * k + 1][B] & mesh.is_bface[s][hi_n]
@@ -673,14 +723,24 @@ def piso_step(mesh: Mesh, u, p, dt, nu, S=None, bval=None, opts: Optional[Option
     if opts.update_outflow:
         bval = outflow_update(mesh, u, bval, dt)
     C, rhs0 = assemble_C(mesh, u, nu, dt, S, bval)
-    rhs = rhs0 - grad_p(mesh, p) if opts.pred_grad_p else rhs0
     X = mesh.has_cross
-    # non-orthogonal meshes: the cross-derivative terms are deferred to the
-    # right-hand side with the previous iterate, n_nonortho solves each
+    if opts.nonortho_split not in ("paper", "deferred"):
+        raise ValueError(f"unknown nonortho_split {opts.nonortho_split!r}")
+    paper = X and opts.nonortho_split == "paper"
+    xpart = "nbr" if paper else "all"
+    if paper:
+        # App. A.2: the direct-neighbour cross entries join the matrix (Eq.
+        # difNonOrthoMatDiscrete), their boundary-value constants the rhs
+        Mx = cross_matrix(mesh, nu)
+        C = Matrix(C.diag - Mx.diag, C.off - Mx.off)
+        rhs0 = rhs0 + cross_diffusion(mesh, np.zeros_like(u), nu, bval, part="own")
+    rhs = rhs0 - grad_p(mesh, p) if opts.pred_grad_p else rhs0
+    # non-orthogonal meshes: the remaining cross-derivative terms are deferred
+    # to the right-hand side with the previous iterate, n_nonortho solves each
     ustar = u
     ustar_it = [u]
     for _ in range(opts.n_nonortho if X else 1):
-        rhs_m = rhs + cross_diffusion(mesh, ustar, nu, bval) if X else rhs
+        rhs_m = rhs + cross_diffusion(mesh, ustar, nu, bval, xpart) if X else rhs
         ustar, adv_info = solve_C(mesh, C, rhs_m, ustar, opts)
         ustar_it.append(ustar)
     A = C.diag
@@ -689,7 +749,7 @@ def piso_step(mesh: Mesh, u, p, dt, nu, S=None, bval=None, opts: Optional[Option
     corr = []
     p_infos = []
     for _ in range(opts.n_correctors):
-        rhs0_k = rhs0 + cross_diffusion(mesh, uk, nu, bval) if X else rhs0
+        rhs0_k = rhs0 + cross_diffusion(mesh, uk, nu, bval, xpart) if X else rhs0
         h = pressure_rhs_vec(mesh, C, rhs0_k, uk)
         b = divergence(mesh, h, bval)
         b = b - b.mean()
@@ -705,8 +765,7 @@ def piso_step(mesh: Mesh, u, p, dt, nu, S=None, bval=None, opts: Optional[Option
         uk, pk = unew, x
     tape = dict(u=u, p=p, S=S, nu=nu, dt=dt, bval=bval, bval_in=bval_in, outflow_updated=updated, C=C,
                 rhs0=rhs0, rhs=rhs, ustar=ustar, ustar_it=ustar_it, Pm=Pm, corr=corr, u_out=uk, p_out=pk,
-                adv_info=adv_info,
-                p_infos=p_infos)
+                adv_info=adv_info, p_infos=p_infos, xpart=xpart)
     return uk, pk, tape
 
 
@@ -778,6 +837,7 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
     only the bypass paths of Eq. jnone remain."""
     opts = opts or Options()
     X = mesh.has_cross
+    xpart = tape.get("xpart", "all")
     d, N = mesh.ndim, mesh.N
     C, Pm = tape["C"], tape["Pm"]
     A = C.diag
@@ -853,12 +913,12 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
         for s in range(mesh.nsides):
             gCoff[s] -= np.sum(gg * uin[:, mesh.safe_nb[s]], axis=0) * mesh.inner[s]
         if X:
-            gxu, gxb = cross_diffusion_T(mesh, gg, nu)
+            gxu, gxb = cross_diffusion_T(mesh, gg, nu, xpart)
             gu = gu + gxu
             for s in range(mesh.nsides):
                 gbX[s] += gxb[s]
             if nu:
-                gnu_x += float(np.sum(gg * cross_diffusion(mesh, uin, nu, bval))) / nu
+                gnu_x += float(np.sum(gg * cross_diffusion(mesh, uin, nu, bval, xpart))) / nu
     if X:
         gp_in_x = gx_carry
     # pressure matrix built from w = alpha / A
@@ -879,11 +939,11 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
             gA -= np.sum(z * its[m], axis=0)
             for s in range(mesh.nsides):
                 gCoff[s] -= np.sum(z * its[m][:, mesh.safe_nb[s]], axis=0) * mesh.inner[s]
-            gxu, gxb = cross_diffusion_T(mesh, z, nu)
+            gxu, gxb = cross_diffusion_T(mesh, z, nu, xpart)
             for s in range(mesh.nsides):
                 gbX[s] += gxb[s]
             if nu:
-                gnu_x += float(np.sum(z * cross_diffusion(mesh, its[m - 1], nu, bval))) / nu
+                gnu_x += float(np.sum(z * cross_diffusion(mesh, its[m - 1], nu, bval, xpart))) / nu
             gm = gxu
         gu_pred = gm
     else:
@@ -893,6 +953,16 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
         for s in range(mesh.nsides):
             gCoff[s] -= np.sum(z * ustar[:, mesh.safe_nb[s]], axis=0) * mesh.inner[s]
     grhs0 += grhs
+    if xpart == "nbr":
+        # the paper's split: C holds -M (linear in nu) and rhs0 the constant
+        # part of the direct-neighbour cross terms (linear in nu and in the
+        # boundary values)
+        M1 = cross_matrix(mesh, 1.0)
+        gnu_x -= float(np.sum(gA * M1.diag)) + float(np.sum(gCoff * M1.off))
+        gnu_x += float(np.sum(grhs0 * cross_diffusion(mesh, np.zeros((d, N)), 1.0, bval, part="own")))
+        _, gxb = cross_diffusion_T(mesh, grhs0, nu, part="own")
+        for s in range(mesh.nsides):
+            gbX[s] += gxb[s]
     gp_in = -grad_p_T(mesh, grhs) if opts.pred_grad_p else np.zeros(N)
     if X:
         gp_in = gp_in + gp_in_x

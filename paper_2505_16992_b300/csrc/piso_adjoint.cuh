@@ -593,6 +593,7 @@ __global__ void __launch_bounds__(MAXT, 1) adj_kernel(const __grid_constant__ La
   g.epoch = 0;
   g.timeout_ns = L.o.timeout_ns;
   g.withhold = (L.o.withhold_cta == g.rank) ? 1 : 0;
+  g.trace = L.o.trace;
   adj_group<real, ND, ILU>(A, L.o, g);
 }
 

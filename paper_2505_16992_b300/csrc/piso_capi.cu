@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -85,6 +86,8 @@ struct piso_domain {
   // workspace arrays (element pointers)
   void* ws[64] = {nullptr};
   void* tape_ws = nullptr;     // internal tape (last step)
+  bool tape_ws_valid = false;  // tape_ws holds the record of the domain's last forward step (that step was a
+                               // piso_step or batch step without a caller tape)
   uint32_t* bar = nullptr;
   double* partials = nullptr;
   int32_t* status = nullptr;
@@ -347,6 +350,20 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
   c.ncta = d->ncta;
 }
 
+#ifdef PISO_TRACE
+// Phase-timing ring of trace builds: [PISO_TRACE_LEN][4] stamps in device
+// memory, allocated on first use and handed to every kernel through the solver
+// options (the kernels of all translation units write this one buffer).
+uint64_t* g_trace_buf = nullptr;
+uint64_t* trace_buffer() {
+  if (!g_trace_buf) {
+    if (cudaMalloc((void**)&g_trace_buf, sizeof(uint64_t) * 4 * PISO_TRACE_LEN) != cudaSuccess) g_trace_buf = nullptr;
+    else cudaMemset(g_trace_buf, 0, sizeof(uint64_t) * 4 * PISO_TRACE_LEN);
+  }
+  return g_trace_buf;
+}
+#endif
+
 SolverOpts solver_opts(const piso_options& o) {
   SolverOpts s;
   s.n_corr = o.n_correctors;
@@ -364,6 +381,11 @@ SolverOpts solver_opts(const piso_options& o) {
   s.p_inner_rtol = o.p_inner_rtol;
   s.grad_paths = o.grad_paths;
   s.ilu_soff = -1;
+#ifdef PISO_TRACE
+  s.trace = trace_buffer();
+#else
+  s.trace = nullptr;
+#endif
   return s;
 }
 
@@ -1092,9 +1114,11 @@ piso_status piso_step(piso_domain* d, const void* u_in, const void* p_in, void* 
   if (!(dt > 0) || !std::isfinite(dt)) return fail(d, PISO_EINVAL, "dt must be positive and finite");
   if (!(nu >= 0) || !std::isfinite(nu)) return fail(d, PISO_EINVAL, "nu must be non-negative and finite");
   cudaStream_t st = (cudaStream_t)stream;
+  d->tape_ws_valid = false;
   piso_status s = d->prec == PISO_FP64 ? launch_fwd<double>(d, u_in, p_in, u_out, p_out, dt, nu, S, tape, st)
                                        : launch_fwd<float>(d, u_in, p_in, u_out, p_out, dt, nu, S, tape, st);
   if (s) return s;
+  d->tape_ws_valid = (tape == nullptr);
   s = enqueue_readback(d, st);
   if (s) return s;
   d->pending = true;
@@ -1154,6 +1178,7 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
     std::tuple<int, int, int> best = {saved_threads, saved_ncta, saved_line};
     piso_status s = PISO_OK;
     CUDA_TRY(d, cudaMemcpyAsync(bk, d->bval, bb, cudaMemcpyDeviceToDevice, st));
+    d->tape_ws_valid = false;      // the trial steps record into the domain's own tape
     for (auto& c : cand) {
       d->threads = std::get<0>(c);
       d->ncta = std::get<1>(c);
@@ -1280,7 +1305,10 @@ constexpr size_t STATIC_SCRATCH_BYTES = 32ull << 20;   // 32 MiB, held on every 
 __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
-void* g_static_ptr[MAX_DEVICES] = {nullptr};
+// Device address of g_static_scratch per device, looked up on first use.  The
+// entries are atomic, so host threads making their first call on a device at
+// the same time each store the same address without a data race.
+std::atomic<void*> g_static_ptr[MAX_DEVICES];
 
 // Byte layout of the forward kernel's scratch inside the static buffer.
 struct StaticLayout {
@@ -1326,15 +1354,16 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
   int dev = 0;
   CUDA_TRY(d, cudaGetDevice(&dev));
   if (dev < 0 || dev >= MAX_DEVICES) return fail(d, PISO_EINVAL, "device index %d out of range", dev);
-  if (!g_static_ptr[dev]) {   // set-up, once per device, with that device current
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-    if (e != cudaSuccess || !ptr)
+  void* sp = g_static_ptr[dev].load(std::memory_order_acquire);
+  if (!sp) {   // set-up, once per device, with that device current
+    cudaError_t e = cudaGetSymbolAddress(&sp, g_static_scratch);
+    if (e != cudaSuccess || !sp)
       return fail(d, PISO_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-    g_static_ptr[dev] = ptr;
+    g_static_ptr[dev].store(sp, std::memory_order_release);
   }
-  char* base = (char*)g_static_ptr[dev];
+  char* base = (char*)sp;
   cudaStream_t st = (cudaStream_t)stream;
+  d->tape_ws_valid = false;   // this step's record lives in the shared buffer, not in the domain
   CUDA_TRY(d, cudaMemsetAsync(base + SL.bar, 0, 64, st));      // barrier counter, status and counts start at 0
   CUDA_TRY(d, cudaMemsetAsync(base + SL.status, 0, 64, st));
   CUDA_TRY(d, cudaMemsetAsync(base + SL.istats, 0, 64, st));
@@ -1405,7 +1434,8 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
 // Copy the phase-timing trace (trace builds only): n entries of 4 stamps.
 extern "C" int piso_trace_read(uint64_t* out, int n) {
   if (n > PISO_TRACE_LEN) n = PISO_TRACE_LEN;
-  if (cudaMemcpyFromSymbol(out, g_piso_trace, sizeof(uint64_t) * 4 * n) != cudaSuccess) return -1;
+  if (!g_trace_buf) return 0;
+  if (cudaMemcpy(out, g_trace_buf, sizeof(uint64_t) * 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
   return n;
 }
 #endif

@@ -318,22 +318,23 @@ struct Group {
   uint32_t epoch;
   uint64_t timeout_ns;
   int32_t withhold;     // fault injection: this CTA skips its first arrival (1) or not (0)
+  uint64_t* trace;      // phase-timing ring (PISO_TRACE builds), or nullptr
 };
 
 // Optional phase-timing trace (build with -DPISO_TRACE): CTA 0 of the launch
-// records globaltimer stamps at four points of every phase boundary — work
-// done, partials published, barrier passed, totals gathered — into a ring of
-// PISO_TRACE_LEN entries.  Off by default; it changes no computation.
+// records globaltimer stamps at four points of every phase boundary - work
+// done, partials published, barrier passed, totals gathered - into a ring of
+// PISO_TRACE_LEN entries of four stamps at Group::trace (a device buffer the
+// host side owns and passes in with the solver options, so every translation
+// unit writes the same buffer).  Off by default; it changes no computation.
 #ifdef PISO_TRACE
 constexpr int PISO_TRACE_LEN = 8192;
-__device__ uint64_t g_piso_trace[PISO_TRACE_LEN][4];
-__device__ uint32_t g_piso_trace_n;
 #define PISO_STAMP(slot, k)                                                   \
   do {                                                                        \
-    if (blockIdx.x == 0 && threadIdx.x == 0) {                                \
+    if (g.trace && blockIdx.x == 0 && threadIdx.x == 0) {                     \
       uint64_t t_;                                                            \
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                  \
-      g_piso_trace[(slot) % PISO_TRACE_LEN][k] = t_;                          \
+      g.trace[((slot) % PISO_TRACE_LEN) * 4 + (k)] = t_;                      \
     }                                                                         \
   } while (0)
 #else

@@ -575,6 +575,7 @@ __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const __grid_constant__ La
   g.epoch = 0;
   g.timeout_ns = L.o.timeout_ns;
   g.withhold = (L.o.withhold_cta == g.rank) ? 1 : 0;
+  g.trace = L.o.trace;
   fwd_group<real, ND, MODE>(A, L.o, g);
 }
 

@@ -19,6 +19,7 @@ struct SolverOpts {
   double p_inner_rtol;       // FP32 mode: inner CG tolerance per refinement round
   int32_t grad_paths;        // adjoint: bit 1 keeps the advection-solve paths, bit 2 the pressure-solve paths
   int32_t ilu_soff;          // byte offset of the ILU(0) sweep area in dynamic shared memory, -1: none
+  uint64_t* trace;           // phase-timing ring of PISO_TRACE builds ([PISO_TRACE_LEN][4]), else nullptr
 };
 
 // Fill the CTA's neighbour table (dynamic shared memory) when its cell range

@@ -157,19 +157,27 @@ class Domain:
         capi.check(rc, self.h)
         return st.as_dict()
 
-    def step_adjoint(self, du_out, dp_out=None, tape=None, stream=None, want=("u", "p", "S", "nu")):
-        """Adjoint of the last (or taped) step: returns (du_in, dp_in, dS, dnu)."""
+    def step_adjoint(self, du_out, dp_out=None, tape=None, stream=None, want=("u", "p", "S", "nu"), sync=True,
+                     du_in=None, dp_in=None, dS=None):
+        """Adjoint of the last (or taped) step: returns (du_in, dp_in, dS, dnu,
+        stats).  sync=False only enqueues (no dnu or statistics read back; they
+        come back as None)."""
         d = self.ndim
-        du_in = torch.empty((d, self.N), dtype=self.dtype, device="cuda") if "u" in want else None
-        dp_in = torch.empty((self.N,), dtype=self.dtype, device="cuda") if "p" in want else None
-        dS = torch.empty((d, self.N), dtype=self.dtype, device="cuda") if "S" in want else None
+        if du_in is None and "u" in want:
+            du_in = torch.empty((d, self.N), dtype=self.dtype, device="cuda")
+        if dp_in is None and "p" in want:
+            dp_in = torch.empty((self.N,), dtype=self.dtype, device="cuda")
+        if dS is None and "S" in want:
+            dS = torch.empty((d, self.N), dtype=self.dtype, device="cuda")
         dnu = C.c_double(0.0)
-        st = capi.Stats()
+        st = capi.Stats() if sync else None
         rc = self.lib.piso_step_adjoint(self.h, capi.dptr(tape), capi.dptr(du_out), capi.dptr(dp_out),
                                         capi.dptr(du_in), capi.dptr(dp_in), capi.dptr(dS),
-                                        C.byref(dnu) if "nu" in want else None, _stream_ptr(stream),
-                                        C.byref(st))
+                                        C.byref(dnu) if ("nu" in want and sync) else None, _stream_ptr(stream),
+                                        C.byref(st) if sync else None)
         capi.check(rc, self.h)
+        if not sync:
+            return du_in, dp_in, dS, None, None
         return du_in, dp_in, dS, dnu.value, st.as_dict()
 
     def get_boundary(self) -> np.ndarray:
@@ -402,21 +410,6 @@ def frame_record(stats: PlaneStats, q):
 
 def time_averaged_record(stats: PlaneStats, qs):
     return TimeAveragedRecordFunction.apply(stats, *qs)
-
-
-def stats_loss(stats: PlaneStats, qs, ref_mean, ref_m2, lam_U=1.0, lam_uu=1.0, lam_frame=1.0):
-    """L_stats of Eq. TCFstatsLossGeneric (Sec. 3.3) with one weight per kind:
-    squared errors of the mean profiles and second-order statistics per plane
-    (averaged over the planes) for the time-averaged record of all frames plus
-    lam_frame times the same terms of every frame's own record."""
-    def terms(rec):
-        _, mean, m2, _ = stats.split(rec)
-        ny = mean.shape[0]
-        return (lam_U * ((mean - ref_mean) ** 2).sum() + lam_uu * ((m2 - ref_m2) ** 2).sum()) / ny
-    total = terms(time_averaged_record(stats, qs))
-    for q in qs:
-        total = total + lam_frame * terms(frame_record(stats, q))
-    return total
 
 
 def cell_gradients(domain: Domain, u, p=None, stream=None):

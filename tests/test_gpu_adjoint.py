@@ -207,3 +207,26 @@ def test_boundary_adjoint_matches_gpu_finite_difference():
     e = 1e-4
     fd = (8 * (L(e) - L(-e)) - (L(2 * e) - L(-2 * e))) / (12 * e)
     assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
+
+
+def test_adjoint_without_a_recorded_step_is_refused():
+    """A NULL tape means the domain's own record of its last forward step: it
+    must exist, else the call is out of order (PISO_ESTATE) instead of
+    differentiating a stale or empty record."""
+    c = W.cavity2d(16)
+    dom = gpu_domain(c)
+    d = c.ndim
+    u, p = to_dev(dom, c.u0, d), to_dev(dom, c.p0)
+    g = torch.ones_like(u)
+    with pytest.raises(capi.PisoError) as e:          # no step yet
+        dom.step_adjoint(g)
+    assert e.value.status == 7               # PISO_ESTATE
+    tape = dom.new_tape()
+    dom.step(u, p, c.dt, c.nu, tape=tape)             # recorded into a caller tape only
+    with pytest.raises(capi.PisoError) as e:
+        dom.step_adjoint(g)
+    assert e.value.status == 7               # PISO_ESTATE
+    du_t = dom.step_adjoint(g, tape=tape)[0]          # the caller's tape works
+    dom.step(u, p, c.dt, c.nu)                        # same step into the domain's own record
+    du_w = dom.step_adjoint(g)[0]
+    assert torch.equal(du_t, du_w)

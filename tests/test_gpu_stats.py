@@ -11,6 +11,7 @@ import torch
 import oracle as O
 from oracle import stats as OS
 from paper_2505_16992_b300 import capi
+from paper_2505_16992_b300 import losses as LS
 from paper_2505_16992_b300 import solver as SV
 from paper_2505_16992_b300 import workloads as W
 from gpu_util import gpu_domain, host, rel_err, to_dev
@@ -163,7 +164,7 @@ def test_stats_loss_gradient_matches_oracle():
     ref_mean = rng.standard_normal((res[1], 3))
     ref_m2 = rng.standard_normal((res[1], 3, 3))
     qs = [to_dev(dom, q, 3).requires_grad_(True) for q in frames]
-    L = SV.stats_loss(st, qs, torch.tensor(ref_mean, device="cuda"), torch.tensor(ref_m2, device="cuda"),
+    L = LS.stats_loss(st, qs, torch.tensor(ref_mean, device="cuda"), torch.tensor(ref_m2, device="cuda"),
                       lam_U=1.0, lam_uu=0.5, lam_frame=0.25)
     L.backward()
     recs = [OS.frame_record(q, res) for q in frames]
@@ -202,7 +203,7 @@ def test_stats_loss_through_rollout_matches_finite_differences():
         for _ in range(3):
             u, p = SV.piso_step(dom, u, p, c.dt, c.nu, S)
             frames.append(u)
-        return SV.stats_loss(st, frames, ref_mean, ref_m2, lam_frame=0.5)
+        return LS.stats_loss(st, frames, ref_mean, ref_m2, lam_frame=0.5)
 
     u0 = to_dev(dom, c.u0, 3).requires_grad_(True)
     L = loss(u0)

@@ -1,7 +1,9 @@
 """Pins of the oracle's non-orthogonal terms (App. A.2 "Non-Orthogonal
 Grids": the cross derivatives alpha_jk d_j d_k, j != k, of the viscous term
-and of the pressure operator, deferred to the right-hand sides with the
-previous iterate over non-orthogonal corrector steps), against facts that do
+and of the pressure operator; the direct-neighbour part of the viscous ones in
+the matrix (Eq. difNonOrthoMatDiscrete), the rest deferred to the right-hand
+sides with the previous iterate over non-orthogonal corrector steps), against
+facts that do
 not depend on the oracle: exactness of the full discrete operators on
 quadratic fields of affine (sheared) grids, vanishing cross terms on
 orthogonal grids, the fixed point of the corrector loops, and the
@@ -125,11 +127,13 @@ def test_nonorthogonal_meshes_still_rejected_by_default():
                [(0, s, np.zeros((5 if s < 2 else 6, 2))) for s in range(4)])
 
 
-def test_corrector_loops_converge_to_the_full_discrete_system():
+@pytest.mark.parametrize("split", ["paper", "deferred"])
+def test_corrector_loops_converge_to_the_full_discrete_system(split):
     """With enough non-orthogonal corrector steps the predictor solves the
-    momentum system with the cross terms included (C u* = rhs + X(u*)) and
-    every pressure solve the full pressure system ((P + Y) p = b), to the
-    solver tolerance.  The adjoint is not provided for such meshes."""
+    momentum system with the cross terms included (C u* = rhs + X(u*), C the
+    orthogonal matrix of Eqs. advMatDiscrete / difMatDiscrete) and every
+    pressure solve the full pressure system ((P + Y) p = b), to the solver
+    tolerance, whichever part of the viscous cross terms the matrix holds."""
     res, h, shear = (9, 8), (0.1, 0.1), (0.7,)
     m = _walled_mesh(res, h, shear, seed=4)
     rng = np.random.default_rng(5)
@@ -137,19 +141,92 @@ def test_corrector_loops_converge_to_the_full_discrete_system():
     p0 = rng.standard_normal(m.N)
     S = rng.standard_normal((2, m.N))
     nu, dt = 0.05, 0.02
-    opts = OP.Options(n_nonortho=60, solver="direct")
+    opts = OP.Options(n_nonortho=60, solver="direct", nonortho_split=split)
     u1, p1, tape = O.piso_step(m, u0, p0, dt, nu, S, None, opts)
-    C, rhs, us = tape["C"], tape["rhs"], tape["ustar"]
+    C, rhs = OP.assemble_C(m, u0, nu, dt, S, tape["bval"])
+    us = tape["ustar"]
     res_u = rhs + OP.cross_diffusion(m, us, nu, tape["bval"]) - OP.matvec(m, C, us)
     assert np.abs(res_u).max() <= 1e-10 * np.abs(rhs).max()
-    A = C.diag
+    A = tape["C"].diag
     for cr in tape["corr"]:
         r = cr["b"] - OP.matvec(m, tape["Pm"], cr["x"]) - OP.cross_pressure(m, cr["x"], A)
         r -= r.mean()
         assert np.abs(r).max() <= 1e-10 * np.abs(cr["b"]).max()
     # one step is not the same as the orthogonal scheme on this mesh
-    u1a, _, _ = O.piso_step(m, u0, p0, dt, nu, S, None, OP.Options(n_nonortho=1, solver="direct"))
+    u1a, _, _ = O.piso_step(m, u0, p0, dt, nu, S, None, OP.Options(n_nonortho=1, solver="direct",
+                                                                   nonortho_split=split))
     assert np.abs(u1a - u1).max() > 0
+
+
+def test_paper_split_matrix_holds_the_direct_neighbour_terms():
+    """The split of Eq. difNonOrthoMatDiscrete / Eq. velRHSnonOrtho: the cross
+    terms with P's own central differences are an affine map of u whose matrix
+    touches only P and its direct neighbours (the 2d+1 stencil of C), the rest
+    uses P's diagonal neighbours; together they are the whole cross term."""
+    m = _walled_mesh((7, 6, 5), (0.1, 0.12, 0.09), (0.5, -0.3, 0.4), seed=13)
+    rng = np.random.default_rng(14)
+    u = rng.standard_normal((3, m.N))
+    nu = 0.2
+    M = OP.cross_matrix(m, nu)
+    own = OP.cross_diffusion(m, u, nu, m.bval, part="own")
+    const = OP.cross_diffusion(m, np.zeros_like(u), nu, m.bval, part="own")
+    np.testing.assert_allclose(own, OP.matvec(m, M, u) + const, rtol=1e-12, atol=1e-13 * np.abs(own).max())
+    nbr = OP.cross_diffusion(m, u, nu, m.bval, part="nbr")
+    np.testing.assert_allclose(own + nbr, OP.cross_diffusion(m, u, nu, m.bval), rtol=1e-12,
+                               atol=1e-13 * np.abs(own).max())
+    # the neighbour part does not see P's direct neighbours: perturbing one
+    # cell moves it only at cells for which that cell is a diagonal neighbour
+    # (or a direct neighbour of theirs across a boundary ghost, none here in
+    # the interior)
+    i = 3 + 7 * (3 + 6 * 2)
+    du = np.zeros_like(u)
+    du[1, i] = 1.0
+    moved = np.nonzero(np.abs(OP.cross_diffusion(m, u + du, nu, m.bval, part="nbr") - nbr)[1] > 0)[0]
+    direct = {int(m.nb[s, i]) for s in range(m.nsides)}
+    assert not (set(moved.tolist()) & (direct | {i}))
+
+
+def _wavy_periodic(n, L=2 * math.pi, a=0.35):
+    """A curved periodic box: x = xi + a sin(eta), y = eta + a sin(xi) (period
+    L = 2 pi in both, so the mesh wraps onto itself); alpha_jk varies from
+    cell to cell.  Seeded smooth initial field."""
+    t = np.arange(n + 1) * L / n
+    E, X = np.meshgrid(t, t, indexing="ij")
+    V = np.stack([X + a * np.sin(E), E + a * np.sin(X)], axis=-1)
+    m = O.Mesh(2, [((n, n, 1), V)], [(0, 0, 0, 1), (0, 2, 0, 3)], allow_nonorthogonal=True)
+    rng = np.random.default_rng(16)
+    u0 = rng.standard_normal((2, m.N))
+    return m, u0, rng.standard_normal(m.N)
+
+
+def test_splits_differ_at_one_corrector_step_and_agree_when_converged():
+    """Both splits converge to the same full momentum system, so the converged
+    predictors agree.  A = diag C differs only where a Dirichlet ghost puts a
+    cross entry on the diagonal, so on a mesh without walls (the sheared
+    periodic box) whole converged steps agree too; at n_nonortho = 1 the two
+    are different approximations of it."""
+    m = _walled_mesh((9, 8), (0.1, 0.1), (0.7,), seed=4)
+    rng = np.random.default_rng(15)
+    u0 = rng.standard_normal((2, m.N))
+    p0 = rng.standard_normal(m.N)
+    nu, dt = 0.05, 0.02
+    us = {sp: O.piso_step(m, u0, p0, dt, nu, None, None, OP.Options(n_nonortho=60, solver="direct",
+                                                                    nonortho_split=sp))[2]["ustar"]
+          for sp in ("paper", "deferred")}
+    assert np.abs(us["paper"] - us["deferred"]).max() <= 1e-10 * np.abs(us["paper"]).max()
+    assert np.abs(OP.cross_matrix(m, nu).diag).max() > 0          # walls: A differs at the wall cells
+    mp, u0, p0 = _wavy_periodic(12)
+    assert np.all(OP.cross_matrix(mp, 0.1).diag == 0)               # no walls: A is the same
+    assert np.abs(OP.cross_matrix(mp, 0.1).off).max() > 0           # alpha_jk varies: direct entries
+    out = {}
+    for split in ("paper", "deferred"):
+        for n in (1, 60):
+            out[split, n] = O.piso_step(mp, u0, p0, 0.05, 0.1, None, None,
+                                        OP.Options(n_nonortho=n, solver="direct", nonortho_split=split))[0]
+    scale = np.abs(out["paper", 60]).max()
+    assert np.abs(out["paper", 60] - out["deferred", 60]).max() <= 1e-10 * scale
+    d1 = np.abs(out["paper", 1] - out["deferred", 1]).max() / scale
+    assert d1 > 1e-6, d1
 
 
 def _tg_sheared(n, nu, dt):
@@ -200,10 +277,11 @@ def test_cross_operator_transposes_are_exact():
     u = rng.standard_normal((2, m.N))
     g = rng.standard_normal((2, m.N))
     nu = 0.3
-    gu, gb = OP.cross_diffusion_T(m, g, nu)
-    lhs = float(np.sum(OP.cross_diffusion(m, u, nu, m.bval) * g))
-    rhs = float(np.sum(gu * u)) + sum(float(np.sum(gb[s] * m.bval[s])) for s in range(m.nsides))
-    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    for part in ("all", "own", "nbr"):
+        gu, gb = OP.cross_diffusion_T(m, g, nu, part)
+        lhs = float(np.sum(OP.cross_diffusion(m, u, nu, m.bval, part) * g))
+        rhs = float(np.sum(gu * u)) + sum(float(np.sum(gb[s] * m.bval[s])) for s in range(m.nsides))
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs), part
     p = rng.standard_normal(m.N)
     A = 1.0 + rng.random(m.N)
     gy = rng.standard_normal(m.N)
@@ -214,8 +292,9 @@ def test_cross_operator_transposes_are_exact():
     assert abs(float(np.sum(gA * dA)) - fd) <= 1e-8 * abs(fd)
 
 
+@pytest.mark.parametrize("split", ["paper", "deferred"])
 @pytest.mark.parametrize("periodic", [False, True])
-def test_nonorthogonal_adjoint_matches_central_differences(periodic):
+def test_nonorthogonal_adjoint_matches_central_differences(periodic, split):
     """The adjoint of the non-orthogonal step (two corrector steps): every
     input's directional derivative (u^n, p^n, which now enters through the
     pressure cross terms, S, nu and the boundary values) equals 4th-order
@@ -233,7 +312,7 @@ def test_nonorthogonal_adjoint_matches_central_differences(periodic):
     p0 = rng.standard_normal(N)
     S0 = rng.standard_normal((d, N))
     nu, dt = 0.05, 0.03
-    opts = OP.Options(n_nonortho=2, solver="direct")
+    opts = OP.Options(n_nonortho=2, solver="direct", nonortho_split=split)
     ubar, pbar = rng.standard_normal((d, N)), rng.standard_normal(N)
     _, _, tape = O.piso_step(m, u0, p0, dt, nu, S0, None, opts)
     gu, gp, gS, gnu, gbv = O.piso_step_adjoint(m, tape, ubar, pbar, opts, want_bval=True)

@@ -81,3 +81,17 @@ def test_static_scratch_refuses_domains_that_do_not_fit():
         _static_step(dom, u, p, c.dt, c.nu, None)
     assert e.value.status == 1              # PISO_EINVAL
     assert "bytes of scratch" in str(e.value)
+
+
+def test_adjoint_after_static_step_is_refused():
+    """The static step's record lives in the shared buffer, so an adjoint that
+    asks for the domain's own record (tape NULL) must be refused, not answered
+    from the record of an earlier piso_step."""
+    c = W.cavity2d(16)
+    dom = gpu_domain(c)
+    u, p = to_dev(dom, c.u0, 2), to_dev(dom, c.p0)
+    dom.step(u, p, c.dt, c.nu)
+    _static_step(dom, u, p, c.dt, c.nu, None)
+    with pytest.raises(capi.PisoError) as e:
+        dom.step_adjoint(torch.ones_like(u))
+    assert e.value.status == 7              # PISO_ESTATE
