@@ -119,14 +119,19 @@ typedef struct {
                             autotune).  Batches reject any value but NONE (PISO_EINVAL). */
   int32_t n_nonortho;    /* non-orthogonal meshes (App. A.2 "Non-Orthogonal Grids"): 0 (default)
                             rejects blocks whose cross metrics alpha_jk = J T_j . T_k (j != k) do
-                            not vanish; n >= 1 accepts them: the cross derivatives of the viscous
-                            term and of the pressure operator are deferred to the right-hand sides
-                            with the previous iterate (the predictor's, each corrector's input
-                            velocity, the previous pressure) and every predictor and pressure solve
-                            is repeated n times (non-orthogonal corrector steps).  Forward step only
-                            on such meshes: piso_step_adjoint returns PISO_ESTATE, batches and
-                            pred_grad_p = 1 reject them (PISO_EINVAL).  Ignored on orthogonal
-                            meshes. */
+                            not vanish; 1..4 accepts them.  The cross derivatives of the viscous
+                            term are split as Eq. difNonOrthoMatDiscrete and Eq. velRHSnonOrtho
+                            state: the terms on a cell's direct neighbours join the matrix C, those
+                            on its diagonal neighbours go to the right-hand side with the previous
+                            iterate (the predictor's, each corrector's input velocity); the cross
+                            derivatives of the pressure operator go to the right-hand side whole
+                            with the previous pressure iterate (Eq. pressureRHSnonOrtho; P stays
+                            symmetric for the CG); every predictor and pressure solve is repeated
+                            n times (non-orthogonal corrector steps).  piso_step_adjoint runs those
+                            loops in reverse (p^n then receives a gradient through the pressure
+                            cross terms); the step record holds the iterates, hence the limit 4.
+                            Batches and pred_grad_p = 1 reject such meshes (PISO_EINVAL).
+                            Ignored on orthogonal meshes. */
 } piso_options;
 
 /* Values of piso_options.p_precond. */

@@ -1,9 +1,10 @@
 """Build the CUDA library in-tree for sm_103a (``libpiso.so`` next to this file).
 
 The C ABI and the statistics kernels (piso_capi.cu) and the step kernels
-(piso_kernels_{fwd,adj}_{f32,f64}.cu) are separate translation units compiled
-in parallel (no relocatable device code: each unit carries its own kernels)
-and linked into one shared library."""
+(piso_kernels_{fwd,adj,adjno}_{f32,f64}.cu) are separate translation units
+compiled in parallel (no relocatable device code: each unit carries its own
+kernels) and linked into one shared library.  Objects are kept in _build/ and
+a unit is recompiled only when it or a file it includes changed."""
 from __future__ import annotations
 
 import os
@@ -13,7 +14,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "libpiso.so")
 SRCS = [os.path.join(HERE, "csrc", f) for f in ("piso_capi.cu", "piso_kernels_fwd_f32.cu", "piso_kernels_fwd_f64.cu",
-                                                 "piso_kernels_adj_f32.cu", "piso_kernels_adj_f64.cu")]
+                                                 "piso_kernels_adj_f32.cu", "piso_kernels_adj_f64.cu",
+                                                 "piso_kernels_adjno_f32.cu", "piso_kernels_adjno_f64.cu")]
 DEPS = [os.path.join(HERE, "csrc", f) for f in sorted(os.listdir(os.path.join(HERE, "csrc")))]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include", "piso.h")
 
@@ -31,6 +33,31 @@ def nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
+OBJDIR = os.path.join(HERE, "_build")     # object cache (git-ignored), so an edit rebuilds only what it touches
+
+
+def _deps(src: str):
+    """Files a translation unit depends on: itself, every header of csrc/ and
+    include/piso.h; the C ABI unit also includes the host-side .inc files."""
+    csrc = os.path.join(HERE, "csrc")
+    deps = [src, INCLUDE] + [os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith(".cuh")]
+    if os.path.basename(src) == "piso_capi.cu":
+        deps += [os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith(".inc")]
+    return deps
+
+
+def _obj(src: str) -> str:
+    return os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
+
+
+def _stale(src: str) -> bool:
+    o = _obj(src)
+    if not os.path.exists(o):
+        return True
+    t = os.path.getmtime(o)
+    return any(os.path.getmtime(p) > t for p in _deps(src))
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
@@ -41,27 +68,29 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
-    import tempfile
-    with tempfile.TemporaryDirectory(prefix="piso_build_") as tmpdir:
-        objs, procs = [], []
-        for src in SRCS:
-            obj = os.path.join(tmpdir, os.path.basename(src)[:-3] + ".o")
-            objs.append(obj)
-            procs.append(subprocess.Popen([nvcc()] + NVCC_FLAGS + ["-c", "-o", obj, src],
-                                          stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
-        logs, failed = [], False
-        for p in procs:
-            out, err = p.communicate()
-            logs.append(out + err)
-            failed |= p.returncode != 0
-        if failed:
-            sys.stderr.write("".join(logs))
-            raise RuntimeError("nvcc failed building libpiso.so")
-        tmp = LIB + ".tmp"
-        res = subprocess.run([nvcc()] + LINK_FLAGS + ["-o", tmp] + objs, capture_output=True, text=True)
-        if res.returncode != 0:
-            sys.stderr.write(res.stdout + res.stderr)
-            raise RuntimeError("nvcc failed linking libpiso.so")
+    os.makedirs(OBJDIR, exist_ok=True)
+    todo = [src for src in SRCS if force or _stale(src)]
+    procs = []
+    for src in todo:
+        tmp_obj = _obj(src) + ".tmp"
+        procs.append((src, tmp_obj, subprocess.Popen([nvcc()] + NVCC_FLAGS + ["-c", "-o", tmp_obj, src],
+                                                     stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
+    logs, failed = [], False
+    for src, tmp_obj, p in procs:
+        out, err = p.communicate()
+        logs.append(out + err)
+        if p.returncode != 0:
+            failed = True
+        else:
+            os.replace(tmp_obj, _obj(src))
+    if failed:
+        sys.stderr.write("".join(logs))
+        raise RuntimeError("nvcc failed building libpiso.so")
+    tmp = LIB + ".tmp"
+    res = subprocess.run([nvcc()] + LINK_FLAGS + ["-o", tmp] + [_obj(s) for s in SRCS], capture_output=True, text=True)
+    if res.returncode != 0:
+        sys.stderr.write(res.stdout + res.stderr)
+        raise RuntimeError("nvcc failed linking libpiso.so")
     if verbose:
         sys.stderr.write("".join(logs))
     os.replace(tmp, LIB)

@@ -3,10 +3,18 @@
 // differentiated by transposed solves (A^T db = dx, dA = -db (x) x on the
 // sparsity pattern; App. A.5: the forward solvers with the transposed matrix),
 // every other operation by its exact transpose, read off the implemented
-// forward operator (reading R9).  Boundary values and the outflow update are
-// held fixed.  The gradient paths of Sec. 2.4 (Eq. jnone) are selectable: a
-// path left out makes its solve's output a constant of the backward pass, so
-// the transposed solve and the terms it feeds are skipped.
+// forward operator (reading R9), including the boundary values and the
+// advective outflow update.  The gradient paths of Sec. 2.4 (Eq. jnone) are
+// selectable: a path left out makes its solve's output a constant of the
+// backward pass, so the transposed solve and the terms it feeds are skipped.
+// On non-orthogonal meshes (MODE 2, App. A.2 "Non-Orthogonal Grids" with App.
+// A.4) the non-orthogonal corrector loops run in reverse: per pressure solve
+// the transposed solve, then the transpose of the pressure cross terms in the
+// previous iterate and in A (the starting pressure, p^n for the first
+// corrector, receives a gradient); per predictor solve the transposed solve,
+// then the transpose of the deferred viscous cross terms in the previous
+// iterate and the boundary values; the direct-neighbour cross entries of C add
+// their viscosity and boundary-value derivatives.
 #pragma once
 #include "piso_forward.cuh"
 
@@ -67,7 +75,14 @@ struct AdjCall {
   IluTab ilu;                // ILU(0) tables of the launch layout (when adv_ilu)
   real* ilud;                // [N] ILU(0) reciprocal pivots (rebuilt here from the taped C)
   int32_t adv_ilu;           // 0 none, 1 ILU(0), 2 ILU(0) after a failed plain solve
-  int32_t n_nonortho;        // always 0: the adjoint is not provided on non-orthogonal meshes
+  int32_t n_nonortho;        // non-orthogonal mesh: the domain's n_nonortho (the kernel takes the recorded
+                             // step's count from the tape header)
+  const real* pn;            // [N] recorded p^n (non-orthogonal meshes)
+  const real* xit[4];        // per corrector [3][N]: pressure iterates 1..n-1 of its non-orthogonal loop
+  const real* usit;          // [3][d][N]: predictor iterates 1..n-1
+  real* gyb;                 // [N]   sum of one corrector's transposed pressure solutions
+  real* invA;                // [N]   1 / A (non-orthogonal meshes)
+  real* gdk;                 // [d][d][N] sensitivities to the cells' central differences
   uint32_t* bar;
   double* partials;
   int32_t* status;
@@ -76,8 +91,9 @@ struct AdjCall {
   int32_t cta0, ncta;
 };
 
-template <typename real, int ND, bool ILU>
+template <typename real, int ND, int MODE>
 __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g) {
+  constexpr bool ILU = MODE >= 1;
   __shared__ DomStatic D;
   __shared__ BiState bs;
   __shared__ CgState cs;
@@ -110,6 +126,12 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   const int K = o.n_corr;
   const bool path_adv = (o.grad_paths & 1) != 0;   // Sec. 2.4: gradient through the advection solve
   const bool path_p = (o.grad_paths & 2) != 0;     // Sec. 2.4: gradient through the pressure solves
+  int NO = 0;                                       // non-orthogonal corrector steps of the recorded step
+  if constexpr (MODE == 2) NO = (int)A.hdr[2];
+  const real* Gx = reinterpret_cast<const real*>(D.Gx);
+  const real nu_s = pick<real>(A.hdr[1], (float)A.hdr[1]);
+  Acc<real> anu[1];                                 // dL/dnu, summed over the phases
+  anu[0].zero();
 
   // (G^T W)_P for the cell-centred central gradient with the R5 boundary rule:
   // G(p)_Q = sum_j T_Q,j . 0.5 (p_{nb(Q,+j)} - p_{nb(Q,-j)}), p_Q standing in
@@ -151,6 +173,9 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
         }
         A.Pdiag[P] = pd;
         A.Pinv[P] = real(1) / (-pd);
+        if constexpr (MODE == 2) {
+          if (NO) A.invA[P] = real(1) / aP;
+        }
 #pragma unroll
         for (int s = 0; s < NSD; s++)
           if (c.nb[s] < 0)
@@ -198,6 +223,11 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       X.cells([&](const Cell& c) {
         real v = -gradT(c, A.W);
         if (k == K - 1 && A.dp_out) v += A.dp_out[c.i];
+        if constexpr (MODE == 2) {
+          // dL/d(this corrector's final pressure) through the next corrector's
+          // starting pressure (its pressure cross terms)
+          if (NO && k < K - 1) v += A.gx[c.i];
+        }
         A.gx[c.i] = v;
         A.cx[c.i] = real(0);
         a[0].add(v);
@@ -205,18 +235,71 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       if (!reduce_sync<real, 1>(g, a, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
     }
     // transposed pressure solve: P y = gx - mean (P is symmetric)
-    if (path_p && !pressure_solve<real, ND>(X, cs, rs, o, A.Pdiag, A.Pinv, A.Poff, A.gx, s_mean, A.cx, A.x64, A.rin,
-                                            A.ce, A.crb, A.cwb, A.csb, A.cp, A.istats, A.dstats, k))
+    if (path_p && NO == 0 &&
+        !pressure_solve<real, ND>(X, cs, rs, o, A.Pdiag, A.Pinv, A.Poff, A.gx, s_mean, A.cx, A.x64, A.rin, A.ce,
+                                  A.crb, A.cwb, A.csb, A.cp, A.istats, A.dstats, k))
       return;
+    if constexpr (MODE == 2) {
+      // non-orthogonal corrector steps in reverse: x_m = P^+ (b - Y(x_{m-1}; A)),
+      // m = NO..1, x_0 the corrector's starting pressure; y_m = P^+ (dL/dx_m) feeds
+      // dP (through d(alpha/A)), the divergence (sum of the y_m) and, through
+      // -Y^T y_m, dL/dx_{m-1} and dL/dA
+      if (path_p && NO) {
+        int p_tot = 0;
+        for (int m = NO; m >= 1; m--) {
+          if (!pressure_solve<real, ND>(X, cs, rs, o, A.Pdiag, A.Pinv, A.Poff, A.gx, s_mean, A.cx, A.x64, A.rin,
+                                        A.ce, A.crb, A.cwb, A.csb, A.cp, A.istats, A.dstats, k))
+            return;
+          if (threadIdx.x == 0 && g.rank == 0) p_tot += A.istats[4 + k];
+          const real* xm = (m == NO) ? xk : A.xit[k] + (size_t)(m - 1) * N;
+          const real* xm1 = (m == 1) ? (k == 0 ? A.pn : A.xk[k - 1]) : A.xit[k] + (size_t)(m - 2) * N;
+          X.cells([&](const Cell& c) {
+            const int32_t P = c.i;
+            const real yP = A.cx[P];
+#pragma unroll
+            for (int j = 0; j < ND; j++) {
+              real gwj = 0;
+#pragma unroll
+              for (int e = 0; e < 2; e++) {
+                const int32_t F = c.nb[2 * j + e];
+                if (F >= 0) gwj += real(0.5) * (yP - A.cx[F]) * (xm[P] - xm[F]);
+              }
+              A.gw[(size_t)j * N + P] += gwj;
+            }
+            A.gyb[P] = (m == NO ? real(0) : A.gyb[P]) + yP;
+            A.gA[P] += cross_pres_T1<real, ND>(D, c, A.cx, real(-1), xm1, A.invA, Gx, A.gdk);
+          });
+          if (!plain_sync(g)) return;
+          Acc<real> a1[1];
+          a1[0].zero();
+          X.cells([&](const Cell& c) {
+            const real v = cross_diff_T2<real, ND, false>(c, A.gdk, N, nullptr);
+            A.gx[c.i] = v;
+            A.cx[c.i] = real(0);
+            a1[0].add(v);
+          });
+          if (!reduce_sync<real, 1>(g, a1, [&](const double* q) { s_mean = q[0] / (double)N; })) return;
+        }
+        if (threadIdx.x == 0 && g.rank == 0) A.istats[4 + k] = p_tot;
+      }
+    }
     // R3: dP = -y (x) x on the pattern -> d(alpha/A); h_bar = gu + div^T y;
     //     gg = h_bar / A; dL/dA and dL/drhs0 from h = A^-1 (rhs0 - H u);
     //     boundary values: b has the flux N_b J_P T_j . u_b (R6), so
     //     dL/du_b += N_b J_P T_j (y_P - mean y) (the mean is subtracted at the end)
     Acc<real> ay[1];
     ay[0].zero();
+    const real* ysrc = A.cx;      // the transposed pressure solution (the sum of them, MODE 2)
+    bool gw_here = true;
+    if constexpr (MODE == 2) {
+      if (NO) {
+        ysrc = A.gyb;
+        gw_here = false;          // dP was taken per solve above
+      }
+    }
     X.cells([&](const Cell& c) {
       const int32_t P = c.i;
-      const real yP = path_p ? A.cx[P] : real(0), xP = path_p ? xk[P] : real(0);
+      const real yP = path_p ? ysrc[P] : real(0), xP = path_p ? xk[P] : real(0);
       if (path_p) {
         ay[0].add(yP);
 #pragma unroll
@@ -243,11 +326,11 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
             const int32_t F = c.nb[s];
             if (F < 0) continue;
             const real n = e ? real(1) : real(-1);
-            const real dy = yP - A.cx[F];
-            gwj += real(0.5) * dy * (xP - xk[F]);
+            const real dy = yP - ysrc[F];
+            if (gw_here) gwj += real(0.5) * dy * (xP - xk[F]);
             fb += real(0.5) * n * dy;
           }
-          A.gw[(size_t)j * N + P] += gwj;
+          if (gw_here) A.gw[(size_t)j * N + P] += gwj;
           Fb[j] = fb * J[P];
         }
       }
@@ -290,8 +373,30 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
         }
         A.gu[(size_t)i * N + P] = -v;
       }
+      if constexpr (MODE == 2) {
+        // h carries the deferred viscous cross terms of its input velocity:
+        // their transpose (phase 1) and their viscosity derivative
+        if (NO) {
+          cross_visc_T1<real, ND>(c, A.gg, Gx, J, nu_s, N, A.gdk);
+          real xv[ND];
+          cross_visc<real, ND>(D, c, uin, A.bval, nbf, Gx, J, real(1), xv);
+#pragma unroll
+          for (int i = 0; i < ND; i++) anu[0].add_prod(ggP[i], xv[i]);
+        }
+      }
     });
     if (!plain_sync(g)) return;
+    if constexpr (MODE == 2) {
+      if (NO) {
+        X.cells([&](const Cell& c) {
+#pragma unroll
+          for (int i = 0; i < ND; i++)
+            A.gu[(size_t)i * N + c.i] +=
+                cross_diff_T2<real, ND, true>(c, A.gdk + (size_t)i * ND * N, N, A.gbval + (size_t)i * nbf);
+        });
+        if (!plain_sync(g)) return;
+      }
+    }
   }
 
   // R5: dL/dA from the pressure matrix (w = alpha / A); start the transposed
@@ -325,41 +430,117 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       return;
   }
   // the transposed solve with the preconditioning of the forward one: the
-  // factors of C^T are the transposed factors of C (same pivots)
+  // factors of C^T are the transposed factors of C (same pivots).  On
+  // non-orthogonal meshes the predictor's corrector steps run in reverse:
+  // u*_m = C^-1 (rhs0 + X(u*_{m-1})), m = NO..1, u*_0 = u^n; z_m = C^-T dL/du*_m
+  // feeds dC, rhs0 and, through X^T z_m, dL/du*_{m-1} and the boundary values.
   int ilu_used = 0;
-  if constexpr (ILU) {
-    if (path_adv) {
+  int adv_tot[3] = {0, 0, 0};
+  if (path_adv) {
+    IluPre<real> IP{};
+    IluSmem<real, ND> IS{};
+    if constexpr (ILU) {
       // the level tables exist only when the ILU(0) preconditioner is on
-      const IluPre<real> IP = A.adv_ilu ? ilu_setup<real>(A.ilu, A.ilud, g.rank) : IluPre<real>{};
-      const IluSmem<real, ND> IS = ilu_smem<real, ND>(X, o);
-      if (A.adv_ilu == 1) {
-        ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
-        ilu_used = 1;
-        if (!bicgstab_ilu<real, ND, true>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv[0],
-                                          A.vv[0], A.pv[1], A.vv[1], A.t, IS))
-          return;
-      } else {
+      if (A.adv_ilu) IP = ilu_setup<real>(A.ilu, A.ilud, g.rank);
+      IS = ilu_smem<real, ND>(X, o);
+    }
+    bool factored = false;
+    auto solveT = [&]() -> bool {
+      if constexpr (ILU) {
+        if (A.adv_ilu == 1) {
+          if (!factored) ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
+          factored = true;
+          ilu_used = 1;
+          return bicgstab_ilu<real, ND, true>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv[0],
+                                              A.vv[0], A.pv[1], A.vv[1], A.t, IS);
+        }
         if (!bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t))
-          return;
+          return false;
         if (A.adv_ilu == 2 && !bicg_all_conv<ND>(bs)) {
           bicg_restart<real, ND>(X, bs, A.z, static_cast<const real*>(nullptr), A.r, A.rhat, o.adv_rtol, o.atol,
                                  g.status);
-          ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
+          if (!factored) ilu_factor<real, ND>(X, IP, A.Cdiag, A.Coff, IS);
+          factored = true;
           ilu_used = 2;
-          if (!bicgstab_ilu<real, ND, true>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv[0],
-                                            A.vv[0], A.pv[1], A.vv[1], A.t, IS))
+          return bicgstab_ilu<real, ND, true>(X, IP, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv[0],
+                                              A.vv[0], A.pv[1], A.vv[1], A.t, IS);
+        }
+        return true;
+      } else {
+        return bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t);
+      }
+    };
+    for (int m = NO > 0 ? NO : 1; m >= 1; m--) {
+      if (!solveT()) return;
+      if (threadIdx.x == 0)
+        for (int q = 0; q < ND; q++) adv_tot[q] += bs.iters[q] + bs.iters_prev[q];
+      if constexpr (MODE == 2) {
+        if (NO) {
+          const real* usm = (m == NO) ? A.ustar : A.usit + (size_t)(m - 1) * ND * N;
+          const real* usm1 = (m == 1) ? A.un : A.usit + (size_t)(m - 2) * ND * N;
+          // dC = -z (x) u*_m on the pattern, dL/drhs0 += z, X^T z (phase 1)
+          X.cells([&](const Cell& c) {
+            const int32_t P = c.i;
+            real zP[ND];
+            real ga = 0;
+#pragma unroll
+            for (int i = 0; i < ND; i++) {
+              zP[i] = A.z[(size_t)i * N + P];
+              ga += zP[i] * usm[(size_t)i * N + P];
+              A.grhs0[(size_t)i * N + P] += zP[i];
+            }
+            A.gA[P] -= ga;
+#pragma unroll
+            for (int s = 0; s < NSD; s++) {
+              const int32_t F = c.nb[s];
+              if (F < 0) continue;
+              real acc = 0;
+#pragma unroll
+              for (int i = 0; i < ND; i++) acc += zP[i] * usm[(size_t)i * N + F];
+              A.gCoff[(size_t)s * N + P] -= acc;
+            }
+            cross_visc_T1<real, ND>(c, A.z, Gx, J, nu_s, N, A.gdk);
+            real xv[ND];
+            cross_visc<real, ND>(D, c, usm1, A.bval, nbf, Gx, J, real(1), xv);
+#pragma unroll
+            for (int i = 0; i < ND; i++) anu[0].add_prod(zP[i], xv[i]);
+          });
+          if (!plain_sync(g)) return;
+          // X^T z (phase 2): dL/du*_{m-1}; the next transposed solve starts from it
+          Acc<real> a[2 * ND];
+#pragma unroll
+          for (int q = 0; q < 2 * ND; q++) a[q].zero();
+          X.cells([&](const Cell& c) {
+            const int32_t P = c.i;
+#pragma unroll
+            for (int i = 0; i < ND; i++) {
+              const real gm = cross_diff_T2<real, ND, true>(c, A.gdk + (size_t)i * ND * N, N, A.gbval + (size_t)i * nbf);
+              if (m > 1) {
+                A.z[(size_t)i * N + P] = 0;
+                A.r[(size_t)i * N + P] = gm;
+                A.rhat[(size_t)i * N + P] = gm;
+                a[i].add_prod(gm, gm);
+                a[ND + i].add_prod(gm, gm);
+              } else {
+                A.gu[(size_t)i * N + P] = gm;    // dL/du^n through the predictor's cross terms
+              }
+            }
+          });
+          if (m > 1) {
+            if (!reduce_sync<real, 2 * ND>(g, a,
+                                           [&](const double* q) { bicg_start<ND>(bs, q, o.adv_rtol, o.atol, g.status); }))
+              return;
+          } else if (!plain_sync(g)) {
             return;
+          }
         }
       }
     }
-  } else {
-    if (path_adv && !bicgstab<real, ND, true>(X, bs, o.adv_maxit, A.Cdiag, A.Coff, A.z, A.r, A.rhat, A.pv, A.vv, A.t))
-      return;
   }
   if (path_adv && threadIdx.x == 0 && g.rank == 0) {
     int nc = 0;
     for (int k = 0; k < ND; k++) {
-      A.istats[k] = bs.iters[k] + bs.iters_prev[k];
+      A.istats[k] = adv_tot[k];
       A.dstats[k] = sqrt(bs.res2[k]);
       if (!bs.conv[k]) nc = 1;
     }
@@ -369,14 +550,16 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   }
   // R6: dC = -z (x) u* on the pattern; dL/drhs0 += z; outputs dS and the
   //     1/dt part of du_in; W = T . z for the predictor pressure gradient
-  Acc<real> anu[1];
-  anu[0].zero();
+  bool z_here = path_adv;     // MODE 2 took the z terms per predictor solve above
+  if constexpr (MODE == 2) {
+    if (NO) z_here = false;
+  }
   X.cells([&](const Cell& c) {
     const int32_t P = c.i;
     real zP[ND];
 #pragma unroll
     for (int i = 0; i < ND; i++) zP[i] = 0;
-    if (path_adv) {
+    if (z_here) {
       real ga = 0;
 #pragma unroll
       for (int i = 0; i < ND; i++) {
@@ -401,6 +584,22 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       A.du_in[(size_t)i * N + P] = gr[i] * inv_dt;
       if (A.dS) A.dS[(size_t)i * N + P] = gr[i];
     }
+    if constexpr (MODE == 2) {
+      if (NO) {
+        // dL/du^n through the predictor's cross terms; rhs0 holds the
+        // constant part of the direct-neighbour cross entries (linear in nu
+        // and in the boundary values)
+        if (path_adv)
+#pragma unroll
+          for (int i = 0; i < ND; i++) A.du_in[(size_t)i * N + P] += A.gu[(size_t)i * N + P];
+        real W[ND], x0[ND];
+        cross_w<real, ND>(c, Gx, N, W);
+        cross_const<real, ND>(D, c, W, A.bval, nbf, Gx, J, x0);
+#pragma unroll
+        for (int i = 0; i < ND; i++) anu[0].add_prod(gr[i], x0[i]);
+        cross_const_T<real, ND>(D, c, W, A.grhs0, Gx, J, nu_s, nbf, A.gbval);
+      }
+    }
     if (o.pred_grad_p) {
 #pragma unroll
       for (int j = 0; j < ND; j++) {
@@ -413,7 +612,6 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
     // nu from the Dirichlet terms of the right-hand side (Eq. velRHSdiscrete),
     // and the boundary values there: rhs0_i += u_b,i (2 alpha nu / J - N_f T_j . u_b)
     const real invJ = real(1) / J[P];
-    const real nu_s = pick<real>(A.hdr[1], (float)A.hdr[1]);
 #pragma unroll
     for (int s = 0; s < NSD; s++) {
       const int32_t F = c.nb[s];
@@ -441,9 +639,30 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   //     fluxes U_f = (U_P + U_F)/2, U = J T . u^n, and the nu terms of C
   X.cells([&](const Cell& c) {
     const int32_t P = c.i;
-    if (A.dp_in) A.dp_in[P] = o.pred_grad_p ? -gradT(c, A.W) : real(0);
     const real invJ = real(1) / J[P];
     const real gAP = A.gA[P];
+    if constexpr (MODE == 2) {
+      if (NO) {
+        // dL/dp^n through the first corrector's pressure cross terms; nu
+        // through the direct-neighbour cross entries of C (C = ... - nu M1)
+        if (A.dp_in) A.dp_in[P] = path_p ? A.gx[P] : real(0);
+        real W[ND];
+        cross_w<real, ND>(c, Gx, N, W);
+        real m = 0;
+#pragma unroll
+        for (int s = 0; s < NSD; s++) {
+          const real n = (s & 1) ? real(1) : real(-1);
+          const real h = n * real(0.5) * W[s >> 1] * invJ;
+          if (c.nb[s] >= 0) m += A.gCoff[(size_t)s * N + P] * h;
+          else m -= gAP * h;
+        }
+        anu[0].add(-m);
+      } else if (A.dp_in) {
+        A.dp_in[P] = real(0);
+      }
+    } else if (A.dp_in) {
+      A.dp_in[P] = o.pred_grad_p ? -gradT(c, A.W) : real(0);
+    }
     real Ub[ND];
 #pragma unroll
     for (int j = 0; j < ND; j++) Ub[j] = 0;
@@ -578,7 +797,9 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   }
 }
 
-template <typename real, int ND, int MAXT, bool ILU>
+// MODE 0: the plain step's adjoint; 1: with the ILU(0)-preconditioned
+// transposed predictor solve; 2: also the non-orthogonal terms.
+template <typename real, int ND, int MAXT, int MODE>
 __global__ void __launch_bounds__(MAXT, 1) adj_kernel(const __grid_constant__ Launch<AdjCall<real>> L) {
   __shared__ AdjCall<real> A;
   const int gi = find_group(L.ngroups, L.cta_first);
@@ -594,7 +815,7 @@ __global__ void __launch_bounds__(MAXT, 1) adj_kernel(const __grid_constant__ La
   g.timeout_ns = L.o.timeout_ns;
   g.withhold = (L.o.withhold_cta == g.rank) ? 1 : 0;
   g.trace = L.o.trace;
-  adj_group<real, ND, ILU>(A, L.o, g);
+  adj_group<real, ND, MODE>(A, L.o, g);
 }
 
 }  // namespace piso

@@ -28,8 +28,8 @@ using namespace piso;
 namespace piso {
 const void* fwd_kernel_addr_f32(int nd, bool wide, int mode);
 const void* fwd_kernel_addr_f64(int nd, bool wide, int mode);
-const void* adj_kernel_addr_f32(int nd, bool wide, bool ilu);
-const void* adj_kernel_addr_f64(int nd, bool wide, bool ilu);
+const void* adj_kernel_addr_f32(int nd, bool wide, int mode);
+const void* adj_kernel_addr_f64(int nd, bool wide, int mode);
 }  // namespace piso
 
 namespace {
@@ -124,6 +124,7 @@ struct piso_batch {
   std::vector<int32_t> cta_first;
   int32_t* d_cta_first = nullptr;
   size_t call_bytes = 0;       // bytes of one group's call record (the larger of forward and adjoint)
+  int mode = 0;                // kernel instantiation: 0 plain, 2 when a member is non-orthogonal
   void* dev = nullptr;         // piso_batch_dev: device and pinned buffers of the batch launches
   std::string err;
 };
@@ -229,6 +230,7 @@ enum WsIdx {
   W_LFA, W_LFM, W_LFC, W_ILUD, W_BX,
   // adjoint scratch
   A_GA, A_GCOFF, A_GRHS0, A_GW, A_W, A_GG, A_GU, A_GX, A_Z, A_DU,
+  A_GYB, A_GDK,    // non-orthogonal meshes only
   W_COUNT
 };
 
@@ -243,13 +245,27 @@ int ws_units(int k, int nd) {
       return 2;     // N doubles (two float units; the FP64 mode over-allocates)
     case A_GCOFF:
       return 2 * nd;
+    case A_GYB:
+      return 1;
+    case A_GDK:
+      return nd * nd;
     default:
       return nd;
   }
 }
 
+// workspace arrays a domain allocates: the adjoint's non-orthogonal scratch
+// only on non-orthogonal meshes
+bool ws_needed(int k, bool has_cross) { return has_cross || (k != A_GYB && k != A_GDK); }
+
+// Non-orthogonal corrector iterates a step record can hold (the adjoint needs
+// them); piso_options.n_nonortho is limited to this.
+constexpr int NONORTHO_MAX = 4;
+
 struct TapeLayout {
-  size_t hdr, un, cdiag, coff, ustar, h[4], xk[4], uc[4], bval, bval_in, total;
+  size_t hdr, un, cdiag, coff, ustar, h[4], xk[4], uc[4], bval, bval_in;
+  size_t pn, xit[4], usit;   // non-orthogonal meshes: p^n and the iterates 1..n-1 (0: not recorded)
+  size_t total;
 };
 
 TapeLayout tape_layout(const piso_domain* d) {
@@ -274,6 +290,11 @@ TapeLayout tape_layout(const piso_domain* d) {
   }
   t.bval = take(nd * std::max(d->nbf, 1));
   t.bval_in = take(nd * std::max(d->nbf, 1));
+  if (d->has_cross) {
+    t.pn = take(N);
+    for (int k = 0; k < 4; k++) t.xit[k] = take((NONORTHO_MAX - 1) * N);
+    t.usit = take((NONORTHO_MAX - 1) * nd * N);
+  }
   t.total = off;
   return t;
 }
@@ -305,6 +326,11 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
   c.bval_rec = (real*)(tb + L.bval);
   c.bval_in_rec = (real*)(tb + L.bval_in);
   c.hdr = (double*)(tb + L.hdr);
+  if (d->has_cross) {
+    c.pn = (real*)(tb + L.pn);
+    for (int k = 0; k < 4; k++) c.xit[k] = (real*)(tb + L.xit[k]);
+    c.usit = (real*)(tb + L.usit);
+  }
   c.U = (real*)d->ws[W_U];
   c.rhs0 = (real*)d->ws[W_RHS0];
   c.r = (real*)d->ws[W_R];
@@ -471,9 +497,9 @@ cudaError_t coop_launch(const void* kernel, int grid, int threads, void** args, 
 constexpr int WIDE = 768;   // the wide instantiations of piso_kernels_*.cu
 inline int width_class(int threads) { return threads > 512 ? WIDE : 512; }
 
-// Forward instantiation: mode 0 plain, 1 with the ILU(0) predictor, 2 also
-// with the non-orthogonal cross terms; the adjoint has plain and ILU(0) ones
-// (it is not provided on non-orthogonal meshes).  Batches take the plain ones.
+// Kernel instantiations (forward and adjoint alike): mode 0 plain, 1 with the
+// ILU(0) predictor, 2 also with the non-orthogonal cross terms.  Batches take
+// the plain ones.
 template <typename real>
 const void* fwd_ptr_t(int nd, int threads, int mode = 0) {
   const bool wide = width_class(threads) == WIDE;
@@ -481,21 +507,22 @@ const void* fwd_ptr_t(int nd, int threads, int mode = 0) {
 }
 
 template <typename real>
-const void* adj_ptr_t(int nd, int threads, bool ilu = false) {
+const void* adj_ptr_t(int nd, int threads, int mode = 0) {
   const bool wide = width_class(threads) == WIDE;
-  return sizeof(real) == 4 ? adj_kernel_addr_f32(nd, wide, ilu) : adj_kernel_addr_f64(nd, wide, ilu);
+  return sizeof(real) == 4 ? adj_kernel_addr_f32(nd, wide, mode) : adj_kernel_addr_f64(nd, wide, mode);
 }
 
 const void* fwd_kernel_ptr(int prec, int nd, int threads = 512, int mode = 0) {
   return prec == PISO_FP64 ? fwd_ptr_t<double>(nd, threads, mode) : fwd_ptr_t<float>(nd, threads, mode);
 }
 
-const void* adj_kernel_ptr(int prec, int nd, int threads = 512, bool ilu = false) {
-  return prec == PISO_FP64 ? adj_ptr_t<double>(nd, threads, ilu) : adj_ptr_t<float>(nd, threads, ilu);
+const void* adj_kernel_ptr(int prec, int nd, int threads = 512, int mode = 0) {
+  return prec == PISO_FP64 ? adj_ptr_t<double>(nd, threads, mode) : adj_ptr_t<float>(nd, threads, mode);
 }
 
 bool uses_ilu(const piso_domain* d) { return d->opts.adv_precond != PISO_ADV_PRECOND_NONE; }
 int fwd_mode(const piso_domain* d) { return d->has_cross ? 2 : (uses_ilu(d) ? 1 : 0); }
+int adj_mode(const piso_domain* d) { return fwd_mode(d); }
 
 // ILU(0) tables for the current launch layout (App. A.5 preconditioner of the
 // BiCGStab).  Each CTA preconditions with the diagonal block of the cells it
@@ -619,7 +646,7 @@ piso_status choose_shape(piso_domain* d) {
     return fail(d, PISO_EINVAL, "block_threads must be a multiple of 32 in [32, %d]", WIDE);
   int sms = 148;
   int cap_f = max_coresident(fwd_kernel_ptr(d->prec, d->ndim, threads, fwd_mode(d)), threads, &sms);
-  int cap_a = max_coresident(adj_kernel_ptr(d->prec, d->ndim, threads, uses_ilu(d)), threads, nullptr);
+  int cap_a = max_coresident(adj_kernel_ptr(d->prec, d->ndim, threads, adj_mode(d)), threads, nullptr);
   int cap = std::min(cap_f, cap_a);
   if (cap <= 0) return fail(d, PISO_ECUDA, "kernel cannot be resident with %d threads", threads);
   int want = d->opts.ctas > 0 ? d->opts.ctas : std::min(sms, (int)((d->N + threads - 1) / threads));
@@ -825,7 +852,8 @@ static piso_status validate_options(piso_domain* d, const piso_options* o) {
     return fail(d, PISO_EINVAL, "p_precond must be PISO_PRECOND_AUTO, _JACOBI or _LINE");
   if (o->adv_precond < PISO_ADV_PRECOND_NONE || o->adv_precond > PISO_ADV_PRECOND_ILU_ON_FAILURE)
     return fail(d, PISO_EINVAL, "adv_precond must be PISO_ADV_PRECOND_NONE, _ILU or _ILU_ON_FAILURE");
-  if (o->n_nonortho < 0 || o->n_nonortho > 64) return fail(d, PISO_EINVAL, "n_nonortho must be 0..64");
+  if (o->n_nonortho < 0 || o->n_nonortho > NONORTHO_MAX)
+    return fail(d, PISO_EINVAL, "n_nonortho must be 0..%d (the step record holds that many iterates)", NONORTHO_MAX);
   if (d && d->has_cross && (o->n_nonortho < 1 || o->pred_grad_p))
     return fail(d, PISO_EINVAL, "a non-orthogonal mesh needs n_nonortho >= 1 and pred_grad_p = 0");
   return PISO_OK;
@@ -1005,7 +1033,8 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
     d->bf_um = a.take((size_t)nd * nbf1 * e);
     d->bval = a.take((size_t)nd * nbf1 * e);
     d->gbval = a.take((size_t)nd * nbf1 * e);
-    for (int k = 0; k < W_COUNT; k++) d->ws[k] = a.take((size_t)ws_units(k, nd) * N * e);
+    for (int k = 0; k < W_COUNT; k++)
+      d->ws[k] = ws_needed(k, d->has_cross) ? a.take((size_t)ws_units(k, nd) * N * e) : nullptr;
     d->tape_ws = a.take(tape_layout(d).total);
     d->bar = (uint32_t*)a.take(64);
     d->status = (int32_t*)a.take(64);
@@ -1169,7 +1198,7 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
       for (int w : {512, WIDE}) {
         int sms = 148;
         const int cap = std::min(max_coresident(fwd_kernel_ptr(d->prec, d->ndim, w, fwd_mode(d)), w, &sms),
-                                 max_coresident(adj_kernel_ptr(d->prec, d->ndim, w, uses_ilu(d)), w, nullptr));
+                                 max_coresident(adj_kernel_ptr(d->prec, d->ndim, w, adj_mode(d)), w, nullptr));
         const int one_per_thread = (int)std::min<int64_t>(cap, (d->N + w - 1) / w);
         for (int nc : {std::min(cap, sms), one_per_thread})
           if (nc >= 1 && std::find(cand.begin(), cand.end(), std::make_tuple(w, nc, pl)) == cand.end())

@@ -66,6 +66,9 @@ struct FwdCall {
                              // (read by the extended instantiation of the kernel only)
   int32_t n_nonortho;        // non-orthogonal mesh: solves per predictor / pressure solve (0: orthogonal)
   real* bx;                  // [N]    pressure right-hand side with the cross terms (non-orthogonal)
+  real* pn;                  // [N]    tape: p^n (non-orthogonal meshes; null otherwise)
+  real* xit[4];              // [3][N] tape: per corrector the pressure iterates 1..n-1 of its non-orthogonal loop
+  real* usit;                // [3][d][N] tape: the predictor iterates 1..n-1
   // group control
   uint32_t* bar;
   double* partials;
@@ -197,6 +200,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   if (threadIdx.x == 0 && g.rank == 0) {
     A.hdr[0] = A.dt;
     A.hdr[1] = A.nu;
+    A.hdr[2] = (MODE == 2) ? (double)A.n_nonortho : 0.0;
   }
 
   // F1: contravariant flux U^j = J T_j . u^n (App. A.2) and the tape copy of u^n
@@ -206,6 +210,9 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
     for (int k = 0; k < ND; k++) {
       u[k] = A.u_in[(size_t)k * N + P];
       A.un[(size_t)k * N + P] = u[k];
+    }
+    if constexpr (MODE == 2) {
+      if (A.n_nonortho && A.pn) A.pn[P] = A.p_in[P];   // the first corrector's starting pressure
     }
 #pragma unroll
     for (int j = 0; j < ND; j++) {
@@ -233,6 +240,19 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
 #pragma unroll
       for (int k = 0; k < ND; k++)
         rhs[k] = A.u_in[(size_t)k * N + P] * inv_dt + (A.S ? A.S[(size_t)k * N + P] : real(0));
+      // non-orthogonal meshes: the direct-neighbour cross entries of Eq.
+      // difNonOrthoMatDiscrete (C gets -(nu/J_P) W_k (q_{k+} - q_{k-}) / 2, a
+      // Dirichlet ghost 2 u_b - q_P putting its -q_P part on the diagonal and
+      // its 2 u_b part on rhs0, beside the tangential fluxes through P's
+      // Dirichlet faces)
+      real Wx[ND], bx[ND];
+#pragma unroll
+      for (int k = 0; k < ND; k++) Wx[k] = bx[k] = 0;
+      bool nonortho = false;
+      if constexpr (MODE == 2) {
+        nonortho = A.n_nonortho > 0;
+        if (nonortho) cross_w<real, ND>(c, reinterpret_cast<const real*>(D.Gx), N, Wx);
+      }
 #pragma unroll
       for (int s = 0; s < NSD; s++) {
         const int j = s >> 1;
@@ -244,6 +264,9 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
           const real Df = nu * real(0.5) * (aP + AL[(size_t)j * N + F]);
           off[s] = (real(0.5) * n * Uf - Df) * invJ;
           diag += (real(0.5) * n * Uf + Df) * invJ;
+          if constexpr (MODE == 2) {
+            if (nonortho) off[s] -= n * real(0.5) * Wx[j] * nu * invJ;
+          }
         } else {
           const int32_t f = -1 - F;
           real ub[ND], tu = 0;
@@ -258,8 +281,21 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
 #pragma unroll
           for (int k = 0; k < ND; k++) rhs[k] += ub[k] * w;
           off[s] = real(0);
+          if constexpr (MODE == 2) {
+            if (nonortho) {
+              diag += n * real(0.5) * Wx[j] * nu * invJ;
+#pragma unroll
+              for (int k = 0; k < ND; k++) bx[k] += n * Wx[j] * ub[k];
+              cross_bface<real, ND>(D, c, s, A.bval, nbf, reinterpret_cast<const real*>(D.Gx), bx);
+            }
+          }
         }
         A.Coff[(size_t)s * N + P] = off[s];
+      }
+      if constexpr (MODE == 2) {
+        if (nonortho)
+#pragma unroll
+          for (int k = 0; k < ND; k++) rhs[k] += nu * invJ * bx[k];
       }
       A.Cdiag[P] = diag;
       const real ia = real(1) / diag;
@@ -356,6 +392,10 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
         const int32_t P = c.i;
         real xv[ND];
         cross_visc<real, ND>(D, c, A.ustar, A.bval, nbf, reinterpret_cast<const real*>(D.Gx), J, nu, xv);
+        if (A.usit)   // tape: the predictor iterate u*_m for the adjoint
+#pragma unroll
+          for (int k = 0; k < ND; k++)
+            A.usit[((size_t)(m - 1) * ND + k) * N + P] = A.ustar[(size_t)k * N + P];
 #pragma unroll
         for (int k = 0; k < ND; k++) {
           const real b = A.rhs0[(size_t)k * N + P] + xv[k];
@@ -499,6 +539,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
           const int32_t P = c.i;
           const real bm = A.b[P] - cross_pres<real, ND>(D, c, A.cx, A.invA, reinterpret_cast<const real*>(D.Gx));
           A.bx[P] = bm;
+          if (m > 0 && A.xit[kc]) A.xit[kc][(size_t)(m - 1) * N + P] = A.cx[P];   // tape: the iterate x_m
           a[0].add(bm);
         });
         if (!reduce_sync<real, 1>(g, a, [&](const double* q) {

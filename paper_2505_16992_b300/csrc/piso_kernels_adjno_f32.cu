@@ -1,0 +1,12 @@
+// Adjoint step kernels of non-orthogonal meshes (MODE 2), float storage, in a
+// translation unit of their own so they build in parallel with the others.
+#include "piso_adjoint.cuh"
+
+namespace piso {
+
+const void* adjno_kernel_addr_f32(int nd, bool wide) {
+  if (wide) return nd == 2 ? (const void*)adj_kernel<float, 2, 768, 2> : (const void*)adj_kernel<float, 3, 768, 2>;
+  return nd == 2 ? (const void*)adj_kernel<float, 2, 512, 2> : (const void*)adj_kernel<float, 3, 512, 2>;
+}
+
+}  // namespace piso

@@ -4,20 +4,27 @@
 // of cell P on axis j gets, for every k != j, N_f mean(alpha_jk) (d_k q)_f,
 // where (d_k q)_f is the mean of the central differences along k of P and of
 // its neighbour across the face: summed over P's faces this is the central
-// d_j d_k q.  The matrices C and P keep their orthogonal stencils; these terms
-// go to the right-hand sides with the previous iterate (the predictor's, each
-// corrector's input velocity, the previous pressure), and the solves are
-// repeated n_nonortho times.
-//   - velocity: (nu / J_P) times the sum; a missing neighbour in a cell
+// d_j d_k q.
+//   - velocity, (nu / J_P) times the sum: the halves with P's own
+//     differences touch only P's direct neighbours and join the matrix C
+//     (Eq. difNonOrthoMatDiscrete: W_k(P) = sum over P's inner faces on the
+//     axes j != k of N_f mean(alpha_jk) / 2 multiplies (q_{k+} - q_{k-}) / 2);
+//     their boundary-value constants and the tangential fluxes through
+//     Dirichlet faces go to rhs0 once per step; the halves with the
+//     neighbour's differences (P's diagonal neighbours, Eq. velRHSnonOrtho)
+//     go to the right-hand sides with the previous iterate (the predictor's,
+//     each corrector's input velocity).  A missing neighbour in a cell
 //     difference is the ghost 2 u_b - u_Q of the Dirichlet face; on a
 //     Dirichlet face of P the tangential derivative is half the difference of
 //     the boundary values on the same side at P's k-neighbours (P's own value
 //     where a k-neighbour has no face there);
-//   - pressure: the cell-integrated sum with mean(alpha_jk / A); a missing
-//     neighbour in a cell difference is p_Q, and no cross flux crosses a
-//     Dirichlet-velocity face (zero-Neumann pressure, App. A.3).
-// Neighbours of neighbours are located arithmetically (locate), so the terms
-// can be formed for any cell of the domain.
+//   - pressure: the whole cell-integrated sum with mean(alpha_jk / A) goes to
+//     the right-hand side with the previous pressure iterate (its direct part
+//     in P would make P unsymmetric for the CG); a missing neighbour in a cell
+//     difference is p_Q, and no cross flux crosses a Dirichlet-velocity face
+//     (zero-Neumann pressure, App. A.3).
+// The solves are repeated n_nonortho times.  Neighbours of neighbours are
+// located arithmetically (locate), so the terms can be formed for any cell.
 #pragma once
 
 namespace piso {
@@ -39,8 +46,60 @@ __device__ __forceinline__ real cell_diff(const Cell& c, const real* q, const re
   return real(0.5) * (vh - vl);
 }
 
-// (nu / J_P) sum_j sum_{k != j} sum_f N_f mean(alpha_jk) (d_k u)_f for the ND
-// components of u [ND][N] at cell c; bval [ND][nbf].
+// W_k(P) = sum over P's inner faces f on the axes j != k of N_f mean(alpha_jk)
+// / 2: the coefficient of P's own central difference along k in the viscous
+// cross terms (the direct-neighbour part of Eq. difNonOrthoMatDiscrete).
+template <typename real, int ND>
+__device__ __forceinline__ void cross_w(const Cell& c, const real* Gx, int32_t N, real (&W)[ND]) {
+  const int32_t P = c.i;
+#pragma unroll
+  for (int k = 0; k < ND; k++) W[k] = 0;
+#pragma unroll
+  for (int s = 0; s < 2 * ND; s++) {
+    const int j = s >> 1;
+    const int32_t F = c.nb[s];
+    if (F < 0) continue;
+    const real n = (s & 1) ? real(1) : real(-1);
+#pragma unroll
+    for (int k = 0; k < ND; k++)
+      if (k != j) W[k] += n * real(0.25) * (cross_metric(Gx, N, j, k, P) + cross_metric(Gx, N, j, k, F));
+  }
+}
+
+// Tangential cross flux through a Dirichlet face on side s (axis j) of cell c
+// for every component: sum_{k != j} N_f alpha_jk,P (bq[fh] - bq[fl]) / 2, fh / fl
+// the faces on side s of P's k-neighbours (P's own face where there is none).
+template <typename real, int ND>
+__device__ __forceinline__ void cross_bface(const DomStatic& D, const Cell& c, int s, const real* bval, int32_t nbf,
+                                            const real* Gx, real (&acc)[ND]) {
+  const int32_t N = D.N, P = c.i;
+  const int j = s >> 1;
+  const real n = (s & 1) ? real(1) : real(-1);
+  const int32_t fP = -1 - c.nb[s];
+  for (int k = 0; k < ND; k++) {
+    if (k == j) continue;
+    const real a = cross_metric(Gx, N, j, k, P);
+    int32_t fh = fP, fl = fP;
+    if (c.nb[2 * k + 1] >= 0) {
+      const int32_t t = locate<ND>(D, c.nb[2 * k + 1]).nb[s];
+      if (t < 0) fh = -1 - t;
+    }
+    if (c.nb[2 * k] >= 0) {
+      const int32_t t = locate<ND>(D, c.nb[2 * k]).nb[s];
+      if (t < 0) fl = -1 - t;
+    }
+#pragma unroll
+    for (int q = 0; q < ND; q++) {
+      const real* bq = bval + (size_t)q * nbf;
+      acc[q] += n * a * (real(0.5) * (bq[fh] - bq[fl]));
+    }
+  }
+}
+
+// The deferred viscous cross terms at cell c (Eq. velRHSnonOrtho): (nu / J_P)
+// sum over P's inner faces f on axis j, k != j, of N_f mean(alpha_jk) times
+// half the neighbour's central difference along k, for the ND components of
+// u [ND][N]; bval [ND][nbf] gives the ghosts of the neighbour's differences.
 template <typename real, int ND>
 __device__ __forceinline__ void cross_visc(const DomStatic& D, const Cell& c, const real* u, const real* bval,
                                           int32_t nbf, const real* Gx, const real* J, real nu,
@@ -53,39 +112,16 @@ __device__ __forceinline__ void cross_visc(const DomStatic& D, const Cell& c, co
     const int j = s >> 1;
     const real n = (s & 1) ? real(1) : real(-1);
     const int32_t F = c.nb[s];
-    if (F >= 0) {
-      const Cell cF = locate<ND>(D, F);
-      for (int k = 0; k < ND; k++) {
-        if (k == j) continue;
-        const real a = real(0.5) * (cross_metric(Gx, N, j, k, P) + cross_metric(Gx, N, j, k, F));
+    if (F < 0) continue;
+    const Cell cF = locate<ND>(D, F);
+    for (int k = 0; k < ND; k++) {
+      if (k == j) continue;
+      const real a = real(0.5) * (cross_metric(Gx, N, j, k, P) + cross_metric(Gx, N, j, k, F));
 #pragma unroll
-        for (int q = 0; q < ND; q++) {
-          const real* uq = u + (size_t)q * N;
-          const real* bq = bval + (size_t)q * nbf;
-          const real g = real(0.5) * (cell_diff<real, ND>(c, uq, bq, k) + cell_diff<real, ND>(cF, uq, bq, k));
-          acc[q] += n * a * g;
-        }
-      }
-    } else {
-      const int32_t fP = -1 - F;
-      for (int k = 0; k < ND; k++) {
-        if (k == j) continue;
-        const real a = cross_metric(Gx, N, j, k, P);
-        // faces on side s of P's k-neighbours (P's own where there is none)
-        int32_t fh = fP, fl = fP;
-        if (c.nb[2 * k + 1] >= 0) {
-          const int32_t t = locate<ND>(D, c.nb[2 * k + 1]).nb[s];
-          if (t < 0) fh = -1 - t;
-        }
-        if (c.nb[2 * k] >= 0) {
-          const int32_t t = locate<ND>(D, c.nb[2 * k]).nb[s];
-          if (t < 0) fl = -1 - t;
-        }
-#pragma unroll
-        for (int q = 0; q < ND; q++) {
-          const real* bq = bval + (size_t)q * nbf;
-          acc[q] += n * a * (real(0.5) * (bq[fh] - bq[fl]));
-        }
+      for (int q = 0; q < ND; q++) {
+        const real* uq = u + (size_t)q * N;
+        const real* bq = bval + (size_t)q * nbf;
+        acc[q] += n * a * (real(0.5) * cell_diff<real, ND>(cF, uq, bq, k));
       }
     }
   }
@@ -114,6 +150,187 @@ __device__ __forceinline__ real cross_pres(const DomStatic& D, const Cell& c, co
     }
   }
   return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Transposes of the deferred cross terms for the adjoint step, in gather form
+// (each cell collects what its neighbours' terms send it, so no atomics and a
+// fixed summation order).  The neighbour R across side s of Q sees Q across
+// its opposite side, so the face sign from R is -N_s and the face mean is the
+// same.  Two phases with a group barrier between them: phase 1 forms, per
+// cell, the sensitivity gdk[k] of the cross terms to the cell's own central
+// difference along k; phase 2 spreads gdk back to the cells (and boundary
+// faces) those differences read.
+// ---------------------------------------------------------------------------
+
+// Pressure, phase 1 at cell c for dL/dY = sc g (Y the pressure cross terms at
+// pressure p, A = 1/invA): gdk[k][Q] = sum over Q's inner faces on axes j != k
+// of N_s mean(alpha_jk / A) (g_Q - g_F) / 2; returns dL/dA_Q = -sum N_s
+// alpha_jk,Q / (2 A_Q^2) (d_k p)_f (g_Q - g_F).
+template <typename real, int ND>
+__device__ __forceinline__ real cross_pres_T1(const DomStatic& D, const Cell& c, const real* g, real sc, const real* p,
+                                              const real* invA, const real* Gx, real* gdk) {
+  const int32_t N = D.N, Q = c.i;
+  real acc[ND];
+#pragma unroll
+  for (int k = 0; k < ND; k++) acc[k] = 0;
+  real ga = 0;
+  const real iaQ = invA[Q];
+  for (int s = 0; s < 2 * ND; s++) {
+    const int j = s >> 1;
+    const int32_t F = c.nb[s];
+    if (F < 0) continue;
+    const real n = (s & 1) ? real(1) : real(-1);
+    const Cell cF = locate<ND>(D, F);
+    const real dg = real(0.5) * n * sc * (g[Q] - g[F]);
+    for (int k = 0; k < ND; k++) {
+      if (k == j) continue;
+      const real GQ = cross_metric(Gx, N, j, k, Q);
+      const real a = real(0.5) * (GQ * iaQ + cross_metric(Gx, N, j, k, F) * invA[F]);
+      acc[k] += a * dg;
+      const real gk = real(0.5) * (cell_diff<real, ND>(c, p, nullptr, k) + cell_diff<real, ND>(cF, p, nullptr, k));
+      ga -= GQ * iaQ * iaQ * gk * dg;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < ND; k++) gdk[(size_t)k * N + Q] = acc[k];
+  return ga;
+}
+
+// Phase 2 of both transposes: the transpose of the central differences,
+// sum_k (gdk[k] at the -k neighbour - gdk[k] at the +k neighbour) / 2; a
+// missing neighbour was the ghost of cell Q itself: for the pressure (p_Q) its
+// own gdk[k] / 2 with the sign of that side; for the velocity (2 u_b - u_Q)
+// minus that, and the face value receives gdk[k] with the sign of the side
+// (gbk: the component's boundary-value gradient [nbf], or null).
+template <typename real, int ND, bool VEL>
+__device__ __forceinline__ real cross_diff_T2(const Cell& c, const real* gdk, int32_t N, real* gbk) {
+  const int32_t Q = c.i;
+  real v = 0;
+#pragma unroll
+  for (int k = 0; k < ND; k++) {
+    const real* gk = gdk + (size_t)k * N;
+    const int32_t hi = c.nb[2 * k + 1], lo = c.nb[2 * k];
+    if (lo >= 0) v += real(0.5) * gk[lo];
+    if (hi >= 0) v -= real(0.5) * gk[hi];
+    if (hi < 0) {
+      v += (VEL ? real(-0.5) : real(0.5)) * gk[Q];
+      if (VEL && gbk) gbk[-1 - hi] += gk[Q];
+    }
+    if (lo < 0) {
+      v -= (VEL ? real(-0.5) : real(0.5)) * gk[Q];
+      if (VEL && gbk) gbk[-1 - lo] -= gk[Q];
+    }
+  }
+  return v;
+}
+
+// Velocity (the deferred halves, Eq. velRHSnonOrtho), phase 1 at cell c for
+// g = dL/dX [ND][N] (X at viscosity nu): for every component q,
+// gdk[q][k][Q] = sum over Q's inner faces (axis j, neighbour R) with k != j of
+// -N_s mean(alpha_jk) (nu / J_R) g_q,R / 2.
+template <typename real, int ND>
+__device__ __forceinline__ void cross_visc_T1(const Cell& c, const real* g, const real* Gx, const real* J, real nu,
+                                              int32_t N, real* gdk) {
+  const int32_t Q = c.i;
+  real acc[ND][ND];
+#pragma unroll
+  for (int q = 0; q < ND; q++)
+#pragma unroll
+    for (int k = 0; k < ND; k++) acc[q][k] = 0;
+#pragma unroll
+  for (int s = 0; s < 2 * ND; s++) {
+    const int j = s >> 1;
+    const int32_t R = c.nb[s];
+    if (R < 0) continue;
+    const real n = (s & 1) ? real(1) : real(-1);
+    const real w = -n * real(0.5) * nu / J[R];
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+      if (k == j) continue;
+      const real a = real(0.5) * (cross_metric(Gx, N, j, k, Q) + cross_metric(Gx, N, j, k, R)) * w;
+#pragma unroll
+      for (int q = 0; q < ND; q++) acc[q][k] += a * g[(size_t)q * N + R];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < ND; q++)
+#pragma unroll
+    for (int k = 0; k < ND; k++) gdk[((size_t)q * ND + k) * N + Q] = acc[q][k];
+}
+
+// Transpose, in the boundary values, of the constant part of the matrix
+// (direct-neighbour) cross terms that rhs0 carries (Eq.
+// difNonOrthoMatDiscrete with Dirichlet ghosts, and the tangential fluxes
+// through Dirichlet faces) for g = dL/drhs0 [ND][N]: adds to the gradient of
+// every Dirichlet face of cell c (gbval [ND][nbf]) what the rows of c and of
+// its neighbours along that side send it.  W: cross_w of c.
+template <typename real, int ND>
+__device__ __forceinline__ void cross_const_T(const DomStatic& D, const Cell& c, const real (&W)[ND], const real* g,
+                                              const real* Gx, const real* J, real nu, int32_t nbf, real* gbval) {
+  const int32_t N = D.N, Q = c.i;
+  const real fQ = nu / J[Q];
+#pragma unroll
+  for (int s = 0; s < 2 * ND; s++) {
+    if (c.nb[s] >= 0) continue;
+    const int j = s >> 1;
+    const real n = (s & 1) ? real(1) : real(-1);
+    const int32_t f = -1 - c.nb[s];
+    real acc[ND];
+#pragma unroll
+    for (int q = 0; q < ND; q++) acc[q] = n * W[j] * fQ * g[(size_t)q * N + Q];   // Q's own ghost on this face
+    for (int k = 0; k < ND; k++) {
+      if (k == j) continue;
+      const real hQ = real(0.5) * n * fQ * cross_metric(Gx, N, j, k, Q);
+      const int32_t hi = c.nb[2 * k + 1], lo = c.nb[2 * k];
+      bool hi_face = false, lo_face = false;
+      if (hi >= 0) {
+        hi_face = locate<ND>(D, hi).nb[s] < 0;
+        if (hi_face) {   // Q is the -k neighbour of hi: hi's difference reads this face with -1/2
+          const real hR = real(0.5) * n * (nu / J[hi]) * cross_metric(Gx, N, j, k, hi);
+#pragma unroll
+          for (int q = 0; q < ND; q++) acc[q] -= hR * g[(size_t)q * N + hi];
+        }
+      }
+      if (lo >= 0) {
+        lo_face = locate<ND>(D, lo).nb[s] < 0;
+        if (lo_face) {   // Q is the +k neighbour of lo: +1/2
+          const real hR = real(0.5) * n * (nu / J[lo]) * cross_metric(Gx, N, j, k, lo);
+#pragma unroll
+          for (int q = 0; q < ND; q++) acc[q] += hR * g[(size_t)q * N + lo];
+        }
+      }
+      // Q's own tangential difference uses its own face where a k-neighbour has none
+#pragma unroll
+      for (int q = 0; q < ND; q++) acc[q] += hQ * g[(size_t)q * N + Q] * (real(hi_face ? 0 : 1) - real(lo_face ? 0 : 1));
+    }
+#pragma unroll
+    for (int q = 0; q < ND; q++) gbval[(size_t)q * nbf + f] += acc[q];
+  }
+}
+
+// Per-unit-viscosity constant part of the matrix cross terms of rhs0 at cell
+// c for every component: (1 / J_P) (sum over Dirichlet sides of N_s W_k u_b +
+// the tangential fluxes through P's Dirichlet faces).
+template <typename real, int ND>
+__device__ __forceinline__ void cross_const(const DomStatic& D, const Cell& c, const real (&W)[ND], const real* bval,
+                                            int32_t nbf, const real* Gx, const real* J, real (&out)[ND]) {
+  real acc[ND];
+#pragma unroll
+  for (int q = 0; q < ND; q++) acc[q] = 0;
+#pragma unroll
+  for (int s = 0; s < 2 * ND; s++) {
+    if (c.nb[s] >= 0) continue;
+    const int j = s >> 1;
+    const real n = (s & 1) ? real(1) : real(-1);
+    const int32_t f = -1 - c.nb[s];
+#pragma unroll
+    for (int q = 0; q < ND; q++) acc[q] += n * W[j] * bval[(size_t)q * nbf + f];
+    cross_bface<real, ND>(D, c, s, bval, nbf, Gx, acc);
+  }
+  const real f1 = real(1) / J[c.i];
+#pragma unroll
+  for (int q = 0; q < ND; q++) out[q] = f1 * acc[q];
 }
 
 }  // namespace piso
