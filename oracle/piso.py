@@ -106,8 +106,21 @@ class Options:
 class Mesh:
     """Multi-block structured mesh (Sec. 2.2; App. A.5 Domain/Block/Boundary).
 
-    blocks: sequence of (res, vertices); connections: (blk_a, side_a, blk_b, side_b);
-    dirichlet: (blk, side, values (nfaces, ndim)); outflow: (blk, side, u_m, values).
+    blocks: sequence of (res, vertices); connections: (blk_a, side_a, blk_b, side_b)
+    or (blk_a, side_a, blk_b, side_b, axis_perm, flip_mask); dirichlet: (blk, side,
+    values (nfaces, ndim)); outflow: (blk, side, u_m, values).
+
+    A connection joins side_a of block a to side_b of block b, cell to cell
+    (Sec. 2.2: conformal, matching resolution; App. A.3: it only changes the
+    neighbour lookup): the i-th tangential axis of side_a (ascending axis
+    order) runs along tangential axis (i if axis_perm == 0 else 1 - i) of
+    side_b, reversed when bit i of flip_mask is set; any two sides may be
+    joined, a side to itself as a fold.  The neighbour across a side then has
+    its own frame: nbax[s, P, a] is the neighbour's axis for P's axis a and
+    nbsg[s, P, a] = +1 / -1 its orientation (the normal's orientation follows
+    from the two sides), nbret[s, P] the neighbour's side that faces P.  Every
+    per-axis quantity of a neighbour (contravariant fluxes, alpha_jj, the cross
+    metrics, its central differences) is read through that frame.
     """
 
     def __init__(self, ndim: int, blocks: Sequence, connections: Sequence = (),
@@ -139,21 +152,31 @@ class Mesh:
 
         # --- neighbours and boundary faces
         self.nb = -np.ones((self.nsides, N), dtype=np.int64)
+        self.nbax = np.broadcast_to(np.arange(3), (self.nsides, N, 3)).copy()
+        self.nbsg = np.ones((self.nsides, N, 3))
+        self.nbret = np.repeat(np.array([s ^ 1 for s in range(self.nsides)])[:, None], N, axis=1)
         self.bval = np.zeros((self.nsides, d, N))
         self.is_bface = np.zeros((self.nsides, N), dtype=bool)
         self.is_outflow = np.zeros((self.nsides, N), dtype=bool)
         self.u_m = np.zeros((self.nsides, d, N))
         assigned = {}
-        for (a, sa, b, sb) in connections:
-            if sb // 2 != sa // 2 or sb % 2 == sa % 2:
-                raise ValueError("connections must join opposite sides of the same axis")
-            for key in ((a, sa), (b, sb)):
+        for conn in connections:
+            a, sa, b, sb = conn[:4]
+            perm, flip = (int(conn[4]), int(conn[5])) if len(conn) > 4 else (0, 0)
+            for key in {(a, sa), (b, sb)}:
                 if key in assigned:
                     raise ValueError(f"side {key} has two boundaries")
                 assigned[key] = "conn"
-            self._connect(a, sa, b, sb)
+            self._connect(a, sa, b, sb, perm, flip)
             if (a, sa) != (b, sb):
-                self._connect(b, sb, a, sa)
+                # the inverse map: the swap is its own inverse, the flip bits follow the axes
+                iflip = (((flip & 1) << 1) | ((flip >> 1) & 1)) if perm else flip
+                self._connect(b, sb, a, sa, perm, iflip)
+            else:
+                ca = self.side_cells(a, sa)
+                cb = self.nb[sa, ca]
+                if np.any(cb == ca) or np.any(self.nb[sa, cb] != ca):
+                    raise ValueError("a side joined to itself must pair distinct cells")
         for (blk, s, vals) in dirichlet:
             if (blk, s) in assigned:
                 raise ValueError(f"side {(blk, s)} has two boundaries")
@@ -180,6 +203,7 @@ class Mesh:
         self.safe_nb = np.where(self.nb >= 0, self.nb, np.arange(N)[None, :])
         self.inner = self.nb >= 0
         self.has_outflow = bool(self.is_outflow.any())
+        self.twisted = bool(np.any(self.nbax != np.arange(3)) or np.any(self.nbsg != 1.0))
 
     # -- boundary helpers ------------------------------------------------------
     def side_cells(self, blk: int, s: int) -> np.ndarray:
@@ -199,11 +223,46 @@ class Mesh:
             order = np.argsort(keys[0], kind="stable")
         return o + cells[order]
 
-    def _connect(self, a, sa, b, sb):
-        ca, cb = self.side_cells(a, sa), self.side_cells(b, sb)
-        if len(ca) != len(cb):
-            raise ValueError("connected sides must have matching resolution")
-        self.nb[sa, ca] = cb
+    def _connect(self, a, sa, b, sb, perm=0, flip=0):
+        d = self.ndim
+        ra, rb = self.res[a], self.res[b]
+        ja, jb = sa // 2, sb // 2
+        ta = [x for x in range(3) if x != ja][: d - 1]
+        tb = [x for x in range(3) if x != jb][: d - 1]
+        pt = [1, 0] if perm else [0, 1]
+        if (d == 2 and perm) or perm not in (0, 1) or flip >> (d - 1):
+            raise ValueError("axis_perm / flip_mask out of range")
+        for i in range(d - 1):
+            if ra[ta[i]] != rb[tb[pt[i]]]:
+                raise ValueError("connected sides must have matching resolution")
+        ca = self.side_cells(a, sa)
+        _, coords = _block_index(ra)
+        la = ca - self.offsets[a]
+        cc = [np.zeros(len(ca), dtype=np.int64) for _ in range(3)]
+        cc[jb][:] = rb[jb] - 1 if sb % 2 else 0
+        for i in range(d - 1):
+            v = coords[ta[i]][la]
+            if (flip >> i) & 1:
+                v = ra[ta[i]] - 1 - v
+            cc[tb[pt[i]]] = v
+        self.nb[sa, ca] = self.offsets[b] + cc[0] + rb[0] * (cc[1] + rb[1] * cc[2])
+        ax = list(range(3))
+        sg = [1.0, 1.0, 1.0]
+        ax[ja] = jb
+        sg[ja] = -sign(sa) * sign(sb)       # P's outward normal is the neighbour's inward one
+        for i in range(d - 1):
+            ax[ta[i]] = tb[pt[i]]
+            sg[ta[i]] = -1.0 if (flip >> i) & 1 else 1.0
+        self.nbax[sa, ca] = ax
+        self.nbsg[sa, ca] = sg
+        self.nbret[sa, ca] = sb
+
+    def frame(self, s: int, P: np.ndarray, a):
+        """(the neighbour's axis, its orientation) for P's axis a (an int or an
+        array over P) across side s of the cells P."""
+        if np.isscalar(a):
+            return self.nbax[s, P, a], self.nbsg[s, P, a]
+        return self.nbax[s, P, a], self.nbsg[s, P, a]
 
     def _set_faces(self, blk, s, vals, um):
         cells = self.side_cells(blk, s)
@@ -296,8 +355,9 @@ def assemble_C(mesh: Mesh, u, nu, dt, S, bval):
         j, n = s // 2, sign(s)
         P = np.nonzero(mesh.inner[s])[0]
         F = mesh.nb[s, P]
-        Uf = 0.5 * (U[j, P] + U[j, F])
-        Df = nu * 0.5 * (mesh.alpha[j, P] + mesh.alpha[j, F])
+        jF, eF = mesh.frame(s, P, j)               # the neighbour's flux in P's frame
+        Uf = 0.5 * (U[j, P] + eF * U[jF, F])
+        Df = nu * 0.5 * (mesh.alpha[j, P] + mesh.alpha[jF, F])
         off[s, P] = (0.5 * n * Uf - Df) / mesh.J[P]
         diag[P] += (0.5 * n * Uf + Df) / mesh.J[P]
         B = np.nonzero(mesh.is_bface[s])[0]
@@ -318,11 +378,12 @@ def matvec(mesh: Mesh, M: Matrix, x: np.ndarray) -> np.ndarray:
 
 def matvec_T(mesh: Mesh, M: Matrix, y: np.ndarray) -> np.ndarray:
     """x = M^T y, gathered: the entry of row F = nb(P,s) that points back at P
-    is F's coefficient on the opposite side."""
+    is F's coefficient on its side facing P (the opposite side within a
+    block)."""
     x = M.diag * y
     for s in range(mesh.nsides):
         F = mesh.safe_nb[s]
-        coef = np.where(mesh.inner[s], M.off[opp(s)][F], 0.0)
+        coef = np.where(mesh.inner[s], M.off[mesh.nbret[s], F], 0.0)
         x = x + coef * y[..., F]
     return x
 
@@ -374,7 +435,8 @@ def assemble_P(mesh: Mesh, A: np.ndarray) -> Matrix:
     for s in range(mesh.nsides):
         j = s // 2
         P = np.nonzero(mesh.inner[s])[0]
-        off[s, P] = 0.5 * (w[j, P] + w[j, mesh.nb[s, P]])
+        jF, _ = mesh.frame(s, P, j)
+        off[s, P] = 0.5 * (w[j, P] + w[jF, mesh.nb[s, P]])
     return Matrix(-off.sum(axis=0), off)
 
 
@@ -391,7 +453,8 @@ def divergence(mesh: Mesh, h: np.ndarray, bval) -> np.ndarray:
     for s in range(mesh.nsides):
         j, n = s // 2, sign(s)
         P = np.nonzero(mesh.inner[s])[0]
-        b[P] += n * 0.5 * (F[j, P] + F[j, mesh.nb[s, P]])
+        jF, eF = mesh.frame(s, P, j)
+        b[P] += n * 0.5 * (F[j, P] + eF * F[jF, mesh.nb[s, P]])
         B = np.nonzero(mesh.is_bface[s])[0]
         b[B] += n * mesh.face_flux_b(s, bval[s])[B]
     return b
@@ -400,7 +463,9 @@ def divergence(mesh: Mesh, h: np.ndarray, bval) -> np.ndarray:
 def divergence_T(mesh: Mesh, gb: np.ndarray) -> np.ndarray:
     """Transpose of the inner-face part of ``divergence``:
     h_bar_P = sum_f 0.5 N_f J_P T_j,P (b_bar_P - b_bar_F)  (the neighbour's row
-    sees the same face with the opposite sign)."""
+    sees the same face with the opposite sign: across a permuted or flipped
+    connection both its face sign and its flux's orientation change, and the
+    two signs cancel)."""
     d = mesh.ndim
     gF = np.zeros((d, mesh.N))
     for s in range(mesh.nsides):
@@ -429,16 +494,39 @@ def _cell_diff(mesh: Mesh, q: np.ndarray, k: int, ghost) -> np.ndarray:
     return 0.5 * (hi - lo)
 
 
+def _nb_metric(mesh: Mesh, coef: np.ndarray, s: int, P, F, j: int, k: int):
+    """coef_jk of the neighbours F = nb(P, s) in P's frame (coef (N, d, d))."""
+    jF, ej = mesh.frame(s, P, j)
+    kF, ek = mesh.frame(s, P, k)
+    return ej * ek * coef[F, jF, kF]
+
+
+def _nb_diff(mesh: Mesh, dq, s: int, P, F, k: int):
+    """The central difference along P's axis k of the neighbours F = nb(P, s),
+    from their own differences (dq (d, N), each cell's own axes)."""
+    kF, ek = mesh.frame(s, P, k)
+    return ek * dq[kF, F]
+
+
+def _nb_side(mesh: Mesh, s_conn: int, P, s: int):
+    """The side of the neighbours across s_conn of the cells P that corresponds
+    to P's side s (its axis and orientation through the frame)."""
+    jF, ej = mesh.frame(s_conn, P, s // 2)
+    return 2 * jF + ((sign(s) * ej) > 0).astype(np.int64)
+
+
 def _cross_flux_sum(mesh: Mesh, coef: np.ndarray, dq, bface_grad, part: str = "all") -> np.ndarray:
     """sum_j sum_{k != j} sum_{faces f of P on axis j} N_f c_jk,f g_k,f for one
     scalar field: c_jk,f the face mean of coef (N, d, d) over P and its
-    neighbour, g_k,f the mean of the two cells' central differences dq[k] (N,).
+    neighbour, g_k,f the mean of the two cells' central differences dq[k] (d, N)
+    along P's axis k (the neighbour's values read through its frame).
     Boundary faces: c_jk of P and g_k = bface_grad(s, k) (N,), or no flux when
     bface_grad is None.  part selects the terms: "all"; "own", the halves with
     P's own differences dq[k][P] (its direct neighbours) and the boundary
     faces; "nbr", the halves with the neighbour's differences dq[k][F] (P's
     diagonal neighbours).  "own" + "nbr" = "all"."""
     d = mesh.ndim
+    dq = np.asarray(dq)
     out = np.zeros(mesh.N)
     for s in range(mesh.nsides):
         j, n = s // 2, sign(s)
@@ -448,13 +536,14 @@ def _cross_flux_sum(mesh: Mesh, coef: np.ndarray, dq, bface_grad, part: str = "a
         for k in range(d):
             if k == j:
                 continue
-            cf = 0.5 * (coef[P, j, k] + coef[F, j, k])
+            cf = 0.5 * (coef[P, j, k] + _nb_metric(mesh, coef, s, P, F, j, k))
+            dF = _nb_diff(mesh, dq, s, P, F, k)
             if part == "all":
-                out[P] += n * cf * 0.5 * (dq[k][P] + dq[k][F])
+                out[P] += n * cf * 0.5 * (dq[k][P] + dF)
             elif part == "own":
                 out[P] += n * cf * 0.5 * dq[k][P]
             else:
-                out[P] += n * cf * 0.5 * dq[k][F]
+                out[P] += n * cf * 0.5 * dF
             if bface_grad is not None and len(B) and part != "nbr":
                 out[B] += n * coef[B, j, k] * bface_grad(s, k)[B]
     return out
@@ -471,17 +560,22 @@ def cross_diffusion(mesh: Mesh, u: np.ndarray, nu: float, bval, part: str = "all
     neighbour has none uses its own value in its place)."""
     d = mesh.ndim
     out = np.zeros((d, mesh.N))
+    bval = np.asarray(bval)
     for c in range(d):
         q = u[c]
         ghost = lambda s, c=c, q=q: 2.0 * bval[s][c] - q
-        dq = [_cell_diff(mesh, q, k, ghost) for k in range(d)]
+        dq = np.array([_cell_diff(mesh, q, k, ghost) for k in range(d)])
 
         def bgrad(s, k, c=c):
             fb = bval[s][c]
-            hi_n, lo_n = mesh.safe_nb[2 * k + 1], mesh.safe_nb[2 * k]
-            hi = np.where(mesh.inner[2 * k + 1] & mesh.is_bface[s][hi_n], fb[hi_n], fb)
-            lo = np.where(mesh.inner[2 * k] & mesh.is_bface[s][lo_n], fb[lo_n], fb)
-            return 0.5 * (hi - lo)
+            allc = np.arange(mesh.N)
+            vals = []
+            for sk in (2 * k + 1, 2 * k):
+                Q = mesh.safe_nb[sk]
+                sq = _nb_side(mesh, sk, allc, s)          # the k-neighbour's side matching s
+                ok = mesh.inner[sk] & mesh.is_bface[sq, Q]
+                vals.append(np.where(ok, bval[sq, c, Q], fb))
+            return 0.5 * (vals[0] - vals[1])
         out[c] = nu * _cross_flux_sum(mesh, mesh.G, dq, bgrad, part) / mesh.J
     return out
 
@@ -504,7 +598,7 @@ def cross_matrix(mesh: Mesh, nu: float) -> Matrix:
         F = mesh.nb[s, P]
         for k in range(d):
             if k != j:
-                W[k][P] += n * 0.5 * (mesh.G[P, j, k] + mesh.G[F, j, k]) * 0.5
+                W[k][P] += n * 0.5 * (mesh.G[P, j, k] + _nb_metric(mesh, mesh.G, s, P, F, j, k)) * 0.5
     diag = np.zeros(N)
     off = np.zeros((mesh.nsides, N))
     for k in range(d):
@@ -524,7 +618,7 @@ def cross_pressure(mesh: Mesh, p: np.ndarray, A: np.ndarray) -> np.ndarray:
     crosses a Dirichlet-velocity face (zero-Neumann pressure, App. A.3)."""
     d = mesh.ndim
     ghost = lambda s: p
-    dq = [_cell_diff(mesh, p, k, ghost) for k in range(d)]
+    dq = np.array([_cell_diff(mesh, p, k, ghost) for k in range(d)])
     return _cross_flux_sum(mesh, mesh.G / A[:, None, None], dq, None)
 
 
@@ -548,10 +642,10 @@ def cross_diffusion_T(mesh: Mesh, g: np.ndarray, nu: float, part: str = "all"):
     dL/dX = g."""
     d, N = mesh.ndim, mesh.N
     gu = np.zeros((d, N))
-    gb = [np.zeros((d, N)) for _ in range(mesh.nsides)]
+    gb = np.zeros((mesh.nsides, d, N))
     for c in range(d):
         w = nu * g[c] / mesh.J
-        gdk = [np.zeros(N) for _ in range(d)]
+        gdk = np.zeros((d, N))                      # per cell, along its own axes
         for s in range(mesh.nsides):
             j, n = s // 2, sign(s)
             P = np.nonzero(mesh.inner[s])[0]
@@ -560,21 +654,22 @@ def cross_diffusion_T(mesh: Mesh, g: np.ndarray, nu: float, part: str = "all"):
             for k in range(d):
                 if k == j:
                     continue
-                t = n * 0.5 * (mesh.G[P, j, k] + mesh.G[F, j, k]) * 0.5 * w[P]
+                t = n * 0.5 * (mesh.G[P, j, k] + _nb_metric(mesh, mesh.G, s, P, F, j, k)) * 0.5 * w[P]
                 if part != "nbr":
                     np.add.at(gdk[k], P, t)
                 if part != "own":
-                    np.add.at(gdk[k], F, t)
+                    kF, ek = mesh.frame(s, P, k)
+                    np.add.at(gdk, (kF, F), ek * t)
                 if len(B) and part != "nbr":
                     tb = n * mesh.G[B, j, k] * w[B] * 0.5
-                    hi_n, lo_n = mesh.safe_nb[2 * k + 1][B], mesh.safe_nb[2 * k][B]
-                    hi_ok = mesh.inner[2 * k + 1][B] & mesh.is_bface[s][hi_n]
-                    lo_ok = mesh.inner[2 * k][B] & mesh.is_bface[s][lo_n]
-                    np.add.at(gb[s][c], np.where(hi_ok, hi_n, B), tb)
-                    np.add.at(gb[s][c], np.where(lo_ok, lo_n, B), -tb)
+                    for sk, sg_ in ((2 * k + 1, 1.0), (2 * k, -1.0)):
+                        Q = mesh.safe_nb[sk][B]
+                        sq = _nb_side(mesh, sk, B, s)
+                        ok = mesh.inner[sk][B] & mesh.is_bface[sq, Q]
+                        np.add.at(gb, (np.where(ok, sq, s), c, np.where(ok, Q, B)), sg_ * tb)
         for k in range(d):
             _cell_diff_T(mesh, gdk[k], k, gu[c], -1.0, lambda s, c=c: gb[s][c])
-    return gu, gb
+    return gu, list(gb)
 
 
 def cross_pressure_T(mesh: Mesh, g: np.ndarray, p: np.ndarray, A: np.ndarray):
@@ -583,8 +678,8 @@ def cross_pressure_T(mesh: Mesh, g: np.ndarray, p: np.ndarray, A: np.ndarray):
     d, N = mesh.ndim, mesh.N
     gp = np.zeros(N)
     gA = np.zeros(N)
-    dq = [_cell_diff(mesh, p, k, lambda s: p) for k in range(d)]
-    gdk = [np.zeros(N) for _ in range(d)]
+    dq = np.array([_cell_diff(mesh, p, k, lambda s: p) for k in range(d)])
+    gdk = np.zeros((d, N))
     for s in range(mesh.nsides):
         j, n = s // 2, sign(s)
         P = np.nonzero(mesh.inner[s])[0]
@@ -592,13 +687,15 @@ def cross_pressure_T(mesh: Mesh, g: np.ndarray, p: np.ndarray, A: np.ndarray):
         for k in range(d):
             if k == j:
                 continue
-            cf = 0.5 * (mesh.G[P, j, k] / A[P] + mesh.G[F, j, k] / A[F])
+            GF = _nb_metric(mesh, mesh.G, s, P, F, j, k)
+            cf = 0.5 * (mesh.G[P, j, k] / A[P] + GF / A[F])
             t = n * cf * 0.5 * g[P]
             np.add.at(gdk[k], P, t)
-            np.add.at(gdk[k], F, t)
-            gk = 0.5 * (dq[k][P] + dq[k][F])
+            kF, ek = mesh.frame(s, P, k)
+            np.add.at(gdk, (kF, F), ek * t)
+            gk = 0.5 * (dq[k][P] + _nb_diff(mesh, dq, s, P, F, k))
             np.add.at(gA, P, -n * 0.5 * mesh.G[P, j, k] / A[P] ** 2 * gk * g[P])
-            np.add.at(gA, F, -n * 0.5 * mesh.G[F, j, k] / A[F] ** 2 * gk * g[P])
+            np.add.at(gA, F, -n * 0.5 * GF / A[F] ** 2 * gk * g[P])
     for k in range(d):
         _cell_diff_T(mesh, gdk[k], k, gp, 1.0)
     return gp, gA
@@ -978,8 +1075,9 @@ def piso_step_adjoint(mesh: Mesh, tape: Dict, du_out, dp_out, opts: Optional[Opt
         # off[s,P] = (0.5 n Uf - nu Df)/J_P,  diag[P] += (0.5 n Uf + nu Df)/J_P
         gUf = 0.5 * n * (gCoff[s, P] + gA[P]) / mesh.J[P]
         np.add.at(gU[j], P, 0.5 * gUf)
-        np.add.at(gU[j], F, 0.5 * gUf)
-        Df = 0.5 * (mesh.alpha[j, P] + mesh.alpha[j, F])
+        jF, eF = mesh.frame(s, P, j)
+        np.add.at(gU, (jF, F), eF * 0.5 * gUf)
+        Df = 0.5 * (mesh.alpha[j, P] + mesh.alpha[jF, F])
         gnu += float(np.sum((gA[P] - gCoff[s, P]) * Df / mesh.J[P]))
         B = np.nonzero(mesh.is_bface[s])[0]
         gnu += float(np.sum(gA[B] * 2.0 * mesh.alpha[j, B] / mesh.J[B]))

@@ -1,7 +1,7 @@
 """Build the CUDA library in-tree for sm_103a (``libpiso.so`` next to this file).
 
 The C ABI and the statistics kernels (piso_capi.cu) and the step kernels
-(piso_kernels_{fwd,adj,adjno}_{f32,f64}.cu) are separate translation units
+(piso_kernels_{fwd,fwdno,adj,adjno}_{f32,f64}.cu) are separate translation units
 compiled in parallel (no relocatable device code: each unit carries its own
 kernels) and linked into one shared library.  Objects are kept in _build/ and
 a unit is recompiled only when it or a file it includes changed."""
@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "libpiso.so")
 SRCS = [os.path.join(HERE, "csrc", f) for f in ("piso_capi.cu", "piso_kernels_fwd_f32.cu", "piso_kernels_fwd_f64.cu",
                                                  "piso_kernels_adj_f32.cu", "piso_kernels_adj_f64.cu",
-                                                 "piso_kernels_adjno_f32.cu", "piso_kernels_adjno_f64.cu")]
+                                                 "piso_kernels_adjno_f32.cu", "piso_kernels_adjno_f64.cu",
+                                                 "piso_kernels_fwdno_f32.cu", "piso_kernels_fwdno_f64.cu")]
 DEPS = [os.path.join(HERE, "csrc", f) for f in sorted(os.listdir(os.path.join(HERE, "csrc")))]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include", "piso.h")
 

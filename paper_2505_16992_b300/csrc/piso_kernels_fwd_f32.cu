@@ -1,10 +1,12 @@
 // Forward step kernels, float storage: every instantiation of fwd_kernel
-// (2D/3D, 512/768 threads, modes plain / ILU(0) / non-orthogonal) compiled
-// in a translation unit of its own, so the library's units build in parallel;
+// (2D/3D, 512/768 threads, modes plain / ILU(0); the non-orthogonal ones are
+// in piso_kernels_fwdno_f32.cu) compiled in a translation unit of its own, so the library's units build in parallel;
 // piso_capi.cu launches them through the addresses returned here.
 #include "piso_forward.cuh"
 
 namespace piso {
+
+const void* fwdno_kernel_addr_f32(int nd, bool wide);   // MODE 2, piso_kernels_fwdno_f32.cu
 
 template <int MODE>
 static const void* fwd_addr_f32(int nd, bool wide) {
@@ -13,7 +15,8 @@ static const void* fwd_addr_f32(int nd, bool wide) {
 }
 
 const void* fwd_kernel_addr_f32(int nd, bool wide, int mode) {
-  return mode == 2 ? fwd_addr_f32<2>(nd, wide) : (mode == 1 ? fwd_addr_f32<1>(nd, wide) : fwd_addr_f32<0>(nd, wide));
+  if (mode == 2) return fwdno_kernel_addr_f32(nd, wide);
+  return mode == 1 ? fwd_addr_f32<1>(nd, wide) : fwd_addr_f32<0>(nd, wide);
 }
 
 }  // namespace piso

@@ -344,3 +344,154 @@ def batch2d(count: int = 64, seed: int = 4, nmin: int = 32, nmax: int = 256,
             c.u0[0] = 4.0 * yc * (1.0 - yc) + 0.05 * rng.standard_normal(c.ncells)
             out.append(c)
     return out
+
+
+# ----------------------------------------------------------------------------
+# blocks joined with permuted / flipped axes (Sec. 2.2, App. A.3)
+# ----------------------------------------------------------------------------
+
+def rotate_block_2d(block: Block, quarter_turns: int):
+    """The same cells with the block's index frame turned by quarter_turns x
+    90 degrees (right-handed frames stay right-handed).  Returns (block,
+    old_index) with old_index[new cell] = the cell's index in the input block,
+    and side_map[old side] = new side."""
+    V = block.vertices
+    nx, ny, _ = block.res
+    old = np.arange(nx * ny).reshape(ny, nx)          # old[y, x]
+    side_map = [0, 1, 2, 3]
+    for _ in range(quarter_turns % 4):
+        # new x = old y, new y = (old nx) - old x
+        V = np.transpose(V, (1, 0, 2))[::-1].copy()
+        old = np.transpose(old, (1, 0))[::-1].copy()
+        # old -x -> new +y, old +x -> new -y, old -y -> new -x, old +y -> new +x
+        side_map = [{0: 3, 1: 2, 2: 0, 3: 1}[s] for s in side_map]
+    nyn, nxn = old.shape
+    return Block((nxn, nyn, 1), V), old.ravel(), side_map
+
+
+def rotate_block_x_3d(block: Block):
+    """The block's index frame turned about x: new y = old z, new z = (old ny) -
+    old y.  Returns (block, old_index, side_map) as rotate_block_2d."""
+    V = block.vertices                                  # V[z, y, x]
+    nx, ny, nz = block.res
+    old = np.arange(nx * ny * nz).reshape(nz, ny, nx)
+    # new[z', y', x] = old[z = y', y = ny - 1 - z', x]
+    Vn = np.transpose(V, (1, 0, 2, 3))[::-1].copy()     # Vn[z', y', x] = V[y', NY - z', x]
+    On = np.transpose(old, (1, 0, 2))[::-1].copy()
+    side_map = [0, 1, 5, 4, 2, 3]                       # old -y -> new +z, +y -> -z, -z -> -y, +z -> +y
+    return Block((nx, nz, ny), Vn), On.ravel(), side_map
+
+
+def _fields_from_positions(blocks, ndim, seed_shift=0.0):
+    """Smooth seeded-free initial velocity, pressure and source as functions of
+    the cell centres (so any block layout of the same cells gets the same
+    values)."""
+    xc = np.concatenate([cell_centres(b) for b in blocks], axis=1)
+    x, y = xc[0], xc[1]
+    z = xc[2] if ndim == 3 else 0.0 * x
+    u = np.stack([np.sin(3 * x + 0.5) * np.cos(2 * y) + 0.2 * np.cos(z),
+                  0.5 * np.cos(2 * x) * np.sin(3 * y + seed_shift)] +
+                 ([0.3 * np.sin(x + 2 * y + z)] if ndim == 3 else []))
+    p = np.cos(x + y) + 0.1 * z
+    S = 0.3 * np.stack([np.cos(x - y), np.sin(2 * x)] + ([np.cos(z + x)] if ndim == 3 else []))
+    return u, p, S
+
+
+def two_block_cavity2d(nx: int = 8, ny: int = 6, rot: int = 0, shear: float = 0.0, gamma: float = 1.5,
+                       nu: float = 0.02, dt: float = 0.02):
+    """Lid-driven cavity [0, 2] x [0, 1] of two blocks joined at x = 1 (tanh
+    refinement in y, optional slant x += shear y): block 1's index frame is
+    turned by rot quarter turns, so the joint is an ordinary side-to-side
+    connection (rot 0) or one with a flip / an axis exchange.  The lid
+    (top) moves with u = sin^2(pi x / 2); the other sides are walls.  Returns
+    (case, cell_index) with cell_index[cell of this layout] = the cell's index
+    in the rot = 0 layout."""
+    yv = tanh_vertices(ny, 0.0, 1.0, gamma)
+    A = rect_block(uniform_vertices(nx, 0.0, 1.0), yv)
+    B0 = rect_block(uniform_vertices(nx, 1.0, 2.0), yv)
+    for b in (A, B0):
+        b.vertices[..., 0] += shear * b.vertices[..., 1]
+    B, old, side_map = rotate_block_2d(B0, rot)
+    blocks = [A, B]
+    inv_map = {v: k for k, v in enumerate(side_map)}
+    # the joint: A's +x side to B's (old -x) side; its tangential axis is old y
+    sb = side_map[0]
+    flip = 1 if rot % 4 in (2, 3) else 0
+    conns = [(0, 1, 1, sb, 0, flip)] if (rot % 4) else [(0, 1, 1, 0)]
+
+    def bc(block, side, top):
+        fc = side_face_centres(block, side)
+        v = np.zeros((len(fc), 2))
+        if top:
+            v[:, 0] = np.sin(0.5 * math.pi * (fc[:, 0] - shear * fc[:, 1])) ** 2
+        return v
+    dirichlet = [(0, s, bc(A, s, s == SIDE_YP)) for s in (SIDE_XM, SIDE_YM, SIDE_YP)]
+    for old_side in (SIDE_XP, SIDE_YM, SIDE_YP):
+        s = side_map[old_side]
+        dirichlet.append((1, s, bc(B, s, old_side == SIDE_YP)))
+    u0, p0, S = _fields_from_positions(blocks, 2)
+    cell_index = np.concatenate([np.arange(A.ncells), A.ncells + old])
+    del inv_map
+    return Case("two_block_cavity2d", 2, blocks, conns, dirichlet, [], u0, p0, S, nu, dt, 10), cell_index
+
+
+def two_block_channel3d(nx: int = 5, ny: int = 6, nz: int = 4, turned: bool = False, shear: float = 0.0,
+                        gamma: float = 1.5, nu: float = 0.02, dt: float = 0.02):
+    """3D box [0, 2] x [0, 1] x [0, 1] of two blocks joined at x = 1, periodic
+    in z (each block to itself), walls at y = 0 and y = 1 (the top one
+    sliding with u = 1), an inflow profile at x = 0 and the matching outflow
+    at x = 2; block 1 optionally turned about x (its y and z axes exchanged
+    and one reversed), so the joint needs axis_perm = 1 with a flip.
+    Returns (case, cell_index) as two_block_cavity2d."""
+    yv = tanh_vertices(ny, 0.0, 1.0, gamma)
+    zv = uniform_vertices(nz, 0.0, 1.0)
+    A = rect_block(uniform_vertices(nx, 0.0, 1.0), yv, zv)
+    B0 = rect_block(uniform_vertices(nx, 1.0, 2.0), yv, zv)
+    for b in (A, B0):
+        b.vertices[..., 0] += shear * b.vertices[..., 1]
+    if turned:
+        B, old, side_map = rotate_block_x_3d(B0)
+        conns = [(0, SIDE_XP, 1, SIDE_XM, 1, 1)]
+    else:
+        B, old, side_map = B0, np.arange(B0.ncells), list(range(6))
+        conns = [(0, SIDE_XP, 1, SIDE_XM)]
+    conns += [(0, SIDE_ZP, 0, SIDE_ZM), (1, side_map[SIDE_ZP], 1, side_map[SIDE_ZM])]
+
+    def prof(block, side, kind):
+        fc = side_face_centres(block, side)
+        v = np.zeros((len(fc), 3))
+        if kind == "lid":
+            v[:, 0] = 1.0
+        elif kind == "in":
+            v[:, 0] = 4.0 * fc[:, 1] * (1.0 - fc[:, 1])
+        return v
+    dirichlet = [(0, SIDE_XM, prof(A, SIDE_XM, "in")), (0, SIDE_YM, prof(A, SIDE_YM, "wall")),
+                 (0, SIDE_YP, prof(A, SIDE_YP, "lid"))]
+    for old_side, kind in ((SIDE_XP, "in"), (SIDE_YM, "wall"), (SIDE_YP, "lid")):
+        s = side_map[old_side]
+        dirichlet.append((1, s, prof(B, s, kind)))
+    u0, p0, S = _fields_from_positions([A, B], 3)
+    cell_index = np.concatenate([np.arange(A.ncells), A.ncells + old])
+    return Case("two_block_channel3d", 3, [A, B], conns, dirichlet, [], u0, p0, S, nu, dt, 10), cell_index
+
+
+def slit_cgrid2d(n_xi: int = 16, n_eta: int = 8, a: float = 1.4, b: float = 1.2, nu: float = 0.05,
+                 dt: float = 0.02, u_inf=(1.0, 0.0), skew: float = 0.25):
+    """A C-grid around a slit (App. B: O-/C-grids around obstacles): the block
+    (xi, eta) in [-a, a] x [0, b] mapped by x + i y = (xi + i eta)^2, plus
+    skew * xi * eta in x (which makes the cells non-orthogonal and keeps
+    J = 4 (xi^2 + eta^2) > 0), so its eta = 0 side folds onto itself along the
+    positive x-axis (the cut): cell xi meets cell -xi, which is a connection
+    of that side to itself with its tangential axis reversed.  The other sides
+    carry the free stream u_inf; smooth initial field.  n_xi must be even (no
+    cell meets itself)."""
+    xi = np.linspace(-a, a, n_xi + 1)
+    eta = np.linspace(0.0, b, n_eta + 1)
+    E, X = np.meshgrid(eta, xi, indexing="ij")
+    V = np.stack([X ** 2 - E ** 2 + skew * X * E, 2.0 * X * E], axis=-1)
+    blk = Block((n_xi, n_eta, 1), V)
+    conns = [(0, SIDE_YM, 0, SIDE_YM, 0, 1)]
+    ui = np.asarray(u_inf, dtype=np.float64)
+    dirichlet = [(0, s, np.tile(ui, (side_nfaces(blk.res, s, 2), 1))) for s in (SIDE_XM, SIDE_XP, SIDE_YP)]
+    u0, p0, S = _fields_from_positions([blk], 2)
+    return Case("slit_cgrid2d", 2, [blk], conns, dirichlet, [], u0 * 0.3 + ui[:, None], p0, None, nu, dt, 10)
