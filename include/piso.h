@@ -184,12 +184,22 @@ piso_status piso_domain_create(int32_t ndim, int32_t prec, piso_domain** out);
 piso_status piso_block_add(piso_domain* d, const int32_t res[3], const double* vertices,
                            int32_t* block_id);
 
-/* Join side sa of block a to side sb of block b (Sec. 2.2: a conformal
- * connection with matching resolution; App. A.3: it only changes the
- * neighbour lookup).  sb must be the opposite side of the same axis and the
- * tangential cell orderings must agree; a == b with opposite sides gives a
- * periodic direction. */
-piso_status piso_connect(piso_domain* d, int32_t a, int32_t sa, int32_t b, int32_t sb);
+/* Join side sa of block a to side sb of block b, cell to cell (Sec. 2.2: a
+ * conformal connection with matching resolution; App. A.3: it only changes the
+ * neighbour lookup; App. B: the cuts of O- and C-grids).  Any two sides may be
+ * joined.  The tangential axes of a side are its other axes in ascending order
+ * (2D: one; 3D: two); the i-th tangential axis of sa runs along tangential axis
+ * (axis_perm ? 1 - i : i) of sb (axis_perm is 0 in 2D), reversed when bit i of
+ * flip_mask is set.  a == b with opposite sides and (0, 0) gives a periodic
+ * direction; a side joined to itself (a == b, sa == sb) is a fold, e.g. the cut
+ * of a C-grid, and needs a reversed axis of even length (no cell may meet
+ * itself).  The neighbour across a joint that exchanges or reverses axes keeps
+ * its own frame: its fluxes, metrics and differences are read through it, such
+ * domains run the extended kernel instantiation and the pressure CG uses the
+ * Jacobi preconditioner.  PISO_EINVAL for mismatched resolutions or out-of-
+ * range axis_perm / flip_mask. */
+piso_status piso_connect(piso_domain* d, int32_t a, int32_t sa, int32_t b, int32_t sb, int32_t axis_perm,
+                         int32_t flip_mask);
 
 /* Dirichlet velocity on a block side (App. A.3: values live on the face;
  * pressure is implicitly zero-Neumann there).  values: HOST, [face][ndim]. */

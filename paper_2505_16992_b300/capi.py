@@ -52,7 +52,7 @@ _SIGS = {
     "piso_default_options": (None, [C.POINTER(Options)]),
     "piso_domain_create": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(_P)]),
     "piso_block_add": (C.c_int, [_P, C.POINTER(C.c_int32), _D, C.POINTER(C.c_int32)]),
-    "piso_connect": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "piso_connect": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "piso_set_dirichlet": (C.c_int, [_P, C.c_int32, C.c_int32, _D]),
     "piso_set_advective_outflow": (C.c_int, [_P, C.c_int32, C.c_int32, _D, _D]),
     "piso_finalize": (C.c_int, [_P, C.POINTER(Options)]),

@@ -115,7 +115,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   const bool lines = A.p_line && o.line_cap > 0;
   LinePre<real> LP{};
   if (lines) LP = line_setup<real, ND>(D, g, o, A.lfa, A.lfm, A.lfc);
-  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap), lines ? &LP : nullptr};
+  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap), lines ? &LP : nullptr, D.nbfr};
   const real* J = reinterpret_cast<const real*>(D.J);
   const real* T = reinterpret_cast<const real*>(D.T);
   const real* AL = reinterpret_cast<const real*>(D.alpha);
@@ -138,6 +138,26 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
   // for a missing neighbour.  W_j(Q) = T_Q,j . g_Q is precomputed.
   auto gradT = [&](const Cell& c, const real* Wv) -> real {
     real acc = 0;
+    if constexpr (MODE == 2) {
+      if (D.nbfr) {
+        // a neighbour R reads this cell in its own gradient along R's axis of
+        // its side facing this cell, with +1/2 (this cell its + neighbour) or
+        // -1/2; a missing neighbour stands for this cell itself
+#pragma unroll
+        for (int s = 0; s < 2 * ND; s++) {
+          const int32_t R = c.nb[s];
+          if (R >= 0) {
+            const int rs = fr_ret(D.nbfr[(size_t)s * N + c.i], s);
+            const real w = Wv[(size_t)(rs >> 1) * N + R];
+            acc += (rs & 1) ? real(0.5) * w : real(-0.5) * w;
+          } else {
+            const real w = Wv[(size_t)(s >> 1) * N + c.i];
+            acc += (s & 1) ? real(0.5) * w : real(-0.5) * w;
+          }
+        }
+        return acc;
+      }
+    }
 #pragma unroll
     for (int j = 0; j < ND; j++) {
       const real* w = Wv + (size_t)j * N;
@@ -166,9 +186,18 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
           const int j = s >> 1;
           const int32_t F = c.nb[s];
           real pf = 0;
-          if (F >= 0) pf = real(0.5) * (AL[(size_t)j * N + P] / aP + AL[(size_t)j * N + F] / A.Cdiag[F]);
+          int jF = j;
+          if constexpr (MODE == 2) {
+            if (D.nbfr && F >= 0) jF = fr_ax(D.nbfr[(size_t)s * N + P], j);
+          }
+          if (F >= 0) pf = real(0.5) * (AL[(size_t)j * N + P] / aP + AL[(size_t)jF * N + F] / A.Cdiag[F]);
           pd -= pf;
-          if (s & 1) A.Poff[(size_t)j * N + P] = pf;
+          if constexpr (MODE == 2) {
+            if (D.nbfr) A.Poff[(size_t)s * N + P] = pf;        // every face kept by its cell
+            else if (s & 1) A.Poff[(size_t)j * N + P] = pf;
+          } else {
+            if (s & 1) A.Poff[(size_t)j * N + P] = pf;
+          }
           A.gCoff[(size_t)s * N + P] = 0;
         }
         A.Pdiag[P] = pd;
@@ -273,7 +302,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
           Acc<real> a1[1];
           a1[0].zero();
           X.cells([&](const Cell& c) {
-            const real v = cross_diff_T2<real, ND, false>(c, A.gdk, N, nullptr);
+            const real v = cross_diff_T2<real, ND, false>(c, A.gdk, N, nullptr, D.nbfr);
             A.gx[c.i] = v;
             A.cx[c.i] = real(0);
             a1[0].add(v);
@@ -369,7 +398,11 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
 #pragma unroll
         for (int s = 0; s < NSD; s++) {
           const int32_t F = c.nb[s];
-          if (F >= 0) v += A.Coff[(size_t)(s ^ 1) * N + F] * A.gg[(size_t)i * N + F];
+          int rs = s ^ 1;      // the neighbour's side facing this cell
+          if constexpr (MODE == 2) {
+            if (D.nbfr) rs = fr_ret(D.nbfr[(size_t)s * N + P], s);
+          }
+          if (F >= 0) v += A.Coff[(size_t)rs * N + F] * A.gg[(size_t)i * N + F];
         }
         A.gu[(size_t)i * N + P] = -v;
       }
@@ -377,7 +410,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
         // h carries the deferred viscous cross terms of its input velocity:
         // their transpose (phase 1) and their viscosity derivative
         if (NO) {
-          cross_visc_T1<real, ND>(c, A.gg, Gx, J, nu_s, N, A.gdk);
+          cross_visc_T1<real, ND>(c, A.gg, Gx, J, nu_s, N, A.gdk, D.nbfr);
           real xv[ND];
           cross_visc<real, ND>(D, c, uin, A.bval, nbf, Gx, J, real(1), xv);
 #pragma unroll
@@ -392,7 +425,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
 #pragma unroll
           for (int i = 0; i < ND; i++)
             A.gu[(size_t)i * N + c.i] +=
-                cross_diff_T2<real, ND, true>(c, A.gdk + (size_t)i * ND * N, N, A.gbval + (size_t)i * nbf);
+                cross_diff_T2<real, ND, true>(c, A.gdk + (size_t)i * ND * N, N, A.gbval + (size_t)i * nbf, D.nbfr);
         });
         if (!plain_sync(g)) return;
       }
@@ -499,7 +532,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
               for (int i = 0; i < ND; i++) acc += zP[i] * usm[(size_t)i * N + F];
               A.gCoff[(size_t)s * N + P] -= acc;
             }
-            cross_visc_T1<real, ND>(c, A.z, Gx, J, nu_s, N, A.gdk);
+            cross_visc_T1<real, ND>(c, A.z, Gx, J, nu_s, N, A.gdk, D.nbfr);
             real xv[ND];
             cross_visc<real, ND>(D, c, usm1, A.bval, nbf, Gx, J, real(1), xv);
 #pragma unroll
@@ -514,7 +547,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
             const int32_t P = c.i;
 #pragma unroll
             for (int i = 0; i < ND; i++) {
-              const real gm = cross_diff_T2<real, ND, true>(c, A.gdk + (size_t)i * ND * N, N, A.gbval + (size_t)i * nbf);
+              const real gm = cross_diff_T2<real, ND, true>(c, A.gdk + (size_t)i * ND * N, N, A.gbval + (size_t)i * nbf, D.nbfr);
               if (m > 1) {
                 A.z[(size_t)i * N + P] = 0;
                 A.r[(size_t)i * N + P] = gm;
@@ -593,7 +626,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
 #pragma unroll
           for (int i = 0; i < ND; i++) A.du_in[(size_t)i * N + P] += A.gu[(size_t)i * N + P];
         real W[ND], x0[ND];
-        cross_w<real, ND>(c, Gx, N, W);
+        cross_w<real, ND>(c, Gx, N, W, D.nbfr);
         cross_const<real, ND>(D, c, W, A.bval, nbf, Gx, J, x0);
 #pragma unroll
         for (int i = 0; i < ND; i++) anu[0].add_prod(gr[i], x0[i]);
@@ -647,7 +680,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
         // through the direct-neighbour cross entries of C (C = ... - nu M1)
         if (A.dp_in) A.dp_in[P] = path_p ? A.gx[P] : real(0);
         real W[ND];
-        cross_w<real, ND>(c, Gx, N, W);
+        cross_w<real, ND>(c, Gx, N, W, D.nbfr);
         real m = 0;
 #pragma unroll
         for (int s = 0; s < NSD; s++) {
@@ -658,7 +691,7 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
         }
         anu[0].add(-m);
       } else if (A.dp_in) {
-        A.dp_in[P] = real(0);
+        A.dp_in[P] = o.pred_grad_p ? -gradT(c, A.W) : real(0);
       }
     } else if (A.dp_in) {
       A.dp_in[P] = o.pred_grad_p ? -gradT(c, A.W) : real(0);
@@ -674,11 +707,19 @@ __device__ void adj_group(const AdjCall<real>& A, const SolverOpts& o, Group& g)
       const real aP = AL[(size_t)j * N + P];
       if (F >= 0) {
         const real gcP = A.gCoff[(size_t)s * N + P];
-        const real gcF = A.gCoff[(size_t)(s ^ 1) * N + F];
+        int rs = s ^ 1;        // the neighbour's side facing this cell
+        if constexpr (MODE == 2) {
+          if (D.nbfr) rs = fr_ret(D.nbfr[(size_t)s * N + P], s);
+        }
+        const real gcF = A.gCoff[(size_t)rs * N + F];
         const real own = real(0.5) * n * (gcP + gAP) * invJ;
         const real nbr = -real(0.5) * n * (gcF + A.gA[F]) / J[F];
         Ub[j] += real(0.5) * (own + nbr);
-        const real Df = real(0.5) * (aP + AL[(size_t)j * N + F]);
+        int jF = j;
+        if constexpr (MODE == 2) {
+          if (D.nbfr) jF = fr_ax(D.nbfr[(size_t)s * N + P], j);
+        }
+        const real Df = real(0.5) * (aP + AL[(size_t)jF * N + F]);
         anu[0].add((gAP - gcP) * Df * invJ);
       } else {
         anu[0].add(gAP * real(2) * aP * invJ);

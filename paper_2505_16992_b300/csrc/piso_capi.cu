@@ -39,6 +39,7 @@ thread_local std::string g_create_error;
 struct SideSpec {
   int kind = 0;            // 0 none, 1 connection, 2 dirichlet, 3 outflow
   int other = -1, other_side = -1;
+  int perm = 0, flip = 0;  // connection: tangential axes exchanged / reversed (bit i: this side's axis i)
   std::vector<double> values;   // [face][ndim]
   double um[3] = {0, 0, 0};
 };
@@ -111,6 +112,8 @@ struct piso_domain {
   bool ilu_ready = false;      // tables match (ncta, threads, ownership) of the launches
   int ilu_key[3] = {-1, -1, -1};
   bool has_cross = false;      // some cell has non-zero cross metrics (accepted with n_nonortho >= 1)
+  bool twisted = false;        // some joint exchanges or reverses axes (neighbour frames are stored)
+  int16_t* nbfr = nullptr;     // [2d][N] neighbour frames on the device (twisted domains)
   void* gx = nullptr;          // [d(d-1)/2][N] cross metrics on the device
   bool pending = false;
   cudaStream_t pending_stream = nullptr;
@@ -257,6 +260,12 @@ int ws_units(int k, int nd) {
 // workspace arrays a domain allocates: the adjoint's non-orthogonal scratch
 // only on non-orthogonal meshes
 bool ws_needed(int k, bool has_cross) { return has_cross || (k != A_GYB && k != A_GDK); }
+
+// size of workspace array k for domain d: on domains with joints that
+// exchange or reverse axes every cell keeps its 2d pressure face coefficients
+int ws_units_d(int k, const piso_domain* d) {
+  return (k == W_POFF && d->twisted) ? 2 * d->ndim : ws_units(k, d->ndim);
+}
 
 // Non-orthogonal corrector iterates a step record can hold (the adjoint needs
 // them); piso_options.n_nonortho is limited to this.
@@ -521,7 +530,9 @@ const void* adj_kernel_ptr(int prec, int nd, int threads = 512, int mode = 0) {
 }
 
 bool uses_ilu(const piso_domain* d) { return d->opts.adv_precond != PISO_ADV_PRECOND_NONE; }
-int fwd_mode(const piso_domain* d) { return d->has_cross ? 2 : (uses_ilu(d) ? 1 : 0); }
+// the extended instantiations (mode 2) also carry the neighbour frames of joints
+// that exchange or reverse axes
+int fwd_mode(const piso_domain* d) { return (d->has_cross || d->twisted) ? 2 : (uses_ilu(d) ? 1 : 0); }
 int adj_mode(const piso_domain* d) { return fwd_mode(d); }
 
 // ILU(0) tables for the current launch layout (App. A.5 preconditioner of the
@@ -795,26 +806,53 @@ static piso_status check_side(piso_domain* d, int32_t blk, int32_t side) {
   return PISO_OK;
 }
 
-piso_status piso_connect(piso_domain* d, int32_t a, int32_t sa, int32_t b, int32_t sb) {
+piso_status piso_connect(piso_domain* d, int32_t a, int32_t sa, int32_t b, int32_t sb, int32_t axis_perm,
+                         int32_t flip_mask) {
   piso_status s = check_side(d, a, sa);
   if (s) return s;
   if (!(a == b && sa == sb)) {
     s = check_side(d, b, sb);
     if (s) return s;
   }
-  if (sa / 2 != sb / 2 || sa % 2 == sb % 2)
-    return fail(d, PISO_EINVAL, "connections join opposite sides of the same axis");
+  const int nd = d->ndim;
+  if (axis_perm < 0 || axis_perm > 1 || (nd == 2 && axis_perm))
+    return fail(d, PISO_EINVAL, "axis_perm must be 0 (2D) or 0/1 (3D)");
+  if (flip_mask < 0 || flip_mask >= (1 << (nd - 1))) return fail(d, PISO_EINVAL, "flip_mask out of range");
   const int* ra = d->blocks[a].res;
   const int* rb = d->blocks[b].res;
-  for (int ax = 0; ax < d->ndim; ax++)
-    if (ax != sa / 2 && ra[ax] != rb[ax])
-      return fail(d, PISO_EINVAL, "connected sides need matching resolution");
-  d->blocks[a].side[sa].kind = 1;
-  d->blocks[a].side[sa].other = b;
-  d->blocks[a].side[sa].other_side = sb;
-  d->blocks[b].side[sb].kind = 1;
-  d->blocks[b].side[sb].other = a;
-  d->blocks[b].side[sb].other_side = sa;
+  int ta[2] = {0, 0}, tb[2] = {0, 0}, n = 0, m = 0;
+  for (int x = 0; x < 3; x++) {
+    if (x != sa / 2) ta[n++] = x;
+    if (x != sb / 2) tb[m++] = x;
+  }
+  for (int i = 0; i < nd - 1; i++)
+    if (ra[ta[i]] != rb[tb[axis_perm ? 1 - i : i]])
+      return fail(d, PISO_EINVAL, "connected sides need matching resolution (tangential axis %d)", i);
+  if (a == b && sa == sb) {
+    // a side folded onto itself pairs cells: the map must pair distinct cells
+    if (axis_perm) return fail(d, PISO_EINVAL, "a side joined to itself keeps its axes (axis_perm 0)");
+    bool moves = false;
+    for (int i = 0; i < nd - 1; i++)
+      if (((flip_mask >> i) & 1) && ra[ta[i]] % 2 == 0) moves = true;
+    if (!moves)
+      return fail(d, PISO_EINVAL, "a side joined to itself needs a reversed axis of even length (no cell may meet "
+                                  "itself)");
+  }
+  SideSpec& A = d->blocks[a].side[sa];
+  A.kind = 1;
+  A.other = b;
+  A.other_side = sb;
+  A.perm = axis_perm;
+  A.flip = flip_mask;
+  if (!(a == b && sa == sb)) {
+    // the inverse map: an exchange is its own inverse, the reversal bits follow the axes
+    SideSpec& B = d->blocks[b].side[sb];
+    B.kind = 1;
+    B.other = a;
+    B.other_side = sa;
+    B.perm = axis_perm;
+    B.flip = axis_perm ? (((flip_mask & 1) << 1) | ((flip_mask >> 1) & 1)) : flip_mask;
+  }
   return PISO_OK;
 }
 
@@ -863,6 +901,7 @@ static piso_status validate_options(piso_domain* d, const piso_options* o) {
 static void resolve_precond(piso_domain* d) {
   const int p = d->opts.p_precond;
   d->p_line = (p == PISO_PRECOND_LINE || (p == PISO_PRECOND_AUTO && d->aniso >= 4.0)) ? 1 : 0;
+  if (d->twisted) d->p_line = 0;   // the line factors read the plain face layout: Jacobi there
 }
 
 piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
@@ -906,12 +945,21 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
     for (int s = 0; s < 6; s++) {
       bi.link[s] = -1;
       bi.bfo[s] = 0;
+      bi.lside[s] = (int8_t)(s ^ 1);
+      bi.lperm[s] = 0;
+      bi.lflip[s] = 0;
+      bi.lplain[s] = 1;
     }
     for (int s = 0; s < nsd; s++) {
       const SideSpec& sp = hb.side[s];
       if (sp.kind == 0) return fail(d, PISO_EINVAL, "block %d side %d has no boundary", (int)b, s);
       if (sp.kind == 1) {
         bi.link[s] = sp.other;
+        bi.lside[s] = (int8_t)sp.other_side;
+        bi.lperm[s] = (int8_t)sp.perm;
+        bi.lflip[s] = (int8_t)sp.flip;
+        bi.lplain[s] = (sp.other_side == (s ^ 1) && !sp.perm && !sp.flip) ? 1 : 0;
+        if (!bi.lplain[s]) d->twisted = true;
       } else {
         bi.bfo[s] = nbf;
         int nf = side_nfaces(hb.res, s, nd);
@@ -1033,8 +1081,9 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
     d->bf_um = a.take((size_t)nd * nbf1 * e);
     d->bval = a.take((size_t)nd * nbf1 * e);
     d->gbval = a.take((size_t)nd * nbf1 * e);
+    d->nbfr = d->twisted ? (int16_t*)a.take((size_t)nsd * N * sizeof(int16_t)) : nullptr;
     for (int k = 0; k < W_COUNT; k++)
-      d->ws[k] = ws_needed(k, d->has_cross) ? a.take((size_t)ws_units(k, nd) * N * e) : nullptr;
+      d->ws[k] = ws_needed(k, d->has_cross) ? a.take((size_t)ws_units_d(k, d) * N * e) : nullptr;
     d->tape_ws = a.take(tape_layout(d).total);
     d->bar = (uint32_t*)a.take(64);
     d->status = (int32_t*)a.take(64);
@@ -1057,6 +1106,43 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
   S.T = d->T;
   S.alpha = d->alpha;
   S.Gx = d->gx;
+  S.nbfr = d->nbfr;
+  if (d->twisted) {
+    // neighbour frames: identity inside blocks and across plain joints; across
+    // a joint of side s to side so, the normal axis goes to so's axis (reversed
+    // when both sides have the same sign) and the tangential axes as exchanged
+    // (lperm) and reversed (lflip)
+    std::vector<int16_t> fr((size_t)nsd * N, (int16_t)FRAME_ID);
+    for (size_t b = 0; b < d->blocks.size(); b++) {
+      const BlockInfo& B = S.blk[b];
+      for (int sd = 0; sd < nsd; sd++) {
+        if (B.link[sd] < 0 || B.lplain[sd]) continue;
+        const int j = sd >> 1, so = B.lside[sd], jo = so >> 1;
+        int ax[3] = {0, 1, 2}, ng[3] = {0, 0, 0};
+        int ta[2] = {0, 0}, tb[2] = {0, 0}, n = 0, m = 0;
+        for (int x = 0; x < 3; x++) {
+          if (x != j) ta[n++] = x;
+          if (x != jo) tb[m++] = x;
+        }
+        ax[j] = jo;
+        ng[j] = ((sd & 1) == (so & 1)) ? 1 : 0;
+        for (int i = 0; i < 2; i++) {
+          ax[ta[i]] = tb[B.lperm[sd] ? 1 - i : i];
+          ng[ta[i]] = (B.lflip[sd] >> i) & 1;
+        }
+        const int16_t code = (int16_t)(ax[0] | (ax[1] << 2) | (ax[2] << 4) | (ng[0] << 6) | (ng[1] << 7) | (ng[2] << 8));
+        const int nxb = B.nx, nyb = B.ny, nzb = B.nz;
+        for (int z = 0; z < nzb; z++)
+          for (int y = 0; y < nyb; y++)
+            for (int x = 0; x < nxb; x++) {
+              const int c3[3] = {x, y, z}, n3[3] = {nxb, nyb, nzb};
+              if (c3[j] != ((sd & 1) ? n3[j] - 1 : 0)) continue;
+              fr[(size_t)sd * N + B.off + x + nxb * (y + nyb * z)] = code;
+            }
+      }
+    }
+    CUDA_TRY(d, cudaMemcpy(d->nbfr, fr.data(), fr.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+  }
   S.bf_cell = d->bf_cell;
   S.bf_side = d->bf_side;
   S.bf_out = d->bf_out;
@@ -1353,7 +1439,7 @@ StaticLayout static_layout(const piso_domain* d) {
     off += (bytes + 255) & ~size_t(255);
     return o;
   };
-  for (int k = 0; k < A_GA; k++) L.ws[k] = take((size_t)ws_units(k, d->ndim) * d->N * d->elem);
+  for (int k = 0; k < A_GA; k++) L.ws[k] = take((size_t)ws_units_d(k, d) * d->N * d->elem);
   L.tape = take(tape_layout(d).total);
   L.bar = take(64);
   L.status = take(64);

@@ -55,7 +55,11 @@ inline FastDiv make_fast_div(uint32_t d) {
 // ---------------------------------------------------------------------------
 struct BlockInfo {
   int32_t nx, ny, nz, off;   // resolution and first cell (domain index)
-  int32_t link[6];           // >= 0: block joined at this side (its opposite side); -1: boundary faces
+  int32_t link[6];           // >= 0: block joined at this side; -1: boundary faces
+  int8_t lside[6];           // the joined block's side (the opposite side for a plain joint)
+  int8_t lperm[6];           // 1: the side's two tangential axes run along the other side's in exchanged order
+  int8_t lflip[6];           // bit i: the side's i-th tangential axis (ascending) runs reversed
+  int8_t lplain[6];          // 1: a plain joint (opposite side of the same axis, no exchange, no reversal)
   int32_t bfo[6];            // first boundary face of this side (when link < 0)
   FastDiv dnx, dny;
   int32_t line0;             // first y-line of this block in the domain's line numbering
@@ -72,6 +76,8 @@ struct DomStatic {
   const void* alpha;         // [d][N]  alpha_jj = J T_j . T_j
   const void* Gx;            // [d(d-1)/2][N] cross metrics alpha_jk, j < k, pairs (0,1) (0,2) (1,2); null
                              // on orthogonal meshes
+  const int16_t* nbfr;       // [2d][N] frame of the neighbour across each side (see fr_ax), or null when
+                             // every joint is plain (then every frame is the identity)
   // boundary faces
   const int32_t* bf_cell;    // [nbf] adjacent cell
   const int8_t* bf_side;     // [nbf] side of that cell
@@ -89,6 +95,31 @@ struct Cell {
   int32_t nb[6];
 };
 
+// The neighbour of cell (x, y, z) of block B across side s when that side is
+// joined to side lside of block O with its tangential axes exchanged (lperm)
+// and/or reversed (lflip): the tangential coordinates carried over, the
+// normal one at O's side.
+__host__ __device__ inline int32_t joint_nbr(const BlockInfo& B, const BlockInfo& O, int32_t x, int32_t y, int32_t z,
+                                             int s) {
+  const int j = s >> 1, so = B.lside[s], jo = so >> 1;
+  const int32_t c[3] = {x, y, z};
+  const int32_t nb_[3] = {B.nx, B.ny, B.nz};
+  const int32_t no[3] = {O.nx, O.ny, O.nz};
+  int32_t oc[3] = {0, 0, 0};
+  int ta[2] = {0, 0}, tb[2] = {0, 0}, n = 0, m = 0;
+  for (int a = 0; a < 3; a++) {
+    if (a != j) ta[n++] = a;
+    if (a != jo) tb[m++] = a;
+  }
+  oc[jo] = (so & 1) ? no[jo] - 1 : 0;
+  for (int i = 0; i < 2; i++) {
+    int32_t v = c[ta[i]];
+    if ((B.lflip[s] >> i) & 1) v = nb_[ta[i]] - 1 - v;
+    oc[tb[B.lperm[s] ? 1 - i : i]] = v;
+  }
+  return O.off + oc[0] + O.nx * (oc[1] + O.ny * oc[2]);
+}
+
 __host__ __device__ __forceinline__ int32_t side_nbr(const DomStatic& D, const BlockInfo& B, int32_t i,
                                             int32_t x, int32_t y, int32_t z, int s) {
   switch (s) {
@@ -102,6 +133,7 @@ __host__ __device__ __forceinline__ int32_t side_nbr(const DomStatic& D, const B
   const int32_t t = B.link[s];
   if (t >= 0) {
     const BlockInfo& O = D.blk[t];
+    if (!B.lplain[s]) return joint_nbr(B, O, x, y, z, s);
     switch (s) {
       case 0: return O.off + (O.nx - 1) + O.nx * (y + O.ny * z);
       case 1: return O.off + O.nx * (y + O.ny * z);
@@ -143,6 +175,22 @@ __host__ __device__ __forceinline__ Cell locate(const DomStatic& D, int32_t i) {
 }
 
 __device__ __forceinline__ int32_t safe(int32_t nb, int32_t self) { return nb >= 0 ? nb : self; }
+
+// Frame of the neighbour across a side (joints with exchanged or reversed
+// axes; App. A.3: a connection only changes the neighbour lookup, but the
+// neighbour's per-axis quantities are in its own frame).  A code holds, for
+// each axis a of the cell, the neighbour's axis (2 bits at 2a) and whether it
+// runs reversed (bit 6 + a); FRAME_ID is the identity.
+constexpr int FRAME_ID = 0x24;
+__host__ __device__ __forceinline__ int fr_ax(int code, int a) { return (code >> (2 * a)) & 3; }
+__host__ __device__ __forceinline__ int fr_neg(int code, int a) { return (code >> (6 + a)) & 1; }
+// the neighbour's side that faces the cell, for the cell's side s
+__host__ __device__ __forceinline__ int fr_ret(int code, int s) {
+  return 2 * fr_ax(code, s >> 1) + (((s & 1) == fr_neg(code, s >> 1)) ? 1 : 0);
+}
+__device__ __forceinline__ int fr_code(const int16_t* fr, int32_t N, int s, int32_t i) {
+  return fr ? (int)fr[(size_t)s * N + i] : FRAME_ID;
+}
 
 // Lines of the y-line preconditioner: the cells of one block that share x (and
 // z), in order of y.  Line l of block b (l' = l - line0) starts at x = l' mod nx,

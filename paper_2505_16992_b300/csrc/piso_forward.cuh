@@ -129,7 +129,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   const bool lines = A.p_line && o.line_cap > 0;
   LinePre<real> LP{};
   if (lines) LP = line_setup<real, ND>(D, g, o, A.lfa, A.lfm, A.lfc);
-  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap), lines ? &LP : nullptr};
+  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap), lines ? &LP : nullptr, D.nbfr};
   const real* J = reinterpret_cast<const real*>(D.J);
   const real* T = reinterpret_cast<const real*>(D.T);
   const real* AL = reinterpret_cast<const real*>(D.alpha);
@@ -251,7 +251,7 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
       bool nonortho = false;
       if constexpr (MODE == 2) {
         nonortho = A.n_nonortho > 0;
-        if (nonortho) cross_w<real, ND>(c, reinterpret_cast<const real*>(D.Gx), N, Wx);
+        if (nonortho) cross_w<real, ND>(c, reinterpret_cast<const real*>(D.Gx), N, Wx, D.nbfr);
       }
 #pragma unroll
       for (int s = 0; s < NSD; s++) {
@@ -260,8 +260,19 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
         const int32_t F = c.nb[s];
         const real aP = AL[(size_t)j * N + P];
         if (F >= 0) {
-          const real Uf = real(0.5) * (A.U[(size_t)j * N + P] + A.U[(size_t)j * N + F]);
-          const real Df = nu * real(0.5) * (aP + AL[(size_t)j * N + F]);
+          int jF = j;
+          real eF = real(1);
+          if constexpr (MODE == 2) {
+            // a joint with exchanged or reversed axes: the neighbour's flux and
+            // alpha are its own axis's, in its orientation
+            if (D.nbfr) {
+              const int code = D.nbfr[(size_t)s * N + P];
+              jF = fr_ax(code, j);
+              if (fr_neg(code, j)) eF = real(-1);
+            }
+          }
+          const real Uf = real(0.5) * (A.U[(size_t)j * N + P] + eF * A.U[(size_t)jF * N + F]);
+          const real Df = nu * real(0.5) * (aP + AL[(size_t)jF * N + F]);
           off[s] = (real(0.5) * n * Uf - Df) * invJ;
           diag += (real(0.5) * n * Uf + Df) * invJ;
           if constexpr (MODE == 2) {
@@ -450,9 +461,18 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
           const int j = s >> 1;
           const int32_t F = c.nb[s];
           real pf = 0;
-          if (F >= 0) pf = real(0.5) * (A.Aw[(size_t)j * N + P] + A.Aw[(size_t)j * N + F]);
+          int jF = j;
+          if constexpr (MODE == 2) {
+            if (D.nbfr && F >= 0) jF = fr_ax(D.nbfr[(size_t)s * N + P], j);
+          }
+          if (F >= 0) pf = real(0.5) * (A.Aw[(size_t)j * N + P] + A.Aw[(size_t)jF * N + F]);
           pd -= pf;
-          if (s & 1) A.Poff[(size_t)j * N + P] = pf;
+          if constexpr (MODE == 2) {
+            if (D.nbfr) A.Poff[(size_t)s * N + P] = pf;        // every face kept by its cell
+            else if (s & 1) A.Poff[(size_t)j * N + P] = pf;
+          } else {
+            if (s & 1) A.Poff[(size_t)j * N + P] = pf;
+          }
         }
         A.Pdiag[P] = pd;
         A.Pinv[P] = real(1) / (-pd);
@@ -500,7 +520,16 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
           const real n = (s & 1) ? real(1) : real(-1);
           const int32_t F = c.nb[s];
           if (F >= 0) {
-            b += n * real(0.5) * (A.Fh[(size_t)j * N + P] + A.Fh[(size_t)j * N + F]);
+            int jF = j;
+            real eF = real(1);
+            if constexpr (MODE == 2) {
+              if (D.nbfr) {
+                const int code = D.nbfr[(size_t)s * N + P];
+                jF = fr_ax(code, j);
+                if (fr_neg(code, j)) eF = real(-1);
+              }
+            }
+            b += n * real(0.5) * (A.Fh[(size_t)j * N + P] + eF * A.Fh[(size_t)jF * N + F]);
           } else {
             const int32_t f = -1 - F;
             real tu = 0;

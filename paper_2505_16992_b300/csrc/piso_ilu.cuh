@@ -80,7 +80,7 @@ __device__ void ilu_factor_levels(const Ctx<real, ND>& X, const IluPre<real>& P,
       c_row<real, ND, false>(c, N, Cdiag, Coff, diag, cf);
       real d = diag;
       if (m & 0xffu) {
-        c_row<real, ND, true>(c, N, Cdiag, Coff, diag, ct);
+        c_row<real, ND, true>(c, N, Cdiag, Coff, diag, ct, X.fr);
 #pragma unroll
         for (int s = 0; s < 2 * ND; s++)
           if ((m >> s) & 1u) d -= cf[s] * ct[s] * P.dinv[c.nb[s]];
@@ -111,7 +111,7 @@ __device__ __forceinline__ void ilu_apply(const Ctx<real, ND>& X, const IluPre<r
       const uint32_t m = P.mask[c.i] & 0xffu;
       const real di = P.dinv[c.i];
       real diag, cf[2 * ND];
-      if (m) c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+      if (m) c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf, X.fr);
 #pragma unroll
       for (int k = 0; k < ND; k++) {
         if (!act[k]) continue;
@@ -136,7 +136,7 @@ __device__ __forceinline__ void ilu_apply(const Ctx<real, ND>& X, const IluPre<r
       const Cell c = X.cell(i);
       const real di = P.dinv[i];
       real diag, cf[2 * ND];
-      c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+      c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf, X.fr);
 #pragma unroll
       for (int k = 0; k < ND; k++) {
         if (!act[k]) continue;
@@ -236,7 +236,7 @@ __device__ __forceinline__ void ilu_stage_rows(const Ctx<real, ND>& X, const Ilu
   if (R.i >= 0) {
     const Cell c = X.cell(R.i);
     real diag, cf[2 * ND];
-    c_row<real, ND, TR>(c, X.N, Cdiag, Coff, diag, cf);
+    c_row<real, ND, TR>(c, X.N, Cdiag, Coff, diag, cf, X.fr);
 #pragma unroll
     for (int s = 0; s < 2 * ND; s++) {
       const bool in = ((R.m >> s) | (R.m >> (8 + s))) & 1u;
@@ -261,7 +261,7 @@ __device__ void ilu_factor_fast(const Ctx<real, ND>& X, const IluPre<real>& P, c
     const Cell c = X.cell(R.i);
     real diag, cf[2 * ND], ct[2 * ND];
     c_row<real, ND, false>(c, X.N, Cdiag, Coff, diag, cf);
-    c_row<real, ND, true>(c, X.N, Cdiag, Coff, diag, ct);
+    c_row<real, ND, true>(c, X.N, Cdiag, Coff, diag, ct, X.fr);
 #pragma unroll
     for (int s = 0; s < 2 * ND; s++) {
       S.rc[s * n + t] = ((m >> s) & 1u) ? cf[s] * ct[s] : real(0);
@@ -424,7 +424,7 @@ __device__ bool bicgstab_ilu(const Ctx<real, ND>& X, const IluPre<real>& P, BiSt
       }
       X.cells([&](const Cell& c) {
         real diag, cf[2 * ND];
-        c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+        c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf, X.fr);
 #pragma unroll
         for (int k = 0; k < ND; k++) {
           if (!act[k]) continue;
@@ -470,7 +470,7 @@ __device__ bool bicgstab_ilu(const Ctx<real, ND>& X, const IluPre<real>& P, BiSt
       for (int k = 0; k < 3 * ND; k++) a[k].zero();
       X.cells([&](const Cell& c) {
         real diag, cf[2 * ND];
-        c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+        c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf, X.fr);
 #pragma unroll
         for (int k = 0; k < ND; k++) {
           if (!act[k]) continue;

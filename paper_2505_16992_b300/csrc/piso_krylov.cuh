@@ -58,6 +58,7 @@ struct Ctx {
   int32_t lo, hi, N;
   const int32_t* nbt;   // [2*ND][hi-lo] neighbour table in shared memory, or nullptr
   const LinePre<real>* lp;   // y-line preconditioner of the pressure CG, or nullptr (Jacobi)
+  const int16_t* fr;    // neighbour frames [2*ND][N] when some joint exchanges or reverses axes, else nullptr
   // first cell, stride and end of this thread's walk
   __device__ __forceinline__ int32_t first() const {
     return nbt ? lo + (int32_t)threadIdx.x : g.rank * (int32_t)blockDim.x + (int32_t)threadIdx.x;
@@ -111,25 +112,38 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 // opposite side (gather form, no atomics).
 template <typename real, int ND, bool TR>
 __device__ __forceinline__ void c_row(const Cell& c, int32_t N, const real* Cdiag, const real* Coff, real& diag,
-                                      real (&cf)[2 * ND]) {
+                                      real (&cf)[2 * ND], const int16_t* fr = nullptr) {
   diag = Cdiag[c.i];
 #pragma unroll
   for (int s = 0; s < 2 * ND; s++) {
     const int32_t Q = c.nb[s];
-    if (Q >= 0) cf[s] = TR ? Coff[(size_t)(s ^ 1) * N + Q] : Coff[(size_t)s * N + c.i];
-    else cf[s] = real(0);
+    if (Q >= 0) {
+      if (TR) {   // the neighbour's coefficient on its side facing this cell
+        const int rs = fr ? fr_ret(fr[(size_t)s * N + c.i], s) : (s ^ 1);
+        cf[s] = Coff[(size_t)rs * N + Q];
+      } else {
+        cf[s] = Coff[(size_t)s * N + c.i];
+      }
+    } else {
+      cf[s] = real(0);
+    }
   }
 }
 
 // Face coefficients of the pressure matrix P for cell c (symmetric: the - face
-// of P is the + face of its - neighbour).
+// of P is the + face of its - neighbour).  Domains with joints that exchange
+// or reverse axes (own != nullptr... fr set) keep every cell's 2d face
+// coefficients itself ([2d][N]), since a neighbour's face towards the cell
+// need not be its + face there.
 template <typename real, int ND>
-__device__ __forceinline__ void p_row(const Cell& c, int32_t N, const real* Poff, real (&pf)[2 * ND]) {
+__device__ __forceinline__ void p_row(const Cell& c, int32_t N, const real* Poff, real (&pf)[2 * ND],
+                                      const int16_t* fr = nullptr) {
 #pragma unroll
   for (int s = 0; s < 2 * ND; s++) {
     const int j = s >> 1;
     const int32_t Q = c.nb[s];
-    pf[s] = Q >= 0 ? ((s & 1) ? Poff[(size_t)j * N + c.i] : Poff[(size_t)j * N + Q]) : real(0);
+    if (fr) pf[s] = Q >= 0 ? Poff[(size_t)s * N + c.i] : real(0);
+    else pf[s] = Q >= 0 ? ((s & 1) ? Poff[(size_t)j * N + c.i] : Poff[(size_t)j * N + Q]) : real(0);
   }
 }
 
@@ -409,7 +423,7 @@ __device__ __forceinline__ void bicg_sweep_a(const Ctx<real, ND>& X, int first, 
     }
     const Cell c = X.cell(i);
     real diag, cf[2 * ND];
-    c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+    c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf, X.fr);
     real pP[ND], v[ND], rh[ND];
 #pragma unroll
     for (int k = 0; k < ND; k++) {
@@ -461,7 +475,7 @@ __device__ __forceinline__ void bicg_sweep_b(const Ctx<real, ND>& X, const int (
     }
     const Cell c = X.cell(i);
     real diag, cf[2 * ND];
-    c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf);
+    c_row<real, ND, TR>(c, N, Cdiag, Coff, diag, cf, X.fr);
     real sP[ND], tt[ND];
 #pragma unroll
     for (int k = 0; k < ND; k++) {
@@ -630,7 +644,7 @@ __device__ __forceinline__ void cg_jacobi_sweep(const Ctx<real, ND>& X, int firs
     }
     const Cell c = X.cell(i);
     real pf[2 * ND];
-    p_row<real, ND>(c, N, Poff, pf);
+    p_row<real, ND>(c, N, Poff, pf, X.fr);
     auto sQ = [&](int32_t Q) -> real { return first ? w_i[Q] : w_i[Q] + be * s_o[Q]; };
     auto u1 = [&](int32_t Q) -> real { return (r_i[Q] - al * sQ(Q)) * Pinv[Q]; };
     const int32_t P = c.i;
@@ -690,7 +704,7 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     const real mb = pick<real>(s_mb, s_mbf);
     X.cells([&](const Cell& c) {
       real pf[2 * ND];
-      p_row<real, ND>(c, N, Poff, pf);
+      p_row<real, ND>(c, N, Poff, pf, X.fr);
       const real bp = -(b[c.i] - mb);
       const real xP = x[c.i];
       real px = 0;   // (P x)_P = sum_f P_F (x_F - x_P): exact zero on constants in any precision
@@ -734,7 +748,7 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     const real* r0 = rb[0];
     X.cells([&](const Cell& c) {
       real pf[2 * ND];
-      p_row<real, ND>(c, N, Poff, pf);
+      p_row<real, ND>(c, N, Poff, pf, X.fr);
       const real rP = r0[c.i];
       const real uP = rP * Pinv[c.i];
       real w = 0;    // (A' u)_P = sum_f P_F (u_P - u_F)
@@ -788,7 +802,7 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
       real* r_t = rb[cur];
       X.cells([&](const Cell& c) {
         real pf[2 * ND];
-        p_row<real, ND>(c, N, Poff, pf);
+        p_row<real, ND>(c, N, Poff, pf, X.fr);
         const real xP = x[c.i];
         real px = 0;
 #pragma unroll
@@ -805,7 +819,7 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
       real* s_t = sb[cur ^ 1];
       X.cells([&](const Cell& c) {
         real pf[2 * ND];
-        p_row<real, ND>(c, N, Poff, pf);
+        p_row<real, ND>(c, N, Poff, pf, X.fr);
         const int32_t P = c.i;
         const real uP = r_t[P] * Pinv[P];
         const real pP = pdir[P];
@@ -868,7 +882,7 @@ __device__ bool cg_pressure_refined(const Ctx<real, ND>& X, CgState& cs, RefStat
       a[2].zero();
       X.cells([&](const Cell& c) {
         real pf[2 * ND];
-        p_row<real, ND>(c, N, Poff, pf);
+        p_row<real, ND>(c, N, Poff, pf, X.fr);
         auto xs = [&](int32_t Q) -> double { return round == 0 ? (double)x[Q] : x64[Q]; };
         const int32_t P = c.i;
         const double bp = -((double)b[P] - bmean);

@@ -269,7 +269,7 @@ __device__ __forceinline__ void line_apply_sweep(const Ctx<real, ND>& X, const r
     }
     const Cell c = X.cell(i);
     real pf[2 * ND];
-    p_row<real, ND>(c, N, Poff, pf);
+    p_row<real, ND>(c, N, Poff, pf, X.fr);
     const real uP = u[c.i];
     real uq[2 * ND];
 #pragma unroll
@@ -316,7 +316,7 @@ __device__ bool cg_pressure_line(const Ctx<real, ND>& X, CgState& cs, double rto
     line_batch_cells(L, B, [&](int32_t i, int32_t k, bool) {
       const Cell c = locate<ND>(D, i);
       real pf[2 * ND];
-      p_row<real, ND>(c, N, Poff, pf);
+      p_row<real, ND>(c, N, Poff, pf, X.fr);
       const real bp = -(b[i] - mb);
       const real xP = x[i];
       real px = 0;
@@ -344,7 +344,7 @@ __device__ bool cg_pressure_line(const Ctx<real, ND>& X, CgState& cs, double rto
   // I2: w0 = A' u0 on the usual cell range
   X.cells([&](const Cell& c) {
     real pf[2 * ND];
-    p_row<real, ND>(c, N, Poff, pf);
+    p_row<real, ND>(c, N, Poff, pf, X.fr);
     const real uP = u[c.i];
     real ww = 0;
 #pragma unroll

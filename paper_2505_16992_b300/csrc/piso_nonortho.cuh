@@ -35,6 +35,18 @@ __device__ __forceinline__ real cross_metric(const real* Gx, int32_t N, int j, i
   return Gx[(size_t)(j + k - 1) * N + i];
 }
 
+// alpha_jk of the neighbour across side s of cell i, in cell i's frame (its
+// own metric read through the joint's frame code; the plain reading when fr
+// is null).
+template <typename real>
+__device__ __forceinline__ real cross_metric_nb(const real* Gx, const int16_t* fr, int32_t N, int s, int32_t i,
+                                                int32_t F, int j, int k) {
+  if (!fr) return cross_metric(Gx, N, j, k, F);
+  const int code = fr[(size_t)s * N + i];
+  const real v = cross_metric(Gx, N, fr_ax(code, j), fr_ax(code, k), F);
+  return (fr_neg(code, j) ^ fr_neg(code, k)) ? -v : v;
+}
+
 // Central difference of q along axis k at cell c; bq: this component's
 // boundary values [nbf] (velocity) or null (pressure: the cell's own value).
 template <typename real, int ND>
@@ -46,11 +58,32 @@ __device__ __forceinline__ real cell_diff(const Cell& c, const real* q, const re
   return real(0.5) * (vh - vl);
 }
 
+// Central difference along cell i's axis k of its neighbour cF across side s
+// (the neighbour's own difference along the matching axis, with its
+// orientation).
+template <typename real, int ND>
+__device__ __forceinline__ real cell_diff_nb(const Cell& cF, const real* q, const real* bq, const int16_t* fr,
+                                             int32_t N, int s, int32_t i, int k) {
+  if (!fr) return cell_diff<real, ND>(cF, q, bq, k);
+  const int code = fr[(size_t)s * N + i];
+  const real v = cell_diff<real, ND>(cF, q, bq, fr_ax(code, k));
+  return fr_neg(code, k) ? -v : v;
+}
+
+// The side of cell i's neighbour across side sk that matches cell i's side s.
+__device__ __forceinline__ int side_nb(const int16_t* fr, int32_t N, int sk, int32_t i, int s) {
+  if (!fr) return s;
+  const int code = fr[(size_t)sk * N + i];
+  const int j = s >> 1;
+  return 2 * fr_ax(code, j) + ((((s & 1) ? 1 : 0) ^ fr_neg(code, j)) ? 1 : 0);
+}
+
 // W_k(P) = sum over P's inner faces f on the axes j != k of N_f mean(alpha_jk)
 // / 2: the coefficient of P's own central difference along k in the viscous
 // cross terms (the direct-neighbour part of Eq. difNonOrthoMatDiscrete).
 template <typename real, int ND>
-__device__ __forceinline__ void cross_w(const Cell& c, const real* Gx, int32_t N, real (&W)[ND]) {
+__device__ __forceinline__ void cross_w(const Cell& c, const real* Gx, int32_t N, real (&W)[ND],
+                                        const int16_t* fr = nullptr) {
   const int32_t P = c.i;
 #pragma unroll
   for (int k = 0; k < ND; k++) W[k] = 0;
@@ -62,7 +95,7 @@ __device__ __forceinline__ void cross_w(const Cell& c, const real* Gx, int32_t N
     const real n = (s & 1) ? real(1) : real(-1);
 #pragma unroll
     for (int k = 0; k < ND; k++)
-      if (k != j) W[k] += n * real(0.25) * (cross_metric(Gx, N, j, k, P) + cross_metric(Gx, N, j, k, F));
+      if (k != j) W[k] += n * real(0.25) * (cross_metric(Gx, N, j, k, P) + cross_metric_nb(Gx, fr, N, s, P, F, j, k));
   }
 }
 
@@ -81,11 +114,11 @@ __device__ __forceinline__ void cross_bface(const DomStatic& D, const Cell& c, i
     const real a = cross_metric(Gx, N, j, k, P);
     int32_t fh = fP, fl = fP;
     if (c.nb[2 * k + 1] >= 0) {
-      const int32_t t = locate<ND>(D, c.nb[2 * k + 1]).nb[s];
+      const int32_t t = locate<ND>(D, c.nb[2 * k + 1]).nb[side_nb(D.nbfr, N, 2 * k + 1, P, s)];
       if (t < 0) fh = -1 - t;
     }
     if (c.nb[2 * k] >= 0) {
-      const int32_t t = locate<ND>(D, c.nb[2 * k]).nb[s];
+      const int32_t t = locate<ND>(D, c.nb[2 * k]).nb[side_nb(D.nbfr, N, 2 * k, P, s)];
       if (t < 0) fl = -1 - t;
     }
 #pragma unroll
@@ -116,12 +149,12 @@ __device__ __forceinline__ void cross_visc(const DomStatic& D, const Cell& c, co
     const Cell cF = locate<ND>(D, F);
     for (int k = 0; k < ND; k++) {
       if (k == j) continue;
-      const real a = real(0.5) * (cross_metric(Gx, N, j, k, P) + cross_metric(Gx, N, j, k, F));
+      const real a = real(0.5) * (cross_metric(Gx, N, j, k, P) + cross_metric_nb(Gx, D.nbfr, N, s, P, F, j, k));
 #pragma unroll
       for (int q = 0; q < ND; q++) {
         const real* uq = u + (size_t)q * N;
         const real* bq = bval + (size_t)q * nbf;
-        acc[q] += n * a * (real(0.5) * cell_diff<real, ND>(cF, uq, bq, k));
+        acc[q] += n * a * (real(0.5) * cell_diff_nb<real, ND>(cF, uq, bq, D.nbfr, N, s, P, k));
       }
     }
   }
@@ -144,8 +177,10 @@ __device__ __forceinline__ real cross_pres(const DomStatic& D, const Cell& c, co
     const Cell cF = locate<ND>(D, F);
     for (int k = 0; k < ND; k++) {
       if (k == j) continue;
-      const real a = real(0.5) * (cross_metric(Gx, N, j, k, P) * invA[P] + cross_metric(Gx, N, j, k, F) * invA[F]);
-      const real g = real(0.5) * (cell_diff<real, ND>(c, p, nullptr, k) + cell_diff<real, ND>(cF, p, nullptr, k));
+      const real a = real(0.5) * (cross_metric(Gx, N, j, k, P) * invA[P] +
+                                  cross_metric_nb(Gx, D.nbfr, N, s, P, F, j, k) * invA[F]);
+      const real g = real(0.5) * (cell_diff<real, ND>(c, p, nullptr, k) +
+                                  cell_diff_nb<real, ND>(cF, p, nullptr, D.nbfr, N, s, P, k));
       acc += n * a * g;
     }
   }
@@ -186,9 +221,10 @@ __device__ __forceinline__ real cross_pres_T1(const DomStatic& D, const Cell& c,
     for (int k = 0; k < ND; k++) {
       if (k == j) continue;
       const real GQ = cross_metric(Gx, N, j, k, Q);
-      const real a = real(0.5) * (GQ * iaQ + cross_metric(Gx, N, j, k, F) * invA[F]);
+      const real a = real(0.5) * (GQ * iaQ + cross_metric_nb(Gx, D.nbfr, N, s, Q, F, j, k) * invA[F]);
       acc[k] += a * dg;
-      const real gk = real(0.5) * (cell_diff<real, ND>(c, p, nullptr, k) + cell_diff<real, ND>(cF, p, nullptr, k));
+      const real gk = real(0.5) * (cell_diff<real, ND>(c, p, nullptr, k) +
+                                   cell_diff_nb<real, ND>(cF, p, nullptr, D.nbfr, N, s, Q, k));
       ga -= GQ * iaQ * iaQ * gk * dg;
     }
   }
@@ -204,15 +240,29 @@ __device__ __forceinline__ real cross_pres_T1(const DomStatic& D, const Cell& c,
 // minus that, and the face value receives gdk[k] with the sign of the side
 // (gbk: the component's boundary-value gradient [nbf], or null).
 template <typename real, int ND, bool VEL>
-__device__ __forceinline__ real cross_diff_T2(const Cell& c, const real* gdk, int32_t N, real* gbk) {
+__device__ __forceinline__ real cross_diff_T2(const Cell& c, const real* gdk, int32_t N, real* gbk,
+                                              const int16_t* fr = nullptr) {
   const int32_t Q = c.i;
   real v = 0;
 #pragma unroll
   for (int k = 0; k < ND; k++) {
     const real* gk = gdk + (size_t)k * N;
     const int32_t hi = c.nb[2 * k + 1], lo = c.nb[2 * k];
-    if (lo >= 0) v += real(0.5) * gk[lo];
-    if (hi >= 0) v -= real(0.5) * gk[hi];
+    if (fr) {
+      // the neighbour R's own difference reads this cell on R's side facing it
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int s = 2 * k + e;
+        const int32_t R = c.nb[s];
+        if (R < 0) continue;
+        const int rs = fr_ret(fr[(size_t)s * N + Q], s);
+        const real w = gdk[(size_t)(rs >> 1) * N + R];
+        v += (rs & 1) ? real(0.5) * w : real(-0.5) * w;
+      }
+    } else {
+      if (lo >= 0) v += real(0.5) * gk[lo];
+      if (hi >= 0) v -= real(0.5) * gk[hi];
+    }
     if (hi < 0) {
       v += (VEL ? real(-0.5) : real(0.5)) * gk[Q];
       if (VEL && gbk) gbk[-1 - hi] += gk[Q];
@@ -231,7 +281,7 @@ __device__ __forceinline__ real cross_diff_T2(const Cell& c, const real* gdk, in
 // -N_s mean(alpha_jk) (nu / J_R) g_q,R / 2.
 template <typename real, int ND>
 __device__ __forceinline__ void cross_visc_T1(const Cell& c, const real* g, const real* Gx, const real* J, real nu,
-                                              int32_t N, real* gdk) {
+                                              int32_t N, real* gdk, const int16_t* fr = nullptr) {
   const int32_t Q = c.i;
   real acc[ND][ND];
 #pragma unroll
@@ -248,7 +298,7 @@ __device__ __forceinline__ void cross_visc_T1(const Cell& c, const real* g, cons
 #pragma unroll
     for (int k = 0; k < ND; k++) {
       if (k == j) continue;
-      const real a = real(0.5) * (cross_metric(Gx, N, j, k, Q) + cross_metric(Gx, N, j, k, R)) * w;
+      const real a = real(0.5) * (cross_metric(Gx, N, j, k, Q) + cross_metric_nb(Gx, fr, N, s, Q, R, j, k)) * w;
 #pragma unroll
       for (int q = 0; q < ND; q++) acc[q][k] += a * g[(size_t)q * N + R];
     }
@@ -282,23 +332,34 @@ __device__ __forceinline__ void cross_const_T(const DomStatic& D, const Cell& c,
     for (int k = 0; k < ND; k++) {
       if (k == j) continue;
       const real hQ = real(0.5) * n * fQ * cross_metric(Gx, N, j, k, Q);
-      const int32_t hi = c.nb[2 * k + 1], lo = c.nb[2 * k];
       bool hi_face = false, lo_face = false;
-      if (hi >= 0) {
-        hi_face = locate<ND>(D, hi).nb[s] < 0;
-        if (hi_face) {   // Q is the -k neighbour of hi: hi's difference reads this face with -1/2
-          const real hR = real(0.5) * n * (nu / J[hi]) * cross_metric(Gx, N, j, k, hi);
+      // a k-neighbour R reads this face in its own tangential difference (the
+      // face of its side matching s): with 1/2 if this cell is R's + neighbour
+      // along that difference, -1/2 if its - neighbour; the term's sign N_s
+      // alpha_jk of R in R's frame is the same in this cell's frame up to the
+      // joint's orientation of j
 #pragma unroll
-          for (int q = 0; q < ND; q++) acc[q] -= hR * g[(size_t)q * N + hi];
+      for (int e = 0; e < 2; e++) {
+        const int sk = 2 * k + e;
+        const int32_t R = c.nb[sk];
+        if (R < 0) continue;
+        const bool face = locate<ND>(D, R).nb[side_nb(D.nbfr, N, sk, Q, s)] < 0;
+        if (e) hi_face = face;
+        else lo_face = face;
+        if (!face) continue;
+        real hR;
+        bool plus;
+        if (D.nbfr) {
+          const int code = D.nbfr[(size_t)sk * N + Q];
+          const real Gr = cross_metric(Gx, N, fr_ax(code, j), fr_ax(code, k), R);
+          hR = real(0.5) * n * (fr_neg(code, j) ? -Gr : Gr) * (nu / J[R]);
+          plus = (fr_ret(code, sk) & 1) != 0;
+        } else {
+          hR = real(0.5) * n * (nu / J[R]) * cross_metric(Gx, N, j, k, R);
+          plus = !e;
         }
-      }
-      if (lo >= 0) {
-        lo_face = locate<ND>(D, lo).nb[s] < 0;
-        if (lo_face) {   // Q is the +k neighbour of lo: +1/2
-          const real hR = real(0.5) * n * (nu / J[lo]) * cross_metric(Gx, N, j, k, lo);
 #pragma unroll
-          for (int q = 0; q < ND; q++) acc[q] += hR * g[(size_t)q * N + lo];
-        }
+        for (int q = 0; q < ND; q++) acc[q] += (plus ? hR : -hR) * g[(size_t)q * N + R];
       }
       // Q's own tangential difference uses its own face where a k-neighbour has none
 #pragma unroll

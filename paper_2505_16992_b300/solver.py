@@ -52,8 +52,8 @@ class Domain:
         capi.check(self.lib.piso_block_add(self.h, r, vp, C.byref(bid)), self.h)
         return bid.value
 
-    def connect(self, a, sa, b, sb):
-        capi.check(self.lib.piso_connect(self.h, a, sa, b, sb), self.h)
+    def connect(self, a, sa, b, sb, axis_perm=0, flip_mask=0):
+        capi.check(self.lib.piso_connect(self.h, a, sa, b, sb, axis_perm, flip_mask), self.h)
 
     def set_dirichlet(self, blk, side, values):
         _, vp = capi.dbuf(values)
@@ -93,8 +93,8 @@ class Domain:
         d = cls(case.ndim, precision)
         for b in case.blocks:
             d.add_block(b.res, b.vertices)
-        for (a, sa, b2, sb) in case.connections:
-            d.connect(a, sa, b2, sb)
+        for conn in case.connections:
+            d.connect(*conn)
         for (blk, s, vals) in case.dirichlet:
             d.set_dirichlet(blk, s, vals)
         for (blk, s, um, vals) in case.outflow:

@@ -45,10 +45,12 @@ def test_host_side_validation(lib):
     verts = (C.c_double * 18)(*[0.0] * 18)
     bid = C.c_int32()
     assert lib.piso_block_add(h, res, verts, C.byref(bid)) == 0
-    assert lib.piso_connect(h, 0, 1, 0, 1) == 1          # same side twice
-    assert lib.piso_connect(h, 0, 1, 0, 2) == 1          # different axes
-    assert lib.piso_connect(h, 0, 1, 0, 0) == 0
-    assert lib.piso_connect(h, 0, 1, 0, 0) == 1          # already assigned
+    assert lib.piso_connect(h, 0, 1, 0, 1, 0, 0) == 1    # a fold that pairs each cell with itself
+    assert lib.piso_connect(h, 0, 1, 0, 0, 1, 0) == 1    # no axis exchange in 2D
+    assert lib.piso_connect(h, 0, 1, 0, 0, 0, 2) == 1    # 2D sides have one tangential axis
+    assert lib.piso_connect(h, 0, 1, 0, 0, 0, 0) == 0
+    assert lib.piso_connect(h, 0, 1, 0, 0, 0, 0) == 1    # already assigned
+    assert lib.piso_connect(h, 0, 2, 0, 2, 0, 1) == 0    # a fold (C-grid cut) with its axis reversed
     st = capi.Stats()
     assert lib.piso_step(h, None, None, None, None, 0.1, 0.1, None, None, None, C.byref(st)) == 7
     assert lib.piso_finalize(h, None) == 1               # y sides missing
