@@ -469,20 +469,17 @@ def time_statistics(dom, u, p, nu, steps, flush, peak):
                                   "frac": achieved / peak, "bytes_per_launch": d * N * w}}
 
 
-def run_batch(args):
+def time_batch(prec, kw, steps, warmup, with_adj, flush, threads=0, clocks=False):
     """The batch of 64 independent 2D cavity/channel simulations (sides 32..256,
     Re 100..2000, seed 4) advanced together: one persistent launch for the
-    forward step of all members and one for their adjoint."""
-    import numpy as np
+    forward step of all members and one for their adjoint, captured once in a
+    CUDA graph and replayed; the launch shape autotuned for the batch unless a
+    CTA width is given.  Returns sim-steps/s and the details."""
     import torch
     from paper_2505_16992_b300 import capi, workloads as W
     from paper_2505_16992_b300.solver import Batch, Domain
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     cases = W.batch2d()
-    prec = args.precision
-    rtol = 1e-6 if prec == "fp32" else 1e-10
-    opts = capi.default_options(adv_rtol=rtol, p_rtol=rtol, p_maxit=20000, adv_maxit=2000,
-                                block_threads=args.threads or 768)
+    opts = capi.default_options(p_maxit=20000, adv_maxit=2000, block_threads=threads or 768, **kw)
     doms = [Domain.from_case(c, prec, opts) for c in cases]
     us = [d.field(c.u0, 2) for d, c in zip(doms, cases)]
     ps = [d.field(c.p0) for d, c in zip(doms, cases)]
@@ -493,9 +490,7 @@ def run_batch(args):
     gs = [torch.randn(u.shape, generator=g0, dtype=u.dtype).cuda() for u in us]   # seeded adjoint seeds
     b = Batch(doms, opts)
     dts, nus = [c.dt for c in cases], [c.nu for c in cases]
-    with_adj = args.mode == "fwdadj"
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-
+    shape = b.autotune(us, ps, dts, nus, Ss) if not threads else (threads, None, None)
     gdu = [torch.empty_like(g) for g in gs]
     gdp = [torch.empty((d.N,), dtype=d.dtype, device="cuda") for d in doms]
     gdS = [torch.empty_like(g) for g in gs]
@@ -505,12 +500,12 @@ def run_batch(args):
         if with_adj:
             b.step_adjoint(gs, sync=False, du_in=gdu, dp_in=gdp, dS=gdS)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one()
     _, _, st = b.step(us, ps, dts, nus, Ss, u_out=uo, p_out=po)
+    if with_adj:
+        b.step_adjoint(gs, du_in=gdu, dp_in=gdp, dS=gdS)
     torch.cuda.synchronize()
-    # the forward and adjoint launches of a step captured once in a CUDA graph
-    # and replayed (the graph records the same arguments every replay)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     graph = torch.cuda.CUDAGraph()
@@ -526,8 +521,8 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     tot = 0.0
     clk_path = os.path.join(tempfile.gettempdir(), f"piso_clocks_{os.getpid()}.csv")
-    proc, fh = clocks_sampler_start(clk_path)
-    for _ in range(args.steps):
+    proc, fh = clocks_sampler_start(clk_path) if clocks else (None, None)
+    for _ in range(steps):
         flush.fill_(0.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -535,25 +530,40 @@ def run_batch(args):
         e1.record(stream)
         e1.synchronize()
         tot += e0.elapsed_time(e1) / 1e3
-    clocks = clocks_sampler_stop(proc, fh, clk_path, 0)
+    clk = clocks_sampler_stop(proc, fh, clk_path, 0) if clocks else None
     _, _, st_after = b.step(us, ps, dts, nus, Ss, u_out=uo, p_out=po)     # replayed steps still converge
-    assert all(s["status"] == "PISO_OK" for s in st_after), "batch step failed after graph replays"
+    assert all(x["status"] == "PISO_OK" for x in st_after), "batch step failed after graph replays"
     cells = sum(c.ncells for c in cases)
-    value = len(cases) * args.steps / tot
+    return {"sim_steps_per_s": len(cases) * steps / tot, "ms_per_step": 1e3 * tot / steps,
+            "cell_updates_per_s": cells * steps / tot, "cells": cells, "members": len(cases),
+            "launch": {"threads": shape[0], "ctas": shape[1], "autotuned": not threads},
+            "p_iters_max": max(max(x["p_iters"][:2]) for x in st),
+            "p_iters_min": min(min(x["p_iters"][:2]) for x in st),
+            "p_rounds_max": max(max(x["p_rounds"][:2]) for x in st), "clocks": clk}
+
+
+def run_batch(args):
+    """The batch workload as its own JSON line."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    prec = args.precision
+    rtol = 1e-6 if prec == "fp32" else 1e-10
+    with_adj = args.mode == "fwdadj"
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    r = time_batch(prec, dict(adv_rtol=rtol, p_rtol=rtol), args.steps, args.warmup, with_adj, flush,
+                   threads=args.threads, clocks=True)
     line = {"metric": "batched PISO sim-steps/s (64 independent 2D sims, fwd+adjoint)" if with_adj else
                       "batched PISO sim-steps/s (64 independent 2D sims, fwd)",
-            "value": value, "unit": "sim-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "value": r["sim_steps_per_s"], "unit": "sim-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": "batch64: 2D cavities/channels, side U{32..256}, Re U[100,2000], seed 4",
-                       "cells": cells, "krylov_rtol": rtol, "ctas": b.total_ctas if hasattr(b, "total_ctas") else None,
+                       "cells": r["cells"], "krylov_rtol": rtol, "launch": r["launch"],
                        "l2": "flushed between timed steps (256 MB write, untimed)",
                        "cuda_graph": "forward + adjoint launches of a step captured once, replayed per step"},
-            "cell_updates_per_s": cells * args.steps / tot,
-            "p_iters_max": max(max(s["p_iters"][:2]) for s in st),
-            "p_iters_min": min(min(s["p_iters"][:2]) for s in st),
-            "gpu_launches": args.steps * (2 if with_adj else 1),
-            "clocks": clocks}
+            "cell_updates_per_s": r["cell_updates_per_s"], "p_iters_max": r["p_iters_max"],
+            "p_iters_min": r["p_iters_min"], "gpu_launches": args.steps * (2 if with_adj else 1),
+            "clocks": r["clocks"]}
     print(json.dumps(line))
     return 0
 
@@ -620,6 +630,7 @@ def main():
                     help="skip timing the forward step on the channel with slanted (non-orthogonal) cells")
     ap.add_argument("--no-ilu-compare", action="store_true",
                     help="skip timing the BiCGStab preconditioners on the strongly stretched channel")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form timing in the default run")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline arm only: skip the other precision arms, the above-L2 channel, the gradient "
                          "paths, statistics and preconditioner comparisons")
@@ -804,6 +815,20 @@ def main():
         large["roofline"] = fwd_roofline(larm, lres, peak, peak_kind, ltraffic)
         del larm
 
+    # ---- the batched form (64 independent 2D simulations in one launch, CUDA
+    # graph, autotuned launch shape) in both precisions, at matched relative
+    # residuals of the Krylov solves (the divergence left by the correctors)
+    batch = None
+    if extras and not args.no_batch:
+        bsteps = max(5, args.steps // 4)
+        batch = {"workload": "batch64: 64 independent 2D cavities/channels, side U{32..256}, Re U[100,2000], "
+                             "seed 4; forward + adjoint per step, one CUDA graph replay",
+                 "fp32_rtol1e-6": time_batch("fp32", dict(adv_rtol=1e-6, p_rtol=1e-6), bsteps, 3, True, flush),
+                 "fp64_rtol1e-6": time_batch("fp64", dict(adv_rtol=1e-6, p_rtol=1e-6), bsteps, 3, True, flush),
+                 "fp32_refined1e-10": time_batch("fp32", dict(adv_rtol=1e-6, p_rtol=1e-6, p_refine_rtol=1e-10),
+                                                 bsteps, 3, True, flush),
+                 "fp64_rtol1e-10": time_batch("fp64", dict(adv_rtol=1e-10, p_rtol=1e-10), bsteps, 3, True, flush)}
+
     statistics_obj = None
     if not args.no_stats and extras:
         statistics_obj = time_statistics(dom, arm.u0, arm.p0, case.nu, max(5, args.steps // 3), flush, peak)
@@ -870,6 +895,8 @@ def main():
                                              pressure_precond=large["pressure_precond"])
         if parity is not None:
             line["parity"] = parity
+        if batch is not None:
+            line["batch"] = batch
         if ilu_cmp is not None:
             line["adv_precond_compare"] = ilu_cmp
         if no_cmp is not None:

@@ -349,6 +349,18 @@ piso_status piso_batch_step_adjoint(piso_batch* b, const void* const* du_out,
                                     void* const* dp_in, void* const* dS, double* dnu,
                                     void* stream, piso_stats* stats);
 
+/* Launch-shape autotuner of a batch (no counterpart in the paper; a B300
+ * execution choice): times one forward step of the given state (arrays of n
+ * device pointers / values as for piso_batch_step; the inputs are not modified
+ * and the members' boundary values are restored) with CTAs of 512 and 768
+ * threads, with all co-resident CTAs and with three quarters of them (each
+ * layout apportioned by expected work), and keeps the fastest for the batch's
+ * later launches.  threads_out, ctas_out, ms_out (host, may be NULL) receive
+ * the choice and its time.  Allocates trial outputs; synchronises the stream. */
+piso_status piso_batch_autotune(piso_batch* b, const void* const* u_in, const void* const* p_in, const double* dt,
+                                const double* nu, const void* const* S, void* stream, int32_t* threads_out,
+                                int32_t* ctas_out, double* ms_out);
+
 void piso_batch_destroy(piso_batch* b);
 
 /* ---- turbulence statistics (Sec. 2.5 "Operators for Turbulence Statistics";

@@ -38,12 +38,12 @@ OBJDIR = os.path.join(HERE, "_build")     # object cache (git-ignored), so an ed
 
 
 def _deps(src: str):
-    """Files a translation unit depends on: itself, every header of csrc/ and
-    include/piso.h; the C ABI unit also includes the host-side .inc files."""
+    """Files a translation unit depends on: itself and every header of csrc/;
+    the C ABI unit also includes include/piso.h and the host-side .inc files."""
     csrc = os.path.join(HERE, "csrc")
-    deps = [src, INCLUDE] + [os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith(".cuh")]
+    deps = [src] + [os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith(".cuh")]
     if os.path.basename(src) == "piso_capi.cu":
-        deps += [os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith(".inc")]
+        deps += [INCLUDE] + [os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith(".inc")]
     return deps
 
 

@@ -78,6 +78,9 @@ _SIGS = {
                                   C.POINTER(_P), _P, C.POINTER(Stats)]),
     "piso_batch_step_adjoint": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                           C.POINTER(_P), _D, _P, C.POINTER(Stats)]),
+    "piso_batch_autotune": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), _D, _D, C.POINTER(_P), _P,
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                      _D]),
     "piso_batch_destroy": (None, [_P]),
     "piso_stats_create": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(_P)]),
     "piso_stats_record_size": (C.c_int32, [_P]),

@@ -129,7 +129,11 @@ __device__ void fwd_group(const FwdCall<real>& A, const SolverOpts& o, Group& g)
   const bool lines = A.p_line && o.line_cap > 0;
   LinePre<real> LP{};
   if (lines) LP = line_setup<real, ND>(D, g, o, A.lfa, A.lfm, A.lfc);
-  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap), lines ? &LP : nullptr, D.nbfr};
+  // neighbour frames only in the extended instantiation (a compile-time null
+  // elsewhere, so the plain Krylov rows carry no frame test)
+  const int16_t* frames = nullptr;
+  if constexpr (MODE == 2) frames = D.nbfr;
+  const Ctx<real, ND> X{D, g, lo, hi, N, build_nbt<ND>(D, lo, hi, o.nbt_cap), lines ? &LP : nullptr, frames};
   const real* J = reinterpret_cast<const real*>(D.J);
   const real* T = reinterpret_cast<const real*>(D.T);
   const real* AL = reinterpret_cast<const real*>(D.alpha);

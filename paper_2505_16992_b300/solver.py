@@ -236,6 +236,18 @@ class Batch:
         capi.check(rc, None)
         return u_out, p_out, ([s.as_dict() for s in st] if st is not None else None)
 
+    def autotune(self, us, ps, dts, nus, Ss=None, stream=None):
+        """Pick the fastest CTA width and count for this batch on this state;
+        returns (threads, ctas, ms)."""
+        n = len(self.domains)
+        Ss = [None] * n if Ss is None else Ss
+        t, c, ms = C.c_int32(), C.c_int32(), C.c_double()
+        rc = self.lib.piso_batch_autotune(self.h, self._ptrs(us), self._ptrs(ps), (C.c_double * n)(*dts),
+                                          (C.c_double * n)(*nus), self._ptrs(Ss), _stream_ptr(stream), C.byref(t),
+                                          C.byref(c), C.byref(ms))
+        capi.check(rc, None)
+        return t.value, c.value, ms.value
+
     def step_adjoint(self, du_out, dp_out=None, stream=None, sync=True, du_in=None, dp_in=None, dS=None):
         """Adjoint of every member's last step.  sync=False enqueues only (no
         statistics or dnu read back; usable inside CUDA-graph capture)."""

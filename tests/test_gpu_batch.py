@@ -176,3 +176,46 @@ def test_batch_forward_and_adjoint_graph_and_back_to_back_enqueues():
     for i in range(len(cases)):
         assert torch.equal(uo[i], ref_u[i]) and torch.equal(po[i], ref_p[i]), i
         assert torch.equal(du[i], ref_du[i]) and torch.equal(dS[i], ref_dS[i]), i
+
+
+def test_batch_autotune_keeps_parity_and_inputs():
+    """The batch autotuner times the forward step with 512- and 768-thread
+    CTAs and two CTA totals, restores the state, and the chosen layout steps
+    every member as the oracle does (forward and adjoint)."""
+    cases = W.batch2d(count=6, seed=9, nmin=8, nmax=40)
+    doms, us, ps, Ss = _members(cases)
+    b = Batch(doms, capi.default_options(adv_rtol=1e-13, p_rtol=1e-13))
+    u_before = [host(u).copy() for u in us]
+    dts, nus = [c.dt for c in cases], [c.nu for c in cases]
+    threads, ctas, ms = b.autotune(us, ps, dts, nus, Ss)
+    assert threads in (512, 768) and ctas >= len(cases) and ms > 0
+    assert all(np.array_equal(host(u), u0) for u, u0 in zip(us, u_before))
+    with pytest.raises(capi.PisoError):
+        b.step_adjoint([torch.ones_like(u) for u in us])        # the trials are not a step to differentiate
+    uo, po, st = b.step(us, ps, dts, nus, Ss)
+    rng = np.random.default_rng(2)
+    gus = [rng.standard_normal((2, c.ncells)) for c in cases]
+    du, dp, dS, dnu, ast = b.step_adjoint([to_dev(d, g, 2) for d, g in zip(doms, gus)])
+    for i, c in enumerate(cases):
+        assert st[i]["status"] == "PISO_OK" and ast[i]["status"] == "PISO_OK", (i, st[i], ast[i])
+        m = O.mesh_from_case(c)
+        u1, p1, tape = O.piso_step(m, c.u0, c.p0, c.dt, c.nu, c.S)
+        assert rel_err(host(uo[i]), u1) <= 1e-10, i
+        gu, gp, gS, gnu = O.piso_step_adjoint(m, tape, gus[i], np.zeros(c.ncells))
+        assert rel_err(host(du[i]), gu) <= 1e-8, i
+
+
+def test_batch_fp32_refined_pressure_reaches_fp64_tolerance():
+    """The mixed-precision batch with FP64-refined pressure solves reaches the
+    same relative residual as the FP64 batch (1e-10 of each right-hand side)
+    and the FP64 oracle's velocity to FP32 rounding."""
+    cases = W.batch2d(count=5, seed=10, nmin=16, nmax=48)
+    doms, us, ps, Ss = _members(cases, "fp32", adv_rtol=1e-7, p_rtol=1e-6, p_refine_rtol=1e-10)
+    b = Batch(doms, capi.default_options(adv_rtol=1e-7, p_rtol=1e-6, p_refine_rtol=1e-10))
+    uo, po, st = b.step(us, ps, [c.dt for c in cases], [c.nu for c in cases], Ss)
+    for i, c in enumerate(cases):
+        assert st[i]["status"] == "PISO_OK", (i, st[i])
+        assert all(res <= 1e-10 * rhs * 1.01 for res, rhs in zip(st[i]["p_resid"][:2], st[i]["p_rhs_norm"][:2])), st[i]
+        m = O.mesh_from_case(c)
+        u1, p1, _ = O.piso_step(m, c.u0, c.p0, c.dt, c.nu, c.S)
+        assert rel_err(host(uo[i]), u1) <= 2e-5, (i, rel_err(host(uo[i]), u1))
