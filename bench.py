@@ -631,6 +631,8 @@ def main():
     ap.add_argument("--no-ilu-compare", action="store_true",
                     help="skip timing the BiCGStab preconditioners on the strongly stretched channel")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form timing in the default run")
+    ap.add_argument("--size", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                    help="channel resolution in place of the workload's (same recipe)")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline arm only: skip the other precision arms, the above-L2 channel, the gradient "
                          "paths, statistics and preconditioner comparisons")
@@ -668,6 +670,9 @@ def main():
     stretched = args.workload == "channel3d-stretched"      # the case for the ILU(0) BiCGStab (App. A.5)
     sheared = args.workload == "channel3d-sheared"          # a non-orthogonal grid (App. A.2)
     extra = dict(gamma=3.0, dt=0.2) if stretched else (dict(shear=0.5) if sheared else {})
+    if args.size:
+        sizes[args.workload] = tuple(args.size)
+    headline = headline and sizes[args.workload] == (64, 48, 32)
     case = W.channel3d(*sizes[args.workload], **extra)
     if sheared:
         args.mode = "fwd"              # the adjoint step is not provided on non-orthogonal meshes
