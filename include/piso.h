@@ -99,7 +99,9 @@ typedef struct {
                             PISO_PRECOND_JACOBI; PISO_PRECOND_LINE: the block diagonal of -P made of
                             its y-lines inside each block, solved exactly (Thomas factors formed once
                             per step; the CG iteration then takes two group barriers instead of one).
-                            Batches (piso_batch_*) always use Jacobi. */
+                            In batches (piso_batch_*) each member keeps the choice its own
+                            options resolved to (the line form needs launch-wide staging for two
+                            of the longest such lines; without room every member uses Jacobi). */
   int32_t adv_precond;   /* preconditioner of the advection-diffusion BiCGStab (App. A.5: incomplete
                             LU, for grids with strongly varying cell sizes, enabled per case, and
                             optionally only after the plain solve failed):
