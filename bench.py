@@ -28,12 +28,17 @@ L2_FLUSH_BYTES = 256 << 20          # > 126 MB L2
 # algorithmic traffic model: every array a phase touches, counted once per
 # phase (neighbour re-reads are cache hits), in words per cell
 # ---------------------------------------------------------------------------
-def cg_words_per_cell(d: int, it_p: int, line: bool) -> float:
+def cg_words_per_cell(d: int, it_p: int, line: bool, fused: bool = False) -> float:
     """Stored-array words per cell of one pressure CG solve (start + iterations).
     Jacobi (one phase per iteration): r, w, s, 1/diag, p, x, P faces read; p, x,
-    s, r, w written.  y-line (two phases): phase A reads u, w, r, x, p, s and the
-    three line factors and writes p, s, x, r, u; phase B reads u and the P faces
-    and writes w."""
+    s, r, w written.  y-line, split form (two phases): phase A reads u, w, r, x,
+    p, s and the three line factors and writes p, s, x, r, u; phase B reads u and
+    the P faces and writes w.  y-line, fused form (one phase; u, p, x, the line
+    factors and the P faces stay in shared memory for the whole solve): r, w, s
+    read, r, w, s, x written; its start reads x, b, the P faces and the three
+    factors and writes r0, then reads r0 and writes w0."""
+    if line and fused:
+        return (d + 7) + 2 + it_p * 7
     if line:
         return (d + 7) + (d + 2) + it_p * (14 + d + 2)
     return (d + 4) + (d + 3) + it_p * (d + 11)
@@ -52,7 +57,8 @@ def bicg_words_per_cell(d: int, it_a: int, ilu: bool) -> float:
     return it_a * (21 * d + 2)
 
 
-def fwd_words_per_cell(d: int, adv_iters, p_iters, line: bool = False, ilu: bool = False) -> float:
+def fwd_words_per_cell(d: int, adv_iters, p_iters, line: bool = False, ilu: bool = False,
+                       fused: bool = False) -> float:
     """Stored-array words per cell one forward launch touches (each array once
     per phase; neighbour re-reads are cache hits).  One line per kernel phase."""
     it_a = max(adv_iters) if adv_iters else 0
@@ -65,13 +71,14 @@ def fwd_words_per_cell(d: int, adv_iters, p_iters, line: bool = False, ilu: bool
         w += d + 3                    # C2: divergence, x0
         if line and k == 0:
             w += 5                    # line factors: diag P, +y faces -> fa, fm, fc
-        w += cg_words_per_cell(d, it_p, line)
+        w += cg_words_per_cell(d, it_p, line, fused)
         w += d * d + 2 * d + 2        # C4: correction
     w += 3                            # final pressure
     return w
 
 
-def adj_words_per_cell(d: int, adv_iters, p_iters, line: bool = False, ilu: bool = False) -> float:
+def adj_words_per_cell(d: int, adv_iters, p_iters, line: bool = False, ilu: bool = False,
+                       fused: bool = False) -> float:
     it_a = max(adv_iters) if adv_iters else 0
     w = 6 * d + 3                     # R0 extra on the first pass: rebuild P, clear accumulators
     if line and any(p_iters):
@@ -79,7 +86,7 @@ def adj_words_per_cell(d: int, adv_iters, p_iters, line: bool = False, ilu: bool
     for it_p in p_iters:
         w += d * d + 2 * d + 4        # R0: W = T gu / A, dL/dA
         w += d + 3                    # R1: -G^T W
-        w += cg_words_per_cell(d, it_p, line)   # CG on P
+        w += cg_words_per_cell(d, it_p, line, fused)   # CG on P
         w += d * d + 7 * d + 6        # R3: d(alpha/A), div^T y, gg, dL/dA, dL/drhs0
         w += 9 * d                    # R4: -H^T gg, dL/dH
     w += 6 * d + 3                    # R5: start of the C^T solve
@@ -287,6 +294,8 @@ class Arm:
         if pc == capi.PISO_PRECOND_AUTO:
             pc = capi.PISO_PRECOND_LINE if dom.uses_line_precond() else capi.PISO_PRECOND_JACOBI
         self.pc_used = "y-line" if pc == capi.PISO_PRECOND_LINE else "jacobi"
+        # y-line CG iteration form: one group barrier per iteration (fused) or two
+        self.line_form = None if self.pc_used != "y-line" else ("fused" if dom.uses_fused_lines() else "split")
         self.g = torch.ones_like(self.u0)          # adjoint seed dL/du^{n+1} = 1
         self.w = 4 if prec == "fp32" else 8
 
@@ -374,6 +383,7 @@ def arm_summary(arm, res, with_adj):
     out = {"fwd_steps_per_s": 1e3 * len(res["fwd_ms"]) / sum(res["fwd_ms"]),
            "fwd_ms": statistics.mean(res["fwd_ms"]),
            "launch": {"threads": arm.shape[0], "ctas": arm.shape[1]}, "pressure_precond": arm.pc_used,
+           "line_form": arm.line_form,
            "iterations": iter_summary(res["stats"], res["adj_stats"], d)}
     if with_adj:
         out["fwdadj_steps_per_s"] = 1e3 * len(res["step_ms"]) / sum(res["step_ms"])
@@ -389,7 +399,7 @@ def fwd_roofline(arm, res, peak, peak_kind, traffic=None, extra_words=0.0):
     byts = 0.0
     for st in res["stats"]:
         words = fwd_words_per_cell(d, st["adv_iters"][:d], st["p_iters"][:2], line=arm.pc_used == "y-line",
-                                   ilu=st["adv_precond_used"] == 1) + extra_words
+                                   ilu=st["adv_precond_used"] == 1, fused=arm.line_form == "fused") + extra_words
         byts += words * N * arm.w
     achieved = byts / (sum(res["fwd_ms"]) / 1e3) / 1e9
     words_mean = byts / len(res["stats"]) / (N * arm.w)
@@ -622,6 +632,8 @@ def main():
     ap.add_argument("--refine", type=float, default=0.0, help="FP32: FP64-refined pressure tolerance")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "line"],
                     help="pressure CG preconditioner (auto: the autotuner times both on anisotropic grids)")
+    ap.add_argument("--line-split", action="store_true",
+                    help="y-line CG with two group barriers per iteration even where the fused form fits")
     ap.add_argument("--adv-precond", default="none", choices=["none", "ilu", "ilu_on_failure"],
                     help="BiCGStab preconditioner of the predictor solve (ILU(0), or ILU(0) after a failed plain solve)")
     ap.add_argument("--nonortho", type=int, default=1,
@@ -680,7 +692,8 @@ def main():
     rtol = 1e-6 if prec == "fp32" else 1e-10
     pc_code = {"auto": capi.PISO_PRECOND_AUTO, "jacobi": capi.PISO_PRECOND_JACOBI, "line": capi.PISO_PRECOND_LINE}
     opts_kw = dict(adv_rtol=rtol, p_rtol=rtol, p_refine_rtol=args.refine, p_precond=pc_code[args.precond],
-                   adv_precond=ADV_PRECOND[args.adv_precond], n_nonortho=args.nonortho if sheared else 0)
+                   adv_precond=ADV_PRECOND[args.adv_precond], n_nonortho=args.nonortho if sheared else 0,
+                   p_line_split=1 if args.line_split else 0)
     d, N = case.ndim, case.ncells
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     with_adj = args.mode == "fwdadj"
@@ -878,7 +891,8 @@ def main():
                        "state": "advances: each timed step starts from the previous step's output",
                        "parallelism": "replicas" if world > 1 else "single",
                        "launch": {"threads": arm.shape[0], "ctas": arm.shape[1], "autotuned": args.threads == 0},
-                       "pressure_precond": arm.pc_used, "adv_precond": args.adv_precond},
+                       "pressure_precond": arm.pc_used, "line_form": arm.line_form,
+                       "adv_precond": args.adv_precond},
             "iterations": summ["iterations"],
             "fwd_ms": summ["fwd_ms"],
             "cell_updates_per_s": value * N,

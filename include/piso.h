@@ -98,7 +98,7 @@ typedef struct {
                             k != y, as on wall-refined channels) and Jacobi otherwise;
                             PISO_PRECOND_JACOBI; PISO_PRECOND_LINE: the block diagonal of -P made of
                             its y-lines inside each block, solved exactly (Thomas factors formed once
-                            per step; the CG iteration then takes two group barriers instead of one).
+                            per step; see p_line_split for how its CG iteration synchronises).
                             In batches (piso_batch_*) each member keeps the choice its own
                             options resolved to (the line form needs launch-wide staging for two
                             of the longest such lines; without room every member uses Jacobi). */
@@ -134,6 +134,14 @@ typedef struct {
                             cross terms); the step record holds the iterates, hence the limit 4.
                             Batches and pred_grad_p = 1 reject such meshes (PISO_EINVAL).
                             Ignored on orthogonal meshes. */
+  int32_t p_line_split;  /* how a y-line preconditioned CG iterates.  0 (default): with one group
+                            barrier per iteration wherever every CTA of the launch can hold its own
+                            lines and the lines next to them (halo lines) in shared memory: each
+                            CTA then also solves its halo lines, so w = A u needs no second
+                            barrier (the same recurrences; results differ from the split form
+                            only by rounding).  1: always two barriers per iteration (a line phase,
+                            then w = A u).  Domains whose lines do not fit, and batches, use the
+                            split form; piso_pressure_line_fused reports which one a domain runs. */
 } piso_options;
 
 /* Values of piso_options.p_precond. */
@@ -230,6 +238,13 @@ piso_status piso_get_options(const piso_domain* d, piso_options* opts);
  * or PISO_PRECOND_LINE; PISO_PRECOND_AUTO resolved from the grid), or -1 for a
  * NULL or unfinalized domain. */
 int32_t piso_pressure_precond(const piso_domain* d);
+
+/* 1 when the domain's next step runs its y-line preconditioned CG in the
+ * fused form (one group barrier per iteration; see p_line_split), 0 when it
+ * runs the split form or the Jacobi CG, -1 for a NULL or unfinalized domain.
+ * The plan behind the fused form (own and halo lines per CTA, neighbour slots)
+ * is built on the host whenever the launch layout changes. */
+int32_t piso_pressure_line_fused(const piso_domain* d);
 
 int64_t piso_num_cells(const piso_domain* d);
 int32_t piso_num_boundary_faces(const piso_domain* d);

@@ -80,6 +80,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src, tmp_obj, p in procs:
         out, err = p.communicate()
         logs.append(out + err)
+        with open(_obj(src)[:-2] + ".log", "w") as f:   # ptxas resource usage of the unit's kernels
+            f.write(out + err)
         if p.returncode != 0:
             failed = True
         else:

@@ -24,7 +24,7 @@ class Options(C.Structure):
                 ("p_maxit", C.c_int32), ("block_threads", C.c_int32), ("ctas", C.c_int32),
                 ("timeout_s", C.c_double), ("fault_withhold_cta", C.c_int32), ("p_refine_rtol", C.c_double),
                 ("p_inner_rtol", C.c_double), ("grad_paths", C.c_int32), ("p_precond", C.c_int32),
-                ("adv_precond", C.c_int32), ("n_nonortho", C.c_int32)]
+                ("adv_precond", C.c_int32), ("n_nonortho", C.c_int32), ("p_line_split", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -59,6 +59,7 @@ _SIGS = {
     "piso_set_options": (C.c_int, [_P, C.POINTER(Options)]),
     "piso_get_options": (C.c_int, [_P, C.POINTER(Options)]),
     "piso_pressure_precond": (C.c_int32, [_P]),
+    "piso_pressure_line_fused": (C.c_int32, [_P]),
     "piso_num_cells": (C.c_int64, [_P]),
     "piso_num_boundary_faces": (C.c_int32, [_P]),
     "piso_tape_bytes": (C.c_size_t, [_P]),

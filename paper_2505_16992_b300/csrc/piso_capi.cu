@@ -111,6 +111,15 @@ struct piso_domain {
   IluTab ilu_tab{};
   bool ilu_ready = false;      // tables match (ncta, threads, ownership) of the launches
   int ilu_key[3] = {-1, -1, -1};
+  // plan of the fused y-line CG iteration for the current CTA count
+  void* lf_buf = nullptr;
+  bool lf_ready = false;
+  int lf_ncta = -1;
+  int32_t lf_own_cap = 0, lf_slot_cap = 0, lf_bytes = 0;
+  const int32_t* lf_off = nullptr;
+  const int32_t* lf_nown = nullptr;
+  const int32_t* lf_lines = nullptr;
+  const int16_t* lf_nbs = nullptr;
   bool has_cross = false;      // some cell has non-zero cross metrics (accepted with n_nonortho >= 1)
   bool twisted = false;        // some joint exchanges or reverses axes (neighbour frames are stored)
   int16_t* nbfr = nullptr;     // [2d][N] neighbour frames on the device (twisted domains)
@@ -386,14 +395,15 @@ void fill_fwd_call(piso_domain* d, FwdCall<real>& c, const void* u_in, const voi
 }
 
 #ifdef PISO_TRACE
-// Phase-timing ring of trace builds: [PISO_TRACE_LEN][4] stamps in device
+// Phase-timing ring of trace builds: [PISO_TRACE_LEN][PISO_TRACE_STAMPS] stamps in device
 // memory, allocated on first use and handed to every kernel through the solver
 // options (the kernels of all translation units write this one buffer).
 uint64_t* g_trace_buf = nullptr;
 uint64_t* trace_buffer() {
   if (!g_trace_buf) {
-    if (cudaMalloc((void**)&g_trace_buf, sizeof(uint64_t) * 4 * PISO_TRACE_LEN) != cudaSuccess) g_trace_buf = nullptr;
-    else cudaMemset(g_trace_buf, 0, sizeof(uint64_t) * 4 * PISO_TRACE_LEN);
+    if (cudaMalloc((void**)&g_trace_buf, sizeof(uint64_t) * PISO_TRACE_STAMPS * PISO_TRACE_LEN) != cudaSuccess)
+      g_trace_buf = nullptr;
+    else cudaMemset(g_trace_buf, 0, sizeof(uint64_t) * PISO_TRACE_STAMPS * PISO_TRACE_LEN);
   }
   return g_trace_buf;
 }
@@ -416,6 +426,13 @@ SolverOpts solver_opts(const piso_options& o) {
   s.p_inner_rtol = o.p_inner_rtol;
   s.grad_paths = o.grad_paths;
   s.ilu_soff = -1;
+  s.lf_off = nullptr;
+  s.lf_nown = nullptr;
+  s.lf_lines = nullptr;
+  s.lf_nbs = nullptr;
+  s.lf_own_cap = 0;
+  s.lf_slot_cap = 0;
+  s.lf_bytes = 0;
 #ifdef PISO_TRACE
   s.trace = trace_buffer();
 #else
@@ -424,9 +441,12 @@ SolverOpts solver_opts(const piso_options& o) {
   return s;
 }
 
-// Dynamic shared memory for the per-CTA neighbour table: 2*ndim int32 per cell
-// of the largest CTA range, when that fits beside the static shared memory.
-constexpr size_t NBT_MAX_BYTES = 160 * 1024;
+// Dynamic shared memory of a step launch (neighbour table, line staging, ILU
+// sweep area), at most this much.  Every step kernel's static shared memory
+// plus this must stay within the 227 KB a CTA may opt into (the largest static
+// area, the FP32 non-orthogonal adjoint's, is ~68 KB; tests/test_capi_symbols.py
+// checks the sum against the build's resource report).
+constexpr size_t NBT_MAX_BYTES = 156 * 1024;
 
 size_t nbt_bytes(int ndim, int64_t N, int ncta, int32_t* cap) {
   const int64_t per = (N + ncta - 1) / ncta;
@@ -477,7 +497,22 @@ size_t launch_smem(const piso_domain* d, int ncta, SolverOpts* o) {
   cap = std::min<size_t>(cap, (size_t)(std::min<int64_t>(lines_per, LINE_LBMAX) + 1) * lmax);
   cap = std::max<size_t>(cap, 2 * (size_t)lmax);
   o->line_cap = (int32_t)cap;
-  size_t total = nbt + LINE_ARRAYS * e * cap + ints;
+  size_t stage = LINE_ARRAYS * e * cap;
+  // the fused CG's arrays alias the staging arrays (each fused solve re-fills them)
+  if (d->lf_ready && d->lf_ncta == ncta && !d->opts.p_line_split) {
+    const size_t st2 = std::max(stage, (size_t)d->lf_bytes);
+    if (nbt + st2 + ints + (ilu ? 16 + ilu : 0) <= NBT_MAX_BYTES) {
+      stage = st2;
+      o->lf_off = d->lf_off;
+      o->lf_nown = d->lf_nown;
+      o->lf_lines = d->lf_lines;
+      o->lf_nbs = d->lf_nbs;
+      o->lf_own_cap = d->lf_own_cap;
+      o->lf_slot_cap = d->lf_slot_cap;
+      o->lf_bytes = d->lf_bytes;
+    }
+  }
+  size_t total = nbt + stage + ints;
   if (ilu) {
     total = al16(total);
     o->ilu_soff = (int32_t)total;
@@ -641,6 +676,157 @@ piso_status check_ilu(piso_domain* d) {
   return PISO_OK;
 }
 
+// Plan of the fused y-line CG iteration (cg_pressure_fused) for d->ncta CTAs:
+// each CTA's own lines, the halo lines that hold the other neighbours of its
+// cells, and the shared-memory slot of every neighbour of every own cell
+// (cell y of local line l at slot y * P + l, P = local lines | 1).  Own lines
+// are consecutive runs of the domain's lines walked block by block in strips
+// of tx columns along z (tx >= nx: the plain x-then-z order), so a CTA owns a
+// compact patch of columns and few halo lines; of the strip widths tried the
+// one with the smallest shared footprint is kept.  No plan (lf_ready false)
+// when the y-line preconditioner is off, two-phase iterations are asked for,
+// or no CTA layout fits in shared memory.
+template <int ND>
+static piso_status build_linefuse_nd(piso_domain* d) {
+  const DomStatic& S = d->h_static;
+  const int ncta = d->ncta;
+  const int32_t nl = S.nlines, lmax = std::max(S.lmax, 1), N = d->N;
+  const size_t e = d->elem;
+  constexpr int NS = 2 * ND;
+  // the own cells alone must fit (u, p, x, face coefficients, neighbour slots)
+  const int64_t own_min = (int64_t)((nl + ncta - 1) / ncta) * lmax;
+  if (nl < ncta || own_min * ((3 + NS) * e + NS * 2) > (int64_t)NBT_MAX_BYTES) return PISO_OK;
+  std::vector<int32_t> cline(N), cy(N), nbr((size_t)N * NS);
+  for (int32_t i = 0; i < N; i++) {
+    const Cell c = locate<ND>(S, i);
+    cline[i] = line_of(S, c);
+    cy[i] = c.y;
+    for (int q = 0; q < NS; q++) nbr[(size_t)i * NS + q] = c.nb[q];
+  }
+  auto order_for = [&](int tx, std::vector<int32_t>& ord) {
+    ord.clear();
+    for (int b = 0; b < S.nblocks; b++) {
+      const BlockInfo& B = S.blk[b];
+      const int w = std::min(tx, B.nx);
+      for (int x0 = 0; x0 < B.nx; x0 += w)
+        for (int z = 0; z < B.nz; z++)
+          for (int x = x0; x < std::min(x0 + w, B.nx); x++) ord.push_back(B.line0 + x + B.nx * z);
+    }
+  };
+  struct Layout {
+    std::vector<int32_t> off, nown, lines;
+    int32_t own_cap = 0, slot_cap = 0, max_loc = 0;
+    size_t bytes = 0;
+  };
+  std::vector<int32_t> mark(nl, -1), loc(nl, 0), ord;
+  auto layout_for = [&](const std::vector<int32_t>& ord_, Layout& Lo) {
+    Lo.off.assign(1, 0);
+    Lo.nown.clear();
+    Lo.lines.clear();
+    Lo.own_cap = Lo.slot_cap = Lo.max_loc = 0;
+    std::fill(mark.begin(), mark.end(), -1);
+    for (int r = 0; r < ncta; r++) {
+      const int32_t a = (int32_t)(((int64_t)nl * r) / ncta), z = (int32_t)(((int64_t)nl * (r + 1)) / ncta);
+      const size_t base = Lo.lines.size();
+      for (int32_t t = a; t < z; t++) {
+        mark[ord_[t]] = r;
+        Lo.lines.push_back(ord_[t]);
+      }
+      for (int32_t t = a; t < z; t++) {
+        const LineDesc ld = line_desc(S, ord_[t]);
+        for (int32_t y = 0; y < ld.len; y++) {
+          const int32_t i = ld.start + y * ld.stride;
+          for (int q = 0; q < NS; q++) {
+            const int32_t j = nbr[(size_t)i * NS + q];
+            if (j < 0 || mark[cline[j]] == r) continue;
+            mark[cline[j]] = r;
+            Lo.lines.push_back(cline[j]);
+          }
+        }
+      }
+      const int32_t n_own = z - a, n_loc = (int32_t)(Lo.lines.size() - base);
+      Lo.nown.push_back(n_own);
+      Lo.off.push_back((int32_t)Lo.lines.size());
+      Lo.own_cap = std::max(Lo.own_cap, n_own * lmax);
+      Lo.slot_cap = std::max(Lo.slot_cap, (n_loc | 1) * lmax);
+      Lo.max_loc = std::max(Lo.max_loc, n_loc);
+    }
+    Lo.bytes = ((e * (5 * (size_t)Lo.slot_cap + (3 + NS) * (size_t)Lo.own_cap) + 4 * (size_t)Lo.slot_cap +
+                 2 * NS * (size_t)Lo.own_cap) + 15) & ~size_t(15);
+  };
+  Layout best, cur;
+  bool have = false;
+  int maxnx = 1;
+  for (int b = 0; b < S.nblocks; b++) maxnx = std::max(maxnx, S.blk[b].nx);
+  for (int tx = 1;; tx *= 2) {
+    const int t = std::min(tx, maxnx);
+    order_for(t, ord);
+    layout_for(ord, cur);
+    const bool ok = cur.max_loc <= LINE_LBMAX && cur.slot_cap <= 32767;
+    if (ok && (!have || cur.bytes < best.bytes)) {
+      best = cur;
+      have = true;
+    }
+    if (t >= maxnx) break;
+  }
+  if (!have || best.bytes > NBT_MAX_BYTES) return PISO_OK;
+  // neighbour slots of the own cells, [ncta][NS][own_cap], own cell y * n_own + t
+  const int32_t oc = best.own_cap;
+  std::vector<int16_t> nbs((size_t)ncta * NS * oc, (int16_t)-1);
+  for (int r = 0; r < ncta; r++) {
+    const int32_t a = best.off[r], n_loc = best.off[r + 1] - a, n_own = best.nown[r], P = n_loc | 1;
+    for (int32_t t = 0; t < n_loc; t++) loc[best.lines[a + t]] = t;
+    for (int32_t t = 0; t < n_own; t++) {
+      const LineDesc ld = line_desc(S, best.lines[a + t]);
+      for (int32_t y = 0; y < ld.len; y++) {
+        const int32_t i = ld.start + y * ld.stride, k = y * n_own + t;
+        for (int q = 0; q < NS; q++) {
+          const int32_t j = nbr[(size_t)i * NS + q];
+          if (j >= 0) nbs[((size_t)r * NS + q) * oc + k] = (int16_t)(cy[j] * P + loc[cline[j]]);
+        }
+      }
+    }
+  }
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t o_off = 0, o_nown = al(sizeof(int32_t) * (ncta + 1)), o_lines = o_nown + al(sizeof(int32_t) * ncta),
+               o_nbs = o_lines + al(sizeof(int32_t) * best.lines.size()), total = o_nbs + al(sizeof(int16_t) * nbs.size());
+  if (d->lf_buf) {
+    CUDA_TRY(d, cudaDeviceSynchronize());   // no launch in flight may still read the old plan
+    CUDA_TRY(d, cudaFree(d->lf_buf));
+    d->lf_buf = nullptr;
+  }
+  CUDA_TRY(d, cudaMalloc(&d->lf_buf, total));
+  char* bb = (char*)d->lf_buf;
+  CUDA_TRY(d, cudaMemcpy(bb + o_off, best.off.data(), sizeof(int32_t) * (ncta + 1), cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(bb + o_nown, best.nown.data(), sizeof(int32_t) * ncta, cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(bb + o_lines, best.lines.data(), sizeof(int32_t) * best.lines.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(d, cudaMemcpy(bb + o_nbs, nbs.data(), sizeof(int16_t) * nbs.size(), cudaMemcpyHostToDevice));
+  d->lf_off = (const int32_t*)(bb + o_off);
+  d->lf_nown = (const int32_t*)(bb + o_nown);
+  d->lf_lines = (const int32_t*)(bb + o_lines);
+  d->lf_nbs = (const int16_t*)(bb + o_nbs);
+  d->lf_own_cap = best.own_cap;
+  d->lf_slot_cap = best.slot_cap;
+  d->lf_bytes = (int32_t)best.bytes;
+  d->lf_ncta = ncta;
+  d->lf_ready = true;
+  return PISO_OK;
+}
+
+piso_status build_linefuse(piso_domain* d) {
+  if (!d->p_line || d->opts.p_line_split || d->twisted) return PISO_OK;
+  if (d->lf_ready && d->lf_ncta == d->ncta) return PISO_OK;
+  d->lf_ready = false;
+  return d->ndim == 3 ? build_linefuse_nd<3>(d) : build_linefuse_nd<2>(d);
+}
+
+// Launch-layout tables: ILU(0) levels and the fused y-line plan.
+piso_status build_tables(piso_domain* d) {
+  const piso_status s = build_ilu(d);
+  if (s) return s;
+  return build_linefuse(d);
+}
+
 int max_coresident(const void* kernel, int threads, int* sms_out) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -667,7 +853,7 @@ piso_status choose_shape(piso_domain* d) {
   d->threads = threads;
   d->ncta = want;
   d->sms = sms;
-  return build_ilu(d);
+  return build_tables(d);
 }
 
 piso_status collect_stats(piso_domain* d, piso_stats* st) {
@@ -760,6 +946,7 @@ void piso_default_options(piso_options* o) {
   o->p_inner_rtol = 1e-4;
   o->grad_paths = PISO_GRAD_ADV | PISO_GRAD_P;
   o->p_precond = PISO_PRECOND_AUTO;
+  o->p_line_split = 0;
   o->adv_precond = PISO_ADV_PRECOND_NONE;
   o->n_nonortho = 0;
 }
@@ -888,6 +1075,7 @@ static piso_status validate_options(piso_domain* d, const piso_options* o) {
   if (o->grad_paths & ~(PISO_GRAD_ADV | PISO_GRAD_P)) return fail(d, PISO_EINVAL, "grad_paths: unknown bits");
   if (o->p_precond < PISO_PRECOND_AUTO || o->p_precond > PISO_PRECOND_LINE)
     return fail(d, PISO_EINVAL, "p_precond must be PISO_PRECOND_AUTO, _JACOBI or _LINE");
+  if (o->p_line_split != 0 && o->p_line_split != 1) return fail(d, PISO_EINVAL, "p_line_split must be 0 or 1");
   if (o->adv_precond < PISO_ADV_PRECOND_NONE || o->adv_precond > PISO_ADV_PRECOND_ILU_ON_FAILURE)
     return fail(d, PISO_EINVAL, "adv_precond must be PISO_ADV_PRECOND_NONE, _ILU or _ILU_ON_FAILURE");
   if (o->n_nonortho < 0 || o->n_nonortho > NONORTHO_MAX)
@@ -1213,6 +1401,13 @@ int32_t piso_pressure_precond(const piso_domain* d) {
   return d->p_line ? PISO_PRECOND_LINE : PISO_PRECOND_JACOBI;
 }
 
+int32_t piso_pressure_line_fused(const piso_domain* d) {
+  if (!d || !d->finalized) return -1;
+  SolverOpts so = solver_opts(d->opts);
+  launch_smem(d, d->ncta, &so);
+  return d->p_line && so.lf_off ? 1 : 0;
+}
+
 int64_t piso_num_cells(const piso_domain* d) { return d ? d->N : -1; }
 int32_t piso_num_boundary_faces(const piso_domain* d) { return d ? d->nbf : -1; }
 
@@ -1258,7 +1453,8 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
   if (!d->finalized) return fail(d, PISO_ESTATE, "autotune before finalize");
   cudaStream_t st = (cudaStream_t)stream;
   const auto key = std::make_tuple(d->ndim, d->prec, (int)d->N, (int)d->blocks.size(),
-                                   (d->opts.n_correctors * 4 + d->opts.p_precond) * 4 + d->opts.adv_precond);
+                                   ((d->opts.n_correctors * 4 + d->opts.p_precond) * 4 + d->opts.adv_precond) * 2 +
+                                       (d->opts.p_line_split ? 1 : 0));
   auto it = tune_cache().find(key);
   double best_ms = -1.0;
   if (it == tune_cache().end()) {
@@ -1298,7 +1494,7 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
       d->threads = std::get<0>(c);
       d->ncta = std::get<1>(c);
       d->p_line = std::get<2>(c);
-      s = build_ilu(d);
+      s = build_tables(d);
       if (s != PISO_OK) break;
       double t = 1e300;
       for (int rep = 0; rep < 3 && s == PISO_OK; rep++) {
@@ -1335,7 +1531,7 @@ piso_status piso_autotune(piso_domain* d, const void* u, const void* p, double d
   d->opts.block_threads = d->threads;
   d->opts.ctas = d->ncta;
   d->opts.p_precond = d->p_line ? PISO_PRECOND_LINE : PISO_PRECOND_JACOBI;
-  const piso_status sb = build_ilu(d);
+  const piso_status sb = build_tables(d);
   if (sb) return sb;
   if (threads_out) *threads_out = d->threads;
   if (ctas_out) *ctas_out = d->ncta;
@@ -1391,6 +1587,7 @@ void piso_domain_destroy(piso_domain* d) {
   if (d->dmem) cudaFree(d->dmem);
   if (d->h_status) cudaFreeHost(d->h_status);
   if (d->ilu_buf) cudaFree(d->ilu_buf);
+  if (d->lf_buf) cudaFree(d->lf_buf);
   if (d->h_istats) cudaFreeHost(d->h_istats);
   if (d->h_dstats) cudaFreeHost(d->h_dstats);
   if (d->h_dnu) cudaFreeHost(d->h_dnu);
@@ -1546,11 +1743,12 @@ extern "C" piso_status piso_step_static(piso_domain* d, const void* u_in, const 
 }
 
 #ifdef PISO_TRACE
-// Copy the phase-timing trace (trace builds only): n entries of 4 stamps.
+// Copy the phase-timing trace (trace builds only): n entries of PISO_TRACE_STAMPS stamps.
 extern "C" int piso_trace_read(uint64_t* out, int n) {
   if (n > PISO_TRACE_LEN) n = PISO_TRACE_LEN;
   if (!g_trace_buf) return 0;
-  if (cudaMemcpy(out, g_trace_buf, sizeof(uint64_t) * 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  if (cudaMemcpy(out, g_trace_buf, sizeof(uint64_t) * PISO_TRACE_STAMPS * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -1;
   return n;
 }
 #endif

@@ -201,7 +201,7 @@ struct LineDesc {
   int32_t start, stride, len;
 };
 
-__device__ __forceinline__ LineDesc line_desc(const DomStatic& D, int32_t l) {
+__host__ __device__ __forceinline__ LineDesc line_desc(const DomStatic& D, int32_t l) {
   int b = 0;
   while (b + 1 < D.nblocks && l >= D.blk[b + 1].line0) b++;
   const BlockInfo& B = D.blk[b];
@@ -209,6 +209,13 @@ __device__ __forceinline__ LineDesc line_desc(const DomStatic& D, int32_t l) {
   const uint32_t z = fast_div(lp, B.dnx);
   const uint32_t x = lp - z * (uint32_t)B.nx;
   return LineDesc{B.off + (int32_t)x + B.nx * B.ny * (int32_t)z, B.nx, B.ny};
+}
+
+// The line holding a located cell (the inverse of line_desc; the cell's y is
+// its position along the line).
+__host__ __device__ __forceinline__ int32_t line_of(const DomStatic& D, const Cell& c) {
+  const BlockInfo& B = D.blk[c.b];
+  return B.line0 + c.x + B.nx * c.z;
 }
 
 // Per-CTA state of the y-line preconditioner: the Thomas factors of the line
@@ -227,6 +234,18 @@ struct LinePre {
   int32_t* sStride;
   int32_t* sLen;
   int32_t L0, L1, lb;
+  // fused iteration (one group barrier per CG iteration), when this launch has
+  // a plan for it, else fl == nullptr: the CTA's local lines (n_own own lines,
+  // then the halo lines that hold its cells' other neighbours), the
+  // neighbour slots of its own cells ([2 ND][own_cap], -1: boundary face) and
+  // the shared arrays of the fused solve (they alias the staging arrays)
+  const int32_t* fl;
+  const int16_t* fnb;
+  int32_t n_own, n_loc, own_cap, slot_cap;
+  real *fA, *fC, *fM, *fB, *fR;   // [slot_cap]: fa, fc, fm, line right-hand side / solution, r
+  real *fU, *fP, *fX, *fPf;       // [own_cap]: u, p, x of the own cells; [2 ND][own_cap] face coefficients
+  int32_t* fI;                    // [slot_cap] cell of each slot, -1 past the end of its line
+  int16_t* fNb;                   // [2 ND][own_cap] neighbour slots in shared memory
 };
 
 // ---------------------------------------------------------------------------
@@ -257,7 +276,8 @@ __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
 // thread 0's per-iteration update stays on the FP32 pipe (an FP64 instruction
 // issues at ~64 cycles per warp on this GPU).  The product follows Dekker's
 // double-length multiplication with an FMA for the exact partial product, the
-// quotient one correction step q1 + (a - q1 b) / b; relative accuracy ~2^-44.
+// quotient one correction step q1 + (a - q1 b) / b with both partial quotients
+// taken against the rounded reciprocal of b.hi; relative accuracy ~2^-44.
 __device__ __forceinline__ f2 f2_norm(float s, float e) {   // fast two-sum, |s| >= |e|
   f2 r;
   r.hi = s + e;
@@ -273,9 +293,10 @@ __device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
   return f2_norm(p, e);
 }
 __device__ __forceinline__ f2 f2_div(f2 a, f2 b) {
-  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const float rb = __frcp_rn(b.hi);   // one reciprocal for both partial quotients
+  const float q1 = a.hi * rb;
   const f2 r = f2_add(a, f2_neg(f2_mul(f2{q1, 0.f}, b)));
-  return f2_norm(q1, __fdiv_rn(r.hi, b.hi));
+  return f2_norm(q1, r.hi * rb);
 }
 __device__ __forceinline__ bool f2_gt(f2 a, f2 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 __device__ __forceinline__ f2 f2_from_double(double d) {
@@ -372,22 +393,29 @@ struct Group {
 // Optional phase-timing trace (build with -DPISO_TRACE): CTA 0 of the launch
 // records globaltimer stamps at four points of every phase boundary - work
 // done, partials published, barrier passed, totals gathered - into a ring of
-// PISO_TRACE_LEN entries of four stamps at Group::trace (a device buffer the
-// host side owns and passes in with the solver options, so every translation
-// unit writes the same buffer).  Off by default; it changes no computation.
+// PISO_TRACE_LEN entries of PISO_TRACE_STAMPS stamps at Group::trace (a device
+// buffer the host side owns and passes in with the solver options, so every
+// translation unit writes the same buffer); stamps 4.. of an entry mark points
+// inside the phase's work (PISO_TRACE_SYNC lines the CTA up before such a
+// mark).  Off by default; it changes no computation.
 #ifdef PISO_TRACE
 constexpr int PISO_TRACE_LEN = 8192;
+constexpr int PISO_TRACE_STAMPS = 8;
 #define PISO_STAMP(slot, k)                                                   \
   do {                                                                        \
     if (g.trace && blockIdx.x == 0 && threadIdx.x == 0) {                     \
       uint64_t t_;                                                            \
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                  \
-      g.trace[((slot) % PISO_TRACE_LEN) * 4 + (k)] = t_;                      \
+      g.trace[((slot) % PISO_TRACE_LEN) * PISO_TRACE_STAMPS + (k)] = t_;      \
     }                                                                         \
   } while (0)
+#define PISO_TRACE_SYNC() __syncthreads()
 #else
 #define PISO_STAMP(slot, k) \
   do {                      \
+  } while (0)
+#define PISO_TRACE_SYNC() \
+  do {                    \
   } while (0)
 #endif
 
@@ -440,6 +468,10 @@ constexpr int GATHER_UNROLL = 8;
 // bits in the FP32 mode) instead of converted to double.
 template <typename real, int NS, bool RAW = false, typename F>
 __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& update) {
+  // each warp folds its lanes down to KEEP partials per scalar (fewer shuffle
+  // levels in every warp; the rest is summed by one warp per scalar), as many
+  // as the shared buffer holds
+  constexpr int KEEP = NS * 4 <= NSMAX ? 4 : (NS * 2 <= NSMAX ? 2 : 1);
   __shared__ double s_w[MAXW * NSMAX];
   __shared__ double s_tot[NSMAX];
   __shared__ int s_ok;
@@ -447,8 +479,8 @@ __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& up
 #pragma unroll
   for (int k = 0; k < NS; k++) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) a[k].shfl_down_add(off);
-    if (lane == 0) s_w[warp * NSMAX + k] = a[k].pack();
+    for (int off = 16; off >= KEEP; off >>= 1) a[k].shfl_down_add(off);
+    if (lane < KEEP) s_w[(k * MAXW + warp) * KEEP + lane] = a[k].pack();
   }
   __syncthreads();
   PISO_STAMP(g.epoch, 0);
@@ -457,7 +489,7 @@ __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& up
   for (int k = warp; k < NS; k += nw) {
     Acc<real> v;
     v.zero();
-    if (lane < nw) v.unpack_add(s_w[lane * NSMAX + k]);
+    for (int t = lane; t < nw * KEEP; t += 32) v.unpack_add(s_w[k * MAXW * KEEP + t]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v.shfl_down_add(off);
     if (lane == 0) __stcg(P + (size_t)k * g.ncta + g.rank, v.pack());

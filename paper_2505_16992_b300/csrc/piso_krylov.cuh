@@ -20,6 +20,14 @@ struct SolverOpts {
   int32_t grad_paths;        // adjoint: bit 1 keeps the advection-solve paths, bit 2 the pressure-solve paths
   int32_t ilu_soff;          // byte offset of the ILU(0) sweep area in dynamic shared memory, -1: none
   uint64_t* trace;           // phase-timing ring of PISO_TRACE builds ([PISO_TRACE_LEN][4]), else nullptr
+  // plan of the fused y-line CG iteration (cg_pressure_fused), or lf_off == nullptr
+  const int32_t* lf_off;     // [ncta + 1] CTA r's local lines are lf_lines[lf_off[r] .. lf_off[r + 1])
+  const int32_t* lf_nown;    // [ncta] the first lf_nown[r] of them are its own lines
+  const int32_t* lf_lines;   // line ids
+  const int16_t* lf_nbs;     // [ncta][2 ND][lf_own_cap] neighbour slots of the own cells
+  int32_t lf_own_cap;        // own cells per CTA the plan reserves (own lines x longest line)
+  int32_t lf_slot_cap;       // staged cells per CTA (pitch x longest line)
+  int32_t lf_bytes;          // bytes of the fused arrays in dynamic shared memory
 };
 
 // Fill the CTA's neighbour table (dynamic shared memory) when its cell range
@@ -685,9 +693,12 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
                             const real* Pdiag, const real* Pinv, const real* Poff, const real* b, double bmean,
                             real* x, real* const (&rb)[2], real* const (&wb)[2], real* const (&sb)[2],
                             real* pdir, int stall_window = 0) {
-  if (X.lp)   // y-line preconditioner (piso_lines.cuh)
+  if (X.lp) {   // y-line preconditioner (piso_lines.cuh)
+    if (X.lp->fl)
+      return cg_pressure_fused<real, ND>(X, cs, rtol, atol, maxit, Poff, b, bmean, x, rb, wb, sb, stall_window);
     return cg_pressure_line<real, ND>(X, cs, rtol, atol, maxit, Poff, b, bmean, x, rb[0], rb[1], wb[0], sb[0], pdir,
                                       stall_window);
+  }
   const int32_t N = X.N;
   // I1: r0 = b' - A' x0 with b' = -(b - mean), A' = -P
   __shared__ double s_mb;

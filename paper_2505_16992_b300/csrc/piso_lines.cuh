@@ -23,9 +23,9 @@
 // contiguous range of lines, stages them in shared memory in batches (cell
 // (line, y) of a batch at index y * pitch + line), updates r, x, p, s there and
 // solves its lines; in the second, every CTA applies -P to u on its usual cell
-// range.  A line solve is one warp: the two recurrences are affine maps
-// composed by a warp-level parallel prefix (Kogge-Stone), each lane holding a
-// contiguous chunk of the line.
+// range.  A line is solved by a group of 8 to 32 lanes of one warp: the two
+// recurrences are affine maps composed by a parallel prefix over the group
+// (Kogge-Stone), each lane holding a contiguous chunk of the line.
 // This header is included from piso_krylov.cuh (it uses Ctx, CgState and the
 // group reductions defined there).
 #pragma once
@@ -37,20 +37,47 @@ constexpr int LINE_ARRAYS = 4;     // staged reals per cell: fa, fm r (then the 
 
 // This CTA's share of the y-line preconditioner: lines [L0, L1) of the group
 // and the staging area behind the neighbour table in dynamic shared memory
-// (LINE_ARRAYS arrays of o.line_cap reals, then 3 x LINE_LBMAX ints).
+// (LINE_ARRAYS arrays of o.line_cap reals, or the fused solve's arrays where
+// those are larger, then 3 x LINE_LBMAX ints).
 template <typename real, int ND>
 __device__ __forceinline__ LinePre<real> line_setup(const DomStatic& D, const Group& g, const SolverOpts& o,
                                                     real* fa, real* fm, real* fc) {
   extern __shared__ int32_t s_nbt[];
   LinePre<real> L;
   const size_t nbt_bytes = ((size_t)o.nbt_cap * 2 * ND * sizeof(int32_t) + 15) & ~size_t(15);
-  real* sr = reinterpret_cast<real*>(reinterpret_cast<char*>(s_nbt) + nbt_bytes);
+  char* base = reinterpret_cast<char*>(s_nbt) + nbt_bytes;
+  real* sr = reinterpret_cast<real*>(base);
   const size_t cap = (size_t)o.line_cap;
   L.sA = sr;
   L.sB = sr + cap;
   L.sC = sr + 2 * cap;
   L.sR = sr + 3 * cap;
-  int32_t* si = reinterpret_cast<int32_t*>(sr + LINE_ARRAYS * cap);
+  const size_t stage = LINE_ARRAYS * cap * sizeof(real);
+  const bool fused = o.lf_off != nullptr;
+  int32_t* si = reinterpret_cast<int32_t*>(base + (fused ? max(stage, (size_t)o.lf_bytes) : stage));
+  L.fl = nullptr;
+  L.fnb = nullptr;
+  if (fused) {
+    const int32_t a = o.lf_off[g.rank];
+    L.fl = o.lf_lines + a;
+    L.n_own = o.lf_nown[g.rank];
+    L.n_loc = o.lf_off[g.rank + 1] - a;
+    L.own_cap = o.lf_own_cap;
+    L.slot_cap = o.lf_slot_cap;
+    L.fnb = o.lf_nbs + (size_t)g.rank * 2 * ND * o.lf_own_cap;
+    const size_t sc = (size_t)o.lf_slot_cap, oc = (size_t)o.lf_own_cap;
+    L.fA = sr;
+    L.fC = sr + sc;
+    L.fM = sr + 2 * sc;
+    L.fB = sr + 3 * sc;
+    L.fR = sr + 4 * sc;
+    L.fU = sr + 5 * sc;
+    L.fP = L.fU + oc;
+    L.fX = L.fP + oc;
+    L.fPf = L.fX + oc;
+    L.fI = reinterpret_cast<int32_t*>(L.fPf + 2 * ND * oc);
+    L.fNb = reinterpret_cast<int16_t*>(L.fI + sc);
+  }
   L.sStart = si;
   L.sStride = si + LINE_LBMAX;
   L.sLen = si + 2 * LINE_LBMAX;
@@ -114,64 +141,87 @@ __device__ __forceinline__ void line_batch_cells(const LinePre<real>& L, const L
   }
 }
 
-// Solve the staged lines in place: on entry sB = fm * r, sA = fa, sC = fc; on
-// exit sB = M^-1 r.  One warp per line; lane j holds the chunk
-// [j E, min(len, (j + 1) E)) with E = ceil(len / 32).
-template <typename real>
-__device__ __forceinline__ void line_batch_solve(const LinePre<real>& L, const LineBatch& B) {
-  __syncthreads();
+// Solve nb staged lines (cell y of line l at y * P + l) in place: on entry
+// sB = fm * r, sA = fa, sC = fc; on exit sB = M^-1 r.  A line is solved by W
+// lanes of a warp (32 / W lines per warp at a time); lane j of its group
+// holds the chunk [j E, min(len, (j + 1) E)) with E = ceil(len / W).
+template <typename real, int W>
+__device__ __forceinline__ void line_solve_w(const real* __restrict__ sA, real* __restrict__ sB,
+                                             const real* __restrict__ sC, const int32_t* sLen, int32_t nb,
+                                             int32_t P) {
+  constexpr int G = 32 / W;   // lines per warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int32_t P = B.pitch;
-  for (int32_t l = warp; l < B.nb; l += nw) {
-    const int32_t len = L.sLen[l];
-    const int32_t E = (len + 31) >> 5;
-    const int32_t y0 = min(len, lane * E), y1 = min(len, y0 + E);
+  const int j = lane % W;
+  for (int32_t lb = warp * G; lb < nb; lb += nw * G) {   // uniform over the warp
+    const int32_t l = lb + lane / W;
+    const int32_t len = l < nb ? sLen[l] : 0;
+    const int32_t E = (len + W - 1) / W;
+    const int32_t y0 = min(len, j * E), y1 = min(len, y0 + E);
     // forward: g_y = a_y g_{y-1} + b_y; this lane's chunk as one map g -> A g + Bv
     real A = real(1), Bv = real(0);
     for (int32_t y = y0; y < y1; y++) {
-      const real a = L.sA[y * P + l];
+      const real a = sA[y * P + l];
       A = a * A;
-      Bv = a * Bv + L.sB[y * P + l];
+      Bv = a * Bv + sB[y * P + l];
     }
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {      // inclusive prefix of the maps over lanes
-      const real Au = __shfl_up_sync(0xffffffffu, A, off);
-      const real Bu = __shfl_up_sync(0xffffffffu, Bv, off);
-      if (lane >= off) {
+    for (int off = 1; off < W; off <<= 1) {       // inclusive prefix of the maps over the group
+      const real Au = __shfl_up_sync(0xffffffffu, A, off, W);
+      const real Bu = __shfl_up_sync(0xffffffffu, Bv, off, W);
+      if (j >= off) {
         Bv = A * Bu + Bv;
         A = A * Au;
       }
     }
-    real g = __shfl_up_sync(0xffffffffu, Bv, 1);   // g just before this chunk (g_{-1} = 0)
-    if (lane == 0) g = real(0);
+    real g = __shfl_up_sync(0xffffffffu, Bv, 1, W);   // g just before this chunk (g_{-1} = 0)
+    if (j == 0) g = real(0);
     for (int32_t y = y0; y < y1; y++) {
-      g = L.sA[y * P + l] * g + L.sB[y * P + l];
-      L.sB[y * P + l] = g;
+      g = sA[y * P + l] * g + sB[y * P + l];
+      sB[y * P + l] = g;
     }
     // backward: z_y = c_y z_{y+1} + g_y; the chunk as one map z_next -> C z_next + G
-    real Cm = real(1), G = real(0);
+    real Cm = real(1), Gz = real(0);
     for (int32_t y = y1 - 1; y >= y0; y--) {
-      const real c = L.sC[y * P + l];
-      G = c * G + L.sB[y * P + l];
+      const real c = sC[y * P + l];
+      Gz = c * Gz + sB[y * P + l];
       Cm = c * Cm;
     }
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {      // suffix composition over lanes
-      const real Cd = __shfl_down_sync(0xffffffffu, Cm, off);
-      const real Gd = __shfl_down_sync(0xffffffffu, G, off);
-      if (lane + off < 32) {
-        G = Cm * Gd + G;
+    for (int off = 1; off < W; off <<= 1) {       // suffix composition over the group
+      const real Cd = __shfl_down_sync(0xffffffffu, Cm, off, W);
+      const real Gd = __shfl_down_sync(0xffffffffu, Gz, off, W);
+      if (j + off < W) {
+        Gz = Cm * Gd + Gz;
         Cm = Cm * Cd;
       }
     }
-    real z = __shfl_down_sync(0xffffffffu, G, 1);  // z just after this chunk (z_len = 0)
-    if (lane == 31) z = real(0);
+    real z = __shfl_down_sync(0xffffffffu, Gz, 1, W);  // z just after this chunk (z_len = 0)
+    if (j == W - 1) z = real(0);
     for (int32_t y = y1 - 1; y >= y0; y--) {
-      z = L.sC[y * P + l] * z + L.sB[y * P + l];
-      L.sB[y * P + l] = z;
+      z = sC[y * P + l] * z + sB[y * P + l];
+      sB[y * P + l] = z;
     }
   }
+}
+
+// The group width is the widest that still solves all nb lines in one round
+// of the CTA's warps (narrower groups: longer serial chunks, fewer shuffle
+// steps; 8 lanes at the narrowest).
+template <typename real>
+__device__ __forceinline__ void line_solve(const real* __restrict__ sA, real* __restrict__ sB,
+                                           const real* __restrict__ sC, const int32_t* sLen, int32_t nb,
+                                           int32_t P) {
   __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (nb <= nw) line_solve_w<real, 32>(sA, sB, sC, sLen, nb, P);
+  else if (nb <= 2 * nw) line_solve_w<real, 16>(sA, sB, sC, sLen, nb, P);
+  else line_solve_w<real, 8>(sA, sB, sC, sLen, nb, P);
+  __syncthreads();
+}
+
+template <typename real>
+__device__ __forceinline__ void line_batch_solve(const LinePre<real>& L, const LineBatch& B) {
+  line_solve<real>(L.sA, L.sB, L.sC, L.sLen, B.nb, B.pitch);
 }
 
 // Thomas factors of every line block of -P (once per step, after P is
@@ -282,6 +332,37 @@ __device__ __forceinline__ void line_apply_sweep(const Ctx<real, ND>& X, const r
   }
 }
 
+// Thread 0, end of the start phase of a line-preconditioned CG, from the
+// totals q = (||b'||^2, ||r0||^2, (r0, u0), (w0, u0)): tolerance, state and the
+// first coefficients.
+template <typename real>
+__device__ __forceinline__ void line_cg_start(CgState& cs, const double* q, double rtol, double atol,
+                                              int32_t* status) {
+  cs.tol2 = fmax(rtol * rtol * q[0], atol * atol);
+  cs.res2 = q[1];
+  cs.best = q[1];
+  if (sizeof(real) == 4) {
+    cs.ftol2 = f2_from_double(cs.tol2);
+    cs.fbest = f2_from_double(q[1]);
+    cs.fres2 = cs.fbest;
+  }
+  cs.best_it = 0;
+  cs.stalled = 0;
+  cs.it = 0;
+  cs.first = 1;
+  cs.conv = !(cs.res2 > cs.tol2);
+  cs.active = !cs.conv;
+  if (cs.res2 != cs.res2) {
+    cs.active = 0;
+    cs.conv = 0;
+    atomicOr(status, PISO_ERR_NAN);
+  }
+  if (cs.active && cg_coeffs(cs, q[2], q[3], true, status) && sizeof(real) == 4) {
+    cs.fgam = f2_from_double(q[2]);
+    cs.finv_alpha = f2_div(f2_from_double(q[3]), cs.fgam);
+  }
+}
+
 // Line-preconditioned CG on (-P) x = -(b - bmean) in the Chronopoulos-Gear
 // form (one reduction per iteration; R7: b is projected to zero mean):
 //   r0 = b' - A' x0, u0 = M^-1 r0, w0 = A' u0
@@ -354,31 +435,8 @@ __device__ bool cg_pressure_line(const Ctx<real, ND>& X, CgState& cs, double rto
     a[3].add_prod(ww, uP);
   });
   {
-    const bool ok = reduce_sync<real, 4>(X.g, a, [&](const double* q) {
-      cs.tol2 = fmax(rtol * rtol * q[0], atol * atol);
-      cs.res2 = q[1];
-      cs.best = q[1];
-      if (sizeof(real) == 4) {
-        cs.ftol2 = f2_from_double(cs.tol2);
-        cs.fbest = f2_from_double(q[1]);
-        cs.fres2 = cs.fbest;
-      }
-      cs.best_it = 0;
-      cs.stalled = 0;
-      cs.it = 0;
-      cs.first = 1;
-      cs.conv = !(cs.res2 > cs.tol2);
-      cs.active = !cs.conv;
-      if (cs.res2 != cs.res2) {
-        cs.active = 0;
-        cs.conv = 0;
-        atomicOr(X.g.status, PISO_ERR_NAN);
-      }
-      if (cs.active && cg_coeffs(cs, q[2], q[3], true, X.g.status) && sizeof(real) == 4) {
-        cs.fgam = f2_from_double(q[2]);
-        cs.finv_alpha = f2_div(f2_from_double(q[3]), cs.fgam);
-      }
-    });
+    const bool ok = reduce_sync<real, 4>(
+        X.g, a, [&](const double* q) { line_cg_start<real>(cs, q, rtol, atol, X.g.status); });
     if (!ok) return false;
   }
   while (cs.active && cs.it < maxit) {
@@ -412,6 +470,250 @@ __device__ bool cg_pressure_line(const Ctx<real, ND>& X, CgState& cs, double rto
       ok = reduce_sync<real, 3>(
           X.g, c3, [&](const double* q) { cg_iter_update(cs, q[0], q[1], q[2], stall_window, X.g.status); });
     if (!ok) return false;
+  }
+  if (sizeof(real) == 4 && threadIdx.x == 0) cs.res2 = f2_to_double(cs.fres2);
+  return true;
+}
+
+// Visit k = threadIdx.x, k + blockDim.x, ... < total as (q, l) = (k / n, k mod n),
+// carrying the quotient and remainder from one visit to the next (no division
+// inside the loop).
+struct GridWalk {
+  int32_t q, l, dq, dl, n;
+  __device__ __forceinline__ GridWalk(int32_t n_) : n(n_) {
+    const int32_t T = blockDim.x;
+    dq = T / n;
+    dl = T - dq * n;
+    q = threadIdx.x / n;
+    l = threadIdx.x - q * n;
+  }
+  __device__ __forceinline__ void next() {
+    l += dl;
+    q += dq;
+    if (l >= n) {
+      l -= n;
+      q++;
+    }
+  }
+};
+
+template <typename F>
+__device__ __forceinline__ void line_grid(int32_t n, int32_t total, F&& f) {
+  GridWalk w(n);
+  for (int32_t k = threadIdx.x; k < total; k += blockDim.x) {
+    f(k, w.q, w.l);
+    w.next();
+  }
+}
+
+// The line-preconditioned CG with one group barrier per iteration, for
+// launches whose every CTA can hold its own lines and the lines next to them
+// in shared memory (the host builds the plan: own lines, halo lines and the
+// shared slot of every neighbour of every own cell).  Same recurrences as
+// cg_pressure_line; what moves is where u = M^-1 r comes from: each CTA
+// updates s and r on its halo lines too, from the previous iteration's w, s
+// and r (ping-pong buffers that their owners wrote before the last barrier),
+// and solves those lines itself, so the u of every neighbour of an own cell
+// is in shared memory and w = A' u needs no barrier:
+//   per iteration, on own and halo lines: s = w + beta s, r -= alpha s,
+//   u = M^-1 r; on own cells: p = u_prev + beta p, x += alpha p, w = A' u;
+//   one group reduction of gamma = (r, u), delta = (w, u), ||r||^2.
+// Own cells keep u, p, x and their face coefficients in shared memory; r, s
+// and w go to global memory each iteration (the neighbours read them), x too
+// (so it is complete when the solve returns).  Cell y of local line l sits at
+// slot y * P + l (P = n_loc | 1; fI holds its cell index, -1 past the line's
+// end); own cell k = y * n_own + l.
+template <typename real, int ND>
+__device__ bool cg_pressure_fused(const Ctx<real, ND>& X, CgState& cs, double rtol, double atol, int maxit,
+                                  const real* Poff, const real* b, double bmean, real* x, real* const (&rb)[2],
+                                  real* const (&wb)[2], real* const (&sb)[2], int stall_window) {
+  constexpr int NS = 2 * ND;
+  const int32_t N = X.N;
+  const DomStatic& D = X.D;
+  const LinePre<real>& L = *X.lp;
+  const int32_t no = L.n_own, nl = L.n_loc, P = nl | 1, oc = L.own_cap;
+  const int32_t nslot = nl * D.lmax, nown = no * D.lmax;
+  real* __restrict__ fA = L.fA;
+  real* __restrict__ fC = L.fC;
+  real* __restrict__ fM = L.fM;
+  real* __restrict__ fB = L.fB;
+  real* __restrict__ fR = L.fR;
+  real* __restrict__ fU = L.fU;
+  real* __restrict__ fP = L.fP;
+  real* __restrict__ fX = L.fX;
+  real* __restrict__ fPf = L.fPf;
+  int32_t* __restrict__ fI = L.fI;
+  int16_t* __restrict__ fNb = L.fNb;
+  int32_t* sLen = L.sLen;
+  __shared__ double s_mb3;
+  __shared__ float s_mbf3;
+  // S0: lengths of the local lines and the own cells' neighbour slots
+  __syncthreads();   // earlier users of the staging area are done
+  if (threadIdx.x == 0) {
+    s_mb3 = bmean;
+    s_mbf3 = (float)bmean;
+  }
+  for (int32_t t = threadIdx.x; t < nl; t += blockDim.x) {
+    const LineDesc ld = line_desc(D, L.fl[t]);
+    L.sStart[t] = ld.start;
+    L.sStride[t] = ld.stride;
+    sLen[t] = ld.len;
+  }
+  for (int32_t t = threadIdx.x; t < NS * oc; t += blockDim.x) fNb[t] = L.fnb[t];
+  __syncthreads();
+  const real mb = pick<real>(s_mb3, s_mbf3);
+  // S1: cell index and line factors of every slot
+  line_grid(nl, nslot, [&](int32_t, int32_t q, int32_t l) {
+    const int32_t k = q * P + l;
+    if (q >= sLen[l]) {
+      fI[k] = -1;
+      return;
+    }
+    const int32_t i = L.sStart[l] + q * L.sStride[l];
+    fI[k] = i;
+    fA[k] = L.fa[i];
+    fM[k] = L.fm[i];
+    fC[k] = L.fc[i];
+  });
+  __syncthreads();
+  // I1: own cells: face coefficients and x0 to shared memory, r0 = b' - A' x0
+  Acc<real> a[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) a[k].zero();
+  line_grid(no, nown, [&](int32_t k, int32_t q, int32_t l) {
+    const int32_t i = fI[q * P + l];
+    if (i < 0) return;
+    const Cell c = locate<ND>(D, i);
+    real pf[NS];
+    p_row<real, ND>(c, N, Poff, pf);
+    const real xP = x[i];
+    real px = 0;
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+      fPf[s * oc + k] = pf[s];
+      if (c.nb[s] >= 0) px += pf[s] * (x[c.nb[s]] - xP);
+    }
+    fX[k] = xP;
+    const real bp = -(b[i] - mb);
+    const real rr = bp + px;
+    rb[0][i] = rr;
+    a[0].add_prod(bp, bp);
+    a[1].add_prod(rr, rr);
+  });
+  if (!plain_sync(X.g)) return false;
+  // I2: u0 = M^-1 r0 on the local lines, w0 = A' u0 on the own cells
+  {
+    const real* __restrict__ r0 = rb[0];
+    line_grid(nl, nslot, [&](int32_t, int32_t q, int32_t l) {
+      const int32_t k = q * P + l, i = fI[k];
+      if (i < 0) return;
+      const real rr = r0[i];
+      fB[k] = fM[k] * rr;
+      fR[k] = rr;
+    });
+  }
+  line_solve<real>(fA, fB, fC, sLen, nl, P);
+  // w = A' u on the own cells from the solved lines, (r, u) and (w, u)
+  auto own_apply = [&](real* __restrict__ w_o, Acc<real>& ru, Acc<real>& wu) {
+    line_grid(no, nown, [&](int32_t k, int32_t q, int32_t l) {
+      const int32_t sk = q * P + l, i = fI[sk];
+      if (i < 0) return;
+      const real uP = fB[sk];
+      real ww = 0;
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        const int32_t nk = fNb[s * oc + k];
+        if (nk >= 0) ww += fPf[s * oc + k] * (uP - fB[nk]);
+      }
+      w_o[i] = ww;
+      fU[k] = uP;
+      ru.add_prod(fR[sk], uP);
+      wu.add_prod(ww, uP);
+    });
+  };
+  own_apply(wb[0], a[2], a[3]);
+  {
+    const bool ok = reduce_sync<real, 4>(
+        X.g, a, [&](const double* q) { line_cg_start<real>(cs, q, rtol, atol, X.g.status); });
+    if (!ok) return false;
+  }
+  int cur = 0;
+  while (cs.active && cs.it < maxit) {
+    Acc<real> c3[3];
+    c3[0].zero();
+    c3[1].zero();
+    c3[2].zero();
+    const real al = pick<real>(cs.alpha, cs.alpha_f), be = pick<real>(cs.beta, cs.beta_f);
+    const int first = cs.first;
+    const real* __restrict__ r_i = rb[cur];
+    const real* __restrict__ w_i = wb[cur];
+    const real* __restrict__ s_i = sb[cur];
+    real* __restrict__ r_n = rb[cur ^ 1];
+    real* __restrict__ w_n = wb[cur ^ 1];
+    real* __restrict__ s_n = sb[cur ^ 1];
+    const Group& g = X.g;
+    PISO_STAMP(g.epoch, 4);
+    // s = w + beta s, r -= alpha s and the line right-hand sides on every local
+    // line; p and x on the own cells.  Two slots per pass, all their loads
+    // issued before the first store.
+    auto stage = [&](int32_t sk, int32_t q, int32_t l, int32_t i, real wO, real rO, real sO) {
+      const real sv = first ? wO : wO + be * sO;
+      const real rr = rO - al * sv;
+      fB[sk] = fM[sk] * rr;
+      fR[sk] = rr;
+      if (l < no) {
+        const int32_t ko = q * no + l;
+        const real p = first ? fU[ko] : fU[ko] + be * fP[ko];
+        const real xn = fX[ko] + al * p;
+        fP[ko] = p;
+        fX[ko] = xn;
+        s_n[i] = sv;
+        r_n[i] = rr;
+        x[i] = xn;
+        c3[2].add_prod(rr, rr);
+      }
+    };
+    {
+      GridWalk gw(nl);
+      for (int32_t k = threadIdx.x; k < nslot; k += 2 * blockDim.x) {
+        const int32_t q0 = gw.q, l0 = gw.l;
+        gw.next();
+        const int32_t q1 = gw.q, l1 = gw.l;
+        gw.next();
+        const int32_t s0 = q0 * P + l0, s1 = q1 * P + l1;
+        const int32_t i0 = fI[s0], i1 = k + (int32_t)blockDim.x < nslot ? fI[s1] : -1;
+        real w0 = 0, r0 = 0, z0 = 0, w1 = 0, r1 = 0, z1 = 0;
+        if (i0 >= 0) {
+          w0 = w_i[i0];
+          r0 = r_i[i0];
+          if (!first) z0 = s_i[i0];
+        }
+        if (i1 >= 0) {
+          w1 = w_i[i1];
+          r1 = r_i[i1];
+          if (!first) z1 = s_i[i1];
+        }
+        if (i0 >= 0) stage(s0, q0, l0, i0, w0, r0, z0);
+        if (i1 >= 0) stage(s1, q1, l1, i1, w1, r1, z1);
+      }
+    }
+    PISO_TRACE_SYNC();
+    PISO_STAMP(g.epoch, 5);
+    line_solve<real>(fA, fB, fC, sLen, nl, P);
+    PISO_STAMP(g.epoch, 6);
+    own_apply(w_n, c3[0], c3[1]);
+    PISO_TRACE_SYNC();
+    PISO_STAMP(g.epoch, 7);
+    bool ok;
+    if constexpr (sizeof(real) == 4)
+      ok = reduce_sync<real, 3, true>(X.g, c3, [&](const double* q) {
+        cg_iter_update_f2(cs, f2_unpack(q[0]), f2_unpack(q[1]), f2_unpack(q[2]), stall_window, X.g.status);
+      });
+    else
+      ok = reduce_sync<real, 3>(
+          X.g, c3, [&](const double* q) { cg_iter_update(cs, q[0], q[1], q[2], stall_window, X.g.status); });
+    if (!ok) return false;
+    cur ^= 1;
   }
   if (sizeof(real) == 4 && threadIdx.x == 0) cs.res2 = f2_to_double(cs.fres2);
   return true;

@@ -86,6 +86,10 @@ class Domain:
         """True when the pressure CG of the next step uses the y-line preconditioner."""
         return int(self.lib.piso_pressure_precond(self.h)) == capi.PISO_PRECOND_LINE
 
+    def uses_fused_lines(self) -> bool:
+        """True when that y-line CG runs with one group barrier per iteration."""
+        return int(self.lib.piso_pressure_line_fused(self.h)) == 1
+
     @classmethod
     def from_case(cls, case, precision="fp64", options=None, **kw) -> "Domain":
         """Build from an object with ndim/blocks/connections/dirichlet/outflow

@@ -156,3 +156,28 @@ def test_gradient_path_bits_are_validated(lib):
     assert lib.piso_finalize(h, C.byref(o)) == 1
     assert b"grad_paths" in lib.piso_last_error(h)
     lib.piso_domain_destroy(h)
+
+
+def test_step_kernels_fit_the_shared_memory_opt_in():
+    """Static shared memory of every step kernel (from the build's ptxas
+    report) plus the largest dynamic area a launch asks for stays within the
+    227 KB per CTA, so every launch shape can be resident."""
+    src = open(os.path.join(ROOT, "paper_2505_16992_b300", "csrc", "piso_capi.cu")).read()
+    m = re.search(r"constexpr size_t NBT_MAX_BYTES = (\d+) \* 1024;", src)
+    assert m
+    dyn = int(m.group(1)) * 1024
+    logs = [os.path.join(_build.OBJDIR, f) for f in os.listdir(_build.OBJDIR)
+            if f.startswith("piso_kernels_") and f.endswith(".log")] if os.path.isdir(_build.OBJDIR) else []
+    if not logs:
+        pytest.skip("no resource report (library built elsewhere)")
+    seen = 0
+    for path in logs:
+        for part in open(path).read().split("Compiling entry function '")[1:]:
+            name = part.split("'")[0]
+            if "fwd_kernel" not in name and "adj_kernel" not in name:
+                continue
+            sm = re.search(r"(\d+) bytes smem", part)
+            assert sm, name
+            assert int(sm.group(1)) + dyn <= 227 * 1024, (name, int(sm.group(1)))
+            seen += 1
+    assert seen >= 16
