@@ -246,6 +246,15 @@ int32_t piso_pressure_precond(const piso_domain* d);
  * is built on the host whenever the launch layout changes. */
 int32_t piso_pressure_line_fused(const piso_domain* d);
 
+/* 1 when the domain's next step runs its Jacobi CG sweep on four consecutive
+ * cells per thread with vector loads and stores (every block's nx a multiple
+ * of 4, no joint that exchanges or reverses axes, and cells walked in passes
+ * interleaved over the CTAs because a CTA's range exceeds its shared-memory
+ * neighbour table), 0 when it runs one cell per thread or another
+ * preconditioner, -1 for a NULL or unfinalized domain.  Both forms compute
+ * the same iterates up to the summation order of the dot products. */
+int32_t piso_pressure_cg_vec4(const piso_domain* d);
+
 int64_t piso_num_cells(const piso_domain* d);
 int32_t piso_num_boundary_faces(const piso_domain* d);
 

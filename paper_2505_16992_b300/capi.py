@@ -60,6 +60,7 @@ _SIGS = {
     "piso_get_options": (C.c_int, [_P, C.POINTER(Options)]),
     "piso_pressure_precond": (C.c_int32, [_P]),
     "piso_pressure_line_fused": (C.c_int32, [_P]),
+    "piso_pressure_cg_vec4": (C.c_int32, [_P]),
     "piso_num_cells": (C.c_int64, [_P]),
     "piso_num_boundary_faces": (C.c_int32, [_P]),
     "piso_tape_bytes": (C.c_size_t, [_P]),

@@ -1158,6 +1158,9 @@ piso_status piso_finalize(piso_domain* d, const piso_options* opts) {
   }
   d->nbf = nbf;
   d->n_out = n_out;
+  S.vec4 = d->twisted ? 0 : 1;
+  for (int b = 0; b < S.nblocks; b++)
+    if (S.blk[b].nx % 4) S.vec4 = 0;
   S.nbf = nbf;
   S.n_out = n_out;
   // metrics
@@ -1406,6 +1409,13 @@ int32_t piso_pressure_line_fused(const piso_domain* d) {
   SolverOpts so = solver_opts(d->opts);
   launch_smem(d, d->ncta, &so);
   return d->p_line && so.lf_off ? 1 : 0;
+}
+
+int32_t piso_pressure_cg_vec4(const piso_domain* d) {
+  if (!d || !d->finalized) return -1;
+  SolverOpts so = solver_opts(d->opts);
+  launch_smem(d, d->ncta, &so);
+  return !d->p_line && d->h_static.vec4 && so.nbt_cap == 0 ? 1 : 0;
 }
 
 int64_t piso_num_cells(const piso_domain* d) { return d ? d->N : -1; }

@@ -69,6 +69,9 @@ struct DomStatic {
   int32_t ndim, nblocks, N, nbf;
   int32_t n_out;             // number of advective-outflow faces
   int32_t nlines, lmax;      // y-lines (one per block column) and the longest line's length
+  int32_t vec4;              // 1: every block's nx is a multiple of 4 and every joint is plain, so four
+                             // cells (4m .. 4m+3) always share block, row and the layout of their y/z
+                             // neighbours, and [comp][N] arrays hold them in one aligned 4-vector
   BlockInfo blk[MAXB];
   // per-cell metrics, storage precision (void*: float or double)
   const void* J;             // [N]

@@ -683,6 +683,161 @@ __device__ __forceinline__ void cg_jacobi_sweep(const Ctx<real, ND>& X, int firs
   }
 }
 
+// Four consecutive cells of one [comp][N] array as one aligned vector access
+// (16 bytes in FP32, two 16-byte halves in FP64).
+template <typename real>
+struct V4 {
+  real v[4];
+};
+__device__ __forceinline__ V4<float> ld4(const float* __restrict__ p) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  return V4<float>{{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double* __restrict__ p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  return V4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* __restrict__ p, const V4<float>& t) {
+  *reinterpret_cast<float4*>(p) = make_float4(t.v[0], t.v[1], t.v[2], t.v[3]);
+}
+__device__ __forceinline__ void st4(double* __restrict__ p, const V4<double>& t) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(t.v[0], t.v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(t.v[2], t.v[3]);
+}
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// The sweep of cg_jacobi_sweep with four consecutive cells per thread (domains
+// walked in interleaved passes whose blocks all have nx a multiple of 4 and
+// plain joints, DomStatic::vec4).  The four cells share block, row, and their
+// y and z neighbours are four consecutive cells too (or all boundary faces), so
+// every stream is read and written as one aligned vector per array: the own
+// cells' 9 streams, the 4 streams of each y/z neighbour quad and the -y/-z face
+// coefficients of P; inside the quad the x neighbours' values are the quad's
+// own, and only the cells left and right of it are read singly.  Each cell's
+// arithmetic is that of cg_jacobi_sweep, term for term (same values, same
+// summation order of A'u), so only the order of the three dot sums differs.
+// Four times the bytes per load instruction and one neighbour lookup per four
+// cells: the sweep is bound by the memory system, not by the loads a warp can
+// keep in flight or by instruction issue.
+template <typename real, int ND>
+__device__ __forceinline__ void cg_jacobi_sweep4(const Ctx<real, ND>& X, int first, real al, real be,
+                                                 const real* __restrict__ r_i, const real* __restrict__ w_i,
+                                                 const real* __restrict__ s_o, const real* __restrict__ Pinv,
+                                                 const real* __restrict__ Poff, real* __restrict__ pdir,
+                                                 real* __restrict__ x, real* __restrict__ s_n,
+                                                 real* __restrict__ r_n, real* __restrict__ w_n, Acc<real> (&a)[3]) {
+  const int32_t N = X.N, nq = N >> 2, st = X.stride();
+  // u1 = D^-1 (r - al s) at one cell (s = w + be s_old), as cg_jacobi_sweep forms it
+  auto u1s = [&](int32_t Q) -> real {
+    const real sQ = first ? w_i[Q] : w_i[Q] + be * s_o[Q];
+    return (r_i[Q] - al * sQ) * Pinv[Q];
+  };
+  auto u1q = [&](int32_t Q0, real (&u)[4]) {
+    const V4<real> rq = ld4(r_i + Q0), wq = ld4(w_i + Q0), iq = ld4(Pinv + Q0);
+    V4<real> sq{};
+    if (!first) sq = ld4(s_o + Q0);
+#pragma unroll
+    for (int k = 0; k < 4; k++) u[k] = (rq.v[k] - al * (first ? wq.v[k] : wq.v[k] + be * sq.v[k])) * iq.v[k];
+  };
+#pragma unroll 1
+  for (int32_t q = X.first(); q < nq; q += st) {
+    const int32_t i0 = q << 2;
+    const int32_t nxt = (q + st) << 2;
+    if (q + st < nq) {
+      prefetch_l2(r_i + nxt);
+      prefetch_l2(w_i + nxt);
+      prefetch_l2(Pinv + nxt);
+      prefetch_l2(x + nxt);
+      if (!first) {
+        prefetch_l2(s_o + nxt);
+        prefetch_l2(pdir + nxt);
+      }
+#pragma unroll
+      for (int j = 0; j < ND; j++) prefetch_l2(Poff + (size_t)j * N + nxt);
+    }
+    const Cell c = locate<ND>(X.D, i0);
+    const BlockInfo& B = X.D.blk[c.b];
+    const int32_t nR = (c.x + 4 < B.nx) ? i0 + 4 : side_nbr(X.D, B, i0 + 3, c.x + 3, c.y, c.z, 1);
+    const int32_t nL = c.nb[0];
+    // own cells, in an order that lets each value die early: s, r and their
+    // dot products; then p and x (touched only here); then the stencil
+    real u1P[4], w1[4];
+    {
+      const V4<real> rP = ld4(r_i + i0), wP = ld4(w_i + i0), iP = ld4(Pinv + i0);
+      V4<real> sO{};
+      if (!first) sO = ld4(s_o + i0);
+      V4<real> sn, rn;
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        sn.v[k] = first ? wP.v[k] : wP.v[k] + be * sO.v[k];
+        rn.v[k] = rP.v[k] - al * sn.v[k];
+        u1P[k] = rn.v[k] * iP.v[k];
+      }
+      st4(s_n + i0, sn);
+      st4(r_n + i0, rn);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        a[0].add_prod(rn.v[k], u1P[k]);
+        a[2].add_prod(rn.v[k], rn.v[k]);
+      }
+      const V4<real> xP = ld4(x + i0);
+      V4<real> pO{};
+      if (!first) pO = ld4(pdir + i0);
+      V4<real> pn, xn;
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const real uP = rP.v[k] * iP.v[k];
+        pn.v[k] = first ? uP : uP + be * pO.v[k];
+        xn.v[k] = xP.v[k] + al * pn.v[k];
+      }
+      st4(pdir + i0, pn);
+      st4(x + i0, xn);
+    }
+    // x faces (sides 0, 1): inside the quad from registers, the cells left and
+    // right of it read singly
+    {
+      const V4<real> px = ld4(Poff + i0);
+      const real uL = nL >= 0 ? u1s(nL) : real(0), cL = nL >= 0 ? Poff[nL] : real(0);
+      const real uR = nR >= 0 ? u1s(nR) : real(0);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        real w = 0;
+        if (k > 0) w += px.v[k - 1] * (u1P[k] - u1P[k - 1]);
+        else if (nL >= 0) w += cL * (u1P[0] - uL);
+        if (k < 3) w += px.v[k] * (u1P[k] - u1P[k + 1]);
+        else if (nR >= 0) w += px.v[3] * (u1P[3] - uR);
+        w1[k] = w;
+      }
+    }
+    // y and z faces (sides 2 .. 2 ND - 1): a neighbour quad, or boundary faces
+#pragma unroll
+    for (int j = 1; j < ND; j++) {
+      const int32_t Qm = c.nb[2 * j], Qp = c.nb[2 * j + 1];
+      if (Qm >= 0) {
+        real u[4];
+        u1q(Qm, u);
+        const V4<real> cm = ld4(Poff + (size_t)j * N + Qm);
+#pragma unroll
+        for (int k = 0; k < 4; k++) w1[k] += cm.v[k] * (u1P[k] - u[k]);
+      }
+      if (Qp >= 0) {
+        real u[4];
+        u1q(Qp, u);
+        const V4<real> cp = ld4(Poff + (size_t)j * N + i0);
+#pragma unroll
+        for (int k = 0; k < 4; k++) w1[k] += cp.v[k] * (u1P[k] - u[k]);
+      }
+    }
+    V4<real> wn;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      wn.v[k] = w1[k];
+      a[1].add_prod(w1[k], u1P[k]);
+    }
+    st4(w_n + i0, wn);
+  }
+}
+
 // Jacobi-preconditioned CG in the single-reduction form of Chronopoulos and
 // Gear (1989) for  (-P) x = -(b - bmean)  (R7: the pressure system is singular
 // and b is projected to zero mean).  D = -diag(P) is the preconditioner.  On
@@ -780,6 +935,10 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     });
     if (!ok) return false;
   }
+  // four cells per thread where the layout allows it (cg_jacobi_sweep4)
+  const bool v4 = X.D.vec4 && !X.nbt && !X.fr && aligned16(rb[0]) && aligned16(rb[1]) && aligned16(wb[0]) &&
+                  aligned16(wb[1]) && aligned16(sb[0]) && aligned16(sb[1]) && aligned16(Pinv) && aligned16(Poff) &&
+                  aligned16(pdir) && aligned16(x);
   int cur = 0;
   while (cs.active && cs.it < maxit) {
     Acc<real> a[3];
@@ -794,7 +953,10 @@ __device__ bool cg_pressure(const Ctx<real, ND>& X, CgState& cs, double rtol, do
     real* s_n = sb[cur];
     real* r_n = rb[cur ^ 1];
     real* w_n = wb[cur ^ 1];
-    cg_jacobi_sweep<real, ND>(X, first, al, be, r_i, w_i, s_o, Pinv, Poff, pdir, x, s_n, r_n, w_n, a);
+    if (v4)
+      cg_jacobi_sweep4<real, ND>(X, first, al, be, r_i, w_i, s_o, Pinv, Poff, pdir, x, s_n, r_n, w_n, a);
+    else
+      cg_jacobi_sweep<real, ND>(X, first, al, be, r_i, w_i, s_o, Pinv, Poff, pdir, x, s_n, r_n, w_n, a);
     bool ok;
     if constexpr (sizeof(real) == 4)
       ok = reduce_sync<real, 3, true>(X.g, a, [&](const double* q) {

@@ -90,6 +90,10 @@ class Domain:
         """True when that y-line CG runs with one group barrier per iteration."""
         return int(self.lib.piso_pressure_line_fused(self.h)) == 1
 
+    def uses_cg_vec4(self) -> bool:
+        """True when the next step's Jacobi CG sweeps four cells per thread."""
+        return int(self.lib.piso_pressure_cg_vec4(self.h)) == 1
+
     @classmethod
     def from_case(cls, case, precision="fp64", options=None, **kw) -> "Domain":
         """Build from an object with ndim/blocks/connections/dirichlet/outflow
