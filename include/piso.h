@@ -99,9 +99,12 @@ typedef struct {
                             PISO_PRECOND_JACOBI; PISO_PRECOND_LINE: the block diagonal of -P made of
                             its y-lines inside each block, solved exactly (Thomas factors formed once
                             per step; see p_line_split for how its CG iteration synchronises).
-                            In batches (piso_batch_*) each member keeps the choice its own
-                            options resolved to (the line form needs launch-wide staging for two
-                            of the longest such lines; without room every member uses Jacobi). */
+                            In batches (piso_batch_*) a member runs the line form only when its
+                            options say PISO_PRECOND_LINE (a choice PISO_PRECOND_AUTO made from
+                            the grid is not carried over: in a batch the line form needs
+                            launch-wide staging for two of the longest such lines and runs split,
+                            measured slower than Jacobi there); without room every member uses
+                            Jacobi. */
   int32_t adv_precond;   /* preconditioner of the advection-diffusion BiCGStab (App. A.5: incomplete
                             LU, for grids with strongly varying cell sizes, enabled per case, and
                             optionally only after the plain solve failed):
