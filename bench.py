@@ -34,11 +34,12 @@ def cg_words_per_cell(d: int, it_p: int, line: bool, fused: bool = False) -> flo
     s, r, w written.  y-line, split form (two phases): phase A reads u, w, r, x,
     p, s and the three line factors and writes p, s, x, r, u; phase B reads u and
     the P faces and writes w.  y-line, fused form (one phase; u, p, x, the line
-    factors and the P faces stay in shared memory for the whole solve): r, w, s
-    read, r, w, s, x written; its start reads x, b, the P faces and the three
-    factors and writes r0, then reads r0 and writes w0."""
+    factors, the P faces, and r and s of the own and halo lines stay in shared
+    memory for the whole solve): w written by its owner and read back by the
+    halo lines; its start reads x, b, the P faces and the three factors and
+    writes r0, then reads r0 and writes w0; x is written every iteration."""
     if line and fused:
-        return (d + 7) + 2 + it_p * 7
+        return (d + 7) + 2 + it_p * 3
     if line:
         return (d + 7) + (d + 2) + it_p * (14 + d + 2)
     return (d + 4) + (d + 3) + it_p * (d + 11)

@@ -501,7 +501,16 @@ size_t launch_smem(const piso_domain* d, int ncta, SolverOpts* o) {
   // the fused CG's arrays alias the staging arrays (each fused solve re-fills them)
   if (d->lf_ready && d->lf_ncta == ncta && !d->opts.p_line_split) {
     const size_t st2 = std::max(stage, (size_t)d->lf_bytes);
-    if (nbt + st2 + ints + (ilu ? 16 + ilu : 0) <= NBT_MAX_BYTES) {
+    bool fit = nbt + st2 + ints + (ilu ? 16 + ilu : 0) <= NBT_MAX_BYTES;
+    if (!fit && !ilu_b && st2 + ints <= NBT_MAX_BYTES) {
+      // the fused form saves a group barrier per CG iteration, which is worth
+      // more than the neighbour table (the other phases then locate their
+      // cells arithmetically): FP64 on 64x48x32 with 128 CTAs needs this
+      nbt = 0;
+      o->nbt_cap = 0;
+      fit = true;
+    }
+    if (fit) {
       stage = st2;
       o->lf_off = d->lf_off;
       o->lf_nown = d->lf_nown;
@@ -751,7 +760,7 @@ static piso_status build_linefuse_nd(piso_domain* d) {
       Lo.slot_cap = std::max(Lo.slot_cap, (n_loc | 1) * lmax);
       Lo.max_loc = std::max(Lo.max_loc, n_loc);
     }
-    Lo.bytes = ((e * (5 * (size_t)Lo.slot_cap + (3 + NS) * (size_t)Lo.own_cap) + 4 * (size_t)Lo.slot_cap +
+    Lo.bytes = ((e * (6 * (size_t)Lo.slot_cap + (3 + NS) * (size_t)Lo.own_cap) + 4 * (size_t)Lo.slot_cap +
                  2 * NS * (size_t)Lo.own_cap) + 15) & ~size_t(15);
   };
   Layout best, cur;

@@ -245,8 +245,8 @@ struct LinePre {
   const int32_t* fl;
   const int16_t* fnb;
   int32_t n_own, n_loc, own_cap, slot_cap;
-  real *fA, *fC, *fM, *fB, *fR;   // [slot_cap]: fa, fc, fm, line right-hand side / solution, r
-  real *fU, *fP, *fX, *fPf;       // [own_cap]: u, p, x of the own cells; [2 ND][own_cap] face coefficients
+  real *fA, *fC, *fM, *fB, *fR, *fS;   // [slot_cap]: fa, fc, fm, line right-hand side / solution, r, s
+  real *fP, *fX, *fW, *fPf;       // [own_cap]: p, x, w of the own cells; [2 ND][own_cap] face coefficients
   int32_t* fI;                    // [slot_cap] cell of each slot, -1 past the end of its line
   int16_t* fNb;                   // [2 ND][own_cap] neighbour slots in shared memory
 };

@@ -71,10 +71,11 @@ __device__ __forceinline__ LinePre<real> line_setup(const DomStatic& D, const Gr
     L.fM = sr + 2 * sc;
     L.fB = sr + 3 * sc;
     L.fR = sr + 4 * sc;
-    L.fU = sr + 5 * sc;
-    L.fP = L.fU + oc;
+    L.fS = sr + 5 * sc;
+    L.fP = sr + 6 * sc;
     L.fX = L.fP + oc;
-    L.fPf = L.fX + oc;
+    L.fW = L.fX + oc;
+    L.fPf = L.fW + oc;
     L.fI = reinterpret_cast<int32_t*>(L.fPf + 2 * ND * oc);
     L.fNb = reinterpret_cast<int16_t*>(L.fI + sc);
   }
@@ -511,18 +512,23 @@ __device__ __forceinline__ void line_grid(int32_t n, int32_t total, F&& f) {
 // in shared memory (the host builds the plan: own lines, halo lines and the
 // shared slot of every neighbour of every own cell).  Same recurrences as
 // cg_pressure_line; what moves is where u = M^-1 r comes from: each CTA
-// updates s and r on its halo lines too, from the previous iteration's w, s
-// and r (ping-pong buffers that their owners wrote before the last barrier),
-// and solves those lines itself, so the u of every neighbour of an own cell
-// is in shared memory and w = A' u needs no barrier:
+// updates s and r on its halo lines too and solves those lines itself, so the
+// u of every neighbour of an own cell is in shared memory and w = A' u needs
+// no barrier:
 //   per iteration, on own and halo lines: s = w + beta s, r -= alpha s,
 //   u = M^-1 r; on own cells: p = u_prev + beta p, x += alpha p, w = A' u;
 //   one group reduction of gamma = (r, u), delta = (w, u), ||r||^2.
-// Own cells keep u, p, x and their face coefficients in shared memory; r, s
-// and w go to global memory each iteration (the neighbours read them), x too
-// (so it is complete when the solve returns).  Cell y of local line l sits at
-// slot y * P + l (P = n_loc | 1; fI holds its cell index, -1 past the line's
-// end); own cell k = y * n_own + l.
+// r and s of every local line stay in shared memory for the whole solve: a
+// halo line's copy starts from the owner's r0 and then takes the owner's
+// recurrence step for step (the same code, the same w, alpha and beta), so it
+// stays bit-identical to the owner's without being read back.  Only w
+// crosses CTAs: the owners write it (ping-pong buffers, written before the
+// barrier that precedes its reading), and the halo lines read it once per
+// iteration.  Own cells keep p, x, w and their face coefficients in shared
+// memory; x also goes to global memory every iteration (so it is complete at
+// every barrier, the solve's last one included).  Cell y of local line
+// l sits at slot y * P + l (P = n_loc | 1; fI holds its cell index, -1 past
+// the line's end); own cell k = y * n_own + l.
 template <typename real, int ND>
 __device__ bool cg_pressure_fused(const Ctx<real, ND>& X, CgState& cs, double rtol, double atol, int maxit,
                                   const real* Poff, const real* b, double bmean, real* x, real* const (&rb)[2],
@@ -538,9 +544,10 @@ __device__ bool cg_pressure_fused(const Ctx<real, ND>& X, CgState& cs, double rt
   real* __restrict__ fM = L.fM;
   real* __restrict__ fB = L.fB;
   real* __restrict__ fR = L.fR;
-  real* __restrict__ fU = L.fU;
+  real* __restrict__ fS = L.fS;
   real* __restrict__ fP = L.fP;
   real* __restrict__ fX = L.fX;
+  real* __restrict__ fW = L.fW;
   real* __restrict__ fPf = L.fPf;
   int32_t* __restrict__ fI = L.fI;
   int16_t* __restrict__ fNb = L.fNb;
@@ -626,7 +633,7 @@ __device__ bool cg_pressure_fused(const Ctx<real, ND>& X, CgState& cs, double rt
         if (nk >= 0) ww += fPf[s * oc + k] * (uP - fB[nk]);
       }
       w_o[i] = ww;
-      fU[k] = uP;
+      fW[k] = ww;
       ru.add_prod(fR[sk], uP);
       wu.add_prod(ww, uP);
     });
@@ -645,56 +652,47 @@ __device__ bool cg_pressure_fused(const Ctx<real, ND>& X, CgState& cs, double rt
     c3[2].zero();
     const real al = pick<real>(cs.alpha, cs.alpha_f), be = pick<real>(cs.beta, cs.beta_f);
     const int first = cs.first;
-    const real* __restrict__ r_i = rb[cur];
     const real* __restrict__ w_i = wb[cur];
-    const real* __restrict__ s_i = sb[cur];
-    real* __restrict__ r_n = rb[cur ^ 1];
     real* __restrict__ w_n = wb[cur ^ 1];
-    real* __restrict__ s_n = sb[cur ^ 1];
     const Group& g = X.g;
     PISO_STAMP(g.epoch, 4);
     // s = w + beta s, r -= alpha s and the line right-hand sides on every local
-    // line; p and x on the own cells.  Two slots per pass, all their loads
-    // issued before the first store.
-    auto stage = [&](int32_t sk, int32_t q, int32_t l, int32_t i, real wO, real rO, real sO) {
-      const real sv = first ? wO : wO + be * sO;
-      const real rr = rO - al * sv;
-      fB[sk] = fM[sk] * rr;
-      fR[sk] = rr;
-      if (l < no) {
+    // line (r and s from shared memory; w from the own cells' shared copy or,
+    // on halo lines, from its owner's global row); p and x on the own cells.
+    // Four slots per pass, all their global loads issued before the first use.
+    auto stage = [&](int32_t sk, int32_t q, int32_t l, int32_t i, real wO) {
+      const real sv = first ? wO : wO + be * fS[sk];
+      const real rr = fR[sk] - al * sv;
+      if (l < no) {      // the own slot still holds u of the last line solve
         const int32_t ko = q * no + l;
-        const real p = first ? fU[ko] : fU[ko] + be * fP[ko];
+        const real p = first ? fB[sk] : fB[sk] + be * fP[ko];
         const real xn = fX[ko] + al * p;
         fP[ko] = p;
         fX[ko] = xn;
-        s_n[i] = sv;
-        r_n[i] = rr;
-        x[i] = xn;
+        x[i] = xn;      // complete at every barrier: the caller reads x at the neighbours right after the solve
         c3[2].add_prod(rr, rr);
       }
+      fS[sk] = sv;
+      fR[sk] = rr;
+      fB[sk] = fM[sk] * rr;
     };
     {
       GridWalk gw(nl);
-      for (int32_t k = threadIdx.x; k < nslot; k += 2 * blockDim.x) {
-        const int32_t q0 = gw.q, l0 = gw.l;
-        gw.next();
-        const int32_t q1 = gw.q, l1 = gw.l;
-        gw.next();
-        const int32_t s0 = q0 * P + l0, s1 = q1 * P + l1;
-        const int32_t i0 = fI[s0], i1 = k + (int32_t)blockDim.x < nslot ? fI[s1] : -1;
-        real w0 = 0, r0 = 0, z0 = 0, w1 = 0, r1 = 0, z1 = 0;
-        if (i0 >= 0) {
-          w0 = w_i[i0];
-          r0 = r_i[i0];
-          if (!first) z0 = s_i[i0];
+      for (int32_t k = threadIdx.x; k < nslot; k += 4 * (int32_t)blockDim.x) {
+        int32_t qq[4], ll[4], ii[4];
+        real ww[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          qq[j] = gw.q;
+          ll[j] = gw.l;
+          gw.next();
+          ii[j] = k + j * (int32_t)blockDim.x < nslot ? fI[qq[j] * P + ll[j]] : -1;
+          ww[j] = 0;
+          if (ii[j] >= 0) ww[j] = ll[j] < no ? fW[qq[j] * no + ll[j]] : w_i[ii[j]];
         }
-        if (i1 >= 0) {
-          w1 = w_i[i1];
-          r1 = r_i[i1];
-          if (!first) z1 = s_i[i1];
-        }
-        if (i0 >= 0) stage(s0, q0, l0, i0, w0, r0, z0);
-        if (i1 >= 0) stage(s1, q1, l1, i1, w1, r1, z1);
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+          if (ii[j] >= 0) stage(qq[j] * P + ll[j], qq[j], ll[j], ii[j], ww[j]);
       }
     }
     PISO_TRACE_SYNC();

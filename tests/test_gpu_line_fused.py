@@ -73,9 +73,11 @@ def test_full_size_channel_fused():
     counts."""
     c = W.channel3d()
     uo, po, _ = oracle_step(O.mesh_from_case(c), c, c.u0, c.p0, c.S)
-    _, (ug, pg, st) = _forward(c, 0)
+    # 128 CTAs of 16 lines (the autotuned shape; in FP64 its fused arrays leave
+    # no room for the shared neighbour table, which is then dropped)
+    _, (ug, pg, st) = _forward(c, 0, ctas=128)
     assert rel_err(ug, uo) <= FP64_REL and rel_err(pg, po) <= 10 * FP64_REL
-    _, (u2, p2, s2) = _forward(c, 1)
+    _, (u2, p2, s2) = _forward(c, 1, ctas=128)
     for k in range(2):
         assert abs(st["p_iters"][k] - s2["p_iters"][k]) <= 1, (st["p_iters"], s2["p_iters"])
     _, (u3, p3, s3) = _forward(c, 0, "fp32", block_threads=768, ctas=128, adv_rtol=1e-6, p_rtol=1e-6)
