@@ -114,6 +114,29 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Four consecutive cells of one [comp][N] array as one aligned vector access
+// (16 bytes in FP32, two 16-byte halves in FP64).
+template <typename real>
+struct V4 {
+  real v[4];
+};
+__device__ __forceinline__ V4<float> ld4(const float* __restrict__ p) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  return V4<float>{{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double* __restrict__ p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  return V4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* __restrict__ p, const V4<float>& t) {
+  *reinterpret_cast<float4*>(p) = make_float4(t.v[0], t.v[1], t.v[2], t.v[3]);
+}
+__device__ __forceinline__ void st4(double* __restrict__ p, const V4<double>& t) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(t.v[0], t.v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(t.v[2], t.v[3]);
+}
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 // Row coefficients of C (TR = false) or C^T (TR = true) for cell c:
 // (M y)_P = diag * y_P + sum_s cf[s] * y_{nb(P,s)} over inner faces.  The
 // entry of C^T on the face to F = nb(P,s) is F's own coefficient on the
@@ -547,6 +570,208 @@ __device__ __forceinline__ void bicg_sweep_c(const Ctx<real, ND>& X, const int (
   }
 }
 
+// Neighbours of a quad of four cells (cells 4m .. 4m+3 of a DomStatic::vec4
+// domain walked in interleaved passes): the cell left of the quad, the cell
+// right of it, and per y/z side the first cell of the neighbour quad (or a
+// negative boundary-face code: all four cells have a boundary face there).
+template <int ND>
+struct Quad {
+  int32_t i0, nL, nR;
+  int32_t nb[2 * ND];
+};
+template <int ND>
+__device__ __forceinline__ Quad<ND> quad_at(const DomStatic& D, int32_t i0) {
+  const Cell c = locate<ND>(D, i0);
+  const BlockInfo& B = D.blk[c.b];
+  Quad<ND> q;
+  q.i0 = i0;
+  q.nL = c.nb[0];
+  q.nR = (c.x + 4 < B.nx) ? i0 + 4 : side_nbr(D, B, i0 + 3, c.x + 3, c.y, c.z, 1);
+#pragma unroll
+  for (int s = 0; s < 2 * ND; s++) q.nb[s] = c.nb[s];
+  return q;
+}
+
+// Row coefficients of C (TR = false) or C^T (TR = true) for the four cells of
+// a quad, as c_row gives them cell by cell: cf[s].v[k] for side s of cell k
+// (zero across a boundary face), diag.v[k].
+template <typename real, int ND, bool TR>
+__device__ __forceinline__ void c_row4(const Quad<ND>& q, int32_t N, const real* __restrict__ Cdiag,
+                                       const real* __restrict__ Coff, V4<real>& diag, V4<real> (&cf)[2 * ND]) {
+  const int32_t i0 = q.i0;
+  diag = ld4(Cdiag + i0);
+  if (!TR) {
+#pragma unroll
+    for (int s = 0; s < 2 * ND; s++) cf[s] = ld4(Coff + (size_t)s * N + i0);
+    if (q.nL < 0) cf[0].v[0] = real(0);
+    if (q.nR < 0) cf[1].v[3] = real(0);
+#pragma unroll
+    for (int s = 2; s < 2 * ND; s++)
+      if (q.nb[s] < 0) cf[s] = V4<real>{{real(0), real(0), real(0), real(0)}};
+  } else {
+    // the neighbour's coefficient on its side facing the cell: -x side of
+    // cell k is the +x coefficient of cell k - 1, and so on
+    const V4<real> c1 = ld4(Coff + (size_t)1 * N + i0), c0 = ld4(Coff + i0);
+    cf[0] = V4<real>{{q.nL >= 0 ? Coff[(size_t)1 * N + q.nL] : real(0), c1.v[0], c1.v[1], c1.v[2]}};
+    cf[1] = V4<real>{{c0.v[1], c0.v[2], c0.v[3], q.nR >= 0 ? Coff[q.nR] : real(0)}};
+#pragma unroll
+    for (int s = 2; s < 2 * ND; s++) {
+      const int32_t Q = q.nb[s];
+      cf[s] = Q >= 0 ? ld4(Coff + (size_t)(s ^ 1) * N + Q) : V4<real>{{real(0), real(0), real(0), real(0)}};
+    }
+  }
+}
+
+// (M y) on a quad with y formed on the fly by yv(Q) (one cell) and yq(Q0, out)
+// (a neighbour quad): diag y_P first, then the sides in order, as the one-cell
+// sweeps sum them.
+template <typename real, int ND, typename F1, typename F4>
+__device__ __forceinline__ void quad_apply(const Quad<ND>& q, const V4<real>& diag, const V4<real> (&cf)[2 * ND],
+                                           const real (&yP)[4], F1&& yv, F4&& yq, real (&out)[4]) {
+  const real yL = q.nL >= 0 ? yv(q.nL) : real(0), yR = q.nR >= 0 ? yv(q.nR) : real(0);
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    real v = diag.v[k] * yP[k];
+    v += cf[0].v[k] * (k > 0 ? yP[k - 1] : yL);
+    v += cf[1].v[k] * (k < 3 ? yP[k + 1] : yR);
+    out[k] = v;
+  }
+#pragma unroll
+  for (int s = 2; s < 2 * ND; s++) {
+    if (q.nb[s] < 0) continue;
+    real y[4];
+    yq(q.nb[s], y);
+#pragma unroll
+    for (int k = 0; k < 4; k++) out[k] += cf[s].v[k] * y[k];
+  }
+}
+
+// The BiCGStab sweeps BA, BB, BC with four cells per thread (domains as
+// cg_jacobi_sweep4 takes them): every stream one aligned vector access per
+// quad, one neighbour lookup per quad; the per-cell arithmetic is that of
+// bicg_sweep_a/b/c, only the order of the dot sums changes.
+template <typename real, int ND, bool TR>
+__device__ __forceinline__ void bicg_sweep_a4(const Ctx<real, ND>& X, int first, const int (&act)[ND],
+                                              const real (&beta)[ND], const real (&om)[ND],
+                                              const real* __restrict__ Cdiag, const real* __restrict__ Coff,
+                                              const real* __restrict__ r, const real* __restrict__ pold,
+                                              const real* __restrict__ vold, const real* __restrict__ rhat,
+                                              real* __restrict__ pnew, real* __restrict__ vnew, Acc<real> (&a)[ND]) {
+  const int32_t N = X.N, nq = N >> 2, st = X.stride();
+#pragma unroll 1
+  for (int32_t qi = X.first(); qi < nq; qi += st) {
+    const Quad<ND> q = quad_at<ND>(X.D, qi << 2);
+    const int32_t i0 = q.i0;
+    V4<real> diag, cf[2 * ND];
+    c_row4<real, ND, TR>(q, N, Cdiag, Coff, diag, cf);
+#pragma unroll
+    for (int c = 0; c < ND; c++) {
+      if (!act[c]) continue;
+      const size_t o_ = (size_t)c * N;
+      const real be = beta[c], w = om[c];
+      auto pn = [&](int32_t Q) -> real {
+        const real rq = r[o_ + Q];
+        return first ? rq : rq + be * (pold[o_ + Q] - w * vold[o_ + Q]);
+      };
+      auto pq = [&](int32_t Q0, real (&y)[4]) {
+        const V4<real> rq = ld4(r + o_ + Q0);
+        V4<real> pq_{}, vq{};
+        if (!first) {
+          pq_ = ld4(pold + o_ + Q0);
+          vq = ld4(vold + o_ + Q0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) y[k] = first ? rq.v[k] : rq.v[k] + be * (pq_.v[k] - w * vq.v[k]);
+      };
+      real pP[4], v[4];
+      pq(i0, pP);
+      quad_apply<real, ND>(q, diag, cf, pP, pn, pq, v);
+      st4(pnew + o_ + i0, V4<real>{{pP[0], pP[1], pP[2], pP[3]}});
+      st4(vnew + o_ + i0, V4<real>{{v[0], v[1], v[2], v[3]}});
+      const V4<real> rh = ld4(rhat + o_ + i0);
+#pragma unroll
+      for (int k = 0; k < 4; k++) a[c].add_prod(rh.v[k], v[k]);
+    }
+  }
+}
+
+template <typename real, int ND, bool TR>
+__device__ __forceinline__ void bicg_sweep_b4(const Ctx<real, ND>& X, const int (&act)[ND], const real (&al)[ND],
+                                              const real* __restrict__ Cdiag, const real* __restrict__ Coff,
+                                              const real* __restrict__ r, const real* __restrict__ vnew,
+                                              real* __restrict__ t, Acc<real> (&a)[3 * ND]) {
+  const int32_t N = X.N, nq = N >> 2, st = X.stride();
+#pragma unroll 1
+  for (int32_t qi = X.first(); qi < nq; qi += st) {
+    const Quad<ND> q = quad_at<ND>(X.D, qi << 2);
+    const int32_t i0 = q.i0;
+    V4<real> diag, cf[2 * ND];
+    c_row4<real, ND, TR>(q, N, Cdiag, Coff, diag, cf);
+#pragma unroll
+    for (int c = 0; c < ND; c++) {
+      if (!act[c]) continue;
+      const size_t o_ = (size_t)c * N;
+      const real alc = al[c];
+      auto sv = [&](int32_t Q) -> real { return r[o_ + Q] - alc * vnew[o_ + Q]; };
+      auto sq = [&](int32_t Q0, real (&y)[4]) {
+        const V4<real> rq = ld4(r + o_ + Q0), vq = ld4(vnew + o_ + Q0);
+#pragma unroll
+        for (int k = 0; k < 4; k++) y[k] = rq.v[k] - alc * vq.v[k];
+      };
+      real sP[4], tt[4];
+      sq(i0, sP);
+      quad_apply<real, ND>(q, diag, cf, sP, sv, sq, tt);
+      st4(t + o_ + i0, V4<real>{{tt[0], tt[1], tt[2], tt[3]}});
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        a[c].add_prod(tt[k], sP[k]);
+        a[ND + c].add_prod(tt[k], tt[k]);
+        a[2 * ND + c].add_prod(sP[k], sP[k]);
+      }
+    }
+  }
+}
+
+template <typename real, int ND>
+__device__ __forceinline__ void bicg_sweep_c4(const Ctx<real, ND>& X, const int (&act)[ND], const int (&sc)[ND],
+                                              const real (&al)[ND], const real (&om)[ND],
+                                              const real* __restrict__ pnew, const real* __restrict__ vnew,
+                                              const real* __restrict__ t, const real* __restrict__ rhat,
+                                              real* __restrict__ x, real* __restrict__ r, Acc<real> (&a)[2 * ND]) {
+  const int32_t N = X.N, nq = N >> 2, st = X.stride();
+#pragma unroll 1
+  for (int32_t qi = X.first(); qi < nq; qi += st) {
+    const int32_t i0 = qi << 2;
+#pragma unroll
+    for (int c = 0; c < ND; c++) {
+      if (!act[c]) continue;
+      const size_t o_ = (size_t)c * N + i0;
+      const V4<real> rq = ld4(r + o_), vq = ld4(vnew + o_), pq = ld4(pnew + o_), xq = ld4(x + o_);
+      V4<real> xn, rn;
+      if (sc[c]) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) xn.v[k] = xq.v[k] + al[c] * pq.v[k];
+        st4(x + o_, xn);
+        continue;
+      }
+      const V4<real> tq = ld4(t + o_), rh = ld4(rhat + o_);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const real sP = rq.v[k] - al[c] * vq.v[k];
+        xn.v[k] = xq.v[k] + (al[c] * pq.v[k] + om[c] * sP);
+        rn.v[k] = sP - om[c] * tq.v[k];
+      }
+      st4(x + o_, xn);
+      st4(r + o_, rn);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        a[c].add_prod(rh.v[k], rn.v[k]);
+        a[ND + c].add_prod(rn.v[k], rn.v[k]);
+      }
+    }
+  }
+}
+
 // BiCGStab (van der Vorst 1992) on M x = b, M = C or C^T, for the ND velocity
 // components sharing M, each with its own scalars; converged components
 // freeze.  On entry x = x0, r = b - M x0, rhat = r and bs came from bicg_start.
@@ -554,7 +779,10 @@ __device__ __forceinline__ void bicg_sweep_c(const Ctx<real, ND>& X, const int (
 template <typename real, int ND, bool TR>
 __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const real* Cdiag, const real* Coff,
                          real* x, real* r, const real* rhat, real* const (&pv)[2], real* const (&vv)[2], real* t) {
-  const int32_t N = X.N;
+  // four cells per thread where the layout allows it (as cg_jacobi_sweep4)
+  const bool v4 = X.D.vec4 && !X.nbt && !X.fr && aligned16(Cdiag) && aligned16(Coff) && aligned16(x) &&
+                  aligned16(r) && aligned16(rhat) && aligned16(pv[0]) && aligned16(pv[1]) && aligned16(vv[0]) &&
+                  aligned16(vv[1]) && aligned16(t);
   int cur = 0;
   while (bs.any && bs.it < maxit) {
     // BA: p = r + beta (p - omega v), v = M p
@@ -574,7 +802,10 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       const real* vold = vv[cur ^ 1];
       real* pnew = pv[cur];
       real* vnew = vv[cur];
-      bicg_sweep_a<real, ND, TR>(X, first, act, beta, om, Cdiag, Coff, r, pold, vold, rhat, pnew, vnew, a);
+      if (v4)
+        bicg_sweep_a4<real, ND, TR>(X, first, act, beta, om, Cdiag, Coff, r, pold, vold, rhat, pnew, vnew, a);
+      else
+        bicg_sweep_a<real, ND, TR>(X, first, act, beta, om, Cdiag, Coff, r, pold, vold, rhat, pnew, vnew, a);
       const bool ok = reduce_sync<real, ND>(X.g, a, [&](const double* q) { bicg_update_alpha<ND>(bs, q); });
       if (!ok) return false;
     }
@@ -590,7 +821,10 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
       }
 #pragma unroll
       for (int k = 0; k < 3 * ND; k++) a[k].zero();
-      bicg_sweep_b<real, ND, TR>(X, act, al, Cdiag, Coff, r, vv[cur], t, a);
+      if (v4)
+        bicg_sweep_b4<real, ND, TR>(X, act, al, Cdiag, Coff, r, vv[cur], t, a);
+      else
+        bicg_sweep_b<real, ND, TR>(X, act, al, Cdiag, Coff, r, vv[cur], t, a);
       const bool ok = reduce_sync<real, 3 * ND>(X.g, a, [&](const double* q) { bicg_update_omega<ND>(bs, q); });
       if (!ok) return false;
     }
@@ -608,7 +842,10 @@ __device__ bool bicgstab(const Ctx<real, ND>& X, BiState& bs, int maxit, const r
         a[k].zero();
         a[ND + k].zero();
       }
-      bicg_sweep_c<real, ND>(X, act, sc, al, om, pv[cur], vv[cur], t, rhat, x, r, a);
+      if (v4)
+        bicg_sweep_c4<real, ND>(X, act, sc, al, om, pv[cur], vv[cur], t, rhat, x, r, a);
+      else
+        bicg_sweep_c<real, ND>(X, act, sc, al, om, pv[cur], vv[cur], t, rhat, x, r, a);
       const bool ok = reduce_sync<real, 2 * ND>(X.g, a, [&](const double* q) { bicg_update_rho<ND>(bs, q); });
       if (!ok) return false;
     }
@@ -683,28 +920,6 @@ __device__ __forceinline__ void cg_jacobi_sweep(const Ctx<real, ND>& X, int firs
   }
 }
 
-// Four consecutive cells of one [comp][N] array as one aligned vector access
-// (16 bytes in FP32, two 16-byte halves in FP64).
-template <typename real>
-struct V4 {
-  real v[4];
-};
-__device__ __forceinline__ V4<float> ld4(const float* __restrict__ p) {
-  const float4 t = *reinterpret_cast<const float4*>(p);
-  return V4<float>{{t.x, t.y, t.z, t.w}};
-}
-__device__ __forceinline__ V4<double> ld4(const double* __restrict__ p) {
-  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
-  return V4<double>{{a.x, a.y, b.x, b.y}};
-}
-__device__ __forceinline__ void st4(float* __restrict__ p, const V4<float>& t) {
-  *reinterpret_cast<float4*>(p) = make_float4(t.v[0], t.v[1], t.v[2], t.v[3]);
-}
-__device__ __forceinline__ void st4(double* __restrict__ p, const V4<double>& t) {
-  reinterpret_cast<double2*>(p)[0] = make_double2(t.v[0], t.v[1]);
-  reinterpret_cast<double2*>(p)[1] = make_double2(t.v[2], t.v[3]);
-}
-__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 // The sweep of cg_jacobi_sweep with four consecutive cells per thread (domains
 // walked in interleaved passes whose blocks all have nx a multiple of 4 and

@@ -279,15 +279,16 @@ def test_fp32_refined_adjoint():
 
 def test_fp32_pressure_cg_stall_is_finished_by_refinement():
     """An FP32 pressure CG asked for more than FP32 vectors can deliver
-    (rtol 1e-9) stalls; the step then finishes the solve with FP64-residual
+    (rtol 1e-11; at 1e-9 whether it stalls depends on the rounding of the
+    build) stalls; the step then finishes the solve with FP64-residual
     refinement rounds to the same tolerance instead of running to the
     iteration limit."""
     c = W.cavity2d(32)
-    dom = gpu_domain(c, "fp32", adv_rtol=1e-6, p_rtol=1e-9)
+    dom = gpu_domain(c, "fp32", adv_rtol=1e-6, p_rtol=1e-11)
     u1, p1, st = gpu_step(dom, c, c.u0, c.p0)
     assert st["status"] == "PISO_OK", st
     assert all(r >= 1 for r in st["p_rounds"][:2]), st
-    assert all(res <= 1e-9 * rhs * 1.0000001 for res, rhs in zip(st["p_resid"][:2], st["p_rhs_norm"][:2])), st
+    assert all(res <= 1e-11 * rhs * 1.0000001 for res, rhs in zip(st["p_resid"][:2], st["p_rhs_norm"][:2])), st
     m = O.mesh_from_case(c)
     u_o, p_o, _ = O.piso_step(m, c.u0, c.p0, c.dt, c.nu)
     assert rel_err(u1, u_o) <= FP32_REL

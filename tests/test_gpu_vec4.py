@@ -1,10 +1,11 @@
-"""The Jacobi-preconditioned pressure CG sweeping four consecutive cells per
-thread (vector loads and stores; domains whose CTA ranges are walked in
-interleaved passes and whose blocks all have nx a multiple of 4) against the
-FP64 oracle and against the one-cell-per-thread sweep, through the C ABI.  The
-form changes how the pressure systems of App. A.1 (Eq. pressure) are swept,
-not the recurrences, so the solves must reproduce the oracle's and agree with
-the scalar sweep up to the summation order of the dot products."""
+"""The Jacobi-preconditioned pressure CG and the predictor's BiCGStab sweeping
+four consecutive cells per thread (vector loads and stores; domains whose CTA
+ranges are walked in interleaved passes and whose blocks all have nx a
+multiple of 4) against the FP64 oracle and against the one-cell-per-thread
+sweeps, through the C ABI.  The form changes how the systems of App. A.1
+(Eqs. implEuler1 and pressure) and their transposes in the adjoint are
+swept, not the recurrences, so the solves must reproduce the oracle's and
+agree with the scalar sweeps up to the summation order of the dot products."""
 import numpy as np
 import pytest
 
@@ -69,6 +70,8 @@ def test_vec4_matches_scalar_sweep(name):
     assert rel_err(uv, us) <= 1e-11 and rel_err(pv, ps) <= 1e-9, (rel_err(uv, us), rel_err(pv, ps))
     for k in range(2):
         assert abs(sv["p_iters"][k] - ss["p_iters"][k]) <= 1, (sv["p_iters"], ss["p_iters"])
+    for k in range(c.ndim):
+        assert abs(sv["adv_iters"][k] - ss["adv_iters"][k]) <= 1, (sv["adv_iters"], ss["adv_iters"])
 
 
 def test_vec4_fp32_after_n_steps():
