@@ -290,7 +290,7 @@ class Arm:
         if threads == 0:
             self.shape = dom.autotune(self.u0, self.p0, case.dt, case.nu, self.S)
         else:
-            self.shape = (threads, None, None)
+            self.shape = (threads, opts_kw.get("ctas") or None, None)
         pc = dom.get_options().p_precond
         if pc == capi.PISO_PRECOND_AUTO:
             pc = capi.PISO_PRECOND_LINE if dom.uses_line_precond() else capi.PISO_PRECOND_JACOBI
@@ -630,6 +630,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="skip the turbulence-statistics timing")
     ap.add_argument("--threads", type=int, default=0, help="CTA width; 0 = autotune")
+    ap.add_argument("--ctas", type=int, default=0, help="CTA count with --threads (0: one per SM)")
     ap.add_argument("--refine", type=float, default=0.0, help="FP32: FP64-refined pressure tolerance")
     ap.add_argument("--precond", default="auto", choices=["auto", "jacobi", "line"],
                     help="pressure CG preconditioner (auto: the autotuner times both on anisotropic grids)")
@@ -694,7 +695,7 @@ def main():
     pc_code = {"auto": capi.PISO_PRECOND_AUTO, "jacobi": capi.PISO_PRECOND_JACOBI, "line": capi.PISO_PRECOND_LINE}
     opts_kw = dict(adv_rtol=rtol, p_rtol=rtol, p_refine_rtol=args.refine, p_precond=pc_code[args.precond],
                    adv_precond=ADV_PRECOND[args.adv_precond], n_nonortho=args.nonortho if sheared else 0,
-                   p_line_split=1 if args.line_split else 0)
+                   p_line_split=1 if args.line_split else 0, ctas=args.ctas if args.threads else 0)
     d, N = case.ndim, case.ncells
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     with_adj = args.mode == "fwdadj"
