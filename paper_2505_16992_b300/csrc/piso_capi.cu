@@ -444,9 +444,9 @@ SolverOpts solver_opts(const piso_options& o) {
 // Dynamic shared memory of a step launch (neighbour table, line staging, ILU
 // sweep area), at most this much.  Every step kernel's static shared memory
 // plus this must stay within the 227 KB a CTA may opt into (the largest static
-// area, the FP32 non-orthogonal adjoint's, is ~68 KB; tests/test_capi_symbols.py
+// area, the FP32 non-orthogonal adjoint's, is ~54 KB; tests/test_capi_symbols.py
 // checks the sum against the build's resource report).
-constexpr size_t NBT_MAX_BYTES = 156 * 1024;
+constexpr size_t NBT_MAX_BYTES = 168 * 1024;
 
 size_t nbt_bytes(int ndim, int64_t N, int ncta, int32_t* cap) {
   const int64_t per = (N + ncta - 1) / ncta;

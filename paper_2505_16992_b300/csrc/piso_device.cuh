@@ -472,11 +472,12 @@ constexpr int GATHER_UNROLL = 8;
 template <typename real, int NS, bool RAW = false, typename F>
 __device__ __forceinline__ bool reduce_sync(Group& g, Acc<real> (&a)[NS], F&& update) {
   // each warp folds its lanes down to KEEP partials per scalar (fewer shuffle
-  // levels in every warp; the rest is summed by one warp per scalar), as many
-  // as the shared buffer holds
+  // levels in every warp; the rest is summed by one warp per scalar), at most
+  // NSMAX values per warp; each instantiation holds its own shared arrays,
+  // sized for its NS (static shared memory of the step kernels 70 -> 53 KB)
   constexpr int KEEP = NS * 4 <= NSMAX ? 4 : (NS * 2 <= NSMAX ? 2 : 1);
-  __shared__ double s_w[MAXW * NSMAX];
-  __shared__ double s_tot[NSMAX];
+  __shared__ double s_w[MAXW * NS * KEEP];
+  __shared__ double s_tot[NS];
   __shared__ int s_ok;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll

@@ -73,8 +73,7 @@ def test_full_size_channel_fused():
     counts."""
     c = W.channel3d()
     uo, po, _ = oracle_step(O.mesh_from_case(c), c, c.u0, c.p0, c.S)
-    # 128 CTAs of 16 lines (the autotuned shape; in FP64 its fused arrays leave
-    # no room for the shared neighbour table, which is then dropped)
+    # 128 CTAs of 16 lines (the autotuned shape)
     _, (ug, pg, st) = _forward(c, 0, ctas=128)
     assert rel_err(ug, uo) <= FP64_REL and rel_err(pg, po) <= 10 * FP64_REL
     _, (u2, p2, s2) = _forward(c, 1, ctas=128)
