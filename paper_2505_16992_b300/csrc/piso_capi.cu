@@ -137,6 +137,7 @@ struct piso_batch {
   int32_t* d_cta_first = nullptr;
   size_t call_bytes = 0;       // bytes of one group's call record (the larger of forward and adjoint)
   int mode = 0;                // kernel instantiation: 0 plain, 2 when a member is non-orthogonal
+  std::vector<double> weights; // measured work per member (piso_batch_autotune), or empty: the estimate
   void* dev = nullptr;         // piso_batch_dev: device and pinned buffers of the batch launches
   std::string err;
 };
