@@ -384,12 +384,14 @@ piso_status piso_batch_step_adjoint(piso_batch* b, const void* const* du_out,
  * and the members' boundary values are restored) with CTAs of 512 and 768
  * threads, with all co-resident CTAs and with three quarters of them (each
  * layout apportioned by estimated work), keeps the fastest, then balances its
- * split by measured work: each member's forward step is timed alone on the
- * CTA count the layout gives it, the CTAs are re-apportioned in proportion to
- * time x CTAs, and the new split is kept while the batch's forward launch gets
- * faster (two rounds).  The result holds for the batch's later launches.
- * threads_out, ctas_out, ms_out (host, may be NULL) receive the shape and the
- * time of the kept layout.  Allocates trial outputs; synchronises the stream. */
+ * split by measured work: each member's forward and adjoint steps are timed
+ * alone on the CTA count the layout gives it, the CTAs are re-apportioned in
+ * proportion to time x CTAs, and the new split is kept while the batch's
+ * forward + adjoint launches get faster (two rounds).  The result holds for
+ * the batch's later launches.  threads_out, ctas_out, ms_out (host, may be
+ * NULL) receive the shape and the forward-launch time of the kept layout.
+ * Allocates trial outputs; synchronises the stream; the members' step records
+ * are left invalid (run a batch step before an adjoint). */
 piso_status piso_batch_autotune(piso_batch* b, const void* const* u_in, const void* const* p_in, const double* dt,
                                 const double* nu, const void* const* S, void* stream, int32_t* threads_out,
                                 int32_t* ctas_out, double* ms_out);
