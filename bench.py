@@ -545,12 +545,30 @@ def time_batch(prec, kw, steps, warmup, with_adj, flush, threads=0, clocks=False
     _, _, st_after = b.step(us, ps, dts, nus, Ss, u_out=uo, p_out=po)     # replayed steps still converge
     assert all(x["status"] == "PISO_OK" for x in st_after), "batch step failed after graph replays"
     cells = sum(c.ncells for c in cases)
-    return {"sim_steps_per_s": len(cases) * steps / tot, "ms_per_step": 1e3 * tot / steps,
-            "cell_updates_per_s": cells * steps / tot, "cells": cells, "members": len(cases),
-            "launch": {"threads": shape[0], "ctas": shape[1], "autotuned": not threads},
-            "p_iters_max": max(max(x["p_iters"][:2]) for x in st),
-            "p_iters_min": min(min(x["p_iters"][:2]) for x in st),
-            "p_rounds_max": max(max(x["p_rounds"][:2]) for x in st), "clocks": clk}
+    out = {"sim_steps_per_s": len(cases) * steps / tot, "ms_per_step": 1e3 * tot / steps,
+           "cell_updates_per_s": cells * steps / tot, "cells": cells, "members": len(cases),
+           "launch": {"threads": shape[0], "ctas": shape[1], "autotuned": not threads},
+           "p_iters_max": max(max(x["p_iters"][:2]) for x in st),
+           "p_iters_min": min(min(x["p_iters"][:2]) for x in st),
+           "p_rounds_max": max(max(x["p_rounds"][:2]) for x in st), "clocks": clk}
+    if with_adj:
+        # algorithmic bytes of one replayed step (every replay runs the same
+        # forward and adjoint from the same inputs): the words-per-cell models
+        # at each member's iteration counts, over the measured step time
+        ast = b.step_adjoint(gs, du_in=gdu, dp_in=gdp, dS=gdS)[4]
+        w = 4 if prec == "fp32" else 8
+        byts = 0.0
+        for c, f, a in zip(cases, st_after, ast):
+            d = c.ndim
+            byts += c.ncells * w * (fwd_words_per_cell(d, f["adv_iters"][:d], f["p_iters"][:2])
+                                    + adj_words_per_cell(d, a["adv_iters"][:d], a["p_iters"][:2]))
+        peak, peak_kind = measured_peaks()
+        achieved = byts / (tot / steps) / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "peak_kind": peak_kind, "alg_bytes_per_step": byts,
+                           "what": "forward + adjoint launches of one batch step, algorithmic bytes (the "
+                                   "words-per-cell models at each member's iteration counts) over the step time"}
+    return out
 
 
 def run_batch(args):
@@ -575,6 +593,8 @@ def run_batch(args):
             "cell_updates_per_s": r["cell_updates_per_s"], "p_iters_max": r["p_iters_max"],
             "p_iters_min": r["p_iters_min"], "gpu_launches": args.steps * (2 if with_adj else 1),
             "clocks": r["clocks"]}
+    if "roofline" in r:
+        line["roofline"] = r["roofline"]
     print(json.dumps(line))
     return 0
 
