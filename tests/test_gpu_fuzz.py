@@ -1,0 +1,163 @@
+"""Seeded random configurations against the FP64 oracle, through the C ABI:
+each seed draws a mesh family (cavities 2D/3D, channels 2D/3D, the
+backward-facing step, turned-block joints, the folded C-grid cut), its
+resolution (ragged, from a few cells per side), wall stretching and cell
+slant (App. A.2 cross terms, with 1 or 2 non-orthogonal corrector steps),
+a perturbed state and source, and a launch (CTA width and count, pressure
+preconditioner, BiCGStab preconditioner), then compares the forward step
+(Sec. 2.3, App. A.1) and the adjoint step (Sec. 2.4, App. A.4: gradients of
+u, S, nu, the boundary values, and p where the step depends on it) with the
+oracle.  Every fourth seed runs the FP32 mode."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import piso as OP
+from paper_2505_16992_b300 import capi
+from paper_2505_16992_b300 import workloads as W
+from paper_2505_16992_b300.solver import Batch
+from gpu_util import FP32_REL, FP64_REL, bval_faces, gpu_domain, host, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+ADJ_REL = 1e-8
+FP32_ADJ_REL = 2e-3
+# dL/dnu is one sum over the cells whose terms largely cancel (on a 150-cell
+# step, |dL/dnu| is ~60x smaller than the largest |dL/du|): the FP32 mode's
+# ~1e-4 relative error of the adjoint fields becomes ~5e-3 there, while the
+# oracle itself moves by only 3e-6 when its solves stop at rtol 1e-7.  The
+# FP64 cases check it at ADJ_REL.
+FP32_DNU_REL = 1e-2
+SEEDS = range(64)
+
+
+def _draw_case(rng):
+    kind = int(rng.integers(0, 9))
+    ri = lambda lo, hi: int(rng.integers(lo, hi + 1))
+    if kind == 0:
+        return W.cavity2d(ri(4, 40), stretch=float(rng.choice([0.0, 1.5])), lid_side=ri(0, 3))
+    if kind == 1:
+        return W.channel3d(ri(3, 24), ri(3, 20), ri(3, 16), gamma=float(rng.choice([1.0, 2.0])),
+                           shear=float(rng.choice([0.0, 0.3])), seed=ri(0, 99))
+    if kind == 2:
+        return W.channel2d(ri(3, 32), ri(3, 32), gamma=float(rng.choice([0.0, 1.5])), nu=0.05, dt=0.05)
+    if kind == 3:
+        return W.two_block_cavity2d(ri(3, 10), ri(3, 10), rot=ri(0, 3), shear=float(rng.choice([0.0, 0.3])))[0]
+    if kind == 4:
+        return W.cavity3d(ri(3, 10), periodic_z=bool(rng.integers(0, 2)), nz=ri(3, 10))
+    if kind == 5:
+        return W.taylor_green2d(ri(4, 33))
+    if kind == 6:
+        return W.two_block_channel3d(ri(3, 6), ri(3, 7), ri(3, 5), turned=bool(rng.integers(0, 2)),
+                                     shear=float(rng.choice([0.0, 0.3])))[0]
+    if kind == 7:
+        return W.slit_cgrid2d(2 * ri(3, 10), ri(3, 10))
+    half = ri(2, 6)
+    return W.bfs2d(n_in=(ri(2, 6), half), n_ch=ri(4, 16), n_out=ri(2, 8), half=half, nu=0.01)
+
+
+def _draw_launch(rng, ncells):
+    threads = int(rng.choice([64, 128, 256, 512, 768]))
+    ctas = int(rng.choice([1, 2, 3, 5, 8, 13]))
+    return dict(block_threads=threads, ctas=max(1, min(ctas, ncells // 16)),
+                p_precond=int(rng.choice([capi.PISO_PRECOND_AUTO, capi.PISO_PRECOND_JACOBI,
+                                          capi.PISO_PRECOND_LINE])),
+                adv_precond=int(rng.choice([capi.PISO_ADV_PRECOND_NONE, capi.PISO_ADV_PRECOND_ILU,
+                                            capi.PISO_ADV_PRECOND_ILU_ON_FAILURE])))
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_random_configuration_against_oracle(seed):
+    rng = np.random.default_rng(1000 + seed)
+    c = _draw_case(rng)
+    launch = _draw_launch(rng, c.ncells)
+    fp32 = seed % 4 == 3
+    m = O.mesh_from_case(c, allow_nonorthogonal=True)
+    n_no = int(rng.integers(1, 3)) if m.has_cross else 0
+    precision = "fp32" if fp32 else "fp64"
+    extra = dict(adv_rtol=1e-7, p_rtol=1e-7) if fp32 else dict(adv_rtol=1e-12, p_rtol=1e-12)
+    dom = gpu_domain(c, precision, n_nonortho=n_no, **launch, **extra)
+    d, N = c.ndim, c.ncells
+    u0 = c.u0 + 0.2 * rng.standard_normal((d, N))
+    p0 = c.p0 + rng.standard_normal(N)
+    S0 = (c.S if c.S is not None else 0.0) + 0.1 * rng.standard_normal((d, N))
+    what = (c.name, N, launch, precision, n_no)
+    u1, p1, st = dom.step(to_dev(dom, u0, d), to_dev(dom, p0), c.dt, c.nu, to_dev(dom, S0, d))
+    assert st["status"] == "PISO_OK", (what, st)
+    oo = OP.Options(n_nonortho=max(n_no, 1))
+    uo, po, tape = O.piso_step(m, u0, p0, c.dt, c.nu, S0, None, oo)
+    tol = FP32_REL if fp32 else FP64_REL
+    assert rel_err(host(u1), uo) <= tol, (what, rel_err(host(u1), uo))
+    assert rel_err(host(p1), po) <= 10 * tol, (what, rel_err(host(p1), po))
+    ubar, pbar = rng.standard_normal((d, N)), rng.standard_normal(N)
+    du, dp, dS, dnu, ast = dom.step_adjoint(to_dev(dom, ubar, d), to_dev(dom, pbar))
+    assert ast["status"] == "PISO_OK", (what, ast)
+    gu, gp, gS, gnu, gbv = O.piso_step_adjoint(m, tape, ubar, pbar, oo, want_bval=True)
+    errs = dict(u=rel_err(host(du), gu), S=rel_err(host(dS), gS), nu=abs(dnu - gnu) / max(abs(gnu), 1e-300))
+    if np.any(m.is_bface):
+        errs["bval"] = rel_err(dom.boundary_adjoint(), bval_faces(m, gbv))
+    if m.has_cross:
+        errs["p"] = rel_err(host(dp), gp)
+    else:
+        assert np.all(host(dp) == 0.0), what
+    atol = FP32_ADJ_REL if fp32 else ADJ_REL
+    for k, v in errs.items():
+        assert v <= (FP32_DNU_REL if fp32 and k == "nu" else atol), (what, k, errs)
+
+
+def _draw_member(rng, ndim):
+    while True:
+        c = _draw_case(rng)
+        if c.ndim == ndim:
+            return c
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_batch_against_oracle(seed):
+    """A batch of 2 to 6 random members of one dimension (uneven sizes, mesh
+    families, slants with their own n_nonortho and pressure preconditioners)
+    in one launch of random width and CTA count: every member's forward and
+    adjoint step equal the oracle's."""
+    rng = np.random.default_rng(5000 + seed)
+    ndim = 3 if seed % 3 == 2 else 2
+    k = int(rng.integers(2, 7))
+    cases = [_draw_member(rng, ndim) for _ in range(k)]
+    fp32 = seed % 4 == 3
+    precision = "fp32" if fp32 else "fp64"
+    rt = 1e-7 if fp32 else 1e-12
+    meshes = [O.mesh_from_case(c, allow_nonorthogonal=True) for c in cases]
+    n_no = [int(rng.integers(1, 3)) if m.has_cross else 0 for m in meshes]
+    doms = [gpu_domain(c, precision, n_nonortho=n, adv_rtol=rt, p_rtol=rt,
+                       p_precond=int(rng.choice([capi.PISO_PRECOND_AUTO, capi.PISO_PRECOND_JACOBI,
+                                                 capi.PISO_PRECOND_LINE])))
+            for c, n in zip(cases, n_no)]
+    threads = int(rng.choice([64, 128, 256, 512, 768]))
+    ctas = int(rng.choice([0, k, k + 3, 2 * k + 1]))
+    b = Batch(doms, capi.default_options(adv_rtol=rt, p_rtol=rt, block_threads=threads, ctas=ctas))
+    what = ([(c.name, c.ncells) for c in cases], n_no, threads, ctas, precision)
+    st0 = [(c.u0 + 0.2 * rng.standard_normal((ndim, c.ncells)), c.p0 + rng.standard_normal(c.ncells),
+            (c.S if c.S is not None else 0.0) + 0.1 * rng.standard_normal((ndim, c.ncells))) for c in cases]
+    uo, po, sts = b.step([to_dev(d, s[0], ndim) for d, s in zip(doms, st0)], [to_dev(d, s[1]) for d, s in zip(doms, st0)],
+                         [c.dt for c in cases], [c.nu for c in cases], [to_dev(d, s[2], ndim) for d, s in zip(doms, st0)])
+    assert all(s["status"] == "PISO_OK" for s in sts), (what, sts)
+    bars = [(rng.standard_normal((ndim, c.ncells)), rng.standard_normal(c.ncells)) for c in cases]
+    du, dp, dS, dnu, asts = b.step_adjoint([to_dev(d, g[0], ndim) for d, g in zip(doms, bars)],
+                                           [to_dev(d, g[1]) for d, g in zip(doms, bars)])
+    assert all(s["status"] == "PISO_OK" for s in asts), (what, asts)
+    tol = FP32_REL if fp32 else FP64_REL
+    atol = FP32_ADJ_REL if fp32 else ADJ_REL
+    ntol = FP32_DNU_REL if fp32 else ADJ_REL
+    for i, (c, m, d) in enumerate(zip(cases, meshes, doms)):
+        oo = OP.Options(n_nonortho=max(n_no[i], 1))
+        u1, p1, tape = O.piso_step(m, *st0[i][:2], c.dt, c.nu, st0[i][2], None, oo)
+        assert rel_err(host(uo[i]), u1) <= tol, (what, i, rel_err(host(uo[i]), u1))
+        assert rel_err(host(po[i]), p1) <= 10 * tol, (what, i, rel_err(host(po[i]), p1))
+        gu, gp, gS, gnu, gbv = O.piso_step_adjoint(m, tape, bars[i][0], bars[i][1], oo, want_bval=True)
+        errs = dict(u=rel_err(host(du[i]), gu), S=rel_err(host(dS[i]), gS),
+                    nu=abs(dnu[i] - gnu) / max(abs(gnu), 1e-300))
+        if np.any(m.is_bface):
+            errs["bval"] = rel_err(d.boundary_adjoint(), bval_faces(m, gbv))
+        if m.has_cross:
+            errs["p"] = rel_err(host(dp[i]), gp)
+        for key, v in errs.items():
+            assert v <= (ntol if key == "nu" else atol), (what, i, key, errs)
