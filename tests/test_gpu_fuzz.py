@@ -66,8 +66,7 @@ def _draw_launch(rng, ncells):
                                             capi.PISO_ADV_PRECOND_ILU_ON_FAILURE])))
 
 
-@pytest.mark.parametrize("seed", SEEDS)
-def test_random_configuration_against_oracle(seed):
+def _single(seed, refine32=0.0):
     rng = np.random.default_rng(1000 + seed)
     c = _draw_case(rng)
     launch = _draw_launch(rng, c.ncells)
@@ -75,7 +74,7 @@ def test_random_configuration_against_oracle(seed):
     m = O.mesh_from_case(c, allow_nonorthogonal=True)
     n_no = int(rng.integers(1, 3)) if m.has_cross else 0
     precision = "fp32" if fp32 else "fp64"
-    extra = dict(adv_rtol=1e-7, p_rtol=1e-7) if fp32 else dict(adv_rtol=1e-12, p_rtol=1e-12)
+    extra = dict(adv_rtol=1e-7, p_rtol=1e-7, p_refine_rtol=refine32) if fp32 else dict(adv_rtol=1e-12, p_rtol=1e-12)
     dom = gpu_domain(c, precision, n_nonortho=n_no, **launch, **extra)
     d, N = c.ndim, c.ncells
     u0 = c.u0 + 0.2 * rng.standard_normal((d, N))
@@ -112,12 +111,7 @@ def _draw_member(rng, ndim):
             return c
 
 
-@pytest.mark.parametrize("seed", range(24))
-def test_random_batch_against_oracle(seed):
-    """A batch of 2 to 6 random members of one dimension (uneven sizes, mesh
-    families, slants with their own n_nonortho and pressure preconditioners)
-    in one launch of random width and CTA count: every member's forward and
-    adjoint step equal the oracle's."""
+def _batch(seed, refine32=0.0):
     rng = np.random.default_rng(5000 + seed)
     ndim = 3 if seed % 3 == 2 else 2
     k = int(rng.integers(2, 7))
@@ -127,13 +121,14 @@ def test_random_batch_against_oracle(seed):
     rt = 1e-7 if fp32 else 1e-12
     meshes = [O.mesh_from_case(c, allow_nonorthogonal=True) for c in cases]
     n_no = [int(rng.integers(1, 3)) if m.has_cross else 0 for m in meshes]
-    doms = [gpu_domain(c, precision, n_nonortho=n, adv_rtol=rt, p_rtol=rt,
+    ref = dict(p_refine_rtol=refine32) if fp32 else {}
+    doms = [gpu_domain(c, precision, n_nonortho=n, adv_rtol=rt, p_rtol=rt, **ref,
                        p_precond=int(rng.choice([capi.PISO_PRECOND_AUTO, capi.PISO_PRECOND_JACOBI,
                                                  capi.PISO_PRECOND_LINE])))
             for c, n in zip(cases, n_no)]
     threads = int(rng.choice([64, 128, 256, 512, 768]))
     ctas = int(rng.choice([0, k, k + 3, 2 * k + 1]))
-    b = Batch(doms, capi.default_options(adv_rtol=rt, p_rtol=rt, block_threads=threads, ctas=ctas))
+    b = Batch(doms, capi.default_options(adv_rtol=rt, p_rtol=rt, block_threads=threads, ctas=ctas, **ref))
     what = ([(c.name, c.ncells) for c in cases], n_no, threads, ctas, precision)
     st0 = [(c.u0 + 0.2 * rng.standard_normal((ndim, c.ncells)), c.p0 + rng.standard_normal(c.ncells),
             (c.S if c.S is not None else 0.0) + 0.1 * rng.standard_normal((ndim, c.ncells))) for c in cases]
@@ -161,3 +156,31 @@ def test_random_batch_against_oracle(seed):
             errs["p"] = rel_err(host(dp[i]), gp)
         for key, v in errs.items():
             assert v <= (ntol if key == "nu" else atol), (what, i, key, errs)
+
+
+@pytest.mark.parametrize("seed", SEEDS)
+def test_random_configuration_against_oracle(seed):
+    _single(seed)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_batch_against_oracle(seed):
+    """A batch of 2 to 6 random members of one dimension (uneven sizes, mesh
+    families, slants with their own n_nonortho and pressure preconditioners)
+    in one launch of random width and CTA count: every member's forward and
+    adjoint step equal the oracle's."""
+    _batch(seed)
+
+
+# A wider sweep of the same generators, its FP32 seeds with the pressure
+# solves refined against an FP64 residual to 1e-10: on the ill-conditioned
+# members it draws (the slit C-grid's tip, stretched step cells) the plain
+# FP32 CG stops at an error above the FP32 bars, which the refinement removes.
+@pytest.mark.parametrize("seed", range(64, 464))
+def test_random_configuration_wide_sweep(seed):
+    _single(seed, refine32=1e-10)
+
+
+@pytest.mark.parametrize("seed", range(24, 184))
+def test_random_batch_wide_sweep(seed):
+    _batch(seed, refine32=1e-10)
